@@ -1,0 +1,459 @@
+/*
+ * ews_oracle.c -- plain FP64 CPU oracle of the 3D elastic velocity-stress
+ * staggered-grid finite-difference scheme (arXiv 2112.15071, Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this library.  It shares no code,
+ * header, table or helper with the CUDA path; the two meet only through the
+ * seeded input arrays.
+ *
+ * The oracle is written for a reader checking it against the paper by eye:
+ * one obvious loop per equation term, FP64 throughout, no blocking, fusion or
+ * reordering.  OpenMP only splits the outer loop over z-planes of a pointwise
+ * update (each point is computed exactly as in the serial loop).
+ *
+ * Passages followed (section / equation of the paper):
+ *   Eq. 1 (velocity equation), Eq. 2 and Eq. 3 (stress equation and the
+ *   symmetric stress tensor, isotropic stiffness from lambda, mu), Sec. 2.1.1
+ *   (staggered positions), Sec. 2.1.2 Eq. 4 (4th-order staggered difference),
+ *   Sec. 2.2 (in-place additive updates), Sec. 2.2.1 (medium by trilinear
+ *   interpolation at staggered points), Sec. 2.2.2 (out-of-range fetches),
+ *   Sec. 2.3 (velocity pass then stress pass each step), Sec. 2.4 (receivers
+ *   by trilinear interpolation of the staggered velocities), Sec. 2.5
+ *   (damping of outgoing waves at the edges).
+ *
+ * Readings where the paper is silent or garbled (each listed in the design
+ * notes):
+ *   R1  Eq. 4 lacks the 1/h factor; the derivative is divided by the axis
+ *       spacing.
+ *   R2  element [k][j][i] of each N-sized array holds its component at the
+ *       staggered position of Sec. 2.1.1 relative to cell (i, j, k).
+ *   R3  v lives at half steps, sigma at integer steps; the velocity pass runs
+ *       first and receivers sample v^{n+1/2}.
+ *   R4  medium at staggered points = linear interpolation at half offsets,
+ *       i.e. arithmetic means of 2 (rho) or 4 (mu) cells; rho is averaged and
+ *       then inverted; medium indices past the top edge clamp to the edge.
+ *   R5  wavefield values outside the grid are zero.
+ *   R6  sponge: G(d) = exp(-(alpha (W - d) / W)^2) for a cell d < W cells from
+ *       a face (per axis, product over axes), applied to every field after
+ *       its update, using the element's cell index.
+ *   R7  C-PML (not in the paper): Komatitsch & Martin convolutional PML with
+ *       kappa = 1, d = d0 q^2, alpha = pi f0 (1 - q), d0 = -3 vpmax ln(R) /
+ *       (2 W h); q from the cell index; psi = b psi + a D f; D f -> D f + psi.
+ *   R8  moment source: sigma_ij -= dt M_ij s_n / (dx dy dz), spread by the
+ *       transposed trilinear weights on the sigma_ij grid; force source:
+ *       v_i += dt b F_i s_n / (dx dy dz) on the v_i grid.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_C1 (9.0 / 8.0)   /* Eq. 4 inner weight */
+#define ORC_C2 (-1.0 / 24.0) /* Eq. 4 outer weight */
+
+enum { VX, VY, VZ, SXX, SYY, SZZ, SXY, SXZ, SYZ, NFIELD };
+enum { BND_NONE = 0, BND_SPONGE = 1, BND_CPML = 2 };
+
+/* Staggered offsets of each field (Sec. 2.1.1), in cells. */
+static const double OFF[NFIELD][3] = {
+    {0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5},          /* vx vy vz     */
+    {0, 0, 0},   {0, 0, 0},   {0, 0, 0},            /* sxx syy szz  */
+    {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};   /* sxy sxz syz  */
+
+typedef struct orc_sim {
+    long nx, ny, nz, n;
+    double h[3];
+    double *f[NFIELD];
+    /* effective medium at staggered points (Sec. 2.2.1, reading R4) */
+    double *bx, *by, *bz;            /* buoyancy 1/rho at vx, vy, vz points */
+    double *lam, *lp2m;              /* lambda, lambda + 2 mu at normal points */
+    double *mxy, *mxz, *myz;         /* mu at shear points */
+    double vpmax;
+    /* boundary */
+    int boundary, width;
+    double sponge_alpha, pml_R, pml_f0, pml_dt;
+    double *g[3];                    /* 1-D sponge profiles */
+    double *pa[3], *pb[3];           /* 1-D C-PML coefficients */
+    double *psi[18];                 /* C-PML memory variables (full size) */
+} orc_sim;
+
+static inline long IDX(const orc_sim *s, long i, long j, long k) {
+    return (k * s->ny + j) * s->nx + i;
+}
+
+/* Fetch with the zero exterior of reading R5. */
+static inline double fetch(const orc_sim *s, const double *f, long i, long j, long k) {
+    if (i < 0 || j < 0 || k < 0 || i >= s->nx || j >= s->ny || k >= s->nz)
+        return 0.0;
+    return f[IDX(s, i, j, k)];
+}
+
+/* Eq. 4 evaluated at a half-integer position (index + 1/2) along axis a:
+ * samples at index-1, index, index+1, index+2 (positions -3/2 .. +3/2). */
+static inline double d_plus(const orc_sim *s, const double *f, int a, long i, long j, long k) {
+    long di = (a == 0), dj = (a == 1), dk = (a == 2);
+    double fm1 = fetch(s, f, i - di, j - dj, k - dk);
+    double f0 = fetch(s, f, i, j, k);
+    double fp1 = fetch(s, f, i + di, j + dj, k + dk);
+    double fp2 = fetch(s, f, i + 2 * di, j + 2 * dj, k + 2 * dk);
+    return (ORC_C1 * (fp1 - f0) + ORC_C2 * (fp2 - fm1)) / s->h[a];
+}
+
+/* Eq. 4 evaluated at an integer position along axis a, for a field that is
+ * staggered by +1/2 along a: samples at index-2 .. index+1. */
+static inline double d_minus(const orc_sim *s, const double *f, int a, long i, long j, long k) {
+    long di = (a == 0), dj = (a == 1), dk = (a == 2);
+    double fm2 = fetch(s, f, i - 2 * di, j - 2 * dj, k - 2 * dk);
+    double fm1 = fetch(s, f, i - di, j - dj, k - dk);
+    double f0 = fetch(s, f, i, j, k);
+    double fp1 = fetch(s, f, i + di, j + dj, k + dk);
+    return (ORC_C1 * (f0 - fm1) + ORC_C2 * (fp1 - fm2)) / s->h[a];
+}
+
+static long clampi(long i, long n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+static double *zalloc(long n) { return (double *)calloc((size_t)n, sizeof(double)); }
+
+orc_sim *orc_create(long nx, long ny, long nz, double dx, double dy, double dz) {
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    s->nx = nx; s->ny = ny; s->nz = nz; s->n = nx * ny * nz;
+    s->h[0] = dx; s->h[1] = dy; s->h[2] = dz;
+    for (int q = 0; q < NFIELD; ++q) s->f[q] = zalloc(s->n);
+    s->bx = zalloc(s->n); s->by = zalloc(s->n); s->bz = zalloc(s->n);
+    s->lam = zalloc(s->n); s->lp2m = zalloc(s->n);
+    s->mxy = zalloc(s->n); s->mxz = zalloc(s->n); s->myz = zalloc(s->n);
+    long dims[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        s->g[a] = zalloc(dims[a]);
+        s->pa[a] = zalloc(dims[a]);
+        s->pb[a] = zalloc(dims[a]);
+        for (long i = 0; i < dims[a]; ++i) s->g[a][i] = 1.0;
+    }
+    s->boundary = BND_NONE;
+    return s;
+}
+
+void orc_destroy(orc_sim *s) {
+    if (!s) return;
+    for (int q = 0; q < NFIELD; ++q) free(s->f[q]);
+    free(s->bx); free(s->by); free(s->bz); free(s->lam); free(s->lp2m);
+    free(s->mxy); free(s->mxz); free(s->myz);
+    for (int a = 0; a < 3; ++a) { free(s->g[a]); free(s->pa[a]); free(s->pb[a]); }
+    for (int p = 0; p < 18; ++p) free(s->psi[p]);
+    free(s);
+}
+
+/* Effective medium at the staggered points (Sec. 2.2.1, reading R4).
+ * Input: Lame parameters and density per cell, [nz][ny][nx]. */
+void orc_set_medium(orc_sim *s, const double *lam, const double *mu, const double *rho) {
+    long nx = s->nx, ny = s->ny, nz = s->nz;
+    double vpmax = 0.0;
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(s, i, j, k);
+                long ip = clampi(i + 1, nx), jp = clampi(j + 1, ny), kp = clampi(k + 1, nz);
+                /* rho at vx (i+1/2, j, k), vy (i, j+1/2, k), vz (i, j, k+1/2) */
+                s->bx[c] = 1.0 / (0.5 * (rho[c] + rho[IDX(s, ip, j, k)]));
+                s->by[c] = 1.0 / (0.5 * (rho[c] + rho[IDX(s, i, jp, k)]));
+                s->bz[c] = 1.0 / (0.5 * (rho[c] + rho[IDX(s, i, j, kp)]));
+                s->lam[c] = lam[c];
+                s->lp2m[c] = lam[c] + 2.0 * mu[c];
+                /* mu at sxy (i+1/2, j+1/2, k), sxz (i+1/2, j, k+1/2), syz (i, j+1/2, k+1/2) */
+                s->mxy[c] = 0.25 * (mu[c] + mu[IDX(s, ip, j, k)] + mu[IDX(s, i, jp, k)]
+                                    + mu[IDX(s, ip, jp, k)]);
+                s->mxz[c] = 0.25 * (mu[c] + mu[IDX(s, ip, j, k)] + mu[IDX(s, i, j, kp)]
+                                    + mu[IDX(s, ip, j, kp)]);
+                s->myz[c] = 0.25 * (mu[c] + mu[IDX(s, i, jp, k)] + mu[IDX(s, i, j, kp)]
+                                    + mu[IDX(s, i, jp, kp)]);
+                double vp = sqrt((lam[c] + 2.0 * mu[c]) / rho[c]);
+                if (vp > vpmax) vpmax = vp;
+            }
+    s->vpmax = vpmax;
+}
+
+double orc_vpmax(const orc_sim *s) { return s->vpmax; }
+
+/* Damping layers (Sec. 2.5 for the sponge; C-PML is reading R7).
+ * Must be called after orc_set_medium (C-PML uses vpmax) and whenever dt
+ * changes (C-PML coefficients depend on dt). */
+void orc_set_boundary(orc_sim *s, int kind, int width, double sponge_alpha,
+                      double pml_R, double pml_f0, double dt) {
+    long dims[3] = {s->nx, s->ny, s->nz};
+    s->boundary = kind; s->width = width;
+    s->sponge_alpha = sponge_alpha; s->pml_R = pml_R; s->pml_f0 = pml_f0; s->pml_dt = dt;
+    for (int a = 0; a < 3; ++a) {
+        long n = dims[a];
+        for (long i = 0; i < n; ++i) {
+            s->g[a][i] = 1.0; s->pa[a][i] = 0.0; s->pb[a][i] = 0.0;
+            long d = i < n - 1 - i ? i : n - 1 - i;       /* cells from the face */
+            if (kind == BND_SPONGE && d < width) {
+                double x = sponge_alpha * (double)(width - d) / (double)width;
+                s->g[a][i] = exp(-x * x);
+            }
+            if (kind == BND_CPML && (i < width || i >= n - width)) {
+                double q = i < width ? (double)(width - i) / width
+                                     : (double)(i - (n - 1 - width)) / width;
+                double L = width * s->h[a];
+                double d0 = -3.0 * s->vpmax * log(pml_R) / (2.0 * L);
+                double dd = d0 * q * q;
+                double al = M_PI * pml_f0 * (1.0 - q);
+                double b = exp(-(dd + al) * dt);
+                s->pb[a][i] = b;
+                s->pa[a][i] = (dd + al) > 0.0 ? dd * (b - 1.0) / (dd + al) : 0.0;
+            }
+        }
+    }
+    for (int p = 0; p < 18; ++p) {
+        free(s->psi[p]);
+        s->psi[p] = kind == BND_CPML ? zalloc(s->n) : NULL;
+    }
+}
+
+/* C-PML correction of one derivative term (reading R7): inside the slab of
+ * the derivative's axis the memory variable is advanced and added. */
+static inline double pml_term(orc_sim *s, int p, int a, long ia, long c, double d) {
+    long dims[3] = {s->nx, s->ny, s->nz};
+    if (s->boundary != BND_CPML) return d;
+    if (!(ia < s->width || ia >= dims[a] - s->width)) return d;
+    double *psi = s->psi[p];
+    psi[c] = s->pb[a][ia] * psi[c] + s->pa[a][ia] * d;
+    return d + psi[c];
+}
+
+static void apply_sponge(orc_sim *s, int f0, int f1) {
+    if (s->boundary != BND_SPONGE) return;
+    long nx = s->nx, ny = s->ny, nz = s->nz;
+    #pragma omp parallel for
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                double gg = s->g[0][i] * s->g[1][j] * s->g[2][k];
+                for (int q = f0; q < f1; ++q) s->f[q][IDX(s, i, j, k)] *= gg;
+            }
+}
+
+/* Velocity pass, Eq. 1 with Eq. 4 (no source, no sponge):
+ *   v_i += dt * b_i * sum_j D_j sigma_ij. */
+static void velocity_update(orc_sim *s, double dt) {
+    double **f = s->f;
+    long nx = s->nx, ny = s->ny, nz = s->nz;
+    #pragma omp parallel for
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(s, i, j, k);
+                /* vx at (i+1/2, j, k) */
+                double dxx = pml_term(s, 0, 0, i, c, d_plus(s, f[SXX], 0, i, j, k));
+                double dxy = pml_term(s, 1, 1, j, c, d_minus(s, f[SXY], 1, i, j, k));
+                double dxz = pml_term(s, 2, 2, k, c, d_minus(s, f[SXZ], 2, i, j, k));
+                /* vy at (i, j+1/2, k) */
+                double dyx = pml_term(s, 3, 0, i, c, d_minus(s, f[SXY], 0, i, j, k));
+                double dyy = pml_term(s, 4, 1, j, c, d_plus(s, f[SYY], 1, i, j, k));
+                double dyz = pml_term(s, 5, 2, k, c, d_minus(s, f[SYZ], 2, i, j, k));
+                /* vz at (i, j, k+1/2) */
+                double dzx = pml_term(s, 6, 0, i, c, d_minus(s, f[SXZ], 0, i, j, k));
+                double dzy = pml_term(s, 7, 1, j, c, d_minus(s, f[SYZ], 1, i, j, k));
+                double dzz = pml_term(s, 8, 2, k, c, d_plus(s, f[SZZ], 2, i, j, k));
+                f[VX][c] += dt * s->bx[c] * (dxx + dxy + dxz);
+                f[VY][c] += dt * s->by[c] * (dyx + dyy + dyz);
+                f[VZ][c] += dt * s->bz[c] * (dzx + dzy + dzz);
+            }
+}
+
+/* Stress pass, Eq. 2/3 with Eq. 4 (no source, no sponge):
+ *   sigma_ii += dt [(lam + 2 mu) e_ii + lam (e_jj + e_kk)],
+ *   sigma_ij += dt mu (D_j v_i + D_i v_j). */
+static void stress_update(orc_sim *s, double dt) {
+    double **f = s->f;
+    long nx = s->nx, ny = s->ny, nz = s->nz;
+    #pragma omp parallel for
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(s, i, j, k);
+                double exx = pml_term(s, 9, 0, i, c, d_minus(s, f[VX], 0, i, j, k));
+                double eyy = pml_term(s, 10, 1, j, c, d_minus(s, f[VY], 1, i, j, k));
+                double ezz = pml_term(s, 11, 2, k, c, d_minus(s, f[VZ], 2, i, j, k));
+                double vxy = pml_term(s, 12, 1, j, c, d_plus(s, f[VX], 1, i, j, k));
+                double vyx = pml_term(s, 13, 0, i, c, d_plus(s, f[VY], 0, i, j, k));
+                double vxz = pml_term(s, 14, 2, k, c, d_plus(s, f[VX], 2, i, j, k));
+                double vzx = pml_term(s, 15, 0, i, c, d_plus(s, f[VZ], 0, i, j, k));
+                double vyz = pml_term(s, 16, 2, k, c, d_plus(s, f[VY], 2, i, j, k));
+                double vzy = pml_term(s, 17, 1, j, c, d_plus(s, f[VZ], 1, i, j, k));
+                double l = s->lam[c], l2m = s->lp2m[c];
+                f[SXX][c] += dt * (l2m * exx + l * (eyy + ezz));
+                f[SYY][c] += dt * (l2m * eyy + l * (exx + ezz));
+                f[SZZ][c] += dt * (l2m * ezz + l * (exx + eyy));
+                f[SXY][c] += dt * s->mxy[c] * (vxy + vyx);
+                f[SXZ][c] += dt * s->mxz[c] * (vxz + vzx);
+                f[SYZ][c] += dt * s->myz[c] * (vyz + vzy);
+            }
+}
+
+/* Trilinear weights of a point on the grid of field q (Sec. 2.4): the 8
+ * neighbouring elements and their weights.  Returns 0 if any neighbour with a
+ * nonzero weight falls outside the grid. */
+static int trilinear(const orc_sim *s, int q, const double pos[3], long idx[8], double w[8]) {
+    long dims[3] = {s->nx, s->ny, s->nz};
+    long i0[3]; double fr[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = pos[a] / s->h[a] - OFF[q][a];
+        double fl = floor(u);
+        i0[a] = (long)fl; fr[a] = u - fl;
+    }
+    int m = 0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di, ++m) {
+                double wx = di ? fr[0] : 1.0 - fr[0];
+                double wy = dj ? fr[1] : 1.0 - fr[1];
+                double wz = dk ? fr[2] : 1.0 - fr[2];
+                long ii = i0[0] + di, jj = i0[1] + dj, kk = i0[2] + dk;
+                w[m] = wx * wy * wz;
+                if (ii < 0 || jj < 0 || kk < 0 || ii >= dims[0] || jj >= dims[1] || kk >= dims[2]) {
+                    if (w[m] != 0.0) return 0;
+                    idx[m] = -1;
+                } else {
+                    idx[m] = IDX(s, ii, jj, kk);
+                }
+            }
+    return 1;
+}
+
+/* Force source into the velocity pass (reading R8). */
+static int inject_force(orc_sim *s, double dt, const double pos[3], const double F[3], double amp) {
+    double vol = s->h[0] * s->h[1] * s->h[2];
+    const double *b[3] = {s->bx, s->by, s->bz};
+    for (int q = 0; q < 3; ++q) {
+        long idx[8]; double w[8];
+        if (!trilinear(s, q, pos, idx, w)) return 0;
+        for (int m = 0; m < 8; ++m)
+            if (idx[m] >= 0) s->f[q][idx[m]] += w[m] * dt * b[q][idx[m]] * F[q] * amp / vol;
+    }
+    return 1;
+}
+
+/* Moment-rate source into the stress pass (reading R8); M = (xx, yy, zz, xy, xz, yz). */
+static int inject_moment(orc_sim *s, double dt, const double pos[3], const double M[6], double amp) {
+    double vol = s->h[0] * s->h[1] * s->h[2];
+    for (int c = 0; c < 6; ++c) {
+        int q = SXX + c;
+        long idx[8]; double w[8];
+        if (!trilinear(s, q, pos, idx, w)) return 0;
+        for (int m = 0; m < 8; ++m)
+            if (idx[m] >= 0) s->f[q][idx[m]] -= w[m] * dt * M[c] * amp / vol;
+    }
+    return 1;
+}
+
+/* One velocity pass with optional force (kind 1) and the sponge. */
+int orc_step_velocity(orc_sim *s, double dt, int src_kind, const double *pos,
+                      const double *comp, double amp) {
+    velocity_update(s, dt);
+    if (src_kind == 1 && !inject_force(s, dt, pos, comp, amp)) return -1;
+    apply_sponge(s, VX, VZ + 1);
+    return 0;
+}
+
+/* One stress pass with optional moment source (kind 0) and the sponge. */
+int orc_step_stress(orc_sim *s, double dt, int src_kind, const double *pos,
+                    const double *comp, double amp) {
+    stress_update(s, dt);
+    if (src_kind == 0 && !inject_moment(s, dt, pos, comp, amp)) return -1;
+    apply_sponge(s, SXX, SYZ + 1);
+    return 0;
+}
+
+/* Trilinear sample of vx, vy, vz at each receiver (Sec. 2.4).
+ * out[c * nrec + r] for component c. */
+int orc_sample(const orc_sim *s, int nrec, const double *rpos, double *out) {
+    for (int r = 0; r < nrec; ++r)
+        for (int q = 0; q < 3; ++q) {
+            long idx[8]; double w[8];
+            if (!trilinear(s, q, rpos + 3 * r, idx, w)) return -1;
+            double acc = 0.0;
+            for (int m = 0; m < 8; ++m)
+                if (idx[m] >= 0) acc += w[m] * s->f[q][idx[m]];
+            out[q * nrec + r] = acc;
+        }
+    return 0;
+}
+
+/* The time loop (Sec. 2.3, reading R3): for n = 0 .. nt-1
+ *   velocity pass (+ force s_n) -> sponge -> receivers record v^{n+1/2}
+ *   stress pass (- moment s_n)  -> sponge.
+ * seis is [3][nrec][nt].  snap (optional) receives every field of
+ * snap_mask each snap_every steps after the stress pass, [nsnap][nmask][N]. */
+int orc_forward(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
+                const double *comp, const double *wavelet, int nrec, const double *rpos,
+                double *seis, int snap_every, unsigned snap_mask, double *snap) {
+    double *tmp = (double *)malloc(sizeof(double) * 3 * (nrec > 0 ? nrec : 1));
+    long isnap = 0;
+    for (int n = 0; n < nt; ++n) {
+        if (orc_step_velocity(s, dt, src_kind, pos, comp, wavelet[n]) != 0) { free(tmp); return -1; }
+        if (nrec > 0) {
+            if (orc_sample(s, nrec, rpos, tmp) != 0) { free(tmp); return -2; }
+            for (int q = 0; q < 3; ++q)
+                for (int r = 0; r < nrec; ++r)
+                    seis[((long)q * nrec + r) * nt + n] = tmp[q * nrec + r];
+        }
+        if (orc_step_stress(s, dt, src_kind, pos, comp, wavelet[n]) != 0) { free(tmp); return -1; }
+        if (snap && snap_every > 0 && (n + 1) % snap_every == 0) {
+            for (int q = 0; q < NFIELD; ++q)
+                if (snap_mask & (1u << q)) {
+                    memcpy(snap + isnap * s->n, s->f[q], sizeof(double) * s->n);
+                    ++isnap;
+                }
+        }
+    }
+    free(tmp);
+    return 0;
+}
+
+/* Wavefield state access: state is [9][N] in field order vx vy vz sxx syy szz sxy sxz syz. */
+void orc_get_state(const orc_sim *s, double *out) {
+    for (int q = 0; q < NFIELD; ++q) memcpy(out + q * s->n, s->f[q], sizeof(double) * s->n);
+}
+void orc_set_state(orc_sim *s, const double *in) {
+    for (int q = 0; q < NFIELD; ++q) memcpy(s->f[q], in + q * s->n, sizeof(double) * s->n);
+    for (int p = 0; p < 18; ++p)
+        if (s->psi[p]) memset(s->psi[p], 0, sizeof(double) * s->n);
+}
+/* C-PML memory variables, [18][N] (zeros outside the slabs). */
+int orc_get_psi(const orc_sim *s, double *out) {
+    if (s->boundary != BND_CPML) return -1;
+    for (int p = 0; p < 18; ++p) memcpy(out + p * s->n, s->psi[p], sizeof(double) * s->n);
+    return 0;
+}
+
+/* Effective-medium arrays, [8][N]: bx by bz lam lp2m mxy mxz myz. */
+void orc_get_medium(const orc_sim *s, double *out) {
+    const double *m[8] = {s->bx, s->by, s->bz, s->lam, s->lp2m, s->mxy, s->mxz, s->myz};
+    for (int q = 0; q < 8; ++q) memcpy(out + q * s->n, m[q], sizeof(double) * s->n);
+}
+
+/* Discrete energy of the leapfrog scheme (boundaries off, no source):
+ *   E^n = 1/2 sum rho_v v^{n-1/2} v^{n+1/2} + 1/2 sum sigma^n : C^{-1} : sigma^n,
+ * times the cell volume.  vprev = v^{n-1/2} as [3][N]; the current state
+ * holds v^{n+1/2} and sigma^n. */
+double orc_energy(const orc_sim *s, const double *vprev) {
+    double kin = 0.0, pot = 0.0;
+    const double *b[3] = {s->bx, s->by, s->bz};
+    for (int q = 0; q < 3; ++q)
+        for (long c = 0; c < s->n; ++c)
+            kin += vprev[q * s->n + c] * s->f[q][c] / b[q][c];
+    for (long c = 0; c < s->n; ++c) {
+        double l = s->lam[c], mu = 0.5 * (s->lp2m[c] - l);
+        double sxx = s->f[SXX][c], syy = s->f[SYY][c], szz = s->f[SZZ][c];
+        double tr = sxx + syy + szz;
+        /* isotropic compliance: e = (sigma - lam / (3 lam + 2 mu) tr I) / (2 mu) */
+        double enorm = (sxx * sxx + syy * syy + szz * szz
+                        - l / (3.0 * l + 2.0 * mu) * tr * tr) / (2.0 * mu);
+        pot += enorm;
+        pot += s->f[SXY][c] * s->f[SXY][c] / s->mxy[c];
+        pot += s->f[SXZ][c] * s->f[SXZ][c] / s->mxz[c];
+        pot += s->f[SYZ][c] * s->f[SYZ][c] / s->myz[c];
+    }
+    return 0.5 * (kin + pot) * s->h[0] * s->h[1] * s->h[2];
+}
