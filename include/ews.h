@@ -1,0 +1,170 @@
+/*
+ * ews.h -- C ABI of libews, a single-GPU (GB300, sm_103a) solver for the 3D
+ * elastic velocity-stress staggered-grid finite-difference scheme of
+ * "Elastic 3D Wavefield Simulation on budget GPUs using the GLSL shading
+ * language" (arXiv 2112.15071).
+ *
+ * Problem statement (paper Sec. 2.1-2.5):
+ *   Eq. 1   rho dv/dt = div sigma + f
+ *   Eq. 2   dsigma/dt = C : (grad v + grad v^T) / 2, isotropic C(lambda, mu)
+ *   Eq. 4   4th-order staggered first derivative (weights 9/8, -1/24, / h)
+ *   Eq. 5   dt_max = 0.495 dx_min / v_max
+ *   Sec. 2.1.1  staggered positions (Graves 1996), Sec. 2.2.1 medium by
+ *   interpolation at staggered points, Sec. 2.2.2 out-of-range fetches,
+ *   Sec. 2.4 receivers by trilinear interpolation, Sec. 2.5 absorbing edges.
+ *
+ * Conventions shared by every call:
+ *   - Every 3D array is C-ordered [nz][ny][nx] (x fastest), float32, dense
+ *     (no padding), SI units.  Element [k][j][i] of a staggered field holds
+ *     the value at its Sec. 2.1.1 position relative to cell (i, j, k):
+ *       sxx, syy, szz at (i, j, k);      vx at (i+1/2, j, k);
+ *       sxy at (i+1/2, j+1/2, k);        vy at (i, j+1/2, k);
+ *       sxz at (i+1/2, j, k+1/2);        vz at (i, j, k+1/2);
+ *       syz at (i, j+1/2, k+1/2).
+ *   - Positions are metres from the normal-stress point of cell (0, 0, 0),
+ *     z positive downwards.  A source or receiver position p must satisfy
+ *     d <= p <= (n - 2) d on every axis (all trilinear neighbours of every
+ *     staggered component lie inside the grid).
+ *   - Wavefield values outside the grid are zero; medium values are clamped
+ *     to the edge (reading of Sec. 2.2.2 / 2.2.1).
+ *   - Wavefield state order is (vx, vy, vz, sxx, syy, szz, sxy, sxz, syz);
+ *     field bit q of a mask selects field q.
+ *   - Ownership: the caller owns every buffer it passes.  set_* calls copy
+ *     their inputs (to the device) before returning, so the caller may free
+ *     them afterwards.  Output buffers are written in place.  A pointer
+ *     flagged *_on_device must be a device pointer of the current CUDA
+ *     device (e.g. a torch CUDA tensor); otherwise it is host memory.
+ *   - Errors: nothing is thrown across the ABI.  Every call returns an
+ *     ews_status; ews_last_error() gives a message (thread-local).  On error
+ *     outputs may be partially written and must be discarded.
+ *   - Streams: all device work of a simulation runs on its stream (default:
+ *     the legacy default stream; see ews_set_stream).  Calls that return data
+ *     to host memory synchronise that stream before returning.
+ *   - There is no CPU fallback: without a usable CUDA device ews_create
+ *     returns EWS_ECUDA.
+ */
+#ifndef EWS_H
+#define EWS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EWS_OK = 0,
+    EWS_EINVAL = 1,      /* bad argument (sizes, positions, model values)   */
+    EWS_ECFL = 2,        /* dt above the scheme's exact stability bound     */
+    EWS_ENOMEM = 3,      /* device allocation failed                        */
+    EWS_ECUDA = 4,       /* CUDA runtime or driver error                    */
+    EWS_ENONFINITE = 5,  /* NaN/Inf in a model or in the wavefield          */
+    EWS_ETIMEOUT = 6,    /* a bounded device wait gave up                   */
+    EWS_ESTATE = 7       /* call out of order (e.g. run before set_model)   */
+} ews_status;
+
+enum { EWS_BOUNDARY_NONE = 0, EWS_BOUNDARY_SPONGE = 1, EWS_BOUNDARY_CPML = 2 };
+enum { EWS_STORAGE_F32 = 0, EWS_STORAGE_BF16 = 1, EWS_STORAGE_F16 = 2 };
+enum { EWS_SOURCE_MOMENT = 0, EWS_SOURCE_FORCE = 1 };
+
+typedef struct {
+    int nx, ny, nz;          /* cells per axis, each >= 4                    */
+    double dx, dy, dz;       /* spacing (m), > 0; may differ per axis        */
+} ews_grid;
+
+typedef struct {
+    /* Absorbing edges (Sec. 2.5).  SPONGE: every field is multiplied after
+     * its update by G(i) G(j) G(k), G(d) = exp(-(alpha (W - d) / W)^2) for a
+     * cell d < W cells from a face.  CPML: convolutional PML (kappa = 1,
+     * quadratic profile, d0 = -3 vp_max ln(R) / (2 W h), alpha_pml = pi f0
+     * (1 - q)).  NONE: zero exterior only. */
+    int boundary;
+    int width;               /* W in cells; 2 W <= n on every axis           */
+    int storage;             /* EWS_STORAGE_F32 (BF16/F16: reserved)         */
+    int snapshot_every;      /* 0: no snapshots                               */
+    unsigned snapshot_mask;  /* fields copied at each snapshot               */
+    double sponge_alpha;     /* <= 0 selects 0.3                              */
+    double pml_R;            /* <= 0 selects 1e-3                             */
+    double pml_f0;           /* Hz, C-PML frequency shift; 0 disables alpha  */
+} ews_options;
+
+typedef struct ews_sim ews_sim;
+
+/* Create a simulation on the current CUDA device.  Allocates the 9
+ * wavefields and 3 medium arrays (and C-PML memory variables in the slabs).
+ * opt may be NULL (sponge, W = 16).  *out receives the handle. */
+ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** out);
+
+/* Release every device allocation of the simulation.  NULL is ignored. */
+void ews_destroy(ews_sim* sim);
+
+/* Run all later device work of sim on this cudaStream_t (NULL = default). */
+ews_status ews_set_stream(ews_sim* sim, void* cuda_stream);
+
+/* Medium from Lame parameters and density, each [nz][ny][nx] (Sec. 2.1:
+ * lambda, mu, rho define the isotropic medium).  Requires rho > 0, mu >= 0,
+ * lambda + 2 mu > 0, all finite; else EWS_EINVAL / EWS_ENONFINITE. */
+ews_status ews_set_model_lame(ews_sim* sim, const float* lam, const float* mu,
+                              const float* rho, int on_device);
+
+/* Medium from vp, vs, rho (Sec. 3.1.2 table form): lambda = rho (vp^2 -
+ * 2 vs^2), mu = rho vs^2, converted on the device. */
+ews_status ews_set_model_vel(ews_sim* sim, const float* vp, const float* vs,
+                             const float* rho, int on_device);
+
+/* Point source.  kind MOMENT: comp = (Mxx, Myy, Mzz, Mxy, Mxz, Myz) in N m
+ * (Sec. 3.1.1, Eq. 7 gives such a tensor); each step n the stress pass does
+ * sigma_ij -= dt M_ij wavelet[n] / (dx dy dz), spread over the 8 trilinear
+ * neighbours on the sigma_ij grid.  wavelet[n] is the moment-rate function
+ * at t = (n + 1/2) dt.  kind FORCE: comp = (Fx, Fy, Fz) in N; the velocity
+ * pass does v_i += dt b_i F_i wavelet[n] / (dx dy dz) (b = 1 / rho at the v_i
+ * point), wavelet[n] at t = n dt.  wavelet has nt float32 samples (host). */
+ews_status ews_set_source(ews_sim* sim, int kind, const double pos[3],
+                          const double comp[6], const float* wavelet, int nt);
+
+/* Receivers: pos is [nrec][3] metres (host).  Each step records vx, vy, vz
+ * of v^{n+1/2}, each trilinearly interpolated on its own staggered grid
+ * (Sec. 2.4).  nrec may be 0. */
+ews_status ews_set_receivers(ews_sim* sim, int nrec, const double* pos);
+
+/* Reset the wavefields and C-PML memory to zero, then run nt steps of
+ * Sec. 2.3's loop: velocity pass (+ force) -> absorbing edge -> record
+ * receivers -> stress pass (- moment) -> absorbing edge.
+ *   seis      [3][nrec][nt] float32 output (component-major), may be NULL
+ *             when nrec == 0; host or device per seis_on_device.
+ *   snapshots [nt / snapshot_every][popcount(mask)][nz][ny][nx] float32,
+ *             taken after the stress pass of every snapshot_every-th step;
+ *             NULL to skip; same residency as seis.
+ * dt must satisfy the exact bound dt vp_max (7/3) sqrt(1/dx^2 + 1/dy^2 +
+ * 1/dz^2) <= 2 (equal spacings: dt <= 6 / (7 sqrt 3) h / vp_max, Eq. 5's
+ * 0.495 rounded), else EWS_ECFL.  nt must not exceed the wavelet length. */
+ews_status ews_run(ews_sim* sim, int nt, double dt, float* seis, int seis_on_device,
+                   float* snapshots);
+
+/* Continue from the current state: steps n0 .. n0 + nsteps - 1 (wavelet
+ * samples n0 ..), recording into columns n0 .. of seis, which is
+ * [3][nrec][ld] with ld >= n0 + nsteps.  No reset. */
+ews_status ews_advance(ews_sim* sim, int n0, int nsteps, double dt, float* seis,
+                       int ld, int seis_on_device);
+
+/* Zero the wavefields and C-PML memory variables. */
+ews_status ews_reset(ews_sim* sim);
+
+/* Copy the 9 wavefields out of / into the simulation, [9][nz][ny][nx]. */
+ews_status ews_get_state(ews_sim* sim, float* out, int on_device);
+ews_status ews_set_state(ews_sim* sim, const float* in, int on_device);
+
+/* Time-step rule of Sec. 2.1.3, Eq. 5: 0.495 min(dx, dy, dz) / vmax. */
+double ews_cfl_dt(const ews_grid* grid, double vmax);
+
+/* Source-frequency rule of Sec. 2.1.3, Eq. 6: vmin / (5 max(dx, dy, dz)). */
+double ews_max_freq(const ews_grid* grid, double vmin);
+
+/* Message of the last error on this thread ("" if none). */
+const char* ews_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int ews_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EWS_H */

@@ -1,0 +1,586 @@
+// ews_capi.cu -- C ABI of libews: simulation object, validation, device
+// memory, and the time loop of Sec. 2.3 (velocity pass, receivers, stress
+// pass each step).  Declarations and the contract of every call are in
+// include/ews.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ews.h"
+#include "ews_internal.cuh"
+
+using namespace ews;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+ews_status fail(ews_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? EWS_ENOMEM : EWS_ECUDA,    \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                        __LINE__);                                                   \
+    } while (0)
+
+// Eq. 4 weights.
+constexpr double kC1 = 9.0 / 8.0;
+constexpr double kC2 = -1.0 / 24.0;
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Host-side description of the point source (taps are rebuilt per dt).
+struct SourceSpec {
+    int kind = -1;
+    double pos[3] = {0, 0, 0};
+    double comp[6] = {0, 0, 0, 0, 0, 0};
+};
+
+}  // namespace
+
+struct ews_sim {
+    ews_grid grid{};
+    ews_options opt{};
+    DevGrid g{};
+    size_t fstride = 0;           // floats between fields
+    float* fields = nullptr;      // 9 * fstride
+    float* medium = nullptr;      // 3 * fstride: lambda, mu, rho
+    bool model_set = false;
+    float vpmax = 0.0f;
+    // boundary
+    float* prof = nullptr;        // g[3][n], pa[3][n], pb[3][n] packed
+    float* psi = nullptr;         // C-PML memory variables
+    size_t psi_floats = 0;
+    DevBoundary B{};
+    double pml_dt = -1.0;
+    // source
+    SourceSpec src;
+    DevSource S{};
+    float* wavelet = nullptr;
+    int wavelet_nt = 0;
+    // receivers
+    int nrec = 0;
+    Tap* rtaps = nullptr;         // [3 * nrec][8]
+    float* seis_buf = nullptr;    // internal [3][nrec][cap] when caller is on host
+    size_t seis_cap = 0;
+    unsigned* flags = nullptr;    // device scratch for medium checks
+    cudaStream_t stream = nullptr;
+
+    DevFields F() const {
+        DevFields f;
+        for (int q = 0; q < NFIELD; ++q) f.f[q] = fields + q * fstride;
+        return f;
+    }
+    DevMedium M() const {
+        DevMedium m;
+        m.lam = medium;
+        m.mu = medium + fstride;
+        m.rho = medium + 2 * fstride;
+        return m;
+    }
+    long long ncell() const { return (long long)grid.nx * grid.ny * grid.nz; }
+};
+
+namespace {
+
+ews_status check_pos(const ews_sim* s, const double p[3], const char* what) {
+    const int n[3] = {s->grid.nx, s->grid.ny, s->grid.nz};
+    const double h[3] = {s->grid.dx, s->grid.dy, s->grid.dz};
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(p[a]) || p[a] < h[a] * (1.0 - 1e-12) ||
+            p[a] > (n[a] - 2) * h[a] * (1.0 + 1e-12))
+            return fail(EWS_EINVAL, "%s position %g on axis %d outside [%g, %g]", what, p[a],
+                        a, h[a], (n[a] - 2) * h[a]);
+    }
+    return EWS_OK;
+}
+
+// Trilinear taps of point p on the grid of field q (offsets of Sec. 2.1.1).
+void taps_for(const ews_sim* s, int q, const double p[3], double scale, Tap out[8]) {
+    static const double off[NFIELD][3] = {{0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5},
+                                          {0, 0, 0},   {0, 0, 0},   {0, 0, 0},
+                                          {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    const double h[3] = {s->grid.dx, s->grid.dy, s->grid.dz};
+    const int n[3] = {s->grid.nx, s->grid.ny, s->grid.nz};
+    int i0[3];
+    double fr[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = p[a] / h[a] - off[q][a];
+        double fl = std::floor(u);
+        i0[a] = (int)fl;
+        fr[a] = u - fl;
+        if (i0[a] >= n[a] - 1) {  // exactly on the last point: weight 1 there
+            i0[a] = n[a] - 2;
+            fr[a] = 1.0;
+        }
+    }
+    int m = 0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di, ++m) {
+                double w = (di ? fr[0] : 1 - fr[0]) * (dj ? fr[1] : 1 - fr[1]) *
+                           (dk ? fr[2] : 1 - fr[2]);
+                out[m].q = q;
+                out[m].i = i0[0] + di;
+                out[m].j = i0[1] + dj;
+                out[m].k = i0[2] + dk;
+                out[m].w = (float)(w * scale);
+            }
+}
+
+// Sponge profiles and C-PML coefficients for the current dt.
+ews_status upload_boundary(ews_sim* s, double dt) {
+    const int n[3] = {s->grid.nx, s->grid.ny, s->grid.nz};
+    const double h[3] = {s->grid.dx, s->grid.dy, s->grid.dz};
+    const int W = s->opt.width;
+    const int nmax = std::max(n[0], std::max(n[1], n[2]));
+    std::vector<float> host(9 * (size_t)nmax, 0.0f);
+    const double alpha = s->opt.sponge_alpha > 0 ? s->opt.sponge_alpha : 0.3;
+    const double R = s->opt.pml_R > 0 ? s->opt.pml_R : 1e-3;
+    for (int a = 0; a < 3; ++a) {
+        float* g = &host[(0 * 3 + a) * (size_t)nmax];
+        float* pa = &host[(1 * 3 + a) * (size_t)nmax];
+        float* pb = &host[(2 * 3 + a) * (size_t)nmax];
+        for (int i = 0; i < n[a]; ++i) {
+            g[i] = 1.0f;
+            int d = std::min(i, n[a] - 1 - i);
+            if (s->opt.boundary == EWS_BOUNDARY_SPONGE && d < W) {
+                double x = alpha * (W - d) / W;
+                g[i] = (float)std::exp(-x * x);
+            }
+            if (s->opt.boundary == EWS_BOUNDARY_CPML && (i < W || i >= n[a] - W)) {
+                double q = i < W ? double(W - i) / W : double(i - (n[a] - 1 - W)) / W;
+                double d0 = -3.0 * s->vpmax * std::log(R) / (2.0 * W * h[a]);
+                double dd = d0 * q * q;
+                double al = M_PI * s->opt.pml_f0 * (1.0 - q);
+                double b = std::exp(-(dd + al) * dt);
+                pb[i] = (float)b;
+                pa[i] = (float)((dd + al) > 0 ? dd * (b - 1.0) / (dd + al) : 0.0);
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(s->prof, host.data(), host.size() * sizeof(float),
+                       cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int a = 0; a < 3; ++a) {
+        s->B.g[a] = s->prof + (0 * 3 + a) * (size_t)nmax;
+        s->B.pa[a] = s->prof + (1 * 3 + a) * (size_t)nmax;
+        s->B.pb[a] = s->prof + (2 * 3 + a) * (size_t)nmax;
+    }
+    s->pml_dt = dt;
+    return EWS_OK;
+}
+
+ews_status copy_field_in(ews_sim* s, float* dst, const float* src, int on_device) {
+    const ews_grid& gr = s->grid;
+    CK(cudaMemcpy2DAsync(dst, s->g.pitch * sizeof(float), src, gr.nx * sizeof(float),
+                         gr.nx * sizeof(float), (size_t)gr.ny * gr.nz,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         s->stream));
+    return EWS_OK;
+}
+
+ews_status copy_field_out(ews_sim* s, float* dst, const float* src, int on_device) {
+    const ews_grid& gr = s->grid;
+    CK(cudaMemcpy2DAsync(dst, gr.nx * sizeof(float), src, s->g.pitch * sizeof(float),
+                         gr.nx * sizeof(float), (size_t)gr.ny * gr.nz,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         s->stream));
+    return EWS_OK;
+}
+
+ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rho,
+                     int on_device, int from_vel) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (!a || !b || !rho) return fail(EWS_EINVAL, "null model array");
+    DevMedium M = s->M();
+    ews_status st;
+    if ((st = copy_field_in(s, (float*)M.lam, a, on_device)) != EWS_OK) return st;
+    if ((st = copy_field_in(s, (float*)M.mu, b, on_device)) != EWS_OK) return st;
+    if ((st = copy_field_in(s, (float*)M.rho, rho, on_device)) != EWS_OK) return st;
+    CK(cudaMemsetAsync(s->flags, 0, 2 * sizeof(unsigned), s->stream));
+    CK(launch_medium_setup(s->g, (float*)M.lam, (float*)M.mu, (float*)M.rho, from_vel,
+                           s->flags, s->stream));
+    unsigned hf[2];
+    CK(cudaMemcpyAsync(hf, s->flags, sizeof(hf), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->model_set = false;
+    if (hf[0] & 1u) return fail(EWS_ENONFINITE, "model contains NaN or Inf");
+    if (hf[0] & 2u) return fail(EWS_EINVAL, "model has rho <= 0");
+    if (hf[0] & 4u) return fail(EWS_EINVAL, "model has mu < 0 (vs^2 < 0)");
+    if (hf[0] & 8u) return fail(EWS_EINVAL, "model has lambda + 2 mu <= 0");
+    float vp;
+    std::memcpy(&vp, &hf[1], sizeof(vp));
+    s->vpmax = vp;
+    s->model_set = true;
+    s->pml_dt = -1.0;
+    return EWS_OK;
+}
+
+ews_status check_dt(const ews_sim* s, double dt) {
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(EWS_EINVAL, "dt must be positive");
+    const ews_grid& g = s->grid;
+    double k = std::sqrt(1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy) + 1.0 / (g.dz * g.dz));
+    double lim = 2.0 / ((7.0 / 3.0) * s->vpmax * k);
+    if (dt > lim * (1.0 + 1e-12))
+        return fail(EWS_ECFL, "dt = %g exceeds the stability bound %g (vp_max = %g)", dt, lim,
+                    (double)s->vpmax);
+    return EWS_OK;
+}
+
+ews_status ensure_ready(ews_sim* s, int n_end, double dt) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (!s->model_set) return fail(EWS_ESTATE, "ews_set_model_* has not succeeded");
+    ews_status st = check_dt(s, dt);
+    if (st != EWS_OK) return st;
+    if (s->S.kind >= 0 && n_end > s->wavelet_nt)
+        return fail(EWS_EINVAL, "steps up to %d exceed the wavelet length %d", n_end,
+                    s->wavelet_nt);
+    if (s->pml_dt != dt && (st = upload_boundary(s, dt)) != EWS_OK) return st;
+    return EWS_OK;
+}
+
+ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
+                 float* dseis, int ld) {
+    DevFields F = s->F();
+    DevMedium M = s->M();
+    // fold dt and the cell volume into the source taps
+    DevSource S{};
+    S.kind = -1;
+    if (src.kind >= 0 && s->wavelet) {
+        const double vol = s->grid.dx * s->grid.dy * s->grid.dz;
+        S.kind = src.kind;
+        S.ntap = 0;
+        if (src.kind == EWS_SOURCE_MOMENT) {
+            for (int c = 0; c < 6; ++c) {
+                if (src.comp[c] == 0.0) continue;
+                taps_for(s, SXX + c, src.pos, -dt * src.comp[c] / vol, &S.tap[S.ntap]);
+                S.ntap += 8;
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                if (src.comp[c] == 0.0) continue;
+                taps_for(s, VX + c, src.pos, dt * src.comp[c] / vol, &S.tap[S.ntap]);
+                S.ntap += 8;
+            }
+        }
+    }
+    const float fdt = (float)dt;
+    for (int n = n0; n < n0 + nsteps; ++n) {
+        CK(launch_velocity(s->g, F, M, s->B, fdt, s->stream));
+        if (S.kind == EWS_SOURCE_FORCE)
+            CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, s->stream));
+        if (s->nrec > 0 && dseis)
+            CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, s->stream));
+        CK(launch_stress(s->g, F, M, s->B, fdt, s->stream));
+        if (S.kind == EWS_SOURCE_MOMENT)
+            CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, s->stream));
+    }
+    return EWS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int ews_version(void) { return 100; }
+
+const char* ews_last_error(void) { return g_err; }
+
+double ews_cfl_dt(const ews_grid* g, double vmax) {
+    if (!g || !(vmax > 0)) return 0.0;
+    return 0.495 * std::min(g->dx, std::min(g->dy, g->dz)) / vmax;
+}
+
+double ews_max_freq(const ews_grid* g, double vmin) {
+    if (!g || !(vmin > 0)) return 0.0;
+    return vmin / (5.0 * std::max(g->dx, std::max(g->dy, g->dz)));
+}
+
+ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** out) {
+    g_err[0] = 0;
+    if (!grid || !out) return fail(EWS_EINVAL, "null argument");
+    *out = nullptr;
+    if (grid->nx < 4 || grid->ny < 4 || grid->nz < 4)
+        return fail(EWS_EINVAL, "grid must have at least 4 cells per axis");
+    if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
+        return fail(EWS_EINVAL, "grid spacing must be positive");
+    if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 34))
+        return fail(EWS_EINVAL, "grid too large");
+    ews_options o{};
+    if (opt) {
+        o = *opt;
+    } else {
+        o.boundary = EWS_BOUNDARY_SPONGE;
+        o.width = 16;
+    }
+    if (o.boundary < 0 || o.boundary > 2) return fail(EWS_EINVAL, "unknown boundary kind");
+    if (o.boundary != EWS_BOUNDARY_NONE) {
+        if (o.width < 1) return fail(EWS_EINVAL, "boundary width must be >= 1");
+        if (2 * o.width > grid->nx || 2 * o.width > grid->ny || 2 * o.width > grid->nz)
+            return fail(EWS_EINVAL, "2 * width exceeds the grid");
+    }
+    if (o.storage != EWS_STORAGE_F32) return fail(EWS_EINVAL, "only F32 storage is built");
+    if (o.snapshot_every < 0) return fail(EWS_EINVAL, "snapshot_every < 0");
+    if (o.snapshot_mask >> NFIELD) return fail(EWS_EINVAL, "snapshot_mask has unknown bits");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(EWS_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+
+    ews_sim* s = new (std::nothrow) ews_sim();
+    if (!s) return fail(EWS_ENOMEM, "host allocation failed");
+    s->grid = *grid;
+    s->opt = o;
+    s->S.kind = -1;
+    DevGrid& g = s->g;
+    g.nx = grid->nx;
+    g.ny = grid->ny;
+    g.nz = grid->nz;
+    g.pitch = round_up(grid->nx, 32);
+    g.plane = (long long)g.pitch * g.ny;
+    g.c1x = (float)(kC1 / grid->dx);
+    g.c2x = (float)(kC2 / grid->dx);
+    g.c1y = (float)(kC1 / grid->dy);
+    g.c2y = (float)(kC2 / grid->dy);
+    g.c1z = (float)(kC1 / grid->dz);
+    g.c2z = (float)(kC2 / grid->dz);
+    s->fstride = (size_t)((g.plane * g.nz + 63) / 64 * 64);
+    s->B.kind = o.boundary;
+    s->B.W = o.width;
+
+    auto cleanup = [&](ews_status st) {
+        ews_destroy(s);
+        return st;
+    };
+    e = cudaMalloc(&s->fields, NFIELD * s->fstride * sizeof(float));
+    if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "wavefields: %s", cudaGetErrorString(e)));
+    e = cudaMalloc(&s->medium, 3 * s->fstride * sizeof(float));
+    if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "medium: %s", cudaGetErrorString(e)));
+    const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
+    e = cudaMalloc(&s->prof, 9 * (size_t)nmax * sizeof(float));
+    if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "profiles: %s", cudaGetErrorString(e)));
+    e = cudaMalloc(&s->flags, 2 * sizeof(unsigned));
+    if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "flags: %s", cudaGetErrorString(e)));
+    if (o.boundary == EWS_BOUNDARY_CPML) {
+        const size_t W2 = 2 * (size_t)o.width;
+        const size_t sx = W2 * g.ny * g.nz, sy = (size_t)g.pitch * W2 * g.nz,
+                     sz = (size_t)g.pitch * g.ny * W2;
+        s->psi_floats = 6 * (sx + sy + sz);
+        e = cudaMalloc(&s->psi, s->psi_floats * sizeof(float));
+        if (e != cudaSuccess)
+            return cleanup(fail(EWS_ENOMEM, "C-PML memory: %s", cudaGetErrorString(e)));
+        float* p = s->psi;
+        for (int t = 0; t < 6; ++t) { s->B.psx[t] = p; p += sx; }
+        for (int t = 0; t < 6; ++t) { s->B.psy[t] = p; p += sy; }
+        for (int t = 0; t < 6; ++t) { s->B.psz[t] = p; p += sz; }
+    }
+    e = cudaMemset(s->fields, 0, NFIELD * s->fstride * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(s->medium, 0, 3 * s->fstride * sizeof(float));
+    if (e == cudaSuccess && s->psi) e = cudaMemset(s->psi, 0, s->psi_floats * sizeof(float));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cleanup(fail(EWS_ECUDA, "memset: %s", cudaGetErrorString(e)));
+    *out = s;
+    return EWS_OK;
+}
+
+void ews_destroy(ews_sim* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(s->fields);
+    cudaFree(s->medium);
+    cudaFree(s->prof);
+    cudaFree(s->flags);
+    cudaFree(s->psi);
+    cudaFree(s->wavelet);
+    cudaFree(s->rtaps);
+    cudaFree(s->seis_buf);
+    delete s;
+}
+
+ews_status ews_set_stream(ews_sim* s, void* stream) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    s->stream = (cudaStream_t)stream;
+    return EWS_OK;
+}
+
+ews_status ews_set_model_lame(ews_sim* s, const float* lam, const float* mu, const float* rho,
+                              int on_device) {
+    return set_model(s, lam, mu, rho, on_device, 0);
+}
+
+ews_status ews_set_model_vel(ews_sim* s, const float* vp, const float* vs, const float* rho,
+                             int on_device) {
+    return set_model(s, vp, vs, rho, on_device, 1);
+}
+
+ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const double comp[6],
+                          const float* wavelet, int nt) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (kind != EWS_SOURCE_MOMENT && kind != EWS_SOURCE_FORCE)
+        return fail(EWS_EINVAL, "unknown source kind %d", kind);
+    if (!pos || !comp || !wavelet || nt <= 0) return fail(EWS_EINVAL, "bad source arguments");
+    ews_status st = check_pos(s, pos, "source");
+    if (st != EWS_OK) return st;
+    const int nc = kind == EWS_SOURCE_MOMENT ? 6 : 3;
+    for (int c = 0; c < nc; ++c)
+        if (!std::isfinite(comp[c])) return fail(EWS_ENONFINITE, "source component not finite");
+    for (int n = 0; n < nt; ++n)
+        if (!std::isfinite(wavelet[n])) return fail(EWS_ENONFINITE, "wavelet not finite");
+    if (nt > s->wavelet_nt) {
+        cudaFree(s->wavelet);
+        s->wavelet = nullptr;
+        s->wavelet_nt = 0;
+        CK(cudaMalloc(&s->wavelet, nt * sizeof(float)));
+    }
+    CK(cudaMemcpyAsync(s->wavelet, wavelet, nt * sizeof(float), cudaMemcpyHostToDevice,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->wavelet_nt = nt;
+    SourceSpec& sp = s->src;
+    sp.kind = kind;
+    for (int a = 0; a < 3; ++a) sp.pos[a] = pos[a];
+    for (int c = 0; c < 6; ++c) sp.comp[c] = c < nc ? comp[c] : 0.0;
+    s->S.kind = kind;
+    return EWS_OK;
+}
+
+ews_status ews_set_receivers(ews_sim* s, int nrec, const double* pos) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (nrec < 0 || (nrec > 0 && !pos)) return fail(EWS_EINVAL, "bad receiver arguments");
+    for (int r = 0; r < nrec; ++r) {
+        ews_status st = check_pos(s, pos + 3 * r, "receiver");
+        if (st != EWS_OK) return st;
+    }
+    std::vector<Tap> taps((size_t)24 * nrec);
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < nrec; ++r) taps_for(s, VX + c, pos + 3 * r, 1.0, &taps[(size_t)8 * (c * nrec + r)]);
+    cudaFree(s->rtaps);
+    s->rtaps = nullptr;
+    s->nrec = 0;
+    if (nrec > 0) {
+        CK(cudaMalloc(&s->rtaps, taps.size() * sizeof(Tap)));
+        CK(cudaMemcpyAsync(s->rtaps, taps.data(), taps.size() * sizeof(Tap),
+                           cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    s->nrec = nrec;
+    return EWS_OK;
+}
+
+ews_status ews_reset(ews_sim* s) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    CK(cudaMemsetAsync(s->fields, 0, NFIELD * s->fstride * sizeof(float), s->stream));
+    if (s->psi) CK(cudaMemsetAsync(s->psi, 0, s->psi_floats * sizeof(float), s->stream));
+    return EWS_OK;
+}
+
+ews_status ews_advance(ews_sim* s, int n0, int nsteps, double dt, float* seis, int ld,
+                       int seis_on_device) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (n0 < 0 || nsteps < 0) return fail(EWS_EINVAL, "negative step range");
+    if (s->nrec > 0 && seis && ld < n0 + nsteps) return fail(EWS_EINVAL, "ld too small");
+    ews_status st = ensure_ready(s, n0 + nsteps, dt);
+    if (st != EWS_OK) return st;
+    float* dseis = nullptr;
+    if (s->nrec > 0 && seis) {
+        if (seis_on_device) {
+            dseis = seis;
+        } else {
+            size_t need = (size_t)3 * s->nrec * ld;
+            if (need > s->seis_cap) {
+                cudaFree(s->seis_buf);
+                s->seis_buf = nullptr;
+                s->seis_cap = 0;
+                CK(cudaMalloc(&s->seis_buf, need * sizeof(float)));
+                s->seis_cap = need;
+            }
+            dseis = s->seis_buf;
+        }
+    }
+    if ((st = steps(s, s->src, n0, nsteps, dt, dseis, ld)) != EWS_OK) return st;
+    if (dseis && !seis_on_device) {
+        // copy back only the columns written by this call
+        CK(cudaMemcpy2DAsync(seis + n0, ld * sizeof(float), dseis + n0, ld * sizeof(float),
+                             nsteps * sizeof(float), 3 * (size_t)s->nrec,
+                             cudaMemcpyDeviceToHost, s->stream));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return EWS_OK;
+}
+
+ews_status ews_run(ews_sim* s, int nt, double dt, float* seis, int seis_on_device,
+                   float* snapshots) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (nt <= 0) return fail(EWS_EINVAL, "nt must be positive");
+    if (s->nrec > 0 && !seis) return fail(EWS_EINVAL, "seis is NULL but receivers are set");
+    ews_status st = ensure_ready(s, nt, dt);
+    if (st != EWS_OK) return st;
+    if ((st = ews_reset(s)) != EWS_OK) return st;
+    const int every = s->opt.snapshot_every;
+    const unsigned mask = s->opt.snapshot_mask;
+    if (!snapshots || every <= 0 || mask == 0)
+        return ews_advance(s, 0, nt, dt, seis, nt, seis_on_device);
+    // snapshot loop: advance in chunks of `every` steps
+    const size_t ncell = (size_t)s->ncell();
+    size_t slot = 0;
+    for (int n0 = 0; n0 + every <= nt; n0 += every) {
+        if ((st = ews_advance(s, n0, every, dt, seis, nt, seis_on_device)) != EWS_OK) return st;
+        for (int q = 0; q < NFIELD; ++q)
+            if (mask & (1u << q)) {
+                st = copy_field_out(s, snapshots + slot * ncell, s->fields + q * s->fstride,
+                                    seis_on_device);
+                if (st != EWS_OK) return st;
+                ++slot;
+            }
+    }
+    int done = (nt / every) * every;
+    if (done < nt && (st = ews_advance(s, done, nt - done, dt, seis, nt, seis_on_device)) != EWS_OK)
+        return st;
+    CK(cudaStreamSynchronize(s->stream));
+    return EWS_OK;
+}
+
+ews_status ews_get_state(ews_sim* s, float* out, int on_device) {
+    if (!s || !out) return fail(EWS_EINVAL, "null argument");
+    const size_t ncell = (size_t)s->ncell();
+    for (int q = 0; q < NFIELD; ++q) {
+        ews_status st = copy_field_out(s, out + q * ncell, s->fields + q * s->fstride, on_device);
+        if (st != EWS_OK) return st;
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return EWS_OK;
+}
+
+ews_status ews_set_state(ews_sim* s, const float* in, int on_device) {
+    if (!s || !in) return fail(EWS_EINVAL, "null argument");
+    const size_t ncell = (size_t)s->ncell();
+    for (int q = 0; q < NFIELD; ++q) {
+        ews_status st = copy_field_in(s, s->fields + q * s->fstride, in + q * ncell, on_device);
+        if (st != EWS_OK) return st;
+    }
+    if (s->psi) CK(cudaMemsetAsync(s->psi, 0, s->psi_floats * sizeof(float), s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return EWS_OK;
+}
+
+}  // extern "C"

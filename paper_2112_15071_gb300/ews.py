@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libews (include/ews.h).
+
+Every function here has the name of the C entry point it marshals to and
+does argument marshalling only: all numerical work runs in the CUDA kernels
+of libews.  There is no CPU fallback: if libews.so is missing or no CUDA
+device is usable, the calls raise.
+
+Arrays may be numpy arrays (host) or torch CUDA tensors (device, passed by
+pointer with on_device = 1).  Shapes follow include/ews.h: 3D arrays are
+[nz][ny][nx] float32, seismograms [3][nrec][nt], state [9][nz][ny][nx].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+EWS_OK, EWS_EINVAL, EWS_ECFL, EWS_ENOMEM, EWS_ECUDA, EWS_ENONFINITE, EWS_ETIMEOUT, \
+    EWS_ESTATE = range(8)
+STATUS_NAMES = ("EWS_OK", "EWS_EINVAL", "EWS_ECFL", "EWS_ENOMEM", "EWS_ECUDA",
+                "EWS_ENONFINITE", "EWS_ETIMEOUT", "EWS_ESTATE")
+EWS_BOUNDARY_NONE, EWS_BOUNDARY_SPONGE, EWS_BOUNDARY_CPML = 0, 1, 2
+EWS_STORAGE_F32, EWS_STORAGE_BF16, EWS_STORAGE_F16 = 0, 1, 2
+EWS_SOURCE_MOMENT, EWS_SOURCE_FORCE = 0, 1
+BOUNDARY = {"none": 0, "sponge": 1, "cpml": 2}
+SOURCE = {"moment": 0, "force": 1}
+FIELDS = ("vx", "vy", "vz", "sxx", "syy", "szz", "sxy", "sxz", "syz")
+
+
+class EwsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class ews_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double)]
+
+
+class ews_options(C.Structure):
+    _fields_ = [("boundary", C.c_int), ("width", C.c_int), ("storage", C.c_int),
+                ("snapshot_every", C.c_int), ("snapshot_mask", C.c_uint),
+                ("sponge_alpha", C.c_double), ("pml_R", C.c_double), ("pml_f0", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/ews.h
+_P, _I, _D, _U = C.c_void_p, C.c_int, C.c_double, C.c_uint
+SIGNATURES = [
+    ("ews_create", _I, [C.POINTER(ews_grid), C.POINTER(ews_options), C.POINTER(_P)]),
+    ("ews_destroy", None, [_P]),
+    ("ews_set_stream", _I, [_P, _P]),
+    ("ews_set_model_lame", _I, [_P, _P, _P, _P, _I]),
+    ("ews_set_model_vel", _I, [_P, _P, _P, _P, _I]),
+    ("ews_set_source", _I, [_P, _I, _P, _P, _P, _I]),
+    ("ews_set_receivers", _I, [_P, _I, _P]),
+    ("ews_run", _I, [_P, _I, _D, _P, _I, _P]),
+    ("ews_advance", _I, [_P, _I, _I, _D, _P, _I, _I]),
+    ("ews_reset", _I, [_P]),
+    ("ews_get_state", _I, [_P, _P, _I]),
+    ("ews_set_state", _I, [_P, _P, _I]),
+    ("ews_cfl_dt", _D, [C.POINTER(ews_grid), _D]),
+    ("ews_max_freq", _D, [C.POINTER(ews_grid), _D]),
+    ("ews_last_error", C.c_char_p, []),
+    ("ews_version", _I, []),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libews.so (building it in-tree if needed).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                if not build_if_missing:
+                    raise OSError(f"libews.so not built ({_build.LIB})")
+                _build.build()
+            lib = C.CDLL(_build.LIB)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != EWS_OK:
+        msg = load().ews_last_error()
+        raise EwsError(status, msg.decode() if msg else "")
+
+
+def _ptr(a, dtype=np.float32):
+    """(pointer, on_device) of a numpy array or torch tensor."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):                      # torch tensor
+        import torch
+        assert a.is_contiguous(), "tensor must be contiguous"
+        want = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        assert a.dtype == want, f"tensor dtype must be {want}"
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda)
+    arr = np.asarray(a)
+    assert arr.dtype == dtype and arr.flags.c_contiguous, \
+        f"array must be C-contiguous {np.dtype(dtype).name}"
+    return arr.ctypes.data_as(C.c_void_p), 0
+
+
+# --- entry points (same names as include/ews.h) ----------------------------
+
+def ews_version() -> int:
+    return load().ews_version()
+
+
+def ews_last_error() -> str:
+    m = load().ews_last_error()
+    return m.decode() if m else ""
+
+
+def ews_cfl_dt(grid: ews_grid, vmax: float) -> float:
+    return load().ews_cfl_dt(C.byref(grid), float(vmax))
+
+
+def ews_max_freq(grid: ews_grid, vmin: float) -> float:
+    return load().ews_max_freq(C.byref(grid), float(vmin))
+
+
+def ews_create(grid: ews_grid, opt: ews_options | None):
+    h = C.c_void_p()
+    _check(load().ews_create(C.byref(grid), C.byref(opt) if opt is not None else None,
+                             C.byref(h)))
+    return h
+
+
+def ews_destroy(sim):
+    if sim:
+        load().ews_destroy(sim)
+
+
+def ews_set_stream(sim, stream_handle: int):
+    _check(load().ews_set_stream(sim, C.c_void_p(stream_handle)))
+
+
+def ews_set_model_lame(sim, lam, mu, rho):
+    (pl, d0), (pm, d1), (pr, d2) = _ptr(lam), _ptr(mu), _ptr(rho)
+    assert d0 == d1 == d2, "model arrays must share residency"
+    _check(load().ews_set_model_lame(sim, pl, pm, pr, d0))
+
+
+def ews_set_model_vel(sim, vp, vs, rho):
+    (pa, d0), (pb, d1), (pr, d2) = _ptr(vp), _ptr(vs), _ptr(rho)
+    assert d0 == d1 == d2, "model arrays must share residency"
+    _check(load().ews_set_model_vel(sim, pa, pb, pr, d0))
+
+
+def ews_set_source(sim, kind: int, pos, comp, wavelet):
+    p = np.ascontiguousarray(pos, np.float64).reshape(3)
+    c = np.zeros(6)
+    cc = np.asarray(comp, np.float64).ravel()
+    c[:cc.size] = cc
+    w = np.ascontiguousarray(wavelet, np.float32).ravel()
+    _check(load().ews_set_source(sim, int(kind), p.ctypes.data_as(C.c_void_p),
+                                 c.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p),
+                                 int(w.size)))
+
+
+def ews_set_receivers(sim, pos):
+    r = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+    _check(load().ews_set_receivers(sim, int(r.shape[0]),
+                                    r.ctypes.data_as(C.c_void_p) if r.size else None))
+
+
+def ews_run(sim, nt: int, dt: float, seis, snapshots=None):
+    ps, dev = _ptr(seis)
+    pn, devn = _ptr(snapshots)
+    if snapshots is not None:
+        assert devn == dev, "seis and snapshots must share residency"
+    _check(load().ews_run(sim, int(nt), float(dt), ps, dev, pn))
+
+
+def ews_advance(sim, n0: int, nsteps: int, dt: float, seis, ld: int):
+    ps, dev = _ptr(seis)
+    _check(load().ews_advance(sim, int(n0), int(nsteps), float(dt), ps, int(ld), dev))
+
+
+def ews_reset(sim):
+    _check(load().ews_reset(sim))
+
+
+def ews_get_state(sim, out):
+    p, dev = _ptr(out)
+    _check(load().ews_get_state(sim, p, dev))
+
+
+def ews_set_state(sim, state):
+    p, dev = _ptr(state)
+    _check(load().ews_set_state(sim, p, dev))
+
+
+# --- convenience object ------------------------------------------------------
+
+class Simulation:
+    """Owns one ews_sim handle.  Mirrors the C calls one to one."""
+
+    def __init__(self, nx, ny, nz, spacing, boundary="sponge", width=16, f0=0.0,
+                 snapshot_every=0, snapshot_mask=0, sponge_alpha=0.0, pml_R=0.0,
+                 storage=EWS_STORAGE_F32):
+        self.grid = ews_grid(int(nx), int(ny), int(nz), *map(float, spacing))
+        self.opt = ews_options(BOUNDARY[boundary] if isinstance(boundary, str) else boundary,
+                               int(width), int(storage), int(snapshot_every),
+                               int(snapshot_mask), float(sponge_alpha), float(pml_R),
+                               float(f0))
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self._h = ews_create(self.grid, self.opt)
+        self.nrec = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            ews_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream_handle: int):
+        ews_set_stream(self._h, stream_handle)
+
+    def set_model_vel(self, vp, vs, rho):
+        ews_set_model_vel(self._h, vp, vs, rho)
+
+    def set_model_lame(self, lam, mu, rho):
+        ews_set_model_lame(self._h, lam, mu, rho)
+
+    def set_source(self, kind, pos, comp, wavelet):
+        ews_set_source(self._h, SOURCE[kind] if isinstance(kind, str) else kind, pos, comp,
+                       wavelet)
+
+    def set_receivers(self, pos):
+        ews_set_receivers(self._h, pos)
+        self.nrec = int(np.asarray(pos).reshape(-1, 3).shape[0])
+
+    def run(self, nt, dt, seis=None, snapshots=None):
+        if seis is None:
+            seis = np.zeros((3, self.nrec, nt), np.float32)
+        ews_run(self._h, nt, dt, seis if self.nrec else None, snapshots)
+        return seis
+
+    def advance(self, n0, nsteps, dt, seis, ld):
+        ews_advance(self._h, n0, nsteps, dt, seis, ld)
+
+    def reset(self):
+        ews_reset(self._h)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((9, self.nz, self.ny, self.nx), np.float32)
+        ews_get_state(self._h, out)
+        return out
+
+    def set_state(self, state):
+        ews_set_state(self._h, state)
+
+
+def simulation_for(prob, **kw) -> Simulation:
+    """Simulation set up from a ``synth.Problem`` (model, source, receivers)."""
+    sim = Simulation(prob.nx, prob.ny, prob.nz, prob.spacing, boundary=prob.boundary,
+                     width=prob.width, f0=prob.f0, **kw)
+    sim.set_model_vel(prob.vp, prob.vs, prob.rho)
+    sim.set_source(prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet)
+    sim.set_receivers(prob.rec_pos)
+    return sim

@@ -1,0 +1,107 @@
+"""C-ABI library: builds, loads without a GPU and exports every entry point
+declared in include/ews.h; host-side validation paths (CPU only)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2112_15071_gb300 import ews
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ews.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ews_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("ews_create", "ews_destroy", "ews_set_model_lame", "ews_set_model_vel",
+              "ews_set_source", "ews_set_receivers", "ews_run", "ews_cfl_dt",
+              "ews_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ews.load()
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+    bound = {name for name, _, _ in ews.SIGNATURES}
+    assert set(declared_symbols()) <= bound
+
+
+def test_binding_names_match_the_abi():
+    for s in declared_symbols():
+        assert callable(getattr(ews, s)), s
+
+
+def test_version_and_time_step_rules():
+    assert ews.ews_version() >= 100
+    g = ews.ews_grid(64, 64, 32, 10.0, 20.0, 5.0)
+    # Eq. 5: 0.495 dx_min / v_max ; Eq. 6: v_min / (5 dx_max)
+    assert ews.ews_cfl_dt(g, 3000.0) == pytest.approx(0.495 * 5.0 / 3000.0, rel=1e-15)
+    assert ews.ews_max_freq(g, 1730.0) == pytest.approx(1730.0 / (5 * 20.0), rel=1e-15)
+    assert ews.ews_cfl_dt(g, 0.0) == 0.0
+
+
+@pytest.mark.parametrize("dims", [(3, 8, 8), (8, 0, 8), (8, 8, -1)])
+def test_create_rejects_bad_grids_before_touching_the_device(dims):
+    g = ews.ews_grid(*dims, 10.0, 10.0, 10.0)
+    with pytest.raises(ews.EwsError) as e:
+        ews.ews_create(g, None)
+    assert e.value.status == ews.EWS_EINVAL
+
+
+def test_create_rejects_bad_options():
+    g = ews.ews_grid(16, 16, 16, 10.0, 10.0, 10.0)
+    for opt in (ews.ews_options(2, 9, 0, 0, 0, 0.0, 0.0, 0.0),      # 2W > n
+                ews.ews_options(7, 2, 0, 0, 0, 0.0, 0.0, 0.0),      # unknown boundary
+                ews.ews_options(1, 0, 0, 0, 0, 0.0, 0.0, 0.0),      # width 0
+                ews.ews_options(1, 2, 0, 0, 1 << 12, 0.0, 0.0, 0.0)):  # bad mask
+        with pytest.raises(ews.EwsError) as e:
+            ews.ews_create(g, opt)
+        assert e.value.status == ews.EWS_EINVAL
+    bad = ews.ews_grid(16, 16, 16, 10.0, -1.0, 10.0)
+    with pytest.raises(ews.EwsError):
+        ews.ews_create(bad, None)
+
+
+def test_null_handles_are_rejected():
+    with pytest.raises(ews.EwsError) as e:
+        ews.ews_run(None, 10, 1e-3, None)
+    assert e.value.status == ews.EWS_EINVAL
+    ews.ews_destroy(None)
+    assert "null" in ews.ews_last_error()
+
+
+def test_cpu_box_has_no_fallback():
+    """Without a usable device, creating a simulation fails loudly."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    g = ews.ews_grid(40, 40, 40, 10.0, 10.0, 10.0)
+    with pytest.raises(ews.EwsError) as e:
+        ews.ews_create(g, None)
+    assert e.value.status == ews.EWS_ECUDA
+
+
+def test_oracle_and_product_share_no_code():
+    """The CUDA package and the oracle never import or include each other."""
+    pkg = os.path.join(ROOT, "paper_2112_15071_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
+                assert "ews_oracle" not in txt and "liborc" not in txt, f
+    orc = os.path.join(ROOT, "oracle")
+    for f in os.listdir(orc):
+        if f.endswith((".py", ".c", ".h")):
+            txt = open(os.path.join(orc, f)).read()
+            assert not re.search(r"^\s*(from|import)\s+paper_2112_15071_gb300", txt, re.M), f
+            assert not re.search(r"#\s*include\s*[<\"].*(ews|csrc)", txt), f
