@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput of the 3D elastic staggered-grid forward loop on one GB300.
+
+One bench *step* is one full forward simulation of the 256^3 workload: 2000
+time steps of the velocity pass, source injection, receiver sampling and
+stress pass with a 20-cell C-PML, on a 5-layer + Gaussian-correlated +-5 %
+synthetic model with a double-couple source (5 Hz Ricker at 2 km depth) and
+16 x 16 receivers.  Metric: Gcell-updates/s (one cell-update = all 9 fields
+of one cell advanced one time step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
+independent replica of the workload (the path has no exchange step), the
+timing is the max over ranks and `value` counts the cells of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s per FP32 elastic step, % of HBM roofline; adjoint grad time / fwd"
+UNIT = "Gcell-updates/s"
+WORKLOAD = ("256^3 grid, dx=20 m, 2000 steps, 20-cell C-PML, 5 layers vp 2000-6000 m/s "
+            "+ Gaussian-correlated +-5% (200 m), Gardner rho, double couple (30,60,90) "
+            "5 Hz Ricker at 2 km, 16x16 receivers")
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=256, help="cube side (default 256)")
+    ap.add_argument("--nt", type=int, default=2000, help="time steps per bench step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# --- distributed plumbing ----------------------------------------------------
+
+def dist_setup(want: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --- clocks ------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={CLOCK_QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r[2] > 150.0] or rows
+        reasons = sorted({REASONS[i] for r in load for i, v in enumerate(r[3])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(load), "power_w_max": max(r[2] for r in rows),
+                "reasons": reasons}
+
+
+# --- roofline bookkeeping ----------------------------------------------------
+
+def algorithmic_bytes(prob):
+    """Minimal DRAM bytes per launch of each pass (FP32):
+    velocity: read 6 sigma + rho, read+write 3 v           = 13 floats / cell
+    stress:   read 3 v + lambda + mu, read+write 6 sigma   = 17 floats / cell
+    C-PML: each pass reads and writes 3 memory variables per damped direction
+    of every slab cell (24 B per cell-direction and pass)."""
+    n = prob.nx * prob.ny * prob.nz
+    W = prob.width if prob.boundary == "cpml" else 0
+    slab = 2 * W * (prob.ny * prob.nz + prob.nx * prob.nz + prob.nx * prob.ny)
+    return {"velocity": 52 * n + 24 * slab, "stress": 68 * n + 24 * slab,
+            "step_min": 84 * n + 48 * slab, "slab_cell_dirs": slab}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2112_15071_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, workload_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    prof = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(prof):
+        return None
+    sha = kernel_source_sha()
+    pat = re.compile(r"bench-traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+sha=(\S+)\s+"
+                     r"bytes_per_launch=([0-9.eE+]+)")
+    for f in sorted(os.listdir(prof)):
+        if not f.endswith((".md", ".txt")):
+            continue
+        for m in pat.finditer(open(os.path.join(prof, f)).read()):
+            if m.group(1) == kernel and m.group(2) == workload_tag and m.group(3) == sha:
+                return float(m.group(4))
+    return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --- CPU baseline: the FP64 oracle as it stands ------------------------------
+
+def cpu_oracle_rate(prob, seconds: float):
+    """Time the oracle on the host cores on a bounded sample of the workload
+    (the full grid, a number of time steps sized to ~`seconds`)."""
+    from oracle import oracle
+    oracle.build()
+    s = oracle.OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
+    s.set_medium_vel(prob.vp, prob.vs, prob.rho)
+    s.set_boundary(prob.boundary, prob.width, prob.dt, prob.f0)
+    t0 = time.perf_counter()
+    s.forward(2, prob.dt, prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet,
+              prob.rec_pos)
+    per = (time.perf_counter() - t0) / 2
+    nsteps = max(2, min(prob.nt - 2, int(seconds / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    s.forward(nsteps, prob.dt, prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet,
+              prob.rec_pos)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": prob.ncell * nsteps / el / 1e9, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 oracle, full {prob.nx}^3 grid with C-PML, first {nsteps} of "
+                      f"{prob.nt} time steps ({el:.1f} s)"}
+
+
+# --- our arm ------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2112_15071_gb300 import ews, synth
+
+    prob = synth.config2(n=args.n, nt=args.nt)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sim = ews.simulation_for(prob)
+    sim.set_stream(stream.cuda_stream)
+    seis = torch.zeros((3, sim.nrec, prob.nt), device=dev)
+    for _ in range(args.warmup):
+        sim.run(prob.nt, prob.dt, seis)
+    torch.cuda.synchronize()
+    sim.profile(reset=True)
+    sim.set_profiling(True)
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        sim.run(prob.nt, prob.dt, seis)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(t_start.elapsed_time(t_end), world)
+    kms, klaunch = sim.profile(reset=True)
+    sim.set_profiling(False)
+    cells = prob.ncell * prob.nt
+    value = world * cells * args.steps / (ms / 1e3) / 1e9
+
+    # dominant kernel and its roofline
+    names = ews.KERNEL_NAMES
+    dom = int(np.argmax(kms[:len(names)]))
+    alg = algorithmic_bytes(prob)
+    avg_ms = kms[dom] / max(klaunch[dom], 1)
+    dom_bytes = alg.get(names[dom], 0)
+    peak, peak_kind = peaks()
+    achieved = dom_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    traffic = committed_traffic(f"k_{names[dom]}", f"{prob.nx}cube_cpml")
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": f"k_{names[dom]}", "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": dom_bytes,
+            "avg_launch_ms": round(avg_ms, 5)}
+    step_ms = ms / args.steps
+    # whole time step against the fused minimum (84 B per cell-update plus
+    # the C-PML memory variables), per GPU
+    whole_gbs = alg["step_min"] * prob.nt / (step_ms / 1e3) / 1e9
+    whole = {"algorithmic_bytes_per_time_step": alg["step_min"],
+             "achieved_gbs": round(whole_gbs, 1), "frac": round(whole_gbs / peak, 4)}
+    kernel_share = {names[k]: round(kms[k] / max(kms.sum(), 1e-12), 4)
+                    for k in range(len(names)) if klaunch[k]}
+
+    # end to end through the public API with host buffers (pinned)
+    vp = torch.from_numpy(prob.vp).pin_memory().numpy()
+    vs = torch.from_numpy(prob.vs).pin_memory().numpy()
+    rho = torch.from_numpy(prob.rho).pin_memory().numpy()
+    seis_host = torch.zeros((3, sim.nrec, prob.nt), dtype=torch.float32).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_model_vel(vp, vs, rho)
+        sim.run(prob.nt, prob.dt, seis_host)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * cells * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(3 * prob.vp.nbytes),
+           "d2h_bytes_per_step": int(seis_host.nbytes),
+           "steps": e2e_steps, "api": "ews_set_model_vel + ews_run (host buffers)"}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded layered + random model)",
+        "config": {"workload": WORKLOAD, "grid": [prob.nx, prob.ny, prob.nz], "nt": prob.nt,
+                   "dx_m": prob.spacing[0], "boundary": "cpml", "width": prob.width,
+                   "receivers": int(sim.nrec), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (9 fields + 3 medium arrays = 768 MiB "
+                         "resident, 129 MB L2)"},
+        "roofline": roof, "whole_step": whole, "kernel_share": kernel_share,
+        "gpu_launches": int(klaunch.sum()) * world,
+        "e2e": e2e, "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
+    sim.close()
+    return out
+
+
+# --- reference arm: the FP64 oracle on the host cores -------------------------
+
+def run_reference(args, world, rank):
+    from paper_2112_15071_gb300 import synth
+    from oracle import oracle
+    prob = synth.config2(n=args.n, nt=args.nt)
+    oracle.build()
+    s = oracle.OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
+    s.set_medium_vel(prob.vp, prob.vs, prob.rho)
+    s.set_boundary(prob.boundary, prob.width, prob.dt, prob.f0)
+    # each step: a bounded sample of the workload (first few time steps of
+    # the full grid), so the whole run stays within a few minutes
+    t0 = time.perf_counter()
+    s.forward(1, prob.dt, prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet,
+              prob.rec_pos)
+    per = time.perf_counter() - t0
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    sample = max(1, min(20, int(budget / max(per, 1e-6))))
+    for _ in range(args.warmup):
+        s.forward(sample, prob.dt, prob.src_kind, prob.src_pos, prob.src_comp,
+                  prob.wavelet, prob.rec_pos)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.forward(sample, prob.dt, prob.src_kind, prob.src_pos, prob.src_comp,
+                  prob.wavelet, prob.rec_pos)
+    el = time.perf_counter() - t0
+    value = prob.ncell * sample * args.steps / el / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"FP64 oracle on host cores, full {prob.nx}^3 grid with C-PML, {sample} of "
+            f"{prob.nt} time steps per bench step")
+    return {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded layered + random model)", "impl": "reference",
+            "config": {"workload": WORKLOAD, "grid": [prob.nx, prob.ny, prob.nz],
+                       "nt": prob.nt, "sample_steps": sample},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return 0
+    world, rank, local = dist_setup(args.gpus)
+    out = run_ours(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

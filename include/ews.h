@@ -152,6 +152,25 @@ ews_status ews_reset(ews_sim* sim);
 ews_status ews_get_state(ews_sim* sim, float* out, int on_device);
 ews_status ews_set_state(ews_sim* sim, const float* in, int on_device);
 
+/* Kernel classes for launch counting and timing. */
+enum {
+    EWS_KERNEL_VELOCITY = 0,   /* velocity pass, Eq. 1 (+ absorbing edge)      */
+    EWS_KERNEL_STRESS = 1,     /* stress pass, Eq. 2 (+ absorbing edge)        */
+    EWS_KERNEL_INJECT = 2,     /* point-source injection                       */
+    EWS_KERNEL_RECORD = 3,     /* receiver sampling, Sec. 2.4                  */
+    EWS_NKERNEL = 8
+};
+
+/* When on, every kernel launch of the simulation is bracketed by CUDA
+ * events on its stream and its duration accumulated per class.  Launch
+ * counts are accumulated whether or not timing is on. */
+ews_status ews_set_profiling(ews_sim* sim, int on);
+
+/* Accumulated milliseconds and launch counts per kernel class since the
+ * last reset (arrays of EWS_NKERNEL entries; either may be NULL).  If reset
+ * is nonzero the accumulators are zeroed after reading. */
+ews_status ews_get_profile(ews_sim* sim, double* ms, long long* launches, int reset);
+
 /* Time-step rule of Sec. 2.1.3, Eq. 5: 0.495 min(dx, dy, dz) / vmax. */
 double ews_cfl_dt(const ews_grid* grid, double vmax);
 

@@ -78,7 +78,16 @@ struct ews_sim {
     float* seis_buf = nullptr;    // internal [3][nrec][cap] when caller is on host
     size_t seis_cap = 0;
     unsigned* flags = nullptr;    // device scratch for medium checks
+    int* err = nullptr;           // device flag: bounded waits that gave up
+    StencilPlan* plan = nullptr;
     cudaStream_t stream = nullptr;
+    // launch accounting and optional per-launch event timing
+    long long launches[EWS_NKERNEL] = {};
+    double kernel_ms[EWS_NKERNEL] = {};
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;     // reused across calls
+    std::vector<int> ev_class;            // class of the launch ending at event m
+    size_t ev_used = 0;
 
     DevFields F() const {
         DevFields f;
@@ -254,6 +263,23 @@ ews_status ensure_ready(ews_sim* s, int n_end, double dt) {
     return EWS_OK;
 }
 
+// Account one launch of class cls (or open a bracket when cls < 0); with
+// profiling on, record an event after it on the simulation's stream.
+ews_status mark(ews_sim* s, int cls) {
+    if (cls >= 0) s->launches[cls] += 1;
+    if (!s->profiling) return EWS_OK;
+    if (s->ev_used == s->ev_pool.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        s->ev_pool.push_back(e);
+        s->ev_class.push_back(-1);
+    }
+    s->ev_class[s->ev_used] = cls;
+    CK(cudaEventRecord(s->ev_pool[s->ev_used], s->stream));
+    ++s->ev_used;
+    return EWS_OK;
+}
+
 ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
                  float* dseis, int ld) {
     DevFields F = s->F();
@@ -280,16 +306,39 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
         }
     }
     const float fdt = (float)dt;
+    ews_status st;
+    if ((st = mark(s, -1)) != EWS_OK) return st;
     for (int n = n0; n < n0 + nsteps; ++n) {
-        CK(launch_velocity(s->g, F, M, s->B, fdt, s->stream));
-        if (S.kind == EWS_SOURCE_FORCE)
+        CK(launch_velocity(s->plan, s->g, F, s->B, fdt, s->err, s->stream));
+        if ((st = mark(s, EWS_KERNEL_VELOCITY)) != EWS_OK) return st;
+        if (S.kind == EWS_SOURCE_FORCE) {
             CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, s->stream));
-        if (s->nrec > 0 && dseis)
+            if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
+        }
+        if (s->nrec > 0 && dseis) {
             CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, s->stream));
-        CK(launch_stress(s->g, F, M, s->B, fdt, s->stream));
-        if (S.kind == EWS_SOURCE_MOMENT)
+            if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
+        }
+        CK(launch_stress(s->plan, s->g, F, s->B, fdt, s->err, s->stream));
+        if ((st = mark(s, EWS_KERNEL_STRESS)) != EWS_OK) return st;
+        if (S.kind == EWS_SOURCE_MOMENT) {
             CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, s->stream));
+            if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
+        }
     }
+    return EWS_OK;
+}
+
+// Collect the durations of the launches bracketed since the last collect
+// (the stream must have been synchronised).
+ews_status collect_profile(ews_sim* s) {
+    for (size_t m = 1; m < s->ev_used; ++m) {
+        if (s->ev_class[m] < 0) continue;
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, s->ev_pool[m - 1], s->ev_pool[m]));
+        s->kernel_ms[s->ev_class[m]] += ms;
+    }
+    s->ev_used = 0;
     return EWS_OK;
 }
 
@@ -379,24 +428,24 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "profiles: %s", cudaGetErrorString(e)));
     e = cudaMalloc(&s->flags, 2 * sizeof(unsigned));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "flags: %s", cudaGetErrorString(e)));
+    e = cudaMalloc(&s->err, sizeof(int));
+    if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "err: %s", cudaGetErrorString(e)));
     if (o.boundary == EWS_BOUNDARY_CPML) {
-        const size_t W2 = 2 * (size_t)o.width;
-        const size_t sx = W2 * g.ny * g.nz, sy = (size_t)g.pitch * W2 * g.nz,
-                     sz = (size_t)g.pitch * g.ny * W2;
-        s->psi_floats = 6 * (sx + sy + sz);
+        s->psi_floats = 18 * s->fstride;
         e = cudaMalloc(&s->psi, s->psi_floats * sizeof(float));
         if (e != cudaSuccess)
             return cleanup(fail(EWS_ENOMEM, "C-PML memory: %s", cudaGetErrorString(e)));
-        float* p = s->psi;
-        for (int t = 0; t < 6; ++t) { s->B.psx[t] = p; p += sx; }
-        for (int t = 0; t < 6; ++t) { s->B.psy[t] = p; p += sy; }
-        for (int t = 0; t < 6; ++t) { s->B.psz[t] = p; p += sz; }
+        for (int t = 0; t < 18; ++t) s->B.psi[t] = s->psi + t * s->fstride;
     }
     e = cudaMemset(s->fields, 0, NFIELD * s->fstride * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(s->medium, 0, 3 * s->fstride * sizeof(float));
     if (e == cudaSuccess && s->psi) e = cudaMemset(s->psi, 0, s->psi_floats * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup(fail(EWS_ECUDA, "memset: %s", cudaGetErrorString(e)));
+    e = stencil_plan_create(s->g, s->F(), s->M(), s->B, &s->plan);
+    if (e != cudaSuccess)
+        return cleanup(fail(EWS_ECUDA, "stencil plan (TMA descriptors): %s", cudaGetErrorString(e)));
     *out = s;
     return EWS_OK;
 }
@@ -409,10 +458,13 @@ void ews_destroy(ews_sim* s) {
     cudaFree(s->medium);
     cudaFree(s->prof);
     cudaFree(s->flags);
+    cudaFree(s->err);
+    stencil_plan_destroy(s->plan);
     cudaFree(s->psi);
     cudaFree(s->wavelet);
     cudaFree(s->rtaps);
     cudaFree(s->seis_buf);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     delete s;
 }
 
@@ -523,8 +575,16 @@ ews_status ews_advance(ews_sim* s, int n0, int nsteps, double dt, float* seis, i
                              nsteps * sizeof(float), 3 * (size_t)s->nrec,
                              cudaMemcpyDeviceToHost, s->stream));
     }
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
+    if (herr) {
+        CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+        return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up (flags %d)",
+                    herr);
+    }
+    if (s->profiling && (st = collect_profile(s)) != EWS_OK) return st;
     return EWS_OK;
 }
 
@@ -557,6 +617,26 @@ ews_status ews_run(ews_sim* s, int nt, double dt, float* seis, int seis_on_devic
     if (done < nt && (st = ews_advance(s, done, nt - done, dt, seis, nt, seis_on_device)) != EWS_OK)
         return st;
     CK(cudaStreamSynchronize(s->stream));
+    return EWS_OK;
+}
+
+ews_status ews_set_profiling(ews_sim* s, int on) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    s->profiling = on != 0;
+    s->ev_used = 0;
+    return EWS_OK;
+}
+
+ews_status ews_get_profile(ews_sim* s, double* ms, long long* launches, int reset) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    for (int k = 0; k < EWS_NKERNEL; ++k) {
+        if (ms) ms[k] = s->kernel_ms[k];
+        if (launches) launches[k] = s->launches[k];
+        if (reset) {
+            s->kernel_ms[k] = 0.0;
+            s->launches[k] = 0;
+        }
+    }
     return EWS_OK;
 }
 

@@ -9,8 +9,9 @@
 //   * lambda, mu, rho per cell in a second allocation, same layout.  The
 //     staggered-point means of Sec. 2.2.1 are formed in registers by the
 //     stencil kernels; nothing else about the medium is stored.
-//   * C-PML memory variables only inside the damping slabs (6 per axis):
-//       x slabs [nz][ny][2W], y slabs [nz][2W][pitch], z slabs [2W][ny][pitch].
+//   * C-PML memory variables: 18 arrays with the field layout (6 per damped
+//       direction); only slab cells are used, so stencil tiles can bring
+//       them in with the same TMA boxes as the fields.
 //   * seismograms [3][nrec][nt] float32; wavelet [nt] float32.
 #pragma once
 #include <cuda_runtime.h>
@@ -45,10 +46,11 @@ struct DevBoundary {
     const float* g[3];    // sponge profile per axis, length n_axis
     const float* pa[3];   // C-PML a(i) per axis
     const float* pb[3];   // C-PML b(i) per axis
-    // memory variables, index 0..2 velocity terms, 3..5 stress terms
-    float* psx[6];
-    float* psy[6];
-    float* psz[6];
+    // C-PML memory variables, full-size and pitched like the fields:
+    // psi[6 * d + t], d = damped direction (x, y, z), t = 0..2 velocity-pass
+    // terms, 3..5 stress-pass terms.  Only cells inside the slab of
+    // direction d are ever read or written.
+    float* psi[18];
 };
 
 // One injection or sampling tap: field q, element (i, j, k), weight w.
@@ -65,11 +67,18 @@ struct DevSource {
     Tap tap[kMaxSrcTaps]; // w already holds -dt M_c w_tri / V or dt F_c w_tri / V
 };
 
-// Launchers (ews_forward.cu).  All run on `st`.
-cudaError_t launch_velocity(const DevGrid& g, const DevFields& F, const DevMedium& M,
-                            const DevBoundary& B, float dt, cudaStream_t st);
-cudaError_t launch_stress(const DevGrid& g, const DevFields& F, const DevMedium& M,
-                          const DevBoundary& B, float dt, cudaStream_t st);
+// Stencil passes (ews_stencil.cu): TMA tensor maps and launch geometry are
+// built once per simulation (the field and medium addresses never change).
+struct StencilPlan;
+cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevMedium& M,
+                                const DevBoundary& B, StencilPlan** out);
+void stencil_plan_destroy(StencilPlan* p);
+cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
+                            const DevBoundary& B, float dt, int* err, cudaStream_t st);
+cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
+                          const DevBoundary& B, float dt, int* err, cudaStream_t st);
+
+// Sources, receivers and medium set-up (ews_forward.cu).  All run on `st`.
 cudaError_t launch_inject(const DevGrid& g, const DevFields& F, const DevMedium& M,
                           const DevBoundary& B, const DevSource& S, const float* wavelet,
                           int n, cudaStream_t st);

@@ -26,6 +26,9 @@ STATUS_NAMES = ("EWS_OK", "EWS_EINVAL", "EWS_ECFL", "EWS_ENOMEM", "EWS_ECUDA",
 EWS_BOUNDARY_NONE, EWS_BOUNDARY_SPONGE, EWS_BOUNDARY_CPML = 0, 1, 2
 EWS_STORAGE_F32, EWS_STORAGE_BF16, EWS_STORAGE_F16 = 0, 1, 2
 EWS_SOURCE_MOMENT, EWS_SOURCE_FORCE = 0, 1
+EWS_KERNEL_VELOCITY, EWS_KERNEL_STRESS, EWS_KERNEL_INJECT, EWS_KERNEL_RECORD = 0, 1, 2, 3
+EWS_NKERNEL = 8
+KERNEL_NAMES = ("velocity", "stress", "inject", "record")
 BOUNDARY = {"none": 0, "sponge": 1, "cpml": 2}
 SOURCE = {"moment": 0, "force": 1}
 FIELDS = ("vx", "vy", "vz", "sxx", "syy", "szz", "sxy", "sxz", "syz")
@@ -67,6 +70,8 @@ SIGNATURES = [
     ("ews_reset", _I, [_P]),
     ("ews_get_state", _I, [_P, _P, _I]),
     ("ews_set_state", _I, [_P, _P, _I]),
+    ("ews_set_profiling", _I, [_P, _I]),
+    ("ews_get_profile", _I, [_P, _P, _P, _I]),
     ("ews_cfl_dt", _D, [C.POINTER(ews_grid), _D]),
     ("ews_max_freq", _D, [C.POINTER(ews_grid), _D]),
     ("ews_last_error", C.c_char_p, []),
@@ -209,6 +214,19 @@ def ews_set_state(sim, state):
     _check(load().ews_set_state(sim, p, dev))
 
 
+def ews_set_profiling(sim, on: bool):
+    _check(load().ews_set_profiling(sim, int(bool(on))))
+
+
+def ews_get_profile(sim, reset: bool = False):
+    """(ms[EWS_NKERNEL], launches[EWS_NKERNEL]) accumulated per kernel class."""
+    ms = np.zeros(EWS_NKERNEL, np.float64)
+    n = np.zeros(EWS_NKERNEL, np.int64)
+    _check(load().ews_get_profile(sim, ms.ctypes.data_as(C.c_void_p),
+                                  n.ctypes.data_as(C.c_void_p), int(bool(reset))))
+    return ms, n
+
+
 # --- convenience object ------------------------------------------------------
 
 class Simulation:
@@ -269,6 +287,12 @@ class Simulation:
 
     def reset(self):
         ews_reset(self._h)
+
+    def set_profiling(self, on=True):
+        ews_set_profiling(self._h, on)
+
+    def profile(self, reset=False):
+        return ews_get_profile(self._h, reset)
 
     def get_state(self, out=None):
         if out is None:

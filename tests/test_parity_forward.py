@@ -46,13 +46,21 @@ def check_state(got, want, tol=TOL):
 
 
 def test_config1_seismograms(ews, orc):
-    """64^3 homogeneous, sponge 16, explosion, 8 receivers, 500 steps."""
+    """64^3 homogeneous, sponge 16, explosion, 8 receivers, 500 steps.
+    Wavefields are compared at every 100th step against each field's peak
+    norm over the run (late in the run the wave has left the grid and the
+    remaining field is small, so its own norm is not a useful scale)."""
     p = synth.config1()
-    want, osim = orc.run_problem(p, return_sim=True)
-    got, sim = gpu_run(ews, p)
+    want, osnap = orc.run_problem(p, snap_every=100, snap_mask=0x1FF)
+    sim = ews.simulation_for(p, snapshot_every=100, snapshot_mask=0x1FF)
+    snaps = np.zeros((5, 9, p.nz, p.ny, p.nx), np.float32)
+    got = sim.run(p.nt, p.dt, snapshots=snaps)
     assert np.abs(want).max() > 0
     assert rel_l2(got, want) <= TOL, rel_l2(got, want)
-    check_state(sim.get_state(), osim.get_state())
+    for q in range(9):
+        peak = max(np.linalg.norm(osnap[s, q]) for s in range(5))
+        worst = max(np.linalg.norm(snaps[s, q] - osnap[s, q]) for s in range(5))
+        assert worst <= TOL * peak, (q, worst / peak)
 
 
 @pytest.mark.parametrize("dims", [(70, 45, 37), (33, 65, 40), (96, 24, 50)])
@@ -167,6 +175,19 @@ def test_device_buffers_match_host_buffers(ews):
     sim.run(p.nt, p.dt, seis)
     torch.cuda.synchronize()
     assert np.array_equal(seis.cpu().numpy(), a)
+
+
+def test_launch_accounting_and_profiling(ews):
+    p = synth.small_problem(40, 36, 28, nt=50, boundary="cpml", width=6)
+    sim = ews.simulation_for(p)
+    sim.set_profiling(True)
+    sim.run(p.nt, p.dt)
+    ms, n = sim.profile(reset=True)
+    assert n[ews.EWS_KERNEL_VELOCITY] == 50 and n[ews.EWS_KERNEL_STRESS] == 50
+    assert n[ews.EWS_KERNEL_RECORD] == 50 and n[ews.EWS_KERNEL_INJECT] == 50
+    assert ms[ews.EWS_KERNEL_STRESS] > 0 and ms[ews.EWS_KERNEL_VELOCITY] > 0
+    ms2, n2 = sim.profile()
+    assert n2.sum() == 0 and ms2.sum() == 0
 
 
 def test_errors_are_reported(ews):
