@@ -35,13 +35,13 @@ namespace ews {
 namespace {
 
 #ifndef EWS_TILE_Y
-#define EWS_TILE_Y 16
-#endif
-#ifndef EWS_MIN_BLOCKS
-#define EWS_MIN_BLOCKS 2
+#define EWS_TILE_Y 8
 #endif
 #ifndef EWS_ROWS
 #define EWS_ROWS 1
+#endif
+#ifndef EWS_WAVES
+#define EWS_WAVES 4
 #endif
 constexpr int TX = 32, TY = EWS_TILE_Y;
 constexpr int HX = TX + 8, HY = TY + 4;          // halo box
@@ -53,20 +53,22 @@ constexpr int ROWS = EWS_ROWS;                    // cells per thread (adjacent 
 constexpr int RY = TY / ROWS;                     // thread rows
 constexpr int NTH = TX * RY;                      // threads per CTA
 // one slot holds every tile of one plane: velocity 6 halo + 4 core,
-// stress 4 halo + 7 core, and with C-PML up to 9 core tiles of memory
-// variables (3 terms for each damped direction the tile-plane touches)
+// stress 4 halo + 7 core
 constexpr int SLOT_MAIN = (6 * HALO + 4 * CORE) > (4 * HALO + 7 * CORE)
                               ? (6 * HALO + 4 * CORE) : (4 * HALO + 7 * CORE);
 static_assert((SLOT_MAIN * 4) % 128 == 0 && (HALO * 4) % 128 == 0 && (CORE * 4) % 128 == 0,
               "TMA destinations must stay 128-byte aligned");
 static_assert(TY % ROWS == 0, "rows per thread must divide the tile height");
 template <int BND>
-__host__ __device__ constexpr int slot_floats() {
-    return SLOT_MAIN + (BND == BND_CPML ? 9 * CORE : 0);
-}
+__host__ __device__ constexpr int slot_floats() { return SLOT_MAIN; }
+// C-PML memory variables of the output plane live in one extra buffer of 9
+// core tiles (3 terms for each damped direction), refilled for the next
+// output plane as soon as the current one has been consumed.
+constexpr int PSI_FLOATS = 9 * CORE;
 template <int BND>
 constexpr size_t smem_bytes() {
-    return NSLOT * slot_floats<BND>() * sizeof(float) + 8 * NSLOT;
+    return (NSLOT * SLOT_MAIN + (BND == BND_CPML ? PSI_FLOATS : 0)) * sizeof(float) +
+           8 * (NSLOT + 1);
 }
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
@@ -143,29 +145,29 @@ struct PassParams {
     int* err;
 };
 
-// Issue the TMA loads of z-plane `z` of tile (x0, y0) into `slot`; with
-// C-PML also the memory-variable tiles of the damped directions in `dirs`
-// (bit d = direction d).
-template <int NH, int NC, int BND>
+// Issue the TMA loads of z-plane `z` of tile (x0, y0) into `slot`.
+template <int NH, int NC>
 __device__ __forceinline__ void issue_plane(const Maps& m, float* slot, uint64_t* bar, int x0,
-                                            int y0, int z, unsigned dirs) {
-    uint32_t bytes = (NH * HALO + NC * CORE) * (uint32_t)sizeof(float);
-    if (BND == BND_CPML) bytes += __popc(dirs) * 3 * CORE * (uint32_t)sizeof(float);
-    mbar_expect_tx(bar, bytes);
+                                            int y0, int z) {
+    mbar_expect_tx(bar, (NH * HALO + NC * CORE) * (uint32_t)sizeof(float));
 #pragma unroll
     for (int h = 0; h < NH; ++h) tma_load_3d(slot + h * HALO, &m.halo[h], bar, x0 - 4, y0 - 2, z);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
         tma_load_3d(slot + NH * HALO + c * CORE, &m.core[c], bar, x0, y0, z);
-    if (BND == BND_CPML) {
+}
+
+// Issue the TMA loads of the C-PML memory variables of plane `z` for the
+// damped directions in `dirs` (bit d = direction d) into `buf`.
+__device__ __forceinline__ void issue_psi(const Maps& m, float* buf, uint64_t* bar, int x0, int y0,
+                                          int z, unsigned dirs) {
+    mbar_expect_tx(bar, __popc(dirs) * 3 * CORE * (uint32_t)sizeof(float));
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            if ((dirs >> d) & 1u)
+    for (int d = 0; d < 3; ++d)
+        if ((dirs >> d) & 1u)
 #pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    tma_load_3d(slot + SLOT_MAIN + (3 * d + q) * CORE, &m.psi[3 * d + q], bar, x0,
-                                y0, z);
-    }
+            for (int q = 0; q < 3; ++q)
+                tma_load_3d(buf + (3 * d + q) * CORE, &m.psi[3 * d + q], bar, x0, y0, z);
 }
 
 __device__ __forceinline__ bool in_slab(int i, int n, int W) { return i < W || i >= n - W; }
@@ -173,7 +175,7 @@ __device__ __forceinline__ int slab_idx(int i, int n, int W) { return i < W ? i 
 
 __device__ __forceinline__ void ring_init(uint64_t* bars, int tid) {
     if (tid == 0) {
-        for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s <= NSLOT; ++s) mbar_init(&bars[s], 1);   // ring + psi buffer
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -182,8 +184,10 @@ __device__ __forceinline__ void ring_init(uint64_t* bars, int tid) {
 
 // Bounded-failure exit: record, wait for the loads still in flight
 // (planes m .. issued - 1 of the chunk), leave.
-__device__ __noinline__ void fail_exit(int* err, int bit, uint64_t* bars, int m, int issued) {
+__device__ __noinline__ void fail_exit(int* err, int bit, uint64_t* bars, int m, int issued,
+                                       bool psi_pending, uint32_t psi_parity) {
     atomicOr(err, bit);
+    if (psi_pending && !mbar_wait(&bars[NSLOT], psi_parity)) return;
     for (int q = m; q < issued; ++q)
         if (!mbar_wait(&bars[q & (NSLOT - 1)], (uint32_t)((q >> 2) & 1))) return;
 }
@@ -196,6 +200,7 @@ struct Geo {
     bool own[ROWS], sy[ROWS], sx;
     int cy[ROWS];
     float gx, gy[ROWS];
+    float pax, pbx, pay[ROWS], pby[ROWS];            // C-PML a, b of the x and y slabs
     long long obase;                                  // j0 * pitch + i
 
     __device__ __forceinline__ Geo(const PassParams& P) {
@@ -221,6 +226,8 @@ struct Geo {
         }
         sx = BND == BND_CPML && in_slab(i, g.nx, W);
         gx = (BND == BND_SPONGE && i < g.nx) ? __ldg(P.B.g[0] + i) : 1.0f;
+        pax = sx ? __ldg(P.B.pa[0] + i) : 0.f;
+        pbx = sx ? __ldg(P.B.pb[0] + i) : 0.f;
         obase = (long long)j0 * g.pitch + i;
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
@@ -229,6 +236,8 @@ struct Geo {
             cy[rr] = (j + 1 < g.ny) ? HX : 0;
             sy[rr] = BND == BND_CPML && in_slab(j, g.ny, W);
             gy[rr] = (BND == BND_SPONGE && own[rr]) ? __ldg(P.B.g[1] + j) : 1.0f;
+            pay[rr] = sy[rr] ? __ldg(P.B.pa[1] + j) : 0.f;
+            pby[rr] = sy[rr] ? __ldg(P.B.pb[1] + j) : 0.f;
         }
     }
     // damped directions whose memory variables plane z needs
@@ -261,13 +270,20 @@ struct VelQ {
 // the CTA must stop (a wait gave up).
 template <int BND, int PH>
 __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, const Geo<BND>& G,
-                                         VelQ<BND>& Q, float* sm, uint64_t* bars, int m) {
+                                         VelQ<BND>& Q, float* sm, uint64_t* bars, int m,
+                                         uint32_t& psi_n) {
     const DevGrid& g = P.g;
     constexpr int SF = slot_floats<BND>();
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
     const int k = G.z0 - 4 + m;                                    // output plane
     const bool out = m >= 4;
-    const bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
+    // per-plane boundary coefficients of the output plane, fetched before the wait
+    const bool sz = BND == BND_CPML && out && in_slab(k, g.nz, G.W);
+    const float paz = sz ? __ldg(P.B.pa[2] + k) : 0.f, pbz = sz ? __ldg(P.B.pb[2] + k) : 0.f;
+    const float G3 = (BND == BND_SPONGE && out) ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
+    const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;   // damped dirs of k
+    bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
+    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
     const float* sl0 = sm + S0 * SF;
     const float* sl1 = sm + S1 * SF;
     // push own-column values: sigma_zz of plane p, sigma_xz / sigma_yz of p - 1
@@ -290,9 +306,6 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, 
         const float* hr = sk + VH_RHO * HALO;
         const float* hr1 = sl1 + VH_RHO * HALO + G.hc;            // plane k + 1
         const float* vc = sm + S2 * SF + 6 * HALO + G.cc;
-        const float G3 = BND == BND_SPONGE ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
-        const bool sz = BND == BND_CPML && in_slab(k, g.nz, G.W);
-        const float paz = sz ? __ldg(P.B.pa[2] + k) : 0.f, pbz = sz ? __ldg(P.B.pb[2] + k) : 0.f;
         const bool ktop = k + 1 < g.nz;
         const long long o = (long long)k * g.plane + G.obase;
 #pragma unroll
@@ -316,16 +329,16 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, 
             float dzz = g.c1z * (qzz[C] - qzz[B]) + g.c2z * (qzz[D] - qzz[A]);
             if (BND == BND_CPML) {
                 // memory variables of plane k from the slot, updated, stored
-                const float* ps = sm + S2 * SF + SLOT_MAIN + G.cc + rr * TX;
+                const float* ps = sm + NSLOT * SLOT_MAIN + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
-                    pml_upd(p0, p1, p2, __ldg(P.B.pa[0] + G.i), __ldg(P.B.pb[0] + G.i), dxx, dyx, dzx);
+                    pml_upd(p0, p1, p2, G.pax, G.pbx, dxx, dyx, dzx);
                     P.B.psi[0][oo] = p0; P.B.psi[1][oo] = p1; P.B.psi[2][oo] = p2;
                 }
                 if (G.sy[rr]) {
                     float p0 = ps[3 * CORE], p1 = ps[4 * CORE], p2 = ps[5 * CORE];
-                    pml_upd(p0, p1, p2, __ldg(P.B.pa[1] + G.j0 + rr), __ldg(P.B.pb[1] + G.j0 + rr),
+                    pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr],
                             dxy, dyy, dzy);
                     P.B.psi[6][oo] = p0; P.B.psi[7][oo] = p1; P.B.psi[8][oo] = p2;
                 }
@@ -355,38 +368,56 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, 
     }
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && threadIdx.y == 0)
-            fail_exit(P.err, 1, bars, m, min(G.P4, max(NSLOT, m + 2)));
+            fail_exit(P.err, 1, bars, m, min(G.P4, max(NSLOT, m + 2)), kd != 0u, psi_n & 1u);
         return false;
+    }
+    if (BND == BND_CPML) {
+        if (kd) ++psi_n;
+        // the psi buffer is free: fetch the memory variables of the next output plane
+        const int kn = k + 1;
+        if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
+            const unsigned dn = G.dirs(kn, g.nz);
+            if (dn) issue_psi(maps, sm + NSLOT * SLOT_MAIN, &bars[NSLOT], G.x0, G.y0, kn, dn);
+        }
     }
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_plane<6, 4, BND>(maps, sm + S2 * SF, &bars[S2], G.x0, G.y0, G.z0 + m,
-                               G.dirs(G.z0 + m, g.nz));
+        issue_plane<6, 4>(maps, sm + S2 * SF, &bars[S2], G.x0, G.y0, G.z0 + m);
     return true;
 }
 
+// CTAs per SM that the shared-memory footprint allows; the register budget of
+// the kernels is sized for exactly that many.
 template <int BND>
-__global__ void __launch_bounds__(NTH, EWS_MIN_BLOCKS) k_velocity(const __grid_constant__ Maps maps,
+constexpr int min_blocks() {
+    return (227 * 1024) / (int)(smem_bytes<BND>() + 1024) < 1   ? 1
+           : (227 * 1024) / (int)(smem_bytes<BND>() + 1024) > 4 ? 4
+                                                                : (227 * 1024) / (int)(smem_bytes<BND>() + 1024);
+}
+
+template <int BND>
+__global__ void __launch_bounds__(NTH, min_blocks<BND>()) k_velocity(const __grid_constant__ Maps maps,
                                                                   const PassParams P) {
     extern __shared__ __align__(128) float sm[];
     constexpr int SF = slot_floats<BND>();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SF);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+        sm + NSLOT * SF + (BND == BND_CPML ? PSI_FLOATS : 0));
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
     const Geo<BND> G(P);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_plane<6, 4, BND>(maps, sm + s * SF, &bars[s], G.x0, G.y0, G.z0 - 2 + s,
-                                        G.dirs(G.z0 - 2 + s, P.g.nz));
+            issue_plane<6, 4>(maps, sm + s * SF, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
     VelQ<BND> Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
 #pragma unroll
         for (int q = 0; q < 4; ++q) { Q.zz[rr][q] = 0.f; Q.xz[rr][q] = 0.f; Q.yz[rr][q] = 0.f; }
+    uint32_t psi_n = 0;                            // psi-buffer fills consumed
     for (int m = 0; m < G.P4; m += 4) {
-        if (!vel_step<BND, 0>(maps, P, G, Q, sm, bars, m)) return;
-        if (m + 1 < G.P4 && !vel_step<BND, 1>(maps, P, G, Q, sm, bars, m + 1)) return;
-        if (m + 2 < G.P4 && !vel_step<BND, 2>(maps, P, G, Q, sm, bars, m + 2)) return;
-        if (m + 3 < G.P4 && !vel_step<BND, 3>(maps, P, G, Q, sm, bars, m + 3)) return;
+        if (!vel_step<BND, 0>(maps, P, G, Q, sm, bars, m, psi_n)) return;
+        if (m + 1 < G.P4 && !vel_step<BND, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n)) return;
+        if (m + 2 < G.P4 && !vel_step<BND, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n)) return;
+        if (m + 3 < G.P4 && !vel_step<BND, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n)) return;
     }
 }
 
@@ -404,13 +435,20 @@ struct StrQ {
 
 template <int BND, int PH>
 __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, const Geo<BND>& G,
-                                         StrQ<BND>& Q, float* sm, uint64_t* bars, int m) {
+                                         StrQ<BND>& Q, float* sm, uint64_t* bars, int m,
+                                         uint32_t& psi_n) {
     const DevGrid& g = P.g;
     constexpr int SF = slot_floats<BND>();
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
     const int k = G.z0 - 4 + m;
     const bool out = m >= 4;
-    const bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
+    // per-plane boundary coefficients of the output plane, fetched before the wait
+    const bool sz = BND == BND_CPML && out && in_slab(k, g.nz, G.W);
+    const float paz = sz ? __ldg(P.B.pa[2] + k) : 0.f, pbz = sz ? __ldg(P.B.pb[2] + k) : 0.f;
+    const float G3 = (BND == BND_SPONGE && out) ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
+    const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;   // damped dirs of k
+    bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
+    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
     const float* sl0 = sm + S0 * SF;
     const float* sl1 = sm + S1 * SF;
     // push own-column values: vx, vy of plane p, vz of plane p - 1
@@ -429,9 +467,6 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, 
         const float* hmu = sk + SH_MU * HALO;
         const float* hmu1 = (k + 1 < g.nz ? sl1 + G.hc : sk) + SH_MU * HALO;   // plane k + 1
         const float* cr = sm + S2 * SF + 4 * HALO + G.cc;
-        const float G3 = BND == BND_SPONGE ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
-        const bool sz = BND == BND_CPML && in_slab(k, g.nz, G.W);
-        const float paz = sz ? __ldg(P.B.pa[2] + k) : 0.f, pbz = sz ? __ldg(P.B.pb[2] + k) : 0.f;
         const long long o = (long long)k * g.plane + G.obase;
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
@@ -452,16 +487,16 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, 
             float vyz = g.c1z * (qvy[C] - qvy[B]) + g.c2z * (qvy[D] - qvy[A]);
             float vzy = g.c1y * (hvz[R + HX] - hvz[R]) + g.c2y * (hvz[R + 2 * HX] - hvz[R - HX]);
             if (BND == BND_CPML) {
-                const float* ps = sm + S2 * SF + SLOT_MAIN + G.cc + rr * TX;
+                const float* ps = sm + NSLOT * SLOT_MAIN + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
-                    pml_upd(p0, p1, p2, __ldg(P.B.pa[0] + G.i), __ldg(P.B.pb[0] + G.i), exx, vyx, vzx);
+                    pml_upd(p0, p1, p2, G.pax, G.pbx, exx, vyx, vzx);
                     P.B.psi[3][oo] = p0; P.B.psi[4][oo] = p1; P.B.psi[5][oo] = p2;
                 }
                 if (G.sy[rr]) {
                     float p0 = ps[3 * CORE], p1 = ps[4 * CORE], p2 = ps[5 * CORE];
-                    pml_upd(p0, p1, p2, __ldg(P.B.pa[1] + G.j0 + rr), __ldg(P.B.pb[1] + G.j0 + rr),
+                    pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr],
                             eyy, vxy, vzy);
                     P.B.psi[9][oo] = p0; P.B.psi[10][oo] = p1; P.B.psi[11][oo] = p2;
                 }
@@ -501,37 +536,46 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, 
     }
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && threadIdx.y == 0)
-            fail_exit(P.err, 2, bars, m, min(G.P4, max(NSLOT, m + 2)));
+            fail_exit(P.err, 2, bars, m, min(G.P4, max(NSLOT, m + 2)), kd != 0u, psi_n & 1u);
         return false;
     }
+    if (BND == BND_CPML) {
+        if (kd) ++psi_n;
+        // the psi buffer is free: fetch the memory variables of the next output plane
+        const int kn = k + 1;
+        if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
+            const unsigned dn = G.dirs(kn, g.nz);
+            if (dn) issue_psi(maps, sm + NSLOT * SLOT_MAIN, &bars[NSLOT], G.x0, G.y0, kn, dn);
+        }
+    }
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_plane<4, 7, BND>(maps, sm + S2 * SF, &bars[S2], G.x0, G.y0, G.z0 + m,
-                               G.dirs(G.z0 + m, g.nz));
+        issue_plane<4, 7>(maps, sm + S2 * SF, &bars[S2], G.x0, G.y0, G.z0 + m);
     return true;
 }
 
 template <int BND>
-__global__ void __launch_bounds__(NTH, EWS_MIN_BLOCKS) k_stress(const __grid_constant__ Maps maps,
+__global__ void __launch_bounds__(NTH, min_blocks<BND>()) k_stress(const __grid_constant__ Maps maps,
                                                                 const PassParams P) {
     extern __shared__ __align__(128) float sm[];
     constexpr int SF = slot_floats<BND>();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SF);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+        sm + NSLOT * SF + (BND == BND_CPML ? PSI_FLOATS : 0));
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
     const Geo<BND> G(P);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_plane<4, 7, BND>(maps, sm + s * SF, &bars[s], G.x0, G.y0, G.z0 - 2 + s,
-                                        G.dirs(G.z0 - 2 + s, P.g.nz));
+            issue_plane<4, 7>(maps, sm + s * SF, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
     StrQ<BND> Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
 #pragma unroll
         for (int q = 0; q < 4; ++q) { Q.vx[rr][q] = 0.f; Q.vy[rr][q] = 0.f; Q.vz[rr][q] = 0.f; }
+    uint32_t psi_n = 0;                            // psi-buffer fills consumed
     for (int m = 0; m < G.P4; m += 4) {
-        if (!str_step<BND, 0>(maps, P, G, Q, sm, bars, m)) return;
-        if (m + 1 < G.P4 && !str_step<BND, 1>(maps, P, G, Q, sm, bars, m + 1)) return;
-        if (m + 2 < G.P4 && !str_step<BND, 2>(maps, P, G, Q, sm, bars, m + 2)) return;
-        if (m + 3 < G.P4 && !str_step<BND, 3>(maps, P, G, Q, sm, bars, m + 3)) return;
+        if (!str_step<BND, 0>(maps, P, G, Q, sm, bars, m, psi_n)) return;
+        if (m + 1 < G.P4 && !str_step<BND, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n)) return;
+        if (m + 2 < G.P4 && !str_step<BND, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n)) return;
+        if (m + 3 < G.P4 && !str_step<BND, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n)) return;
     }
 }
 
@@ -638,7 +682,7 @@ cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevM
     p->nty = (g.ny + TY - 1) / TY;
     const long long ntile = (long long)p->ntx * p->nty;
     const long long slots = (long long)sms * occ;
-    long long nchunk = slots / ntile;
+    long long nchunk = (slots * EWS_WAVES) / ntile;
     if (nchunk > g.nz / 8) nchunk = g.nz / 8;
     if (nchunk < 1) nchunk = 1;
     p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
