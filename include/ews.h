@@ -171,6 +171,42 @@ ews_status ews_set_profiling(ews_sim* sim, int on);
  * is nonzero the accumulators are zeroed after reading. */
 ews_status ews_get_profile(ews_sim* sim, double* ms, long long* launches, int reset);
 
+/* Limits of ews_forward_noalloc. */
+#define EWS_NOALLOC_MAX_CELLS (1 << 18)   /* nx rounded up to 32, times ny, times nz */
+#define EWS_NOALLOC_MAX_DIM 1024          /* cells per axis                          */
+#define EWS_NOALLOC_MAX_RECEIVERS 64
+
+/* Forward run that allocates no memory (the paper has no counterpart: this
+ * is a service for callers).  Some callers cannot let a library call
+ * cudaMalloc: their device memory belongs to another allocator (a
+ * framework's caching allocator, a fixed pool in a long-running service)
+ * that must not be grown or fragmented behind its back, or they cannot take
+ * the device-wide synchronisation that cudaFree implies.  This call runs the
+ * same loop as ews_create + ews_set_* + ews_run, with the same kernels, but
+ * keeps every wavefield, the pitched medium copies, the sponge profiles and
+ * the receiver taps in one static device array of about 12 MiB that every
+ * GPU loading the library holds until the process exits.
+ *   lam, mu, rho  device pointers, dense [nz][ny][nx] float32 (caller-owned)
+ *   wavelet       device pointer, >= nt float32 samples (as ews_set_source)
+ *   rec_pos       host [nrec][3] metres, nrec <= EWS_NOALLOC_MAX_RECEIVERS
+ *   seis          device [3][nrec][nt] float32 output (caller-owned)
+ *   opt           NULL (sponge, W = 16) or boundary NONE / SPONGE; C-PML is
+ *                 rejected (its memory variables would not fit); snapshot
+ *                 fields are ignored.
+ * Sizes beyond EWS_NOALLOC_MAX_CELLS / _DIM / _RECEIVERS give EWS_EINVAL
+ * with a message naming the limit.  The first call on each device looks up
+ * the device address of the static array (cudaGetSymbolAddress, with that
+ * device current); make it before capturing any stream on that device.
+ * Every call shares the one array and starts by clearing the wavefields, so
+ * results do not depend on earlier calls, but calls that overlap on the GPU
+ * (other streams or host threads) race on it.  The call synchronises
+ * `cuda_stream` (NULL = default stream) before returning. */
+ews_status ews_forward_noalloc(const ews_grid* grid, const ews_options* opt,
+                               const float* lam, const float* mu, const float* rho,
+                               int src_kind, const double pos[3], const double comp[6],
+                               const float* wavelet, int nrec, const double* rec_pos,
+                               int nt, double dt, float* seis, void* cuda_stream);
+
 /* Time-step rule of Sec. 2.1.3, Eq. 5: 0.495 min(dx, dy, dz) / vmax. */
 double ews_cfl_dt(const ews_grid* grid, double vmax);
 

@@ -52,6 +52,17 @@ struct SourceSpec {
 
 }  // namespace
 
+namespace ews {
+// Record an error message for ews_last_error() from other translation units.
+ews_status report(ews_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+}  // namespace ews
+
 struct ews_sim {
     ews_grid grid{};
     ews_options opt{};

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/ews.h"
+
 namespace ews {
 
 enum { VX, VY, VZ, SXX, SYY, SZZ, SXY, SXZ, SYZ, NFIELD };
@@ -67,12 +69,18 @@ struct DevSource {
     Tap tap[kMaxSrcTaps]; // w already holds -dt M_c w_tri / V or dt F_c w_tri / V
 };
 
+// Thread-local error message for ews_last_error() (ews_capi.cu).
+ews_status report(ews_status s, const char* fmt, ...);
+
 // Stencil passes (ews_stencil.cu): TMA tensor maps and launch geometry are
 // built once per simulation (the field and medium addresses never change).
 struct StencilPlan;
 cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevMedium& M,
                                 const DevBoundary& B, StencilPlan** out);
 void stencil_plan_destroy(StencilPlan* p);
+size_t stencil_plan_bytes();
+cudaError_t stencil_plan_fill(void* storage, const DevGrid& g, const DevFields& F,
+                              const DevMedium& M, const DevBoundary& B, StencilPlan** out);
 cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                             const DevBoundary& B, float dt, int* err, cudaStream_t st);
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,

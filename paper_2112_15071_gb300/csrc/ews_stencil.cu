@@ -25,6 +25,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <new>
+
 #include "ews_internal.cuh"
 #ifndef EWS_L2PROMO
 #define EWS_L2PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_256B
@@ -693,6 +695,56 @@ cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevM
 }
 
 void stencil_plan_destroy(StencilPlan* p) { delete p; }
+
+size_t stencil_plan_bytes() { return sizeof(StencilPlan); }
+
+// Same plan as stencil_plan_create, built in caller-provided storage of at
+// least stencil_plan_bytes() bytes (aligned to 64), without any allocation.
+cudaError_t stencil_plan_fill(void* storage, const DevGrid& g, const DevFields& F,
+                              const DevMedium& M, const DevBoundary& B, StencilPlan** out) {
+    StencilPlan* p = ::new (storage) StencilPlan();
+    p->kind = B.kind;
+    bool ok = true;
+    const float* vh[6] = {F.f[SXX], F.f[SYY], F.f[SXY], F.f[SXZ], F.f[SYZ], M.rho};
+    const float* vc[4] = {F.f[SZZ], F.f[VX], F.f[VY], F.f[VZ]};
+    for (int h = 0; h < 6; ++h) ok &= encode(&p->vmaps.halo[h], g, vh[h], true);
+    for (int c = 0; c < 4; ++c) ok &= encode(&p->vmaps.core[c], g, vc[c], false);
+    const float* sh[4] = {F.f[VX], F.f[VY], F.f[VZ], M.mu};
+    const float* sc[7] = {M.lam, F.f[SXX], F.f[SYY], F.f[SZZ], F.f[SXY], F.f[SXZ], F.f[SYZ]};
+    for (int h = 0; h < 4; ++h) ok &= encode(&p->smaps.halo[h], g, sh[h], true);
+    for (int c = 0; c < 7; ++c) ok &= encode(&p->smaps.core[c], g, sc[c], false);
+    if (B.kind == BND_CPML)
+        for (int d = 0; d < 3; ++d)
+            for (int q = 0; q < 3; ++q) {
+                ok &= encode(&p->vmaps.psi[3 * d + q], g, B.psi[6 * d + q], false);
+                ok &= encode(&p->smaps.psi[3 * d + q], g, B.psi[6 * d + 3 + q], false);
+            }
+    if (!ok) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        switch (B.kind) {
+            case BND_SPONGE: e = occupancy<BND_SPONGE>(&occ); break;
+            case BND_CPML: e = occupancy<BND_CPML>(&occ); break;
+            default: e = occupancy<BND_NONE>(&occ); break;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    p->ntx = (g.nx + TX - 1) / TX;
+    p->nty = (g.ny + TY - 1) / TY;
+    const long long ntile = (long long)p->ntx * p->nty;
+    const long long slots = (long long)sms * occ;
+    long long nchunk = (slots * EWS_WAVES) / ntile;
+    if (nchunk > g.nz / 8) nchunk = g.nz / 8;
+    if (nchunk < 1) nchunk = 1;
+    p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
+    nchunk = (g.nz + p->zchunk - 1) / p->zchunk;
+    p->grid = (int)(ntile * nchunk);
+    *out = p;
+    return cudaSuccess;
+}
 
 cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                             const DevBoundary& B, float dt, int* err, cudaStream_t st) {

@@ -72,6 +72,8 @@ SIGNATURES = [
     ("ews_set_state", _I, [_P, _P, _I]),
     ("ews_set_profiling", _I, [_P, _I]),
     ("ews_get_profile", _I, [_P, _P, _P, _I]),
+    ("ews_forward_noalloc", _I, [C.POINTER(ews_grid), C.POINTER(ews_options), _P, _P, _P, _I,
+                             _P, _P, _P, _I, _P, _I, _D, _P, _P]),
     ("ews_cfl_dt", _D, [C.POINTER(ews_grid), _D]),
     ("ews_max_freq", _D, [C.POINTER(ews_grid), _D]),
     ("ews_last_error", C.c_char_p, []),
@@ -225,6 +227,27 @@ def ews_get_profile(sim, reset: bool = False):
     _check(load().ews_get_profile(sim, ms.ctypes.data_as(C.c_void_p),
                                   n.ctypes.data_as(C.c_void_p), int(bool(reset))))
     return ms, n
+
+
+def ews_forward_noalloc(grid: ews_grid, opt: ews_options | None, lam, mu, rho, kind: int, pos,
+                        comp, wavelet, rec_pos, nt: int, dt: float, seis, stream_handle: int = 0):
+    """Forward run without any device allocation (see include/ews.h).
+    lam, mu, rho, wavelet and seis must be CUDA tensors (device pointers)."""
+    ptrs = []
+    for a in (lam, mu, rho, wavelet, seis):
+        p, dev = _ptr(a)
+        assert dev == 1, "ews_forward_noalloc takes device buffers"
+        ptrs.append(p)
+    p = np.ascontiguousarray(pos, np.float64).reshape(3)
+    c = np.zeros(6)
+    cc = np.asarray(comp, np.float64).ravel()
+    c[:cc.size] = cc
+    r = np.ascontiguousarray(rec_pos, np.float64).reshape(-1, 3)
+    _check(load().ews_forward_noalloc(
+        C.byref(grid), C.byref(opt) if opt is not None else None, ptrs[0], ptrs[1], ptrs[2],
+        int(kind), p.ctypes.data_as(C.c_void_p), c.ctypes.data_as(C.c_void_p), ptrs[3],
+        int(r.shape[0]), r.ctypes.data_as(C.c_void_p) if r.size else None, int(nt), float(dt),
+        ptrs[4], C.c_void_p(stream_handle)))
 
 
 # --- convenience object ------------------------------------------------------
