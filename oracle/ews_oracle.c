@@ -457,3 +457,199 @@ double orc_energy(const orc_sim *s, const double *vprev) {
     }
     return 0.5 * (kin + pot) * s->h[0] * s->h[1] * s->h[2];
 }
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the time loop (reverse mode of the discrete scheme; not in the
+ * paper -- it differentiates Eq. 1-4 as discretised above).
+ *
+ * For a functional L of the seismograms with dL/dseis = sadj ([3][nrec][nt]),
+ * returns dL/dlambda, dL/dmu, dL/drho per cell.  Boundary: none or sponge
+ * (the sponge gain is diagonal, so its transpose is itself).  The forward
+ * step n is
+ *     V: v' = G (v + dt B Dsig(sigma) + f_n),   R: s_n = S v',
+ *     T: sigma' = G (sigma + dt C Dv(v') - m_n),
+ * with Dv = -Dsig^T (zero exterior).  Going back through T then V:
+ *     w = G a_sig;  g_C += dt Dv(v') (x) w;  a_v += -dt Dsig(C w) + S^T sadj_n;
+ *     a_sig = w;  u = G a_v;  g_B += (dt Dsig(sigma) + f_n / B) (x) u;
+ *     a_sig += -dt Dv(B u);  a_v = u.
+ * The forward states of each segment are recomputed from checkpoints.
+ * ------------------------------------------------------------------------ */
+
+/* velocity-pass derivative terms of an arbitrary 6-component stress-like
+ * field tau (order sxx syy szz sxy sxz syz) at (i, j, k), no buoyancy. */
+static void div_tau(const orc_sim *s, double *const tau[6], long i, long j, long k, double out[3]) {
+    out[0] = d_plus(s, tau[0], 0, i, j, k) + d_minus(s, tau[3], 1, i, j, k) + d_minus(s, tau[4], 2, i, j, k);
+    out[1] = d_minus(s, tau[3], 0, i, j, k) + d_plus(s, tau[1], 1, i, j, k) + d_minus(s, tau[5], 2, i, j, k);
+    out[2] = d_minus(s, tau[4], 0, i, j, k) + d_minus(s, tau[5], 1, i, j, k) + d_plus(s, tau[2], 2, i, j, k);
+}
+
+/* stress-pass strain-rate terms of an arbitrary 3-component velocity-like
+ * field q at (i, j, k): (exx, eyy, ezz, gxy, gxz, gyz). */
+static void grad_q(const orc_sim *s, double *const q[3], long i, long j, long k, double e[6]) {
+    e[0] = d_minus(s, q[0], 0, i, j, k);
+    e[1] = d_minus(s, q[1], 1, i, j, k);
+    e[2] = d_minus(s, q[2], 2, i, j, k);
+    e[3] = d_plus(s, q[0], 1, i, j, k) + d_plus(s, q[1], 0, i, j, k);
+    e[4] = d_plus(s, q[0], 2, i, j, k) + d_plus(s, q[2], 0, i, j, k);
+    e[5] = d_plus(s, q[1], 2, i, j, k) + d_plus(s, q[2], 1, i, j, k);
+}
+
+int orc_gradient(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
+                 const double *comp, const double *wavelet, int nrec, const double *rpos,
+                 const double *sadj, int ckpt_every, double *g_lam, double *g_mu, double *g_rho) {
+    if (s->boundary == BND_CPML) return -3;
+    const long N = s->n, nx = s->nx, ny = s->ny, nz = s->nz;
+    const int K = ckpt_every > 0 ? ckpt_every : nt;
+    const int nck = (nt + K - 1) / K;
+    double *ck = (double *)calloc((size_t)nck * NFIELD * N, sizeof(double));
+    double *hist = (double *)calloc((size_t)K * (NFIELD + 3) * N, sizeof(double));
+    double *av[3], *as[6], *w[6], *tmp[3], *acc[8];
+    for (int q = 0; q < 3; ++q) { av[q] = zalloc(N); tmp[q] = zalloc(N); }
+    for (int q = 0; q < 6; ++q) { as[q] = zalloc(N); w[q] = zalloc(N); }
+    for (int q = 0; q < 8; ++q) acc[q] = zalloc(N);
+    const double vol = s->h[0] * s->h[1] * s->h[2];
+    int rc = 0;
+    for (int q = 0; q < NFIELD; ++q) memset(s->f[q], 0, sizeof(double) * N);
+    /* forward pass, checkpoint before steps 0, K, 2K, ... */
+    for (int n = 0; n < nt; ++n) {
+        if (n % K == 0) orc_get_state(s, ck + (size_t)(n / K) * NFIELD * N);
+        if (orc_step_velocity(s, dt, src_kind, pos, comp, wavelet[n]) != 0 ||
+            orc_step_stress(s, dt, src_kind, pos, comp, wavelet[n]) != 0) { rc = -1; goto done; }
+    }
+    for (int c = nck - 1; c >= 0; --c) {
+        const int n0 = c * K, n1 = (n0 + K < nt) ? n0 + K : nt;
+        orc_set_state(s, ck + (size_t)c * NFIELD * N);
+        /* recompute the segment: state before step n, then v^{n+1/2} */
+        for (int n = n0; n < n1; ++n) {
+            double *hn = hist + (size_t)(n - n0) * (NFIELD + 3) * N;
+            orc_get_state(s, hn);
+            orc_step_velocity(s, dt, src_kind, pos, comp, wavelet[n]);
+            for (int q = 0; q < 3; ++q) memcpy(hn + (NFIELD + q) * N, s->f[q], sizeof(double) * N);
+            orc_step_stress(s, dt, src_kind, pos, comp, wavelet[n]);
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+            double *hn = hist + (size_t)(n - n0) * (NFIELD + 3) * N;
+            double *sig[6], *vh[3];
+            for (int q = 0; q < 6; ++q) sig[q] = hn + (3 + q) * N;     /* sigma^n  */
+            for (int q = 0; q < 3; ++q) vh[q] = hn + (NFIELD + q) * N; /* v^{n+1/2} */
+            /* reverse of T */
+            for (long k = 0; k < nz; ++k)
+                for (long j = 0; j < ny; ++j)
+                    for (long i = 0; i < nx; ++i) {
+                        long cc = IDX(s, i, j, k);
+                        double G = s->g[0][i] * s->g[1][j] * s->g[2][k];
+                        for (int q = 0; q < 6; ++q) w[q][cc] = G * as[q][cc];
+                    }
+            for (long k = 0; k < nz; ++k)
+                for (long j = 0; j < ny; ++j)
+                    for (long i = 0; i < nx; ++i) {
+                        long cc = IDX(s, i, j, k);
+                        double e[6];
+                        grad_q(s, vh, i, j, k, e);
+                        double l = s->lam[cc], mu = 0.5 * (s->lp2m[cc] - l);
+                        double tr = e[0] + e[1] + e[2], wtr = w[0][cc] + w[1][cc] + w[2][cc];
+                        acc[0][cc] += dt * tr * wtr;                                   /* lambda   */
+                        acc[1][cc] += dt * 2.0 * (e[0] * w[0][cc] + e[1] * w[1][cc] + e[2] * w[2][cc]);
+                        acc[2][cc] += dt * e[3] * w[3][cc];                            /* mu_xy    */
+                        acc[3][cc] += dt * e[4] * w[4][cc];                            /* mu_xz    */
+                        acc[4][cc] += dt * e[5] * w[5][cc];                            /* mu_yz    */
+                        (void)mu;
+                    }
+            {   /* tau = C w, kept in `as` (its old value is no longer needed) */
+                for (long cc = 0; cc < N; ++cc) {
+                    double l = s->lam[cc], l2m = s->lp2m[cc];
+                    double a = w[0][cc], b = w[1][cc], d = w[2][cc];
+                    as[0][cc] = l2m * a + l * (b + d);
+                    as[1][cc] = l2m * b + l * (a + d);
+                    as[2][cc] = l2m * d + l * (a + b);
+                    as[3][cc] = s->mxy[cc] * w[3][cc];
+                    as[4][cc] = s->mxz[cc] * w[4][cc];
+                    as[5][cc] = s->myz[cc] * w[5][cc];
+                }
+                for (long k = 0; k < nz; ++k)
+                    for (long j = 0; j < ny; ++j)
+                        for (long i = 0; i < nx; ++i) {
+                            long cc = IDX(s, i, j, k);
+                            double dv[3];
+                            div_tau(s, as, i, j, k, dv);
+                            for (int q = 0; q < 3; ++q) tmp[q][cc] = dv[q];
+                        }
+                for (int q = 0; q < 3; ++q)
+                    for (long cc = 0; cc < N; ++cc) av[q][cc] -= dt * tmp[q][cc];
+            }
+            /* receivers: a_v += S^T sadj_n */
+            for (int r = 0; r < nrec; ++r)
+                for (int q = 0; q < 3; ++q) {
+                    long idx[8]; double wt[8];
+                    trilinear(s, q, rpos + 3 * r, idx, wt);
+                    double a = sadj[((long)q * nrec + r) * nt + n];
+                    for (int m = 0; m < 8; ++m)
+                        if (idx[m] >= 0) av[q][idx[m]] += wt[m] * a;
+                }
+            for (int q = 0; q < 6; ++q) memcpy(as[q], w[q], sizeof(double) * N);
+            /* reverse of V */
+            const double *b[3] = {s->bx, s->by, s->bz};
+            for (long k = 0; k < nz; ++k)
+                for (long j = 0; j < ny; ++j)
+                    for (long i = 0; i < nx; ++i) {
+                        long cc = IDX(s, i, j, k);
+                        double G = s->g[0][i] * s->g[1][j] * s->g[2][k];
+                        double dsig[3];
+                        div_tau(s, sig, i, j, k, dsig);
+                        for (int q = 0; q < 3; ++q) {
+                            double u = G * av[q][cc];
+                            av[q][cc] = u;
+                            acc[5 + q][cc] += dt * dsig[q] * u;
+                            tmp[q][cc] = b[q][cc] * u;                 /* q = B u */
+                        }
+                    }
+            if (src_kind == 1) {   /* force term f_n / b at the taps */
+                for (int q = 0; q < 3; ++q) {
+                    long idx[8]; double wt[8];
+                    trilinear(s, q, pos, idx, wt);
+                    for (int m = 0; m < 8; ++m)
+                        if (idx[m] >= 0)
+                            acc[5 + q][idx[m]] += wt[m] * dt * comp[q] * wavelet[n] / vol * av[q][idx[m]];
+                }
+            }
+            for (long k = 0; k < nz; ++k)
+                for (long j = 0; j < ny; ++j)
+                    for (long i = 0; i < nx; ++i) {
+                        long cc = IDX(s, i, j, k);
+                        double e[6];
+                        grad_q(s, tmp, i, j, k, e);
+                        for (int q = 0; q < 6; ++q) w[q][cc] = e[q];
+                    }
+            for (int q = 0; q < 6; ++q)
+                for (long cc = 0; cc < N; ++cc) as[q][cc] -= dt * w[q][cc];
+        }
+    }
+    /* medium chain rule: lambda direct; mu normal + 1/4 of each shear mean;
+     * rho through b = 1 / (mean of 2 densities). */
+    for (long cc = 0; cc < N; ++cc) { g_lam[cc] = acc[0][cc]; g_mu[cc] = acc[1][cc]; g_rho[cc] = 0.0; }
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long cc = IDX(s, i, j, k);
+                long ip = clampi(i + 1, nx), jp = clampi(j + 1, ny), kp = clampi(k + 1, nz);
+                long xy[4] = {cc, IDX(s, ip, j, k), IDX(s, i, jp, k), IDX(s, ip, jp, k)};
+                long xz[4] = {cc, IDX(s, ip, j, k), IDX(s, i, j, kp), IDX(s, ip, j, kp)};
+                long yz[4] = {cc, IDX(s, i, jp, k), IDX(s, i, j, kp), IDX(s, i, jp, kp)};
+                for (int m = 0; m < 4; ++m) {
+                    g_mu[xy[m]] += 0.25 * acc[2][cc];
+                    g_mu[xz[m]] += 0.25 * acc[3][cc];
+                    g_mu[yz[m]] += 0.25 * acc[4][cc];
+                }
+                double bx = s->bx[cc], by = s->by[cc], bz = s->bz[cc];
+                g_rho[cc] += -0.5 * bx * bx * acc[5][cc] - 0.5 * by * by * acc[6][cc] - 0.5 * bz * bz * acc[7][cc];
+                g_rho[IDX(s, ip, j, k)] += -0.5 * bx * bx * acc[5][cc];
+                g_rho[IDX(s, i, jp, k)] += -0.5 * by * by * acc[6][cc];
+                g_rho[IDX(s, i, j, kp)] += -0.5 * bz * bz * acc[7][cc];
+            }
+done:
+    free(ck); free(hist);
+    for (int q = 0; q < 3; ++q) { free(av[q]); free(tmp[q]); }
+    for (int q = 0; q < 6; ++q) { free(as[q]); free(w[q]); }
+    for (int q = 0; q < 8; ++q) free(acc[q]);
+    return rc;
+}

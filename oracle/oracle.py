@@ -73,6 +73,8 @@ def lib():
             L.orc_get_medium.argtypes = [P, P]
             L.orc_energy.restype = D
             L.orc_energy.argtypes = [P, P]
+            L.orc_gradient.restype = I
+            L.orc_gradient.argtypes = [P, I, D, I, P, P, P, I, P, P, I, P, P, P]
             _lib = L
     return _lib
 
@@ -203,6 +205,29 @@ class OracleSim:
         if snap is not None:
             return seis, snap.reshape(nsnap, nmask, self.nz, self.ny, self.nx)
         return seis
+
+
+def gradient(prob, sadj, ckpt_every=0, nt=None, medium=None):
+    """dL/d(lambda, mu, rho) per cell for dL/dseis = sadj ([3][nrec][nt]),
+    FP64.  `medium` optionally overrides (lambda, mu, rho)."""
+    nt = prob.nt if nt is None else nt
+    s = OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
+    if medium is None:
+        s.set_medium_vel(prob.vp, prob.vs, prob.rho)
+    else:
+        s.set_medium_lame(*medium)
+    s.set_boundary(prob.boundary, prob.width, prob.dt, prob.f0)
+    k, p, c = s._src(prob.src_kind, prob.src_pos, prob.src_comp)
+    w = np.ascontiguousarray(prob.wavelet, np.float64)
+    r = np.ascontiguousarray(prob.rec_pos, np.float64).reshape(-1, 3)
+    a = np.ascontiguousarray(sadj, np.float64)
+    assert a.shape == (3, r.shape[0], nt)
+    g = np.zeros((3, s.n))
+    rc = s._L.orc_gradient(s._h, int(nt), float(prob.dt), k, _p(p), _p(c), _p(w), r.shape[0],
+                           _p(r), _p(a), int(ckpt_every), _p(g[0]), _p(g[1]), _p(g[2]))
+    if rc != 0:
+        raise ValueError(f"oracle gradient failed ({rc})")
+    return g.reshape(3, s.nz, s.ny, s.nx)
 
 
 def run_problem(prob, nt=None, state=None, boundary=None, snap_every=0, snap_mask=0,
