@@ -145,6 +145,30 @@ ews_status ews_run(ews_sim* sim, int nt, double dt, float* seis, int seis_on_dev
 ews_status ews_advance(ews_sim* sim, int n0, int nsteps, double dt, float* seis,
                        int ld, int seis_on_device);
 
+/* Adjoint gradient (not in the paper, which only runs the forward model;
+ * this is the exact reverse of the discrete loop of ews_run).  For a scalar
+ * L of the seismograms with dL/dseis = seis_adj ([3][nrec][nt], host or
+ * device per adj_on_device), writes dL/dlambda, dL/dmu, dL/drho per cell
+ * ([nz][ny][nx] float32 each, host or device per g_on_device).  Runs the
+ * forward loop from rest storing the 9 wavefields every ckpt_every steps
+ * (0: 50), then for each segment in reverse recomputes its states, keeps
+ * v^{n+1/2}, and steps the adjoint back through the stress and velocity
+ * passes.  Accumulation is FP32 within a segment and FP64 across segments.
+ * Boundaries NONE and SPONGE (C-PML: EWS_EINVAL).  Extra device memory:
+ * (nt / ckpt_every) x 9 + (ckpt_every + 1) x 3 + 17 fields + 8 FP64 fields. */
+ews_status ews_adjoint(ews_sim* sim, int nt, double dt, const float* seis_adj,
+                       int adj_on_device, float* g_lam, float* g_mu, float* g_rho,
+                       int g_on_device, int ckpt_every);
+
+/* Gradient of the L2 misfit J = dt/2 sum_(c,r,n) (seis - observed)^2 with
+ * respect to lambda, mu, rho (one forward with checkpoints, then the
+ * reverse sweep of ews_adjoint with dL/dseis = dt (seis - observed)).
+ * observed is [3][nrec][nt] (host or device per obs_on_device); *misfit
+ * (may be NULL) receives J. */
+ews_status ews_gradient(ews_sim* sim, int nt, double dt, const float* observed,
+                        int obs_on_device, double* misfit, float* g_lam, float* g_mu,
+                        float* g_rho, int g_on_device, int ckpt_every);
+
 /* Zero the wavefields and C-PML memory variables. */
 ews_status ews_reset(ews_sim* sim);
 

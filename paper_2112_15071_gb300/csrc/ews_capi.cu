@@ -99,6 +99,17 @@ struct ews_sim {
     std::vector<cudaEvent_t> ev_pool;     // reused across calls
     std::vector<int> ev_class;            // class of the launch ending at event m
     size_t ev_used = 0;
+    // adjoint buffers (allocated on first use)
+    float* adj = nullptr;                 // P (3), Q (6), FP32 accumulators (8)
+    double* acc64 = nullptr;              // FP64 accumulators (8)
+    float* ckpt = nullptr;                // checkpoints, nck x 9 fields
+    size_t ckpt_cap = 0;                  // fields' worth of floats
+    float* vhist = nullptr;               // velocity history, (K + 1) x 3 fields
+    size_t vhist_cap = 0;
+    float* aux = nullptr;                 // seismogram-sized adjoint source + observed
+    size_t aux_cap = 0;
+    float* gout = nullptr;                // gradient staging for host outputs
+    double* dmisfit = nullptr;
 
     DevFields F() const {
         DevFields f;
@@ -292,7 +303,7 @@ ews_status mark(ews_sim* s, int cls) {
 }
 
 ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
-                 float* dseis, int ld) {
+                 float* dseis, int ld, float* vcap = nullptr) {
     DevFields F = s->F();
     DevMedium M = s->M();
     // fold dt and the cell volume into the source taps
@@ -330,6 +341,10 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
             CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, s->stream));
             if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
         }
+        if (vcap)   // v^{n+1/2} into the history slot of step n (fields 0..2 are contiguous)
+            CK(cudaMemcpyAsync(vcap + (size_t)(n - n0 + 1) * 3 * s->fstride, s->fields,
+                               3 * s->fstride * sizeof(float), cudaMemcpyDeviceToDevice,
+                               s->stream));
         CK(launch_stress(s->plan, s->g, F, s->B, fdt, s->err, s->stream));
         if ((st = mark(s, EWS_KERNEL_STRESS)) != EWS_OK) return st;
         if (S.kind == EWS_SOURCE_MOMENT) {
@@ -350,6 +365,114 @@ ews_status collect_profile(ews_sim* s) {
         s->kernel_ms[s->ev_class[m]] += ms;
     }
     s->ev_used = 0;
+    return EWS_OK;
+}
+
+// Grow a device buffer to at least `need` elements of T.
+template <typename T>
+ews_status ensure_buf(T** buf, size_t* cap, size_t need, const char* what) {
+    if (*buf && *cap >= need) return EWS_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(buf, need * sizeof(T));
+    if (e != cudaSuccess) return fail(EWS_ENOMEM, "%s (%zu bytes): %s", what, need * sizeof(T),
+                                      cudaGetErrorString(e));
+    *cap = need;
+    return EWS_OK;
+}
+
+// Reverse sweep for dL/dseis = sadj (device, [3][nrec][nt]); or, when obs is
+// given, first the L2 misfit residual of a recorded forward run.
+ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const float* sadj_dev,
+                        const float* obs_dev, double* misfit, float* g_lam, float* g_mu,
+                        float* g_rho, int g_on_device) {
+    ews_status st = ensure_ready(s, nt, dt);
+    if (st != EWS_OK) return st;
+    if (s->opt.boundary == EWS_BOUNDARY_CPML)
+        return fail(EWS_EINVAL, "the adjoint supports the none and sponge boundaries");
+    const int K = ckpt_every > 0 ? (ckpt_every < nt ? ckpt_every : nt) : (nt < 50 ? nt : 50);
+    const int nck = (nt + K - 1) / K;
+    const size_t fs = s->fstride;
+    if (!s->adj) {
+        cudaError_t e = cudaMalloc(&s->adj, 17 * fs * sizeof(float));
+        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint state: %s", cudaGetErrorString(e));
+        e = cudaMalloc(&s->acc64, 8 * fs * sizeof(double));
+        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint accumulators: %s", cudaGetErrorString(e));
+        e = cudaMalloc(&s->dmisfit, sizeof(double));
+        if (e != cudaSuccess) return fail(EWS_ENOMEM, "misfit: %s", cudaGetErrorString(e));
+    }
+    if ((st = ensure_buf(&s->ckpt, &s->ckpt_cap, (size_t)nck * 9 * fs, "checkpoints")) != EWS_OK) return st;
+    if ((st = ensure_buf(&s->vhist, &s->vhist_cap, (size_t)(K + 1) * 3 * fs, "velocity history")) != EWS_OK) return st;
+    const size_t nseis = (size_t)3 * s->nrec * nt;
+    if (obs_dev && (st = ensure_buf(&s->aux, &s->aux_cap, 2 * (nseis ? nseis : 1), "adjoint source")) != EWS_OK)
+        return st;
+    AdjFields A;
+    for (int c = 0; c < 3; ++c) A.p[c] = s->adj + c * fs;
+    for (int c = 0; c < 6; ++c) A.q[c] = s->adj + (3 + c) * fs;
+    for (int c = 0; c < 8; ++c) { A.acc[c] = s->adj + (9 + c) * fs; A.acc64[c] = s->acc64 + c * fs; }
+    // forward with checkpoints (and seismograms when a misfit is asked for)
+    if ((st = ews_reset(s)) != EWS_OK) return st;
+    float* dseis = obs_dev ? s->aux : nullptr;
+    for (int c = 0; c < nck; ++c) {
+        const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
+        CK(cudaMemcpyAsync(s->ckpt + (size_t)c * 9 * fs, s->fields, 9 * fs * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s->stream));
+        if ((st = steps(s, s->src, n0, n1 - n0, dt, dseis, nt)) != EWS_OK) return st;
+    }
+    const float* sadj = sadj_dev;
+    if (obs_dev) {
+        float* sa = s->aux + nseis;
+        CK(cudaMemsetAsync(s->dmisfit, 0, sizeof(double), s->stream));
+        CK(launch_residual(s->aux, obs_dev, sa, (long long)nseis, (float)dt, s->dmisfit, s->stream));
+        sadj = sa;
+    }
+    CK(cudaMemsetAsync(s->adj, 0, 17 * fs * sizeof(float), s->stream));
+    CK(cudaMemsetAsync(s->acc64, 0, 8 * fs * sizeof(double), s->stream));
+    const float fdt = (float)dt;
+    for (int c = nck - 1; c >= 0; --c) {
+        const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
+        CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float), cudaMemcpyDeviceToDevice,
+                           s->stream));
+        if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK) return st;
+        for (int n = n1 - 1; n >= n0; --n) {
+            const float* vn = s->vhist + (size_t)(n - n0 + 1) * 3 * fs;
+            const float* vp = s->vhist + (size_t)(n - n0) * 3 * fs;
+            CK(launch_adj_stress(s->g, A, s->M(), s->B, vn, fs, fdt, s->stream));
+            if (s->nrec > 0 && sadj)
+                CK(launch_adj_record(s->g, A, s->rtaps, s->nrec, sadj, nt, n, s->stream));
+            CK(launch_adj_velocity(s->g, A, s->M(), s->B, vn, vp, fs, fdt, s->stream));
+        }
+        CK(launch_acc_flush(s->g, A, s->stream));
+    }
+    const size_t ncell = (size_t)s->ncell();
+    float *gl = g_lam, *gm = g_mu, *gr = g_rho;
+    if (!g_on_device) {
+        size_t cap = s->gout ? 3 * ncell : 0;
+        if ((st = ensure_buf(&s->gout, &cap, 3 * ncell, "gradient staging")) != EWS_OK) return st;
+        gl = s->gout;
+        gm = s->gout + ncell;
+        gr = s->gout + 2 * ncell;
+    }
+    CK(launch_grad_finalize(s->g, A, s->M(), gl, gm, gr, s->stream));
+    if (!g_on_device) {
+        CK(cudaMemcpyAsync(g_lam, gl, ncell * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(g_mu, gm, ncell * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(g_rho, gr, ncell * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (misfit && obs_dev)
+        CK(cudaMemcpyAsync(misfit, s->dmisfit, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    if (herr) {
+        CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+        return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up");
+    }
+    if (s->profiling && (st = collect_profile(s)) != EWS_OK) return st;
     return EWS_OK;
 }
 
@@ -475,6 +598,13 @@ void ews_destroy(ews_sim* s) {
     cudaFree(s->wavelet);
     cudaFree(s->rtaps);
     cudaFree(s->seis_buf);
+    cudaFree(s->adj);
+    cudaFree(s->acc64);
+    cudaFree(s->ckpt);
+    cudaFree(s->vhist);
+    cudaFree(s->aux);
+    cudaFree(s->gout);
+    cudaFree(s->dmisfit);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     delete s;
 }
@@ -672,6 +802,44 @@ ews_status ews_set_state(ews_sim* s, const float* in, int on_device) {
     if (s->psi) CK(cudaMemsetAsync(s->psi, 0, s->psi_floats * sizeof(float), s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return EWS_OK;
+}
+
+ews_status ews_adjoint(ews_sim* s, int nt, double dt, const float* seis_adj, int adj_on_device,
+                       float* g_lam, float* g_mu, float* g_rho, int g_on_device,
+                       int ckpt_every) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (nt <= 0 || !g_lam || !g_mu || !g_rho) return fail(EWS_EINVAL, "bad arguments");
+    if (s->nrec > 0 && !seis_adj) return fail(EWS_EINVAL, "seis_adj is NULL");
+    const float* dadj = seis_adj;
+    if (s->nrec > 0 && !adj_on_device) {
+        const size_t nseis = (size_t)3 * s->nrec * nt;
+        ews_status st = ensure_buf(&s->aux, &s->aux_cap, 2 * nseis, "adjoint source");
+        if (st != EWS_OK) return st;
+        CK(cudaMemcpyAsync(s->aux + nseis, seis_adj, nseis * sizeof(float), cudaMemcpyHostToDevice,
+                           s->stream));
+        dadj = s->aux + nseis;
+    }
+    return adjoint_core(s, nt, dt, ckpt_every, dadj, nullptr, nullptr, g_lam, g_mu, g_rho,
+                        g_on_device);
+}
+
+ews_status ews_gradient(ews_sim* s, int nt, double dt, const float* observed, int obs_on_device,
+                        double* misfit, float* g_lam, float* g_mu, float* g_rho,
+                        int g_on_device, int ckpt_every) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (nt <= 0 || !g_lam || !g_mu || !g_rho || !observed)
+        return fail(EWS_EINVAL, "bad arguments");
+    const size_t nseis = (size_t)3 * s->nrec * nt;
+    ews_status st = ensure_buf(&s->aux, &s->aux_cap, 3 * (nseis ? nseis : 1), "adjoint source");
+    if (st != EWS_OK) return st;
+    const float* dobs = observed;
+    if (!obs_on_device) {
+        CK(cudaMemcpyAsync(s->aux + 2 * nseis, observed, nseis * sizeof(float),
+                           cudaMemcpyHostToDevice, s->stream));
+        dobs = s->aux + 2 * nseis;
+    }
+    return adjoint_core(s, nt, dt, ckpt_every, nullptr, dobs, misfit, g_lam, g_mu, g_rho,
+                        g_on_device);
 }
 
 }  // extern "C"

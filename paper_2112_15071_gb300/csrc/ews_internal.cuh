@@ -69,6 +69,31 @@ struct DevSource {
     Tap tap[kMaxSrcTaps]; // w already holds -dt M_c w_tri / V or dt F_c w_tri / V
 };
 
+// Adjoint state (ews_adjoint.cu): P velocity-like (true adjoint = G P),
+// Q stress-like, FP32 per-segment accumulators and FP64 totals:
+// acc[0] lambda, [1] mu at normal points, [2..4] mu at xy/xz/yz shear points,
+// [5..7] buoyancy at vx/vy/vz points.
+struct AdjFields {
+    float* p[3];
+    float* q[6];
+    float* acc[8];
+    double* acc64[8];
+};
+
+cudaError_t launch_adj_stress(const DevGrid& g, const AdjFields& A, const DevMedium& M,
+                              const DevBoundary& B, const float* vh, size_t fstride, float dt,
+                              cudaStream_t st);
+cudaError_t launch_adj_velocity(const DevGrid& g, const AdjFields& A, const DevMedium& M,
+                                const DevBoundary& B, const float* vn, const float* vp,
+                                size_t fstride, float dt, cudaStream_t st);
+cudaError_t launch_adj_record(const DevGrid& g, const AdjFields& A, const Tap* taps, int nrec,
+                              const float* sadj, int ld, int n, cudaStream_t st);
+cudaError_t launch_acc_flush(const DevGrid& g, const AdjFields& A, cudaStream_t st);
+cudaError_t launch_grad_finalize(const DevGrid& g, const AdjFields& A, const DevMedium& M,
+                                 float* glam, float* gmu, float* grho, cudaStream_t st);
+cudaError_t launch_residual(const float* seis, const float* obs, float* sadj, long long n,
+                            float dt, double* misfit, cudaStream_t st);
+
 // Thread-local error message for ews_last_error() (ews_capi.cu).
 ews_status report(ews_status s, const char* fmt, ...);
 

@@ -70,6 +70,8 @@ SIGNATURES = [
     ("ews_reset", _I, [_P]),
     ("ews_get_state", _I, [_P, _P, _I]),
     ("ews_set_state", _I, [_P, _P, _I]),
+    ("ews_adjoint", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _I, _I]),
+    ("ews_gradient", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _P, _I, _I]),
     ("ews_set_profiling", _I, [_P, _I]),
     ("ews_get_profile", _I, [_P, _P, _P, _I]),
     ("ews_forward_noalloc", _I, [C.POINTER(ews_grid), C.POINTER(ews_options), _P, _P, _P, _I,
@@ -216,6 +218,24 @@ def ews_set_state(sim, state):
     _check(load().ews_set_state(sim, p, dev))
 
 
+def ews_adjoint(sim, nt: int, dt: float, seis_adj, g_lam, g_mu, g_rho, ckpt_every: int = 0):
+    pa, da = _ptr(seis_adj)
+    (pl, d0), (pm, d1), (pr, d2) = _ptr(g_lam), _ptr(g_mu), _ptr(g_rho)
+    assert d0 == d1 == d2, "gradient outputs must share residency"
+    _check(load().ews_adjoint(sim, int(nt), float(dt), pa, da, pl, pm, pr, d0, int(ckpt_every)))
+
+
+def ews_gradient(sim, nt: int, dt: float, observed, g_lam, g_mu, g_rho, ckpt_every: int = 0):
+    """Returns the L2 misfit; gradients are written into g_lam, g_mu, g_rho."""
+    po, do = _ptr(observed)
+    (pl, d0), (pm, d1), (pr, d2) = _ptr(g_lam), _ptr(g_mu), _ptr(g_rho)
+    assert d0 == d1 == d2, "gradient outputs must share residency"
+    mis = C.c_double(0.0)
+    _check(load().ews_gradient(sim, int(nt), float(dt), po, do, C.byref(mis), pl, pm, pr, d0,
+                               int(ckpt_every)))
+    return mis.value
+
+
 def ews_set_profiling(sim, on: bool):
     _check(load().ews_set_profiling(sim, int(bool(on))))
 
@@ -310,6 +330,20 @@ class Simulation:
 
     def reset(self):
         ews_reset(self._h)
+
+    def adjoint(self, nt, dt, seis_adj, ckpt_every=0, out=None):
+        """dL/d(lambda, mu, rho), [3][nz][ny][nx], for dL/dseis = seis_adj."""
+        if out is None:
+            out = np.zeros((3, self.nz, self.ny, self.nx), np.float32)
+        ews_adjoint(self._h, nt, dt, seis_adj, out[0], out[1], out[2], ckpt_every)
+        return out
+
+    def gradient(self, nt, dt, observed, ckpt_every=0, out=None):
+        """(misfit, dJ/d(lambda, mu, rho)) for the L2 misfit against observed."""
+        if out is None:
+            out = np.zeros((3, self.nz, self.ny, self.nx), np.float32)
+        mis = ews_gradient(self._h, nt, dt, observed, out[0], out[1], out[2], ckpt_every)
+        return mis, out
 
     def set_profiling(self, on=True):
         ews_set_profiling(self._h, on)

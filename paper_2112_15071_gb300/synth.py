@@ -313,10 +313,11 @@ def config4(n: int = 192, nt: int = 1500, h: float = 15.0, width: int = 20,
     sp = (h, h, h)
     vp, vs, rho = layered_random(n, n, n, sp, seed=seed)
     c = ((n // 2) * h,) * 3
-    vpt, vst, rhot = add_sphere(vp, vs, sp, c, 300.0 * n / 192.0, 0.10)
+    scale = n * h / (192 * 15.0)        # physical size relative to the 192^3, 15 m case
+    vpt, vst, rhot = add_sphere(vp, vs, sp, c, 300.0 * scale, 0.10)
     vp0, vs0, _ = layered_random(n, n, n, sp, amp=0.0)
-    vp0 = smooth(vp0, sp, 150.0 * n / 192.0)
-    vs0 = smooth(vs0, sp, 150.0 * n / 192.0)
+    vp0 = smooth(vp0, sp, 150.0 * scale)
+    vs0 = smooth(vs0, sp, 150.0 * scale)
     rho0 = gardner(vp0)
     vmax = float(max(vpt.max(), vp0.max()))
     dt = 0.5 * PAPER_CFL * h / vmax

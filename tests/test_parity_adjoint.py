@@ -1,0 +1,123 @@
+"""GPU parity of the adjoint gradient against the FP64 oracle.
+
+The CUDA adjoint (ews_adjoint / ews_gradient through the C ABI) is compared
+with the oracle's exact discrete adjoint on the same seeded inputs (FP32
+GPU vs FP64 CPU: relative L2 per gradient field), and directionally with
+central finite differences of the oracle forward (the stated target:
+gradients within 1e-3 of finite differences).
+"""
+import numpy as np
+import pytest
+
+from paper_2112_15071_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_ORACLE = 1e-4      # FP32 adjoint vs FP64 adjoint, relative L2 per field
+TOL_FD = 1e-3          # FP32 adjoint vs FP64 central finite differences
+
+
+@pytest.fixture(scope="module")
+def ews():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_15071_gb300 import ews as E
+    E.load()
+    return E
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def problem(dims, boundary, kind, nt=120, seed=2):
+    return synth.small_problem(*dims, nt=nt, boundary=boundary, width=5, kind=kind, nrec=6,
+                               seed=seed)
+
+
+@pytest.mark.parametrize("boundary", ["none", "sponge"])
+@pytest.mark.parametrize("kind", ["moment", "force"])
+@pytest.mark.parametrize("dims", [(40, 36, 28), (37, 45, 33)])
+def test_adjoint_matches_oracle(ews, orc, boundary, kind, dims):
+    p = problem(dims, boundary, kind, seed=sum(dims))
+    A = np.random.default_rng(1).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    want = orc.gradient(p, A.astype(np.float64), ckpt_every=25, medium=[a.astype(np.float64) for a in p.lame()])
+    sim = ews.simulation_for(p)
+    sim.set_model_lame(*p.lame())
+    got = sim.adjoint(p.nt, p.dt, A, ckpt_every=25)
+    for q in range(3):
+        assert np.abs(want[q]).max() > 0
+        assert rel(got[q], want[q]) <= TOL_ORACLE, (q, rel(got[q], want[q]))
+
+
+def test_checkpoint_interval_invariance(ews):
+    p = problem((40, 36, 28), "sponge", "moment")
+    A = np.random.default_rng(4).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    sim = ews.simulation_for(p)
+    g1 = sim.adjoint(p.nt, p.dt, A, ckpt_every=7)
+    g2 = sim.adjoint(p.nt, p.dt, A, ckpt_every=p.nt)
+    for q in range(3):
+        assert rel(g1[q], g2[q]) <= 1e-6
+
+
+def test_gradient_against_finite_differences(ews, orc):
+    """Directional derivative of J = dt/2 |s - d|^2 (FP64 central FD on the
+    oracle forward) vs the FP32 GPU gradient, for lambda, mu and rho."""
+    p = problem((36, 32, 30), "sponge", "moment", nt=150, seed=8)
+    lam, mu, rho = [a.astype(np.float64) for a in p.lame()]
+    rng = np.random.default_rng(3)
+    obs = (orc.run_problem(p) * (1 + 0.2 * rng.standard_normal((3, p.rec_pos.shape[0], p.nt))))
+    obs32 = obs.astype(np.float32)
+
+    def J(l, m, r):
+        s = orc.OracleSim(p.nx, p.ny, p.nz, p.spacing)
+        s.set_medium_lame(l, m, r)
+        s.set_boundary("sponge", p.width, p.dt, p.f0)
+        x = s.forward(p.nt, p.dt, p.src_kind, p.src_pos, p.src_comp, p.wavelet, p.rec_pos)
+        return 0.5 * p.dt * float(np.sum((x - obs32) ** 2))
+
+    sim = ews.simulation_for(p)
+    sim.set_model_lame(*p.lame())
+    misfit, g = sim.gradient(p.nt, p.dt, obs32, ckpt_every=30)
+    assert misfit == pytest.approx(J(lam, mu, rho), rel=1e-4)
+    for idx, base in enumerate((lam, mu, rho)):
+        d = rng.standard_normal(base.shape)
+        h = 1e-4 * np.abs(base).mean() / np.abs(d).mean()
+        args = [lam, mu, rho]
+        plus = [a + (h * d if i == idx else 0) for i, a in enumerate(args)]
+        minus = [a - (h * d if i == idx else 0) for i, a in enumerate(args)]
+        fd = (J(*plus) - J(*minus)) / (2 * h)
+        an = float(np.sum(g[idx].astype(np.float64) * d))
+        assert abs(fd - an) <= TOL_FD * abs(fd), (idx, fd, an)
+
+
+def test_config4_48cube_against_fp64_adjoint(ews, orc):
+    """The adjoint benchmark case scaled to 48^3: observed data from the
+    model with the 10 % sphere, gradient at the smoothed starting model."""
+    true, start = synth.config4(n=48, nt=300, h=60.0, width=8)
+    obs = orc.run_problem(true).astype(np.float32)
+    sim = ews.simulation_for(start)
+    misfit, g = sim.gradient(start.nt, start.dt, obs, ckpt_every=50)
+    seis = orc.run_problem(start)
+    want = orc.gradient(start, start.dt * (seis - obs.astype(np.float64)), ckpt_every=50)
+    assert misfit > 0
+    for q in range(3):
+        assert rel(g[q], want[q]) <= TOL_ORACLE, (q, rel(g[q], want[q]))
+
+
+def test_adjoint_device_buffers_and_cpml_refusal(ews):
+    import torch
+    p = problem((40, 36, 28), "none", "force")
+    A = np.random.default_rng(9).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    sim = ews.simulation_for(p)
+    host = sim.adjoint(p.nt, p.dt, A)
+    dev = torch.zeros((3, p.nz, p.ny, p.nx), device="cuda")
+    ews.ews_adjoint(sim.handle, p.nt, p.dt, torch.from_numpy(A).cuda(), dev[0], dev[1], dev[2])
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), host)
+    pc = problem((40, 36, 28), "cpml", "moment")
+    simc = ews.simulation_for(pc)
+    with pytest.raises(ews.EwsError) as e:
+        simc.adjoint(pc.nt, pc.dt, np.zeros((3, pc.rec_pos.shape[0], pc.nt), np.float32))
+    assert e.value.status == ews.EWS_EINVAL
