@@ -51,6 +51,10 @@ def parse_args():
     ap.add_argument("--nt", type=int, default=2000, help="time steps per bench step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint-gradient / forward time ratio")
+    ap.add_argument("--adj-n", type=int, default=192)
+    ap.add_argument("--adj-nt", type=int, default=1500)
     return ap.parse_args()
 
 
@@ -152,11 +156,12 @@ def algorithmic_bytes(prob):
 
 
 def kernel_source_sha() -> str:
+    """Hash of the stencil kernels' source (the kernels the traffic figure
+    belongs to); any edit there voids the committed figure."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2112_15071_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("ews_stencil.cu",):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -306,10 +311,58 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(klaunch.sum()) * world,
         "e2e": e2e, "clocks": clk,
     }
+    if not args.no_adjoint:
+        out["adjoint"] = adjoint_ratio(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
     sim.close()
     return out
+
+
+def adjoint_ratio(args, local):
+    """Adjoint workload: 192^3, dx = 15 m, 1500 steps, sponge 20, explosion,
+    20 x 20 receivers, L2 misfit against data from the model with a 10 %
+    sphere, checkpoints every 50 steps.  Times one forward run and one
+    gradient (forward with checkpoints + segment recompute + adjoint)."""
+    import torch
+    from paper_2112_15071_gb300 import ews, synth
+    true, start = synth.config4(n=args.adj_n, nt=args.adj_nt)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sim_t = ews.simulation_for(true)
+    sim_t.set_stream(stream.cuda_stream)
+    obs = torch.zeros((3, sim_t.nrec, true.nt), device=dev)
+    sim_t.run(true.nt, true.dt, obs)
+    sim_t.close()
+    sim = ews.simulation_for(start)
+    sim.set_stream(stream.cuda_stream)
+    seis = torch.zeros_like(obs)
+    g = torch.zeros((3, start.nz, start.ny, start.nx), device=dev)
+
+    def timed(fn):
+        fn()                                     # warm-up (allocations, plan)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    fwd_ms = timed(lambda: sim.run(start.nt, start.dt, seis))
+    mis = [0.0]
+
+    def grad():
+        mis[0] = ews.ews_gradient(sim.handle, start.nt, start.dt, obs, g[0], g[1], g[2], 50)
+
+    grad_ms = timed(grad)
+    sim.close()
+    return {"workload": f"{start.nx}^3 dx={start.spacing[0]} m, {start.nt} steps, sponge "
+                        f"{start.width}, explosion 6 Hz, {start.rec_pos.shape[0]} receivers, "
+                        "L2 misfit vs 10% sphere model, checkpoints every 50",
+            "forward_ms": round(fwd_ms, 2), "gradient_ms": round(grad_ms, 2),
+            "ratio": round(grad_ms / fwd_ms, 3), "misfit": mis[0]}
 
 
 # --- reference arm: the FP64 oracle on the host cores -------------------------

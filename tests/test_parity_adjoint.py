@@ -121,3 +121,24 @@ def test_adjoint_device_buffers_and_cpml_refusal(ews):
     with pytest.raises(ews.EwsError) as e:
         simc.adjoint(pc.nt, pc.dt, np.zeros((3, pc.rec_pos.shape[0], pc.nt), np.float32))
     assert e.value.status == ews.EWS_EINVAL
+
+
+def test_autograd_function_matches_ews_gradient(ews, orc):
+    """Backpropagating an L2 loss through the differentiable forward run
+    gives the ews_gradient result (same kernels, loss formed by torch)."""
+    import torch
+    from paper_2112_15071_gb300 import autograd as AG
+    p = problem((40, 36, 28), "sponge", "moment", nt=100)
+    sim = ews.simulation_for(p)
+    lam, mu, rho = (torch.from_numpy(a).cuda().requires_grad_(True) for a in p.lame())
+    obs = torch.from_numpy((orc.run_problem(p) * 1.1).astype(np.float32)).cuda()
+    seis = AG.seismograms(sim, lam, mu, rho, p.nt, p.dt, ckpt_every=20)
+    loss = 0.5 * p.dt * ((seis - obs) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    sim2 = ews.simulation_for(p)
+    sim2.set_model_lame(*p.lame())
+    mis, g = sim2.gradient(p.nt, p.dt, obs.cpu().numpy(), ckpt_every=20)
+    assert float(loss) == pytest.approx(mis, rel=1e-5)
+    for q, t in enumerate((lam, mu, rho)):
+        assert rel(t.grad.cpu().numpy(), g[q]) <= 1e-5
