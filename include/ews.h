@@ -58,7 +58,8 @@ typedef enum {
     EWS_ECUDA = 4,       /* CUDA runtime or driver error                    */
     EWS_ENONFINITE = 5,  /* NaN/Inf in a model or in the wavefield          */
     EWS_ETIMEOUT = 6,    /* a bounded device wait gave up                   */
-    EWS_ESTATE = 7       /* call out of order (e.g. run before set_model)   */
+    EWS_ESTATE = 7,      /* call out of order (e.g. run before set_model)   */
+    EWS_ERANGE = 8       /* a scaled FP16 wavefield value left FP16's range */
 } ews_status;
 
 enum { EWS_BOUNDARY_NONE = 0, EWS_BOUNDARY_SPONGE = 1, EWS_BOUNDARY_CPML = 2 };
@@ -78,7 +79,16 @@ typedef struct {
      * (1 - q)).  NONE: zero exterior only. */
     int boundary;
     int width;               /* W in cells; 2 W <= n on every axis           */
-    int storage;             /* EWS_STORAGE_F32 (BF16/F16: reserved)         */
+    /* Storage type of the 9 resident wavefields; arithmetic is FP32 and the
+     * medium is always FP32.  BF16 / F16 hold s_q times field q for a
+     * per-field power-of-two scale s_q (ews_set_field_scales).  Defaults:
+     * s_q = 1 for BF16 (it has FP32's exponent range); for F16, scales
+     * derived at each run start from the source amplitude summed over the
+     * wavelet and the medium's impedance bounds, mapping that bound to 2^13.
+     * Reduced storage is an addition to the method (the paper keeps float
+     * textures, Sec. 3); its error is measured, not bounded.  The adjoint
+     * (ews_adjoint / ews_gradient) needs F32. */
+    int storage;
     int snapshot_every;      /* 0: no snapshots                               */
     unsigned snapshot_mask;  /* fields copied at each snapshot               */
     double sponge_alpha;     /* <= 0 selects 0.3                              */
@@ -89,7 +99,8 @@ typedef struct {
 typedef struct ews_sim ews_sim;
 
 /* Create a simulation on the current CUDA device.  Allocates the 9
- * wavefields and 3 medium arrays (and C-PML memory variables in the slabs).
+ * wavefields (of the storage type) and 3 FP32 medium arrays (and C-PML
+ * memory variables, FP32).
  * opt may be NULL (sponge, W = 16).  *out receives the handle. */
 ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** out);
 
@@ -172,9 +183,23 @@ ews_status ews_gradient(ews_sim* sim, int nt, double dt, const float* observed,
 /* Zero the wavefields and C-PML memory variables. */
 ews_status ews_reset(ews_sim* sim);
 
-/* Copy the 9 wavefields out of / into the simulation, [9][nz][ny][nx]. */
+/* Copy the 9 wavefields out of / into the simulation, [9][nz][ny][nx]
+ * float32 in physical units (16-bit storage is converted with the field
+ * scales; set_state returns EWS_ERANGE if a scaled value exceeds FP16). */
 ews_status ews_get_state(ews_sim* sim, float* out, int on_device);
 ews_status ews_set_state(ews_sim* sim, const float* in, int on_device);
+
+/* Per-field storage scales s[9] (state order) for BF16 / F16 storage: each
+ * a positive power of two, so scaling itself never rounds.  Field q is
+ * stored as s[q] times its value; stencil derivatives are formed on stored
+ * values and multiplied by 1 / s[input field], updates by dt s[output
+ * field].  scale = NULL restores the defaults (see ews_options.storage).
+ * With F32 storage only all-ones is accepted.  Zeroes the wavefields (as
+ * ews_reset) so no field is ever read at another scale than it was
+ * written with.  This has no counterpart in the paper. */
+ews_status ews_set_field_scales(ews_sim* sim, const float* scale);
+/* The scales in use (after a run: the ones that run used). */
+ews_status ews_get_field_scales(ews_sim* sim, float* scale);
 
 /* Kernel classes for launch counting and timing. */
 enum {

@@ -67,11 +67,19 @@ struct ews_sim {
     ews_grid grid{};
     ews_options opt{};
     DevGrid g{};
-    size_t fstride = 0;           // floats between fields
-    float* fields = nullptr;      // 9 * fstride
-    float* medium = nullptr;      // 3 * fstride: lambda, mu, rho
+    size_t fstride = 0;           // elements between fields (and medium arrays)
+    int es = 4;                   // bytes per stored wavefield element
+    float* fields = nullptr;      // 9 * fstride elements of the storage type
+    float* medium = nullptr;      // 3 * fstride floats: lambda, mu, rho
     bool model_set = false;
     float vpmax = 0.0f;
+    float rho_min = 0.0f, zs_min = 0.0f, zp_max = 0.0f;   // medium bounds
+    // per-field storage scales (16-bit storage holds scale[q] x value)
+    float scale[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    bool scale_user = false;      // set by ews_set_field_scales
+    bool fresh = true;            // wavefields are all zero
+    float* stage = nullptr;       // dense float32 staging for 16-bit state I/O
+    size_t stage_cap = 0;
     // boundary
     float* prof = nullptr;        // g[3][n], pa[3][n], pb[3][n] packed
     float* psi = nullptr;         // C-PML memory variables
@@ -80,6 +88,7 @@ struct ews_sim {
     double pml_dt = -1.0;
     // source
     SourceSpec src;
+    double wsum = 0;              // sum of |wavelet|
     DevSource S{};
     float* wavelet = nullptr;
     int wavelet_nt = 0;
@@ -111,11 +120,13 @@ struct ews_sim {
     float* gout = nullptr;                // gradient staging for host outputs
     double* dmisfit = nullptr;
 
+    void* field(int q) const { return (char*)fields + (size_t)q * fstride * es; }
     DevFields F() const {
         DevFields f;
-        for (int q = 0; q < NFIELD; ++q) f.f[q] = fields + q * fstride;
+        for (int q = 0; q < NFIELD; ++q) f.f[q] = (float*)field(q);
         return f;
     }
+    bool wide() const { return opt.storage == EWS_STORAGE_F32; }
     DevMedium M() const {
         DevMedium m;
         m.lam = medium;
@@ -234,6 +245,42 @@ ews_status copy_field_out(ews_sim* s, float* dst, const float* src, int on_devic
     return EWS_OK;
 }
 
+template <typename T>
+ews_status ensure_buf(T** buf, size_t* cap, size_t need, const char* what);
+
+// Wavefield q to / from a dense float32 [nz][ny][nx] array (host or device),
+// converting 16-bit storage with the field's scale.
+ews_status field_out(ews_sim* s, int q, float* dst, int on_device) {
+    if (s->wide()) return copy_field_out(s, dst, (const float*)s->field(q), on_device);
+    float* d = dst;
+    if (!on_device) {
+        ews_status st = ensure_buf(&s->stage, &s->stage_cap, (size_t)s->ncell(), "staging");
+        if (st != EWS_OK) return st;
+        d = s->stage;
+    }
+    CK(launch_field_out(s->g, s->field(q), s->opt.storage, 1.0f / s->scale[q], d, s->stream));
+    if (!on_device)
+        CK(cudaMemcpyAsync(dst, d, (size_t)s->ncell() * sizeof(float), cudaMemcpyDeviceToHost,
+                           s->stream));
+    if (!on_device) CK(cudaStreamSynchronize(s->stream));   // the staging buffer is reused
+    return EWS_OK;
+}
+
+ews_status field_in(ews_sim* s, int q, const float* src, int on_device) {
+    if (s->wide()) return copy_field_in(s, (float*)s->field(q), src, on_device);
+    const float* d = src;
+    if (!on_device) {
+        ews_status st = ensure_buf(&s->stage, &s->stage_cap, (size_t)s->ncell(), "staging");
+        if (st != EWS_OK) return st;
+        CK(cudaMemcpyAsync(s->stage, src, (size_t)s->ncell() * sizeof(float),
+                           cudaMemcpyHostToDevice, s->stream));
+        d = s->stage;
+    }
+    CK(launch_field_in(s->g, d, s->opt.storage, s->scale[q], s->field(q), s->err, s->stream));
+    if (!on_device) CK(cudaStreamSynchronize(s->stream));
+    return EWS_OK;
+}
+
 ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rho,
                      int on_device, int from_vel) {
     if (!s) return fail(EWS_EINVAL, "null simulation");
@@ -243,10 +290,11 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
     if ((st = copy_field_in(s, (float*)M.lam, a, on_device)) != EWS_OK) return st;
     if ((st = copy_field_in(s, (float*)M.mu, b, on_device)) != EWS_OK) return st;
     if ((st = copy_field_in(s, (float*)M.rho, rho, on_device)) != EWS_OK) return st;
-    CK(cudaMemsetAsync(s->flags, 0, 2 * sizeof(unsigned), s->stream));
+    CK(cudaMemsetAsync(s->flags, 0, 5 * sizeof(unsigned), s->stream));
+    CK(cudaMemsetAsync(s->flags + 2, 0x7F, 2 * sizeof(unsigned), s->stream));   // min slots: 3.4e38
     CK(launch_medium_setup(s->g, (float*)M.lam, (float*)M.mu, (float*)M.rho, from_vel,
                            s->flags, s->stream));
-    unsigned hf[2];
+    unsigned hf[5];
     CK(cudaMemcpyAsync(hf, s->flags, sizeof(hf), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->model_set = false;
@@ -254,9 +302,12 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
     if (hf[0] & 2u) return fail(EWS_EINVAL, "model has rho <= 0");
     if (hf[0] & 4u) return fail(EWS_EINVAL, "model has mu < 0 (vs^2 < 0)");
     if (hf[0] & 8u) return fail(EWS_EINVAL, "model has lambda + 2 mu <= 0");
-    float vp;
-    std::memcpy(&vp, &hf[1], sizeof(vp));
-    s->vpmax = vp;
+    float bnd[4];
+    std::memcpy(bnd, &hf[1], sizeof(bnd));
+    s->vpmax = bnd[0];
+    s->rho_min = bnd[1];
+    s->zs_min = bnd[2];
+    s->zp_max = bnd[3];
     s->model_set = true;
     s->pml_dt = -1.0;
     return EWS_OK;
@@ -302,6 +353,44 @@ ews_status mark(ews_sim* s, int cls) {
     return EWS_OK;
 }
 
+// Power of two at or below x (x > 0, finite).
+float pow2_floor(double x) {
+    int e;
+    std::frexp(x, &e);
+    return (float)std::ldexp(1.0, e - 1);
+}
+
+// Default per-field scales of FP16 storage (Sec. 2.4 source terms): the
+// amplitude the source can put into one cell, summed over the whole
+// wavelet, bounds the field it drives; the other field group follows
+// through the impedance relation |sigma| = Z |v| of a plane wave (smallest
+// impedance for v, largest for sigma).  Each scale maps its bound to 2^13,
+// 8x below the FP16 maximum; kernels flag any stored value beyond it.
+void auto_scales(ews_sim* s, double dt) {
+    if (s->opt.storage != EWS_STORAGE_F16 || s->scale_user) return;
+    const double vol = s->grid.dx * s->grid.dy * s->grid.dz;
+    const double zs = (s->zs_min > 0 && s->zs_min < 1e38f) ? s->zs_min : s->zp_max;
+    double vb = 0, sb = 0;
+    if (s->src.kind >= 0 && s->wsum > 0) {
+        double cmax = 0;
+        for (int c = 0; c < 6; ++c) cmax = std::max(cmax, std::fabs(s->src.comp[c]));
+        const double inj = cmax * dt * s->wsum / vol;
+        if (s->src.kind == EWS_SOURCE_MOMENT) {
+            sb = inj;
+            vb = zs > 0 ? sb / zs : 0;
+        } else {
+            vb = s->rho_min > 0 ? inj / s->rho_min : 0;
+            sb = vb * s->zp_max;
+        }
+    }
+    for (int q = 0; q < NFIELD; ++q) {
+        const double bound = q < 3 ? vb : sb;
+        double sc = (bound > 0 && std::isfinite(bound)) ? 8192.0 / bound : 1.0;
+        sc = std::min(std::max(sc, 0x1p-100), 0x1p100);
+        s->scale[q] = pow2_floor(sc);
+    }
+}
+
 ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
                  float* dseis, int ld, float* vcap = nullptr) {
     DevFields F = s->F();
@@ -316,39 +405,48 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
         if (src.kind == EWS_SOURCE_MOMENT) {
             for (int c = 0; c < 6; ++c) {
                 if (src.comp[c] == 0.0) continue;
-                taps_for(s, SXX + c, src.pos, -dt * src.comp[c] / vol, &S.tap[S.ntap]);
+                taps_for(s, SXX + c, src.pos, -dt * src.comp[c] / vol * s->scale[SXX + c],
+                         &S.tap[S.ntap]);
                 S.ntap += 8;
             }
         } else {
             for (int c = 0; c < 3; ++c) {
                 if (src.comp[c] == 0.0) continue;
-                taps_for(s, VX + c, src.pos, dt * src.comp[c] / vol, &S.tap[S.ntap]);
+                taps_for(s, VX + c, src.pos, dt * src.comp[c] / vol * s->scale[VX + c],
+                         &S.tap[S.ntap]);
                 S.ntap += 8;
             }
         }
     }
-    const float fdt = (float)dt;
+    // dt x scale of each output field, 1 / scale of each input field
+    float dto[NFIELD], inv[NFIELD];
+    for (int q = 0; q < NFIELD; ++q) {
+        dto[q] = (float)(dt * s->scale[q]);
+        inv[q] = 1.0f / s->scale[q];
+    }
+    const int stor = s->opt.storage;
+    s->fresh = false;
     ews_status st;
     if ((st = mark(s, -1)) != EWS_OK) return st;
     for (int n = n0; n < n0 + nsteps; ++n) {
-        CK(launch_velocity(s->plan, s->g, F, s->B, fdt, s->err, s->stream));
+        CK(launch_velocity(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
         if ((st = mark(s, EWS_KERNEL_VELOCITY)) != EWS_OK) return st;
         if (S.kind == EWS_SOURCE_FORCE) {
-            CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, s->stream));
+            CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, stor, s->err, s->stream));
             if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
         }
         if (s->nrec > 0 && dseis) {
-            CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, s->stream));
+            CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, stor, inv, s->stream));
             if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
         }
         if (vcap)   // v^{n+1/2} into the history slot of step n (fields 0..2 are contiguous)
             CK(cudaMemcpyAsync(vcap + (size_t)(n - n0 + 1) * 3 * s->fstride, s->fields,
                                3 * s->fstride * sizeof(float), cudaMemcpyDeviceToDevice,
                                s->stream));
-        CK(launch_stress(s->plan, s->g, F, s->B, fdt, s->err, s->stream));
+        CK(launch_stress(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
         if ((st = mark(s, EWS_KERNEL_STRESS)) != EWS_OK) return st;
         if (S.kind == EWS_SOURCE_MOMENT) {
-            CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, s->stream));
+            CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, stor, s->err, s->stream));
             if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
         }
     }
@@ -391,6 +489,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     if (st != EWS_OK) return st;
     if (s->opt.boundary == EWS_BOUNDARY_CPML)
         return fail(EWS_EINVAL, "the adjoint supports the none and sponge boundaries");
+    if (!s->wide()) return fail(EWS_EINVAL, "the adjoint needs F32 wavefield storage");
     const int K = ckpt_every > 0 ? (ckpt_every < nt ? ckpt_every : nt) : (nt < 50 ? nt : 50);
     const int nck = (nt + K - 1) / K;
     const size_t fs = s->fstride;
@@ -521,7 +620,9 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
         if (2 * o.width > grid->nx || 2 * o.width > grid->ny || 2 * o.width > grid->nz)
             return fail(EWS_EINVAL, "2 * width exceeds the grid");
     }
-    if (o.storage != EWS_STORAGE_F32) return fail(EWS_EINVAL, "only F32 storage is built");
+    if (o.storage != EWS_STORAGE_F32 && o.storage != EWS_STORAGE_BF16 &&
+        o.storage != EWS_STORAGE_F16)
+        return fail(EWS_EINVAL, "unknown storage type %d", o.storage);
     if (o.snapshot_every < 0) return fail(EWS_EINVAL, "snapshot_every < 0");
     if (o.snapshot_mask >> NFIELD) return fail(EWS_EINVAL, "snapshot_mask has unknown bits");
     int dev = 0;
@@ -546,6 +647,7 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
     g.c1z = (float)(kC1 / grid->dz);
     g.c2z = (float)(kC2 / grid->dz);
     s->fstride = (size_t)((g.plane * g.nz + 63) / 64 * 64);
+    s->es = o.storage == EWS_STORAGE_F32 ? 4 : 2;
     s->B.kind = o.boundary;
     s->B.W = o.width;
 
@@ -553,14 +655,14 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
         ews_destroy(s);
         return st;
     };
-    e = cudaMalloc(&s->fields, NFIELD * s->fstride * sizeof(float));
+    e = cudaMalloc(&s->fields, NFIELD * s->fstride * s->es);
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "wavefields: %s", cudaGetErrorString(e)));
     e = cudaMalloc(&s->medium, 3 * s->fstride * sizeof(float));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "medium: %s", cudaGetErrorString(e)));
     const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
     e = cudaMalloc(&s->prof, 9 * (size_t)nmax * sizeof(float));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "profiles: %s", cudaGetErrorString(e)));
-    e = cudaMalloc(&s->flags, 2 * sizeof(unsigned));
+    e = cudaMalloc(&s->flags, 5 * sizeof(unsigned));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "flags: %s", cudaGetErrorString(e)));
     e = cudaMalloc(&s->err, sizeof(int));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "err: %s", cudaGetErrorString(e)));
@@ -571,13 +673,13 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
             return cleanup(fail(EWS_ENOMEM, "C-PML memory: %s", cudaGetErrorString(e)));
         for (int t = 0; t < 18; ++t) s->B.psi[t] = s->psi + t * s->fstride;
     }
-    e = cudaMemset(s->fields, 0, NFIELD * s->fstride * sizeof(float));
+    e = cudaMemset(s->fields, 0, NFIELD * s->fstride * s->es);
     if (e == cudaSuccess) e = cudaMemset(s->medium, 0, 3 * s->fstride * sizeof(float));
     if (e == cudaSuccess && s->psi) e = cudaMemset(s->psi, 0, s->psi_floats * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup(fail(EWS_ECUDA, "memset: %s", cudaGetErrorString(e)));
-    e = stencil_plan_create(s->g, s->F(), s->M(), s->B, &s->plan);
+    e = stencil_plan_create(s->g, s->F(), s->M(), s->B, o.storage, &s->plan);
     if (e != cudaSuccess)
         return cleanup(fail(EWS_ECUDA, "stencil plan (TMA descriptors): %s", cudaGetErrorString(e)));
     *out = s;
@@ -605,6 +707,7 @@ void ews_destroy(ews_sim* s) {
     cudaFree(s->aux);
     cudaFree(s->gout);
     cudaFree(s->dmisfit);
+    cudaFree(s->stage);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     delete s;
 }
@@ -648,6 +751,8 @@ ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const doubl
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->wavelet_nt = nt;
+    s->wsum = 0;
+    for (int n = 0; n < nt; ++n) s->wsum += std::fabs((double)wavelet[n]);
     SourceSpec& sp = s->src;
     sp.kind = kind;
     for (int a = 0; a < 3; ++a) sp.pos[a] = pos[a];
@@ -681,8 +786,9 @@ ews_status ews_set_receivers(ews_sim* s, int nrec, const double* pos) {
 
 ews_status ews_reset(ews_sim* s) {
     if (!s) return fail(EWS_EINVAL, "null simulation");
-    CK(cudaMemsetAsync(s->fields, 0, NFIELD * s->fstride * sizeof(float), s->stream));
+    CK(cudaMemsetAsync(s->fields, 0, NFIELD * s->fstride * s->es, s->stream));
     if (s->psi) CK(cudaMemsetAsync(s->psi, 0, s->psi_floats * sizeof(float), s->stream));
+    s->fresh = true;
     return EWS_OK;
 }
 
@@ -693,6 +799,7 @@ ews_status ews_advance(ews_sim* s, int n0, int nsteps, double dt, float* seis, i
     if (s->nrec > 0 && seis && ld < n0 + nsteps) return fail(EWS_EINVAL, "ld too small");
     ews_status st = ensure_ready(s, n0 + nsteps, dt);
     if (st != EWS_OK) return st;
+    if (s->fresh) auto_scales(s, dt);
     float* dseis = nullptr;
     if (s->nrec > 0 && seis) {
         if (seis_on_device) {
@@ -722,8 +829,11 @@ ews_status ews_advance(ews_sim* s, int n0, int nsteps, double dt, float* seis, i
     CK(cudaGetLastError());
     if (herr) {
         CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
-        return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up (flags %d)",
-                    herr);
+        if (herr & 3)
+            return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up (flags %d)",
+                        herr);
+        return fail(EWS_ERANGE, "a wavefield value exceeded the FP16 range: lower the field "
+                                "scales (ews_set_field_scales)");
     }
     if (s->profiling && (st = collect_profile(s)) != EWS_OK) return st;
     return EWS_OK;
@@ -748,8 +858,7 @@ ews_status ews_run(ews_sim* s, int nt, double dt, float* seis, int seis_on_devic
         if ((st = ews_advance(s, n0, every, dt, seis, nt, seis_on_device)) != EWS_OK) return st;
         for (int q = 0; q < NFIELD; ++q)
             if (mask & (1u << q)) {
-                st = copy_field_out(s, snapshots + slot * ncell, s->fields + q * s->fstride,
-                                    seis_on_device);
+                st = field_out(s, q, snapshots + slot * ncell, seis_on_device);
                 if (st != EWS_OK) return st;
                 ++slot;
             }
@@ -785,7 +894,7 @@ ews_status ews_get_state(ews_sim* s, float* out, int on_device) {
     if (!s || !out) return fail(EWS_EINVAL, "null argument");
     const size_t ncell = (size_t)s->ncell();
     for (int q = 0; q < NFIELD; ++q) {
-        ews_status st = copy_field_out(s, out + q * ncell, s->fields + q * s->fstride, on_device);
+        ews_status st = field_out(s, q, out + q * ncell, on_device);
         if (st != EWS_OK) return st;
     }
     CK(cudaStreamSynchronize(s->stream));
@@ -796,11 +905,48 @@ ews_status ews_set_state(ews_sim* s, const float* in, int on_device) {
     if (!s || !in) return fail(EWS_EINVAL, "null argument");
     const size_t ncell = (size_t)s->ncell();
     for (int q = 0; q < NFIELD; ++q) {
-        ews_status st = copy_field_in(s, s->fields + q * s->fstride, in + q * ncell, on_device);
+        ews_status st = field_in(s, q, in + q * ncell, on_device);
         if (st != EWS_OK) return st;
     }
     if (s->psi) CK(cudaMemsetAsync(s->psi, 0, s->psi_floats * sizeof(float), s->stream));
+    s->fresh = false;
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    if (herr) {
+        CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        return fail(EWS_ERANGE, "a state value exceeds the FP16 range at the field scales");
+    }
+    return EWS_OK;
+}
+
+ews_status ews_set_field_scales(ews_sim* s, const float* scale) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (!scale) {                      // back to the defaults
+        for (int q = 0; q < NFIELD; ++q) s->scale[q] = 1.0f;
+        s->scale_user = false;
+        return ews_reset(s);
+    }
+    for (int q = 0; q < NFIELD; ++q) {
+        const float v = scale[q];
+        int e;
+        if (!(v > 0) || !std::isfinite(v) || std::frexp(v, &e) != 0.5f)
+            return fail(EWS_EINVAL, "field scale %d (%g) is not a positive power of two", q,
+                        (double)v);
+    }
+    if (s->wide()) {
+        for (int q = 0; q < NFIELD; ++q)
+            if (scale[q] != 1.0f) return fail(EWS_EINVAL, "F32 storage takes no field scales");
+    }
+    for (int q = 0; q < NFIELD; ++q) s->scale[q] = scale[q];
+    s->scale_user = true;
+    return ews_reset(s);
+}
+
+ews_status ews_get_field_scales(ews_sim* s, float* scale) {
+    if (!s || !scale) return fail(EWS_EINVAL, "null argument");
+    for (int q = 0; q < NFIELD; ++q) scale[q] = s->scale[q];
     return EWS_OK;
 }
 

@@ -1,7 +1,13 @@
 // ews_forward.cu -- small kernels around the stencil passes (sm_103a):
-// point-source injection, receiver sampling (Sec. 2.4) and the medium
-// set-up (vp/vs -> Lame, validity flags, vp_max).  The velocity and stress
-// passes themselves are in ews_stencil.cu.
+// point-source injection, receiver sampling (Sec. 2.4), the medium set-up
+// (vp/vs -> Lame, validity flags, bounds) and the conversion of 16-bit
+// stored fields to and from float32.  The velocity and stress passes
+// themselves are in ews_stencil.cu.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "ews_internal.cuh"
 
 namespace ews {
@@ -16,11 +22,26 @@ __device__ __forceinline__ float med(const float* __restrict__ m, const DevGrid&
     return __ldg(m + (long long)k * g.plane + (long long)j * g.pitch + i);
 }
 
+template <typename T> struct Io;
+template <> struct Io<float> {
+    __device__ static float get(const float* p) { return *p; }
+    __device__ static float put(float x) { return x; }
+};
+template <> struct Io<__nv_bfloat16> {
+    __device__ static float get(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static __nv_bfloat16 put(float x) { return __float2bfloat16_rn(x); }
+};
+template <> struct Io<__half> {
+    __device__ static float get(const __half* p) { return __half2float(*p); }
+    __device__ static __half put(float x) { return __float2half_rn(x); }
+};
+
 // Point-source injection (one thread per tap).  Runs after the pass it
 // belongs to; the sponge gain is applied to the injected amount, which
-// equals injecting before the gain.
+// equals injecting before the gain.  Tap weights include the field scale.
+template <typename T>
 __global__ void k_inject(DevGrid g, DevFields F, DevMedium M, DevBoundary B, DevSource S,
-                         const float* __restrict__ wavelet, int n) {
+                         const float* __restrict__ wavelet, int n, int* err) {
     const int t = threadIdx.x;
     if (t >= S.ntap) return;
     const Tap tp = S.tap[t];
@@ -35,12 +56,20 @@ __global__ void k_inject(DevGrid g, DevFields F, DevMedium M, DevBoundary B, Dev
     if (B.kind == BND_SPONGE)
         amp *= __ldg(B.g[0] + tp.i) * __ldg(B.g[1] + tp.j) * __ldg(B.g[2] + tp.k);
     // several taps may hit the same element (e.g. a source on a grid point)
-    atomicAdd(F.f[tp.q] + c, amp);
+    T* f = reinterpret_cast<T*>(F.f[tp.q]) + c;
+    if constexpr (sizeof(T) == 4) {
+        atomicAdd(f, amp);
+    } else {
+        const float now = Io<T>::get(f) + amp;    // estimate for the range check
+        atomicAdd(f, Io<T>::put(amp));
+        if (std::is_same<T, __half>::value && fabsf(now) > 65504.0f) atomicOr(err, 4);
+    }
 }
 
 // Receiver sampling: one thread per (component, receiver), 8 taps each.
+template <typename T>
 __global__ void k_record(DevGrid g, DevFields F, const Tap* __restrict__ taps, int nrec,
-                         float* __restrict__ seis, int ld, int n) {
+                         float* __restrict__ seis, int ld, int n, float i0, float i1, float i2) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nrec) return;
     const Tap* tp = taps + 8 * t;
@@ -48,22 +77,44 @@ __global__ void k_record(DevGrid g, DevFields F, const Tap* __restrict__ taps, i
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const Tap q = tp[m];
-        acc += q.w * F.f[q.q][(long long)q.k * g.plane + (long long)q.j * g.pitch + q.i];
+        acc += q.w * Io<T>::get(reinterpret_cast<const T*>(F.f[q.q]) +
+                                (long long)q.k * g.plane + (long long)q.j * g.pitch + q.i);
     }
+    if constexpr (sizeof(T) == 2) acc *= (t < nrec ? i0 : t < 2 * nrec ? i1 : i2);
     seis[(long long)t * ld + n] = acc;
 }
 
+// Stored field -> dense float32 (out = stored * inv_s) and back.
+template <typename T>
+__global__ void k_field_out(DevGrid g, const T* __restrict__ f, float inv_s, float* __restrict__ d) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    d[((long long)k * g.ny + j) * g.nx + i] =
+        Io<T>::get(f + (long long)k * g.plane + (long long)j * g.pitch + i) * inv_s;
+}
+template <typename T>
+__global__ void k_field_in(DevGrid g, const float* __restrict__ d, float s, T* __restrict__ f,
+                           int* err) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const float x = d[((long long)k * g.ny + j) * g.nx + i] * s;
+    if (std::is_same<T, __half>::value && fabsf(x) > 65504.0f) atomicOr(err, 4);
+    f[(long long)k * g.plane + (long long)j * g.pitch + i] = Io<T>::put(x);
+}
+
 // In-place medium set-up on pitched arrays: optional (vp, vs) -> (lambda,
-// mu), validity flags and vp_max (as float bits; all values are >= 0).
-// flags_vpmax[0]: bit0 non-finite, bit1 rho <= 0, bit2 mu < 0, bit3
-// lambda + 2 mu <= 0;  flags_vpmax[1]: vp_max bits.
+// mu), validity flags and bounds (as float bits of non-negative values, so
+// unsigned atomics order them).  flags[0]: bit0 non-finite, bit1 rho <= 0,
+// bit2 mu < 0, bit3 lambda + 2 mu <= 0;  flags[1]: max vp; flags[2]: min
+// rho; flags[3]: min sqrt(rho mu) over mu > 0; flags[4]: max sqrt(rho (lambda + 2 mu)).
 __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int from_vel,
-                               unsigned* flags_vpmax) {
+                               unsigned* flags) {
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
     const int k = blockIdx.z;
     unsigned flag = 0;
-    float vp = 0.0f;
+    float vp = 0.0f, zp = 0.0f;
+    float rmin = 3.0e38f, zsmin = 3.0e38f;
     if (i < g.nx && j < g.ny) {
         const long long c = (long long)k * g.plane + (long long)j * g.pitch + i;
         const float r = rho[c];
@@ -79,16 +130,27 @@ __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int fr
         if (!(r > 0.0f)) flag |= 2u;
         if (mu < 0.0f) flag |= 4u;
         if (!(lam + 2.0f * mu > 0.0f)) flag |= 8u;
-        if (flag == 0) vp = sqrtf((lam + 2.0f * mu) / r);
+        if (flag == 0) {
+            vp = sqrtf((lam + 2.0f * mu) / r);
+            zp = sqrtf(r * (lam + 2.0f * mu));
+            rmin = r;
+            if (mu > 0.0f) zsmin = sqrtf(r * mu);
+        }
     }
-    // warp-level reduce, then one atomic per warp
+    // warp-level reduce, then one atomic per warp and quantity
     for (int o = 16; o > 0; o >>= 1) {
         flag |= __shfl_xor_sync(0xffffffffu, flag, o);
         vp = fmaxf(vp, __shfl_xor_sync(0xffffffffu, vp, o));
+        zp = fmaxf(zp, __shfl_xor_sync(0xffffffffu, zp, o));
+        rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+        zsmin = fminf(zsmin, __shfl_xor_sync(0xffffffffu, zsmin, o));
     }
     if ((threadIdx.x & 31) == 0) {
-        if (flag) atomicOr(flags_vpmax, flag);
-        atomicMax(flags_vpmax + 1, __float_as_uint(vp));
+        if (flag) atomicOr(flags, flag);
+        atomicMax(flags + 1, __float_as_uint(vp));
+        atomicMin(flags + 2, __float_as_uint(rmin));
+        atomicMin(flags + 3, __float_as_uint(zsmin));
+        atomicMax(flags + 4, __float_as_uint(zp));
     }
 }
 
@@ -100,24 +162,83 @@ static dim3 plane_grid(const DevGrid& g) {
 
 cudaError_t launch_inject(const DevGrid& g, const DevFields& F, const DevMedium& M,
                           const DevBoundary& B, const DevSource& S, const float* wavelet,
-                          int n, cudaStream_t st) {
+                          int n, int storage, int* err, cudaStream_t st) {
     if (S.kind < 0 || S.ntap == 0) return cudaSuccess;
-    k_inject<<<1, kMaxSrcTaps, 0, st>>>(g, F, M, B, S, wavelet, n);
+    switch (storage) {
+        case EWS_STORAGE_BF16:
+            k_inject<__nv_bfloat16><<<1, kMaxSrcTaps, 0, st>>>(g, F, M, B, S, wavelet, n, err);
+            break;
+        case EWS_STORAGE_F16:
+            k_inject<__half><<<1, kMaxSrcTaps, 0, st>>>(g, F, M, B, S, wavelet, n, err);
+            break;
+        default:
+            k_inject<float><<<1, kMaxSrcTaps, 0, st>>>(g, F, M, B, S, wavelet, n, err);
+            break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps, int nrec,
-                          float* seis, int ld, int n, cudaStream_t st) {
+                          float* seis, int ld, int n, int storage, const float inv[3],
+                          cudaStream_t st) {
     if (nrec <= 0) return cudaSuccess;
     const int nt = 3 * nrec;
-    k_record<<<(nt + 127) / 128, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n);
+    const dim3 grid((nt + 127) / 128);
+    switch (storage) {
+        case EWS_STORAGE_BF16:
+            k_record<__nv_bfloat16><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2]);
+            break;
+        case EWS_STORAGE_F16:
+            k_record<__half><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2]);
+            break;
+        default:
+            k_record<float><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, 1.f, 1.f, 1.f);
+            break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_medium_setup(const DevGrid& g, float* a, float* b, float* rho,
-                                int from_velocities, unsigned* flags_vpmax, cudaStream_t st) {
-    k_medium_setup<<<plane_grid(g), dim3(32, 8), 0, st>>>(g, a, b, rho, from_velocities,
-                                                          flags_vpmax);
+                                int from_velocities, unsigned* flags, cudaStream_t st) {
+    k_medium_setup<<<plane_grid(g), dim3(32, 8), 0, st>>>(g, a, b, rho, from_velocities, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_out(const DevGrid& g, const void* field, int storage, float inv_s,
+                             float* dense, cudaStream_t st) {
+    switch (storage) {
+        case EWS_STORAGE_BF16:
+            k_field_out<<<plane_grid(g), dim3(32, 8), 0, st>>>(
+                g, static_cast<const __nv_bfloat16*>(field), inv_s, dense);
+            break;
+        case EWS_STORAGE_F16:
+            k_field_out<<<plane_grid(g), dim3(32, 8), 0, st>>>(
+                g, static_cast<const __half*>(field), inv_s, dense);
+            break;
+        default:
+            k_field_out<<<plane_grid(g), dim3(32, 8), 0, st>>>(
+                g, static_cast<const float*>(field), inv_s, dense);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_in(const DevGrid& g, const float* dense, int storage, float s,
+                            void* field, int* err, cudaStream_t st) {
+    switch (storage) {
+        case EWS_STORAGE_BF16:
+            k_field_in<<<plane_grid(g), dim3(32, 8), 0, st>>>(
+                g, dense, s, static_cast<__nv_bfloat16*>(field), err);
+            break;
+        case EWS_STORAGE_F16:
+            k_field_in<<<plane_grid(g), dim3(32, 8), 0, st>>>(
+                g, dense, s, static_cast<__half*>(field), err);
+            break;
+        default:
+            k_field_in<<<plane_grid(g), dim3(32, 8), 0, st>>>(
+                g, dense, s, static_cast<float*>(field), err);
+            break;
+    }
     return cudaGetLastError();
 }
 

@@ -1,11 +1,14 @@
 // ews_internal.cuh -- device data structures and kernel launchers of libews.
 //
 // Layout in HBM (one simulation):
-//   * 9 wavefields in one allocation, each [nz][ny][pitch] float32 with
-//     pitch = nx rounded up to 32 floats (128-byte rows, 16-byte aligned for
-//     vector and TMA access).  Padding columns stay zero and are never
-//     written.  Field q starts at base + q * fstride (fstride a multiple of
-//     64 floats).
+//   * 9 wavefields in one allocation, each [nz][ny][pitch] of the storage
+//     type (float32, or bf16 / fp16 holding s_q times the value for a
+//     per-field power-of-two scale s_q) with pitch = nx rounded up to 32
+//     elements (rows of 64 or 128 bytes, 16-byte aligned for TMA).  Padding
+//     columns stay zero and are never written.  Field q starts at element
+//     q * fstride of the allocation (fstride a multiple of 64 elements).
+//     DevFields carries the field base addresses as float*; kernels for
+//     16-bit storage cast them to the storage type.
 //   * lambda, mu, rho per cell in a second allocation, same layout.  The
 //     staggered-point means of Sec. 2.2.1 are formed in registers by the
 //     stencil kernels; nothing else about the medium is stored.
@@ -26,8 +29,8 @@ enum { BND_NONE = 0, BND_SPONGE = 1, BND_CPML = 2 };
 
 struct DevGrid {
     int nx, ny, nz;
-    int pitch;            // floats per row
-    long long plane;      // floats per z-plane = pitch * ny
+    int pitch;            // elements per row
+    long long plane;      // elements per z-plane = pitch * ny
     // Eq. 4 weights divided by the axis spacing (reading: the 1/h factor)
     float c1x, c2x, c1y, c2y, c1z, c2z;
 };
@@ -99,26 +102,44 @@ ews_status report(ews_status s, const char* fmt, ...);
 
 // Stencil passes (ews_stencil.cu): TMA tensor maps and launch geometry are
 // built once per simulation (the field and medium addresses never change).
+// The passes take, per field q, dto[q] = dt s_q (used for the fields they
+// write) and inv[q] = 1 / s_q (used for the 16-bit fields they read); with
+// FP32 storage s_q = 1.  *err collects bit 1 / 2 (a velocity / stress pipeline
+// wait gave up) and bit 4 (a value beyond the FP16 range was stored).
 struct StencilPlan;
 cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevMedium& M,
-                                const DevBoundary& B, StencilPlan** out);
+                                const DevBoundary& B, int storage, StencilPlan** out);
 void stencil_plan_destroy(StencilPlan* p);
 size_t stencil_plan_bytes();
 cudaError_t stencil_plan_fill(void* storage, const DevGrid& g, const DevFields& F,
                               const DevMedium& M, const DevBoundary& B, StencilPlan** out);
+int stencil_plan_storage(const StencilPlan* p);
 cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
-                            const DevBoundary& B, float dt, int* err, cudaStream_t st);
+                            const DevBoundary& B, const float dto[9], const float inv[9],
+                            int* err, cudaStream_t st);
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
-                          const DevBoundary& B, float dt, int* err, cudaStream_t st);
+                          const DevBoundary& B, const float dto[9], const float inv[9],
+                          int* err, cudaStream_t st);
 
-// Sources, receivers and medium set-up (ews_forward.cu).  All run on `st`.
+// Sources, receivers, medium set-up and storage conversion (ews_forward.cu).
+// All run on `st`; `storage` is the EWS_STORAGE_* type of the wavefields.
+// Source tap weights already include the field scale; receivers multiply
+// each sample by inv[component].
 cudaError_t launch_inject(const DevGrid& g, const DevFields& F, const DevMedium& M,
                           const DevBoundary& B, const DevSource& S, const float* wavelet,
-                          int n, cudaStream_t st);
+                          int n, int storage, int* err, cudaStream_t st);
 cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps, int nrec,
-                          float* seis, int ld, int n, cudaStream_t st);
+                          float* seis, int ld, int n, int storage, const float inv[3],
+                          cudaStream_t st);
+// flags[0]: validity bits; flags[1..4]: float bits of max vp, min rho,
+// min sqrt(rho mu) over cells with mu > 0 (else FLT_MAX), max sqrt(rho (lambda + 2 mu)).
 cudaError_t launch_medium_setup(const DevGrid& g, float* a, float* b, float* rho,
-                                int from_velocities, unsigned* flags_vpmax,
-                                cudaStream_t st);
+                                int from_velocities, unsigned* flags, cudaStream_t st);
+// One field between its stored form (pitched, `storage` type, scaled by s)
+// and a dense [nz][ny][nx] float32 array: out = stored / s, stored = s in.
+cudaError_t launch_field_out(const DevGrid& g, const void* field, int storage, float inv_s,
+                             float* dense, cudaStream_t st);
+cudaError_t launch_field_in(const DevGrid& g, const float* dense, int storage, float s,
+                            void* field, int* err, cudaStream_t st);
 
 }  // namespace ews

@@ -189,7 +189,7 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
         NA_CK(cudaMemcpy2DAsync(dst[a], pitch * sizeof(float), src[a], gr.nx * sizeof(float),
                                 gr.nx * sizeof(float), (size_t)gr.ny * gr.nz,
                                 cudaMemcpyDeviceToDevice, stream));
-    NA_CK(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), stream));
+    NA_CK(cudaMemsetAsync(flags, 0, 5 * sizeof(unsigned), stream));   // bounds 2..4 unused here
     NA_CK(launch_medium_setup(g, mlam, mmu, mrho, 0, flags, stream));
     unsigned hf[2] = {0, 0};
     NA_CK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, stream));
@@ -257,13 +257,18 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
     NA_CK(stencil_plan_fill(plan_buf, g, F, M, B, &plan));
 
     // ---- Sec. 2.3 loop ----
-    const float fdt = (float)dt;
+    float dto[NFIELD], inv[NFIELD];
+    for (int q = 0; q < NFIELD; ++q) {
+        dto[q] = (float)dt;
+        inv[q] = 1.0f;
+    }
+    const int f32 = EWS_STORAGE_F32;
     for (int n = 0; n < nt; ++n) {
-        NA_CK(launch_velocity(plan, g, F, B, fdt, err, stream));
-        if (src_kind == EWS_SOURCE_FORCE) NA_CK(launch_inject(g, F, M, B, S, wavelet, n, stream));
-        if (nrec > 0) NA_CK(launch_record(g, F, rtaps, nrec, seis, nt, n, stream));
-        NA_CK(launch_stress(plan, g, F, B, fdt, err, stream));
-        if (src_kind == EWS_SOURCE_MOMENT) NA_CK(launch_inject(g, F, M, B, S, wavelet, n, stream));
+        NA_CK(launch_velocity(plan, g, F, B, dto, inv, err, stream));
+        if (src_kind == EWS_SOURCE_FORCE) NA_CK(launch_inject(g, F, M, B, S, wavelet, n, f32, err, stream));
+        if (nrec > 0) NA_CK(launch_record(g, F, rtaps, nrec, seis, nt, n, f32, inv, stream));
+        NA_CK(launch_stress(plan, g, F, B, dto, inv, err, stream));
+        if (src_kind == EWS_SOURCE_MOMENT) NA_CK(launch_inject(g, F, M, B, S, wavelet, n, f32, err, stream));
     }
     int herr = 0;
     NA_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream));

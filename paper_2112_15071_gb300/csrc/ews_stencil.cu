@@ -9,6 +9,12 @@
 //     fields whose x or y derivative is taken, so every Eq. 4 tap (+-3/2
 //     around a staggered point) of the tile sits in shared memory;
 //   * "core" boxes of 32 x TY cells for fields read only at the cell itself.
+// The 9 wavefields are stored as FP32, BF16 or FP16 (the medium always as
+// FP32); arithmetic is FP32.  A 16-bit field f holds s_f times its value, a
+// power-of-two scale per field: derivatives are taken on stored values and
+// multiplied by 1/s_f, updates by dt s_f of the output field.  16-bit halo
+// boxes are 48 cells wide (x from x0-8) so that every copy starts on a
+// 16-byte boundary.
 // TMA writes zeros outside the grid, which is exactly the zero exterior of
 // the wavefields (Sec. 2.2.2 reading), so there are no edge branches.
 // z-derivatives come from per-thread register queues of 4 planes.  Output
@@ -23,9 +29,12 @@
 // mbarrier wait is bounded: on timeout the CTA records the failure in *err,
 // waits (bounded too) for its copies in flight and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <new>
+#include <type_traits>
 
 #include "ews_internal.cuh"
 #ifndef EWS_L2PROMO
@@ -46,33 +55,83 @@ namespace {
 #define EWS_WAVES 4
 #endif
 constexpr int TX = 32, TY = EWS_TILE_Y;
-constexpr int HX = TX + 8, HY = TY + 4;          // halo box
-constexpr int HALO = HX * HY;                     // floats per halo tile
-constexpr int CORE = TX * TY;                     // floats per core tile
+constexpr int HY = TY + 4;                        // halo rows: y0-2 .. y0+TY+1
+constexpr int HXF = TX + 8;                       // FP32 halo box: x0-4 .. x0+TX+3
+constexpr int HALOF = HXF * HY;                   // floats per FP32 halo tile
+constexpr int CORE = TX * TY;                     // elements per core tile
 constexpr int NSLOT = 4;                          // ring depth (planes) = unroll
 constexpr int MAXH = 6, MAXC = 7;
 constexpr int ROWS = EWS_ROWS;                    // cells per thread (adjacent y rows)
 constexpr int RY = TY / ROWS;                     // thread rows
 constexpr int NTH = TX * RY;                      // threads per CTA
-// one slot holds every tile of one plane: velocity 6 halo + 4 core,
-// stress 4 halo + 7 core
-constexpr int SLOT_MAIN = (6 * HALO + 4 * CORE) > (4 * HALO + 7 * CORE)
-                              ? (6 * HALO + 4 * CORE) : (4 * HALO + 7 * CORE);
-static_assert((SLOT_MAIN * 4) % 128 == 0 && (HALO * 4) % 128 == 0 && (CORE * 4) % 128 == 0,
-              "TMA destinations must stay 128-byte aligned");
 static_assert(TY % ROWS == 0, "rows per thread must divide the tile height");
-template <int BND>
-__host__ __device__ constexpr int slot_floats() { return SLOT_MAIN; }
-// C-PML memory variables of the output plane live in one extra buffer of 9
-// core tiles (3 terms for each damped direction), refilled for the next
-// output plane as soon as the current one has been consumed.
-constexpr int PSI_FLOATS = 9 * CORE;
-template <int BND>
-constexpr size_t smem_bytes() {
-    return (NSLOT * SLOT_MAIN + (BND == BND_CPML ? PSI_FLOATS : 0)) * sizeof(float) +
-           8 * (NSLOT + 1);
-}
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+// Storage of the 9 wavefields: FP32, BF16 or FP16 (arithmetic is FP32).  A
+// TMA tile must start on a 16-byte boundary, so a halo box of 16-bit fields
+// starts 8 cells left of the tile (4 for FP32).
+template <typename T> struct St;
+template <> struct St<float> {
+    static constexpr int HO = 4;
+    static constexpr CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    __device__ static float ld(const float* p) { return *p; }
+    __device__ static float put(float x) { return x; }
+};
+template <> struct St<__nv_bfloat16> {
+    static constexpr int HO = 8;
+    static constexpr CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static __nv_bfloat16 put(float x) { return __float2bfloat16_rn(x); }
+};
+template <> struct St<__half> {
+    static constexpr int HO = 8;
+    static constexpr CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    __device__ static float ld(const __half* p) { return __half2float(*p); }
+    __device__ static __half put(float x) { return __float2half_rn(x); }
+};
+
+// Slot layout of one plane, in bytes (every tile 128-byte aligned):
+//   velocity pass: 5 field halo tiles (sxx syy sxy sxz syz), the rho halo
+//   tile, 4 field core tiles (szz vx vy vz);
+//   stress pass: 3 field halo tiles (vx vy vz), the mu halo tile, the
+//   lambda core tile, 6 field core tiles.
+template <typename T>
+struct Lay {
+    static constexpr int HX = TX + 2 * St<T>::HO;             // field halo box width
+    static constexpr int HALO = HX * HY;                       // elements per field halo tile
+    static constexpr int HB = HALO * (int)sizeof(T);           // bytes per field halo tile
+    static constexpr int CB = CORE * (int)sizeof(T);           // bytes per field core tile
+    static constexpr int FHB = HALOF * 4, FCB = CORE * 4;      // FP32 halo / core tile bytes
+    // velocity pass
+    static constexpr int V_RHO = 5 * HB;
+    static constexpr int V_CORE = V_RHO + FHB;
+    static constexpr int V_BYTES = V_CORE + 4 * CB;
+    // stress pass
+    static constexpr int S_MU = 3 * HB;
+    static constexpr int S_LAM = S_MU + FHB;
+    static constexpr int S_CORE = S_LAM + FCB;
+    static constexpr int S_BYTES = S_CORE + 6 * CB;
+    static constexpr int SLOT = ((V_BYTES > S_BYTES ? V_BYTES : S_BYTES) + 127) / 128 * 128;
+    static_assert(HB % 128 == 0 && CB % 128 == 0 && FHB % 128 == 0 && FCB % 128 == 0,
+                  "TMA destinations must stay 128-byte aligned");
+};
+
+// C-PML memory variables of the output plane live in one extra buffer of 9
+// FP32 core tiles (3 terms for each damped direction), refilled for the next
+// output plane as soon as the current one has been consumed.
+constexpr int PSI_BYTES = 9 * CORE * 4;
+template <int BND, typename T>
+constexpr size_t smem_bytes() {
+    return (size_t)NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0) + 8 * (NSLOT + 1);
+}
+// CTAs per SM that the shared-memory footprint allows; the register budget of
+// the kernels is sized for exactly that many.
+template <int BND, typename T>
+constexpr int min_blocks() {
+    return (227 * 1024) / (int)(smem_bytes<BND, T>() + 1024) < 1   ? 1
+           : (227 * 1024) / (int)(smem_bytes<BND, T>() + 1024) > 4 ? 4
+                                                                   : (227 * 1024) / (int)(smem_bytes<BND, T>() + 1024);
+}
 
 // --- PTX wrappers -------------------------------------------------------------
 
@@ -122,7 +181,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return mbar_try(bar, parity) || mbar_wait_slow(bar, parity);
 }
 
-__device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, uint64_t* bar,
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y, int z) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
@@ -131,32 +190,48 @@ __device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, 
         : "memory");
 }
 
+// Tensor maps of one pass, in slot order: halo[] then core[] as listed in
+// the slot layout above, then the C-PML terms [3 * direction + term].
 struct Maps {
     CUtensorMap halo[MAXH];
     CUtensorMap core[MAXC];
-    CUtensorMap psi[9];      // C-PML terms of this pass: [3 * direction + term]
+    CUtensorMap psi[9];
 };
 
 struct PassParams {
     DevGrid g;
     DevFields F;
     DevBoundary B;
-    float dt;
+    float dto[9];         // per output field: dt x its storage scale
+    float inv[9];         // per input field: 1 / its storage scale (16-bit storage)
     int ntx, nty;
     int zchunk;           // planes per z-chunk
     int* err;
 };
 
 // Issue the TMA loads of z-plane `z` of tile (x0, y0) into `slot`.
-template <int NH, int NC>
-__device__ __forceinline__ void issue_plane(const Maps& m, float* slot, uint64_t* bar, int x0,
-                                            int y0, int z) {
-    mbar_expect_tx(bar, (NH * HALO + NC * CORE) * (uint32_t)sizeof(float));
+template <typename T>
+__device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, uint64_t* bar,
+                                          int x0, int y0, int z) {
+    using L = Lay<T>;
+    mbar_expect_tx(bar, (uint32_t)L::V_BYTES);
 #pragma unroll
-    for (int h = 0; h < NH; ++h) tma_load_3d(slot + h * HALO, &m.halo[h], bar, x0 - 4, y0 - 2, z);
+    for (int h = 0; h < 5; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
+    tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0 - 2, z);
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-        tma_load_3d(slot + NH * HALO + c * CORE, &m.core[c], bar, x0, y0, z);
+    for (int c = 0; c < 4; ++c) tma_load_3d(slot + L::V_CORE + c * L::CB, &m.core[c], bar, x0, y0, z);
+}
+template <typename T>
+__device__ __forceinline__ void issue_str(const Maps& m, unsigned char* slot, uint64_t* bar,
+                                          int x0, int y0, int z) {
+    using L = Lay<T>;
+    mbar_expect_tx(bar, (uint32_t)L::S_BYTES);
+#pragma unroll
+    for (int h = 0; h < 3; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
+    tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0 - 2, z);
+    tma_load_3d(slot + L::S_LAM, &m.core[0], bar, x0, y0, z);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tma_load_3d(slot + L::S_CORE + c * L::CB, &m.core[1 + c], bar, x0, y0, z);
 }
 
 // Issue the TMA loads of the C-PML memory variables of plane `z` for the
@@ -173,7 +248,6 @@ __device__ __forceinline__ void issue_psi(const Maps& m, float* buf, uint64_t* b
 }
 
 __device__ __forceinline__ bool in_slab(int i, int n, int W) { return i < W || i >= n - W; }
-__device__ __forceinline__ int slab_idx(int i, int n, int W) { return i < W ? i : i - (n - 2 * W); }
 
 __device__ __forceinline__ void ring_init(uint64_t* bars, int tid) {
     if (tid == 0) {
@@ -195,12 +269,12 @@ __device__ __noinline__ void fail_exit(int* err, int bit, uint64_t* bars, int m,
 }
 
 // Per-thread geometry shared by both passes.
-template <int BND>
+template <int BND, typename T>
 struct Geo {
-    int x0, y0, z0, P4, i, j0, hc, cc, cx, W;
+    int x0, y0, z0, P4, i, j0, hc, hf, cc, cx, W;
     unsigned tdirs;                                   // tile inside the x / y slabs
     bool own[ROWS], sy[ROWS], sx;
-    int cy[ROWS];
+    int cy[ROWS];                                     // medium y+1 offset (clamped) in FP32 tiles
     float gx, gy[ROWS];
     float pax, pbx, pay[ROWS], pby[ROWS];            // C-PML a, b of the x and y slabs
     long long obase;                                  // j0 * pitch + i
@@ -217,8 +291,9 @@ struct Geo {
         y0 = (t / P.ntx) * TY;
         i = x0 + tx;
         j0 = y0 + ROWS * ty;
-        hc = (ROWS * ty + 2) * HX + tx + 4;           // row 0 cell in a halo tile
-        cc = ROWS * ty * TX + tx;                     // row 0 cell in a core tile
+        hc = (ROWS * ty + 2) * Lay<T>::HX + tx + St<T>::HO;   // row 0 cell, field halo tile
+        hf = (ROWS * ty + 2) * HXF + tx + 4;                  // row 0 cell, FP32 halo tile
+        cc = ROWS * ty * TX + tx;                             // row 0 cell, core tile
         cx = (i + 1 < g.nx) ? 1 : 0;                  // medium clamp at the top edges
         W = P.B.W;
         tdirs = 0;
@@ -235,7 +310,7 @@ struct Geo {
         for (int rr = 0; rr < ROWS; ++rr) {
             const int j = j0 + rr;
             own[rr] = i < g.nx && j < g.ny;
-            cy[rr] = (j + 1 < g.ny) ? HX : 0;
+            cy[rr] = (j + 1 < g.ny) ? HXF : 0;
             sy[rr] = BND == BND_CPML && in_slab(j, g.ny, W);
             gy[rr] = (BND == BND_SPONGE && own[rr]) ? __ldg(P.B.g[1] + j) : 1.0f;
             pay[rr] = sy[rr] ? __ldg(P.B.pa[1] + j) : 0.f;
@@ -256,26 +331,33 @@ __device__ __forceinline__ void pml_upd(float& p0, float& p1, float& p2, float a
     p2 = b * p2 + a * d2; d2 += p2;
 }
 
+// Field tile element as FP32.
+template <typename T>
+__device__ __forceinline__ float F(const T* p, int o) { return St<T>::ld(p + o); }
+template <typename T> constexpr bool kScaled = sizeof(T) == 2;            // 16-bit storage
+template <typename T> constexpr bool kHalf = std::is_same<T, __half>::value;
+// a stored value beyond the FP16 range (it would round to infinity)
+__device__ __forceinline__ bool over(float x) { return fabsf(x) > 65504.0f; }
+
 // ------------------------------------------------------------------------------
-// Velocity pass (Eq. 1 + Eq. 4): halo tiles sxx syy sxy sxz syz rho, core
-// tiles szz vx vy vz.
+// Velocity pass (Eq. 1 + Eq. 4).
 // ------------------------------------------------------------------------------
-enum { VH_SXX, VH_SYY, VH_SXY, VH_SXZ, VH_SYZ, VH_RHO };
+enum { VH_SXX, VH_SYY, VH_SXY, VH_SXZ, VH_SYZ };
 enum { VC_SZZ, VC_VX, VC_VY, VC_VZ };
 
-template <int BND>
 struct VelQ {
     float zz[ROWS][4], xz[ROWS][4], yz[ROWS][4];   // sigma_zz k-1..k+2, sigma_xz/yz k-2..k+1
 };
 
 // One arrival of the z-loop, ring position PH = m mod 4.  Returns false if
 // the CTA must stop (a wait gave up).
-template <int BND, int PH>
-__device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, const Geo<BND>& G,
-                                         VelQ<BND>& Q, float* sm, uint64_t* bars, int m,
-                                         uint32_t& psi_n) {
+template <int BND, typename T, int PH>
+__device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
+                                         const Geo<BND, T>& G, VelQ& Q, unsigned char* sm,
+                                         uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
+    using L = Lay<T>;
+    constexpr int HX = L::HX;
     const DevGrid& g = P.g;
-    constexpr int SF = slot_floats<BND>();
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
     const int k = G.z0 - 4 + m;                                    // output plane
     const bool out = m >= 4;
@@ -286,52 +368,57 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, 
     const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;   // damped dirs of k
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
     if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
-    const float* sl0 = sm + S0 * SF;
-    const float* sl1 = sm + S1 * SF;
+    const unsigned char* sl0 = sm + S0 * L::SLOT;
+    const unsigned char* sl1 = sm + S1 * L::SLOT;
+    const unsigned char* sl2 = sm + S2 * L::SLOT;
     // push own-column values: sigma_zz of plane p, sigma_xz / sigma_yz of p - 1
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr) {
-        Q.zz[rr][PH] = sl0[6 * HALO + VC_SZZ * CORE + G.cc + rr * TX];
+        Q.zz[rr][PH] = F((const T*)(sl0 + L::V_CORE + VC_SZZ * L::CB), G.cc + rr * TX);
         if (m > 0) {
-            Q.xz[rr][PH] = sl1[VH_SXZ * HALO + G.hc + rr * HX];
-            Q.yz[rr][PH] = sl1[VH_SYZ * HALO + G.hc + rr * HX];
+            Q.xz[rr][PH] = F((const T*)(sl1 + VH_SXZ * L::HB), G.hc + rr * HX);
+            Q.yz[rr][PH] = F((const T*)(sl1 + VH_SYZ * L::HB), G.hc + rr * HX);
         }
     }
     if (out && ok) {
         constexpr int A = (PH + 1) & 3, B = (PH + 2) & 3, C = (PH + 3) & 3, D = PH;  // oldest..newest
-        const float* sk = sm + S2 * SF + G.hc;           // plane k, own cell
-        const float* hxx = sk + VH_SXX * HALO;
-        const float* hyy = sk + VH_SYY * HALO;
-        const float* hxy = sk + VH_SXY * HALO;
-        const float* hxz = sk + VH_SXZ * HALO;
-        const float* hyz = sk + VH_SYZ * HALO;
-        const float* hr = sk + VH_RHO * HALO;
-        const float* hr1 = sl1 + VH_RHO * HALO + G.hc;            // plane k + 1
-        const float* vc = sm + S2 * SF + 6 * HALO + G.cc;
+        const T* hxx = (const T*)(sl2 + VH_SXX * L::HB) + G.hc;      // plane k, own cell
+        const T* hyy = (const T*)(sl2 + VH_SYY * L::HB) + G.hc;
+        const T* hxy = (const T*)(sl2 + VH_SXY * L::HB) + G.hc;
+        const T* hxz = (const T*)(sl2 + VH_SXZ * L::HB) + G.hc;
+        const T* hyz = (const T*)(sl2 + VH_SYZ * L::HB) + G.hc;
+        const float* hr = (const float*)(sl2 + L::V_RHO) + G.hf;
+        const float* hr1 = (const float*)(sl1 + L::V_RHO) + G.hf;   // plane k + 1
+        const T* vc = (const T*)(sl2 + L::V_CORE) + G.cc;
         const bool ktop = k + 1 < g.nz;
         const long long o = (long long)k * g.plane + G.obase;
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
             if (!G.own[rr]) continue;
-            const int R = rr * HX;
+            const int R = rr * HX, RF = rr * HXF;
             const float* qxz = Q.xz[rr];
             const float* qyz = Q.yz[rr];
             const float* qzz = Q.zz[rr];
             // vx at (i+1/2, j, k)
-            float dxx = g.c1x * (hxx[R + 1] - hxx[R]) + g.c2x * (hxx[R + 2] - hxx[R - 1]);
-            float dxy = g.c1y * (hxy[R] - hxy[R - HX]) + g.c2y * (hxy[R + HX] - hxy[R - 2 * HX]);
+            float dxx = g.c1x * (F(hxx, R + 1) - F(hxx, R)) + g.c2x * (F(hxx, R + 2) - F(hxx, R - 1));
+            float dxy = g.c1y * (F(hxy, R) - F(hxy, R - HX)) + g.c2y * (F(hxy, R + HX) - F(hxy, R - 2 * HX));
             float dxz = g.c1z * (qxz[C] - qxz[B]) + g.c2z * (qxz[D] - qxz[A]);
             // vy at (i, j+1/2, k)
-            float dyx = g.c1x * (hxy[R] - hxy[R - 1]) + g.c2x * (hxy[R + 1] - hxy[R - 2]);
-            float dyy = g.c1y * (hyy[R + HX] - hyy[R]) + g.c2y * (hyy[R + 2 * HX] - hyy[R - HX]);
+            float dyx = g.c1x * (F(hxy, R) - F(hxy, R - 1)) + g.c2x * (F(hxy, R + 1) - F(hxy, R - 2));
+            float dyy = g.c1y * (F(hyy, R + HX) - F(hyy, R)) + g.c2y * (F(hyy, R + 2 * HX) - F(hyy, R - HX));
             float dyz = g.c1z * (qyz[C] - qyz[B]) + g.c2z * (qyz[D] - qyz[A]);
             // vz at (i, j, k+1/2)
-            float dzx = g.c1x * (hxz[R] - hxz[R - 1]) + g.c2x * (hxz[R + 1] - hxz[R - 2]);
-            float dzy = g.c1y * (hyz[R] - hyz[R - HX]) + g.c2y * (hyz[R + HX] - hyz[R - 2 * HX]);
+            float dzx = g.c1x * (F(hxz, R) - F(hxz, R - 1)) + g.c2x * (F(hxz, R + 1) - F(hxz, R - 2));
+            float dzy = g.c1y * (F(hyz, R) - F(hyz, R - HX)) + g.c2y * (F(hyz, R + HX) - F(hyz, R - 2 * HX));
             float dzz = g.c1z * (qzz[C] - qzz[B]) + g.c2z * (qzz[D] - qzz[A]);
+            if constexpr (kScaled<T>) {     // stored -> physical units
+                dxx *= P.inv[SXX]; dxy *= P.inv[SXY]; dxz *= P.inv[SXZ];
+                dyx *= P.inv[SXY]; dyy *= P.inv[SYY]; dyz *= P.inv[SYZ];
+                dzx *= P.inv[SXZ]; dzy *= P.inv[SYZ]; dzz *= P.inv[SZZ];
+            }
             if (BND == BND_CPML) {
-                // memory variables of plane k from the slot, updated, stored
-                const float* ps = sm + NSLOT * SLOT_MAIN + G.cc + rr * TX;
+                // memory variables of plane k from the psi buffer, updated, stored
+                const float* ps = (const float*)(sm + NSLOT * L::SLOT) + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
@@ -340,8 +427,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, 
                 }
                 if (G.sy[rr]) {
                     float p0 = ps[3 * CORE], p1 = ps[4 * CORE], p2 = ps[5 * CORE];
-                    pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr],
-                            dxy, dyy, dzy);
+                    pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr], dxy, dyy, dzy);
                     P.B.psi[6][oo] = p0; P.B.psi[7][oo] = p1; P.B.psi[8][oo] = p2;
                 }
                 if (sz) {
@@ -351,21 +437,22 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, 
                 }
             }
             // buoyancy at the v points: 1 / mean of the two adjacent densities
-            const float r0 = hr[R];
-            const float bx = __fdividef(2.0f, r0 + hr[R + G.cx]);
-            const float by = __fdividef(2.0f, r0 + hr[R + G.cy[rr]]);
-            const float bz = __fdividef(2.0f, r0 + (ktop ? hr1[R] : r0));
-            float vx = vc[VC_VX * CORE + rr * TX] + P.dt * bx * (dxx + dxy + dxz);
-            float vy = vc[VC_VY * CORE + rr * TX] + P.dt * by * (dyx + dyy + dyz);
-            float vz = vc[VC_VZ * CORE + rr * TX] + P.dt * bz * (dzx + dzy + dzz);
+            const float r0 = hr[RF];
+            const float bx = __fdividef(2.0f, r0 + hr[RF + G.cx]);
+            const float by = __fdividef(2.0f, r0 + hr[RF + G.cy[rr]]);
+            const float bz = __fdividef(2.0f, r0 + (ktop ? hr1[RF] : r0));
+            float vx = F(vc, VC_VX * CORE + rr * TX) + P.dto[VX] * bx * (dxx + dxy + dxz);
+            float vy = F(vc, VC_VY * CORE + rr * TX) + P.dto[VY] * by * (dyx + dyy + dyz);
+            float vz = F(vc, VC_VZ * CORE + rr * TX) + P.dto[VZ] * bz * (dzx + dzy + dzz);
             if (BND == BND_SPONGE) {
                 const float Gs = G3 * G.gy[rr];
                 vx *= Gs; vy *= Gs; vz *= Gs;
             }
+            if constexpr (kHalf<T>) ovf |= over(vx) | over(vy) | over(vz);
             const long long oo = o + rr * g.pitch;
-            P.F.f[VX][oo] = vx;
-            P.F.f[VY][oo] = vy;
-            P.F.f[VZ][oo] = vz;
+            ((T*)P.F.f[VX])[oo] = St<T>::put(vx);
+            ((T*)P.F.f[VY])[oo] = St<T>::put(vy);
+            ((T*)P.F.f[VZ])[oo] = St<T>::put(vz);
         }
     }
     if (__syncthreads_or(!ok)) {
@@ -379,117 +466,114 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P, 
         const int kn = k + 1;
         if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
             const unsigned dn = G.dirs(kn, g.nz);
-            if (dn) issue_psi(maps, sm + NSLOT * SLOT_MAIN, &bars[NSLOT], G.x0, G.y0, kn, dn);
+            if (dn) issue_psi(maps, (float*)(sm + NSLOT * L::SLOT), &bars[NSLOT], G.x0, G.y0, kn, dn);
         }
     }
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_plane<6, 4>(maps, sm + S2 * SF, &bars[S2], G.x0, G.y0, G.z0 + m);
+        issue_vel<T>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
     return true;
 }
 
-// CTAs per SM that the shared-memory footprint allows; the register budget of
-// the kernels is sized for exactly that many.
-template <int BND>
-constexpr int min_blocks() {
-    return (227 * 1024) / (int)(smem_bytes<BND>() + 1024) < 1   ? 1
-           : (227 * 1024) / (int)(smem_bytes<BND>() + 1024) > 4 ? 4
-                                                                : (227 * 1024) / (int)(smem_bytes<BND>() + 1024);
-}
-
-template <int BND>
-__global__ void __launch_bounds__(NTH, min_blocks<BND>()) k_velocity(const __grid_constant__ Maps maps,
-                                                                  const PassParams P) {
-    extern __shared__ __align__(128) float sm[];
-    constexpr int SF = slot_floats<BND>();
+template <int BND, typename T>
+__global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_velocity(const __grid_constant__ Maps maps,
+                                                                        const PassParams P) {
+    extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(
-        sm + NSLOT * SF + (BND == BND_CPML ? PSI_FLOATS : 0));
+        sm + NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0));
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    const Geo<BND> G(P);
+    const Geo<BND, T> G(P);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_plane<6, 4>(maps, sm + s * SF, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
-    VelQ<BND> Q;
+            issue_vel<T>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
+    VelQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
 #pragma unroll
         for (int q = 0; q < 4; ++q) { Q.zz[rr][q] = 0.f; Q.xz[rr][q] = 0.f; Q.yz[rr][q] = 0.f; }
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
+    bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!vel_step<BND, 0>(maps, P, G, Q, sm, bars, m, psi_n)) return;
-        if (m + 1 < G.P4 && !vel_step<BND, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n)) return;
-        if (m + 2 < G.P4 && !vel_step<BND, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n)) return;
-        if (m + 3 < G.P4 && !vel_step<BND, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n)) return;
+        if (!vel_step<BND, T, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return;
+        if (m + 1 < G.P4 && !vel_step<BND, T, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return;
+        if (m + 2 < G.P4 && !vel_step<BND, T, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return;
+        if (m + 3 < G.P4 && !vel_step<BND, T, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return;
     }
+    if constexpr (kHalf<T>)
+        if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
 }
 
 // ------------------------------------------------------------------------------
-// Stress pass (Eq. 2/3 + Eq. 4): halo tiles vx vy vz mu, core tiles lambda
-// and the six stresses.
+// Stress pass (Eq. 2/3 + Eq. 4).
 // ------------------------------------------------------------------------------
-enum { SH_VX, SH_VY, SH_VZ, SH_MU };
-enum { SC_LAM, SC_SXX, SC_SYY, SC_SZZ, SC_SXY, SC_SXZ, SC_SYZ };
+enum { SH_VX, SH_VY, SH_VZ };
+enum { SC_SXX, SC_SYY, SC_SZZ, SC_SXY, SC_SXZ, SC_SYZ };
 
-template <int BND>
 struct StrQ {
     float vx[ROWS][4], vy[ROWS][4], vz[ROWS][4];   // vx/vy k-1..k+2, vz k-2..k+1
 };
 
-template <int BND, int PH>
-__device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, const Geo<BND>& G,
-                                         StrQ<BND>& Q, float* sm, uint64_t* bars, int m,
-                                         uint32_t& psi_n) {
+template <int BND, typename T, int PH>
+__device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
+                                         const Geo<BND, T>& G, StrQ& Q, unsigned char* sm,
+                                         uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
+    using L = Lay<T>;
+    constexpr int HX = L::HX;
     const DevGrid& g = P.g;
-    constexpr int SF = slot_floats<BND>();
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
     const int k = G.z0 - 4 + m;
     const bool out = m >= 4;
-    // per-plane boundary coefficients of the output plane, fetched before the wait
     const bool sz = BND == BND_CPML && out && in_slab(k, g.nz, G.W);
     const float paz = sz ? __ldg(P.B.pa[2] + k) : 0.f, pbz = sz ? __ldg(P.B.pb[2] + k) : 0.f;
     const float G3 = (BND == BND_SPONGE && out) ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
-    const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;   // damped dirs of k
+    const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
     if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
-    const float* sl0 = sm + S0 * SF;
-    const float* sl1 = sm + S1 * SF;
+    const unsigned char* sl0 = sm + S0 * L::SLOT;
+    const unsigned char* sl1 = sm + S1 * L::SLOT;
+    const unsigned char* sl2 = sm + S2 * L::SLOT;
     // push own-column values: vx, vy of plane p, vz of plane p - 1
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr) {
-        Q.vx[rr][PH] = sl0[SH_VX * HALO + G.hc + rr * HX];
-        Q.vy[rr][PH] = sl0[SH_VY * HALO + G.hc + rr * HX];
-        if (m > 0) Q.vz[rr][PH] = sl1[SH_VZ * HALO + G.hc + rr * HX];
+        Q.vx[rr][PH] = F((const T*)(sl0 + SH_VX * L::HB), G.hc + rr * HX);
+        Q.vy[rr][PH] = F((const T*)(sl0 + SH_VY * L::HB), G.hc + rr * HX);
+        if (m > 0) Q.vz[rr][PH] = F((const T*)(sl1 + SH_VZ * L::HB), G.hc + rr * HX);
     }
     if (out && ok) {
         constexpr int A = (PH + 1) & 3, B = (PH + 2) & 3, C = (PH + 3) & 3, D = PH;
-        const float* sk = sm + S2 * SF + G.hc;           // plane k, own cell
-        const float* hvx = sk + SH_VX * HALO;
-        const float* hvy = sk + SH_VY * HALO;
-        const float* hvz = sk + SH_VZ * HALO;
-        const float* hmu = sk + SH_MU * HALO;
-        const float* hmu1 = (k + 1 < g.nz ? sl1 + G.hc : sk) + SH_MU * HALO;   // plane k + 1
-        const float* cr = sm + S2 * SF + 4 * HALO + G.cc;
+        const T* hvx = (const T*)(sl2 + SH_VX * L::HB) + G.hc;       // plane k, own cell
+        const T* hvy = (const T*)(sl2 + SH_VY * L::HB) + G.hc;
+        const T* hvz = (const T*)(sl2 + SH_VZ * L::HB) + G.hc;
+        const float* hmu = (const float*)(sl2 + L::S_MU) + G.hf;
+        const float* hmu1 = (const float*)((k + 1 < g.nz ? sl1 : sl2) + L::S_MU) + G.hf;   // k + 1
+        const float* lc = (const float*)(sl2 + L::S_LAM) + G.cc;
+        const T* cr = (const T*)(sl2 + L::S_CORE) + G.cc;
         const long long o = (long long)k * g.plane + G.obase;
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
             if (!G.own[rr]) continue;
-            const int R = rr * HX;
+            const int R = rr * HX, RF = rr * HXF;
             const float* qvx = Q.vx[rr];
             const float* qvy = Q.vy[rr];
             const float* qvz = Q.vz[rr];
             // normal strain rates at (i, j, k)
-            float exx = g.c1x * (hvx[R] - hvx[R - 1]) + g.c2x * (hvx[R + 1] - hvx[R - 2]);
-            float eyy = g.c1y * (hvy[R] - hvy[R - HX]) + g.c2y * (hvy[R + HX] - hvy[R - 2 * HX]);
+            float exx = g.c1x * (F(hvx, R) - F(hvx, R - 1)) + g.c2x * (F(hvx, R + 1) - F(hvx, R - 2));
+            float eyy = g.c1y * (F(hvy, R) - F(hvy, R - HX)) + g.c2y * (F(hvy, R + HX) - F(hvy, R - 2 * HX));
             float ezz = g.c1z * (qvz[C] - qvz[B]) + g.c2z * (qvz[D] - qvz[A]);
             // shear terms at the shear points
-            float vxy = g.c1y * (hvx[R + HX] - hvx[R]) + g.c2y * (hvx[R + 2 * HX] - hvx[R - HX]);
-            float vyx = g.c1x * (hvy[R + 1] - hvy[R]) + g.c2x * (hvy[R + 2] - hvy[R - 1]);
+            float vxy = g.c1y * (F(hvx, R + HX) - F(hvx, R)) + g.c2y * (F(hvx, R + 2 * HX) - F(hvx, R - HX));
+            float vyx = g.c1x * (F(hvy, R + 1) - F(hvy, R)) + g.c2x * (F(hvy, R + 2) - F(hvy, R - 1));
             float vxz = g.c1z * (qvx[C] - qvx[B]) + g.c2z * (qvx[D] - qvx[A]);
-            float vzx = g.c1x * (hvz[R + 1] - hvz[R]) + g.c2x * (hvz[R + 2] - hvz[R - 1]);
+            float vzx = g.c1x * (F(hvz, R + 1) - F(hvz, R)) + g.c2x * (F(hvz, R + 2) - F(hvz, R - 1));
             float vyz = g.c1z * (qvy[C] - qvy[B]) + g.c2z * (qvy[D] - qvy[A]);
-            float vzy = g.c1y * (hvz[R + HX] - hvz[R]) + g.c2y * (hvz[R + 2 * HX] - hvz[R - HX]);
+            float vzy = g.c1y * (F(hvz, R + HX) - F(hvz, R)) + g.c2y * (F(hvz, R + 2 * HX) - F(hvz, R - HX));
+            if constexpr (kScaled<T>) {     // stored -> physical units
+                exx *= P.inv[VX]; vxy *= P.inv[VX]; vxz *= P.inv[VX];
+                eyy *= P.inv[VY]; vyx *= P.inv[VY]; vyz *= P.inv[VY];
+                ezz *= P.inv[VZ]; vzx *= P.inv[VZ]; vzy *= P.inv[VZ];
+            }
             if (BND == BND_CPML) {
-                const float* ps = sm + NSLOT * SLOT_MAIN + G.cc + rr * TX;
+                const float* ps = (const float*)(sm + NSLOT * L::SLOT) + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
@@ -498,8 +582,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, 
                 }
                 if (G.sy[rr]) {
                     float p0 = ps[3 * CORE], p1 = ps[4 * CORE], p2 = ps[5 * CORE];
-                    pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr],
-                            eyy, vxy, vzy);
+                    pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr], eyy, vxy, vzy);
                     P.B.psi[9][oo] = p0; P.B.psi[10][oo] = p1; P.B.psi[11][oo] = p2;
                 }
                 if (sz) {
@@ -510,30 +593,32 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, 
             }
             // medium: lambda, mu at the cell; mu means at the shear points
             const int cyr = G.cy[rr];
-            const float lam = cr[SC_LAM * CORE + rr * TX];
-            const float mu0 = hmu[R], mxp = hmu[R + G.cx], myp = hmu[R + cyr];
-            const float mzp = hmu1[R];
-            const float mxy = 0.25f * (mu0 + mxp + myp + hmu[R + G.cx + cyr]);
-            const float mxz = 0.25f * (mu0 + mxp + mzp + hmu1[R + G.cx]);
-            const float myz = 0.25f * (mu0 + myp + mzp + hmu1[R + cyr]);
+            const float lam = lc[rr * TX];
+            const float mu0 = hmu[RF], mxp = hmu[RF + G.cx], myp = hmu[RF + cyr];
+            const float mzp = hmu1[RF];
+            const float mxy = 0.25f * (mu0 + mxp + myp + hmu[RF + G.cx + cyr]);
+            const float mxz = 0.25f * (mu0 + mxp + mzp + hmu1[RF + G.cx]);
+            const float myz = 0.25f * (mu0 + myp + mzp + hmu1[RF + cyr]);
             const float l2m = lam + 2.0f * mu0;
-            float s0 = cr[SC_SXX * CORE + rr * TX] + P.dt * (l2m * exx + lam * (eyy + ezz));
-            float s1 = cr[SC_SYY * CORE + rr * TX] + P.dt * (l2m * eyy + lam * (exx + ezz));
-            float s2 = cr[SC_SZZ * CORE + rr * TX] + P.dt * (l2m * ezz + lam * (exx + eyy));
-            float s3 = cr[SC_SXY * CORE + rr * TX] + P.dt * mxy * (vxy + vyx);
-            float s4 = cr[SC_SXZ * CORE + rr * TX] + P.dt * mxz * (vxz + vzx);
-            float s5 = cr[SC_SYZ * CORE + rr * TX] + P.dt * myz * (vyz + vzy);
+            float s0 = F(cr, SC_SXX * CORE + rr * TX) + P.dto[SXX] * (l2m * exx + lam * (eyy + ezz));
+            float s1 = F(cr, SC_SYY * CORE + rr * TX) + P.dto[SYY] * (l2m * eyy + lam * (exx + ezz));
+            float s2 = F(cr, SC_SZZ * CORE + rr * TX) + P.dto[SZZ] * (l2m * ezz + lam * (exx + eyy));
+            float s3 = F(cr, SC_SXY * CORE + rr * TX) + P.dto[SXY] * mxy * (vxy + vyx);
+            float s4 = F(cr, SC_SXZ * CORE + rr * TX) + P.dto[SXZ] * mxz * (vxz + vzx);
+            float s5 = F(cr, SC_SYZ * CORE + rr * TX) + P.dto[SYZ] * myz * (vyz + vzy);
             if (BND == BND_SPONGE) {
                 const float Gs = G3 * G.gy[rr];
                 s0 *= Gs; s1 *= Gs; s2 *= Gs; s3 *= Gs; s4 *= Gs; s5 *= Gs;
             }
+            if constexpr (kHalf<T>)
+                ovf |= over(s0) | over(s1) | over(s2) | over(s3) | over(s4) | over(s5);
             const long long oo = o + rr * g.pitch;
-            P.F.f[SXX][oo] = s0;
-            P.F.f[SYY][oo] = s1;
-            P.F.f[SZZ][oo] = s2;
-            P.F.f[SXY][oo] = s3;
-            P.F.f[SXZ][oo] = s4;
-            P.F.f[SYZ][oo] = s5;
+            ((T*)P.F.f[SXX])[oo] = St<T>::put(s0);
+            ((T*)P.F.f[SYY])[oo] = St<T>::put(s1);
+            ((T*)P.F.f[SZZ])[oo] = St<T>::put(s2);
+            ((T*)P.F.f[SXY])[oo] = St<T>::put(s3);
+            ((T*)P.F.f[SXZ])[oo] = St<T>::put(s4);
+            ((T*)P.F.f[SYZ])[oo] = St<T>::put(s5);
         }
     }
     if (__syncthreads_or(!ok)) {
@@ -543,42 +628,43 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P, 
     }
     if (BND == BND_CPML) {
         if (kd) ++psi_n;
-        // the psi buffer is free: fetch the memory variables of the next output plane
         const int kn = k + 1;
         if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
             const unsigned dn = G.dirs(kn, g.nz);
-            if (dn) issue_psi(maps, sm + NSLOT * SLOT_MAIN, &bars[NSLOT], G.x0, G.y0, kn, dn);
+            if (dn) issue_psi(maps, (float*)(sm + NSLOT * L::SLOT), &bars[NSLOT], G.x0, G.y0, kn, dn);
         }
     }
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_plane<4, 7>(maps, sm + S2 * SF, &bars[S2], G.x0, G.y0, G.z0 + m);
+        issue_str<T>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
     return true;
 }
 
-template <int BND>
-__global__ void __launch_bounds__(NTH, min_blocks<BND>()) k_stress(const __grid_constant__ Maps maps,
-                                                                const PassParams P) {
-    extern __shared__ __align__(128) float sm[];
-    constexpr int SF = slot_floats<BND>();
+template <int BND, typename T>
+__global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_stress(const __grid_constant__ Maps maps,
+                                                                      const PassParams P) {
+    extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(
-        sm + NSLOT * SF + (BND == BND_CPML ? PSI_FLOATS : 0));
+        sm + NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0));
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    const Geo<BND> G(P);
+    const Geo<BND, T> G(P);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_plane<4, 7>(maps, sm + s * SF, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
-    StrQ<BND> Q;
+            issue_str<T>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
+    StrQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
 #pragma unroll
         for (int q = 0; q < 4; ++q) { Q.vx[rr][q] = 0.f; Q.vy[rr][q] = 0.f; Q.vz[rr][q] = 0.f; }
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
+    bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!str_step<BND, 0>(maps, P, G, Q, sm, bars, m, psi_n)) return;
-        if (m + 1 < G.P4 && !str_step<BND, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n)) return;
-        if (m + 2 < G.P4 && !str_step<BND, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n)) return;
-        if (m + 3 < G.P4 && !str_step<BND, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n)) return;
+        if (!str_step<BND, T, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return;
+        if (m + 1 < G.P4 && !str_step<BND, T, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return;
+        if (m + 2 < G.P4 && !str_step<BND, T, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return;
+        if (m + 3 < G.P4 && !str_step<BND, T, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return;
     }
+    if constexpr (kHalf<T>)
+        if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
@@ -594,17 +680,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
-bool encode(CUtensorMap* map, const DevGrid& g, const float* base, bool halo) {
+// Tensor map of one pitched [nz][ny][pitch] array with a box of bw x bh x 1.
+bool encode(CUtensorMap* map, const DevGrid& g, const void* base, CUtensorMapDataType dt,
+            int esize, int bw, int bh) {
     auto fn = encoder();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
-    cuuint64_t strides[2] = {(cuuint64_t)g.pitch * sizeof(float),
-                             (cuuint64_t)g.plane * sizeof(float)};
-    cuuint32_t box[3] = {(cuuint32_t)(halo ? HX : TX), (cuuint32_t)(halo ? HY : TY), 1};
+    cuuint64_t strides[2] = {(cuuint64_t)g.pitch * esize, (cuuint64_t)g.plane * esize};
+    cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
-                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    EWS_L2PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, EWS_L2PROMO,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -616,13 +703,53 @@ cudaError_t prepare(K kern, size_t smem, int* blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, NTH, smem);
 }
 
-template <int BND>
+template <int BND, typename T>
 cudaError_t occupancy(int* occ) {
     int a = 0, b = 0;
-    cudaError_t e = prepare(k_velocity<BND>, smem_bytes<BND>(), &a);
-    if (e == cudaSuccess) e = prepare(k_stress<BND>, smem_bytes<BND>(), &b);
+    cudaError_t e = prepare(k_velocity<BND, T>, smem_bytes<BND, T>(), &a);
+    if (e == cudaSuccess) e = prepare(k_stress<BND, T>, smem_bytes<BND, T>(), &b);
     *occ = a < b ? a : b;
     return e;
+}
+
+template <typename T>
+cudaError_t occupancy_for(int kind, int* occ) {
+    switch (kind) {
+        case BND_SPONGE: return occupancy<BND_SPONGE, T>(occ);
+        case BND_CPML: return occupancy<BND_CPML, T>(occ);
+        default: return occupancy<BND_NONE, T>(occ);
+    }
+}
+
+// Tensor maps of both passes for storage type T (slot order of Lay<T>).
+template <typename T>
+bool encode_maps(Maps* vm, Maps* smp, const DevGrid& g, const DevFields& F, const DevMedium& M,
+                 const DevBoundary& B) {
+    constexpr CUtensorMapDataType dt = St<T>::dtype;
+    constexpr int es = (int)sizeof(T), HX = Lay<T>::HX;
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    bool ok = true;
+    // velocity: field halos sxx syy sxy sxz syz, rho halo; cores szz vx vy vz
+    const float* vh[5] = {F.f[SXX], F.f[SYY], F.f[SXY], F.f[SXZ], F.f[SYZ]};
+    const float* vc[4] = {F.f[SZZ], F.f[VX], F.f[VY], F.f[VZ]};
+    for (int h = 0; h < 5; ++h) ok &= encode(&vm->halo[h], g, vh[h], dt, es, HX, HY);
+    ok &= encode(&vm->halo[5], g, M.rho, f32, 4, HXF, HY);
+    for (int c = 0; c < 4; ++c) ok &= encode(&vm->core[c], g, vc[c], dt, es, TX, TY);
+    // stress: field halos vx vy vz, mu halo; lambda core, then the six stress cores
+    const float* sh[3] = {F.f[VX], F.f[VY], F.f[VZ]};
+    const float* sc[6] = {F.f[SXX], F.f[SYY], F.f[SZZ], F.f[SXY], F.f[SXZ], F.f[SYZ]};
+    for (int h = 0; h < 3; ++h) ok &= encode(&smp->halo[h], g, sh[h], dt, es, HX, HY);
+    ok &= encode(&smp->halo[3], g, M.mu, f32, 4, HXF, HY);
+    ok &= encode(&smp->core[0], g, M.lam, f32, 4, TX, TY);
+    for (int c = 0; c < 6; ++c) ok &= encode(&smp->core[1 + c], g, sc[c], dt, es, TX, TY);
+    // C-PML memory variables (FP32): psi[6 d + t]; velocity pass t = 0..2, stress 3..5
+    if (B.kind == BND_CPML)
+        for (int d = 0; d < 3; ++d)
+            for (int q = 0; q < 3; ++q) {
+                ok &= encode(&vm->psi[3 * d + q], g, B.psi[6 * d + q], f32, 4, TX, TY);
+                ok &= encode(&smp->psi[3 * d + q], g, B.psi[6 * d + 3 + q], f32, 4, TX, TY);
+            }
+    return ok;
 }
 
 }  // namespace
@@ -630,51 +757,38 @@ cudaError_t occupancy(int* occ) {
 struct StencilPlan {
     Maps vmaps, smaps;
     int kind = 0;
+    int storage = EWS_STORAGE_F32;
     int grid = 0;
     int ntx = 0, nty = 0;
     int zchunk = 0;
 };
 
-cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevMedium& M,
-                                const DevBoundary& B, StencilPlan** out) {
-    StencilPlan* p = new StencilPlan();
+namespace {
+
+cudaError_t plan_build(StencilPlan* p, const DevGrid& g, const DevFields& F, const DevMedium& M,
+                       const DevBoundary& B, int storage) {
     p->kind = B.kind;
-    bool ok = true;
-    // velocity: halo sxx syy sxy sxz syz rho; core szz vx vy vz
-    const float* vh[6] = {F.f[SXX], F.f[SYY], F.f[SXY], F.f[SXZ], F.f[SYZ], M.rho};
-    const float* vc[4] = {F.f[SZZ], F.f[VX], F.f[VY], F.f[VZ]};
-    for (int h = 0; h < 6; ++h) ok &= encode(&p->vmaps.halo[h], g, vh[h], true);
-    for (int c = 0; c < 4; ++c) ok &= encode(&p->vmaps.core[c], g, vc[c], false);
-    // stress: halo vx vy vz mu; core lambda sxx syy szz sxy sxz syz
-    const float* sh[4] = {F.f[VX], F.f[VY], F.f[VZ], M.mu};
-    const float* sc[7] = {M.lam, F.f[SXX], F.f[SYY], F.f[SZZ], F.f[SXY], F.f[SXZ], F.f[SYZ]};
-    for (int h = 0; h < 4; ++h) ok &= encode(&p->smaps.halo[h], g, sh[h], true);
-    for (int c = 0; c < 7; ++c) ok &= encode(&p->smaps.core[c], g, sc[c], false);
-    // C-PML memory variables: psi[6 d + t]; velocity pass t = 0..2, stress 3..5
-    if (B.kind == BND_CPML)
-        for (int d = 0; d < 3; ++d)
-            for (int q = 0; q < 3; ++q) {
-                ok &= encode(&p->vmaps.psi[3 * d + q], g, B.psi[6 * d + q], false);
-                ok &= encode(&p->smaps.psi[3 * d + q], g, B.psi[6 * d + 3 + q], false);
-            }
-    if (!ok) {
-        delete p;
-        return cudaErrorInvalidValue;
+    p->storage = storage;
+    bool ok;
+    switch (storage) {
+        case EWS_STORAGE_BF16: ok = encode_maps<__nv_bfloat16>(&p->vmaps, &p->smaps, g, F, M, B); break;
+        case EWS_STORAGE_F16: ok = encode_maps<__half>(&p->vmaps, &p->smaps, g, F, M, B); break;
+        case EWS_STORAGE_F32: ok = encode_maps<float>(&p->vmaps, &p->smaps, g, F, M, B); break;
+        default: return cudaErrorInvalidValue;
     }
+    if (!ok) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
-        switch (B.kind) {
-            case BND_SPONGE: e = occupancy<BND_SPONGE>(&occ); break;
-            case BND_CPML: e = occupancy<BND_CPML>(&occ); break;
-            default: e = occupancy<BND_NONE>(&occ); break;
+        switch (storage) {
+            case EWS_STORAGE_BF16: e = occupancy_for<__nv_bfloat16>(B.kind, &occ); break;
+            case EWS_STORAGE_F16: e = occupancy_for<__half>(B.kind, &occ); break;
+            default: e = occupancy_for<float>(B.kind, &occ); break;
         }
     }
-    if (e != cudaSuccess || occ < 1) {
-        delete p;
-        return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
-    }
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
     // Launch geometry: every tile column is cut into the same z-chunks and
     // chunk c of all tiles is resident at once, so neighbouring tiles march
     // through z together and the halo planes one CTA loads are still in L2
@@ -690,6 +804,68 @@ cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevM
     p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
     nchunk = (g.nz + p->zchunk - 1) / p->zchunk;
     p->grid = (int)(ntile * nchunk);
+    return cudaSuccess;
+}
+
+PassParams pass_params(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
+                       const DevBoundary& B, const float dto[9], const float inv[9], int* err) {
+    PassParams P;
+    P.g = g;
+    P.F = F;
+    P.B = B;
+    for (int q = 0; q < NFIELD; ++q) {
+        P.dto[q] = dto[q];
+        P.inv[q] = inv[q];
+    }
+    P.ntx = sp->ntx;
+    P.nty = sp->nty;
+    P.zchunk = sp->zchunk;
+    P.err = err;
+    return P;
+}
+
+template <typename T>
+void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
+    dim3 blk(TX, RY);
+    switch (sp->kind) {
+        case BND_SPONGE:
+            k_velocity<BND_SPONGE, T><<<sp->grid, blk, smem_bytes<BND_SPONGE, T>(), st>>>(sp->vmaps, P);
+            break;
+        case BND_CPML:
+            k_velocity<BND_CPML, T><<<sp->grid, blk, smem_bytes<BND_CPML, T>(), st>>>(sp->vmaps, P);
+            break;
+        default:
+            k_velocity<BND_NONE, T><<<sp->grid, blk, smem_bytes<BND_NONE, T>(), st>>>(sp->vmaps, P);
+            break;
+    }
+}
+
+template <typename T>
+void launch_s(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
+    dim3 blk(TX, RY);
+    switch (sp->kind) {
+        case BND_SPONGE:
+            k_stress<BND_SPONGE, T><<<sp->grid, blk, smem_bytes<BND_SPONGE, T>(), st>>>(sp->smaps, P);
+            break;
+        case BND_CPML:
+            k_stress<BND_CPML, T><<<sp->grid, blk, smem_bytes<BND_CPML, T>(), st>>>(sp->smaps, P);
+            break;
+        default:
+            k_stress<BND_NONE, T><<<sp->grid, blk, smem_bytes<BND_NONE, T>(), st>>>(sp->smaps, P);
+            break;
+    }
+}
+
+}  // namespace
+
+cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevMedium& M,
+                                const DevBoundary& B, int storage, StencilPlan** out) {
+    StencilPlan* p = new StencilPlan();
+    cudaError_t e = plan_build(p, g, F, M, B, storage);
+    if (e != cudaSuccess) {
+        delete p;
+        return e;
+    }
     *out = p;
     return cudaSuccess;
 }
@@ -703,81 +879,34 @@ size_t stencil_plan_bytes() { return sizeof(StencilPlan); }
 cudaError_t stencil_plan_fill(void* storage, const DevGrid& g, const DevFields& F,
                               const DevMedium& M, const DevBoundary& B, StencilPlan** out) {
     StencilPlan* p = ::new (storage) StencilPlan();
-    p->kind = B.kind;
-    bool ok = true;
-    const float* vh[6] = {F.f[SXX], F.f[SYY], F.f[SXY], F.f[SXZ], F.f[SYZ], M.rho};
-    const float* vc[4] = {F.f[SZZ], F.f[VX], F.f[VY], F.f[VZ]};
-    for (int h = 0; h < 6; ++h) ok &= encode(&p->vmaps.halo[h], g, vh[h], true);
-    for (int c = 0; c < 4; ++c) ok &= encode(&p->vmaps.core[c], g, vc[c], false);
-    const float* sh[4] = {F.f[VX], F.f[VY], F.f[VZ], M.mu};
-    const float* sc[7] = {M.lam, F.f[SXX], F.f[SYY], F.f[SZZ], F.f[SXY], F.f[SXZ], F.f[SYZ]};
-    for (int h = 0; h < 4; ++h) ok &= encode(&p->smaps.halo[h], g, sh[h], true);
-    for (int c = 0; c < 7; ++c) ok &= encode(&p->smaps.core[c], g, sc[c], false);
-    if (B.kind == BND_CPML)
-        for (int d = 0; d < 3; ++d)
-            for (int q = 0; q < 3; ++q) {
-                ok &= encode(&p->vmaps.psi[3 * d + q], g, B.psi[6 * d + q], false);
-                ok &= encode(&p->smaps.psi[3 * d + q], g, B.psi[6 * d + 3 + q], false);
-            }
-    if (!ok) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, occ = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) {
-        switch (B.kind) {
-            case BND_SPONGE: e = occupancy<BND_SPONGE>(&occ); break;
-            case BND_CPML: e = occupancy<BND_CPML>(&occ); break;
-            default: e = occupancy<BND_NONE>(&occ); break;
-        }
-    }
+    cudaError_t e = plan_build(p, g, F, M, B, EWS_STORAGE_F32);
     if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    p->ntx = (g.nx + TX - 1) / TX;
-    p->nty = (g.ny + TY - 1) / TY;
-    const long long ntile = (long long)p->ntx * p->nty;
-    const long long slots = (long long)sms * occ;
-    long long nchunk = (slots * EWS_WAVES) / ntile;
-    if (nchunk > g.nz / 8) nchunk = g.nz / 8;
-    if (nchunk < 1) nchunk = 1;
-    p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
-    nchunk = (g.nz + p->zchunk - 1) / p->zchunk;
-    p->grid = (int)(ntile * nchunk);
     *out = p;
     return cudaSuccess;
 }
 
+int stencil_plan_storage(const StencilPlan* p) { return p->storage; }
+
 cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
-                            const DevBoundary& B, float dt, int* err, cudaStream_t st) {
-    PassParams P{g, F, B, dt, sp->ntx, sp->nty, sp->zchunk, err};
-    dim3 blk(TX, RY);
-    switch (B.kind) {
-        case BND_SPONGE:
-            k_velocity<BND_SPONGE><<<sp->grid, blk, smem_bytes<BND_SPONGE>(), st>>>(sp->vmaps, P);
-            break;
-        case BND_CPML:
-            k_velocity<BND_CPML><<<sp->grid, blk, smem_bytes<BND_CPML>(), st>>>(sp->vmaps, P);
-            break;
-        default:
-            k_velocity<BND_NONE><<<sp->grid, blk, smem_bytes<BND_NONE>(), st>>>(sp->vmaps, P);
-            break;
+                            const DevBoundary& B, const float dto[9], const float inv[9],
+                            int* err, cudaStream_t st) {
+    const PassParams P = pass_params(sp, g, F, B, dto, inv, err);
+    switch (sp->storage) {
+        case EWS_STORAGE_BF16: launch_v<__nv_bfloat16>(sp, P, st); break;
+        case EWS_STORAGE_F16: launch_v<__half>(sp, P, st); break;
+        default: launch_v<float>(sp, P, st); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
-                          const DevBoundary& B, float dt, int* err, cudaStream_t st) {
-    PassParams P{g, F, B, dt, sp->ntx, sp->nty, sp->zchunk, err};
-    dim3 blk(TX, RY);
-    switch (B.kind) {
-        case BND_SPONGE:
-            k_stress<BND_SPONGE><<<sp->grid, blk, smem_bytes<BND_SPONGE>(), st>>>(sp->smaps, P);
-            break;
-        case BND_CPML:
-            k_stress<BND_CPML><<<sp->grid, blk, smem_bytes<BND_CPML>(), st>>>(sp->smaps, P);
-            break;
-        default:
-            k_stress<BND_NONE><<<sp->grid, blk, smem_bytes<BND_NONE>(), st>>>(sp->smaps, P);
-            break;
+                          const DevBoundary& B, const float dto[9], const float inv[9],
+                          int* err, cudaStream_t st) {
+    const PassParams P = pass_params(sp, g, F, B, dto, inv, err);
+    switch (sp->storage) {
+        case EWS_STORAGE_BF16: launch_s<__nv_bfloat16>(sp, P, st); break;
+        case EWS_STORAGE_F16: launch_s<__half>(sp, P, st); break;
+        default: launch_s<float>(sp, P, st); break;
     }
     return cudaGetLastError();
 }

@@ -20,11 +20,12 @@ import numpy as np
 from . import _build
 
 EWS_OK, EWS_EINVAL, EWS_ECFL, EWS_ENOMEM, EWS_ECUDA, EWS_ENONFINITE, EWS_ETIMEOUT, \
-    EWS_ESTATE = range(8)
+    EWS_ESTATE, EWS_ERANGE = range(9)
 STATUS_NAMES = ("EWS_OK", "EWS_EINVAL", "EWS_ECFL", "EWS_ENOMEM", "EWS_ECUDA",
-                "EWS_ENONFINITE", "EWS_ETIMEOUT", "EWS_ESTATE")
+                "EWS_ENONFINITE", "EWS_ETIMEOUT", "EWS_ESTATE", "EWS_ERANGE")
 EWS_BOUNDARY_NONE, EWS_BOUNDARY_SPONGE, EWS_BOUNDARY_CPML = 0, 1, 2
 EWS_STORAGE_F32, EWS_STORAGE_BF16, EWS_STORAGE_F16 = 0, 1, 2
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 EWS_SOURCE_MOMENT, EWS_SOURCE_FORCE = 0, 1
 EWS_KERNEL_VELOCITY, EWS_KERNEL_STRESS, EWS_KERNEL_INJECT, EWS_KERNEL_RECORD = 0, 1, 2, 3
 EWS_NKERNEL = 8
@@ -70,6 +71,8 @@ SIGNATURES = [
     ("ews_reset", _I, [_P]),
     ("ews_get_state", _I, [_P, _P, _I]),
     ("ews_set_state", _I, [_P, _P, _I]),
+    ("ews_set_field_scales", _I, [_P, _P]),
+    ("ews_get_field_scales", _I, [_P, _P]),
     ("ews_adjoint", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _I, _I]),
     ("ews_gradient", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _P, _I, _I]),
     ("ews_set_profiling", _I, [_P, _I]),
@@ -218,6 +221,21 @@ def ews_set_state(sim, state):
     _check(load().ews_set_state(sim, p, dev))
 
 
+def ews_set_field_scales(sim, scale):
+    """scale: 9 powers of two (state order), or None for the defaults."""
+    if scale is None:
+        _check(load().ews_set_field_scales(sim, None))
+        return
+    a = np.ascontiguousarray(scale, np.float32).reshape(9)
+    _check(load().ews_set_field_scales(sim, a.ctypes.data_as(C.c_void_p)))
+
+
+def ews_get_field_scales(sim):
+    a = np.zeros(9, np.float32)
+    _check(load().ews_get_field_scales(sim, a.ctypes.data_as(C.c_void_p)))
+    return a
+
+
 def ews_adjoint(sim, nt: int, dt: float, seis_adj, g_lam, g_mu, g_rho, ckpt_every: int = 0):
     pa, da = _ptr(seis_adj)
     (pl, d0), (pm, d1), (pr, d2) = _ptr(g_lam), _ptr(g_mu), _ptr(g_rho)
@@ -279,6 +297,7 @@ class Simulation:
                  snapshot_every=0, snapshot_mask=0, sponge_alpha=0.0, pml_R=0.0,
                  storage=EWS_STORAGE_F32):
         self.grid = ews_grid(int(nx), int(ny), int(nz), *map(float, spacing))
+        storage = STORAGE[storage] if isinstance(storage, str) else storage
         self.opt = ews_options(BOUNDARY[boundary] if isinstance(boundary, str) else boundary,
                                int(width), int(storage), int(snapshot_every),
                                int(snapshot_mask), float(sponge_alpha), float(pml_R),
@@ -359,6 +378,12 @@ class Simulation:
 
     def set_state(self, state):
         ews_set_state(self._h, state)
+
+    def set_field_scales(self, scale):
+        ews_set_field_scales(self._h, scale)
+
+    def field_scales(self):
+        return ews_get_field_scales(self._h)
 
 
 def simulation_for(prob, **kw) -> Simulation:

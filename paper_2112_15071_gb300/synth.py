@@ -305,6 +305,24 @@ def config3(nx: int = 1024, ny: int = 1024, nz: int = 512, nt: int = 3000,
                    _wavelet_for("force", nt, dt, f0), rec, "sponge", width, f0)
 
 
+def config3_crop(n: int = 128, nt: int = 1000, h: float = 50.0, width: int = 20,
+                 seed: int = SEED) -> Problem:
+    """The large forward recipe re-instantiated on an n^3 crop (128^3) for the
+    storage-error comparison against the oracle: same spacing, model recipe,
+    sponge and receiver layout; the point force sits at the same fraction of
+    the depth (10 km of 25.6 km)."""
+    sp = (h, h, h)
+    vp, vs, rho = layered_random(n, n, n, sp, seed=seed)
+    dt = 0.5 * PAPER_CFL * h / (6000.0 * 1.05)
+    ksrc = int(round(n * 10000.0 / (512 * 50.0)))
+    src = np.array([(n // 2) * h, (n // 2) * h, ksrc * h])
+    f0 = 2.0
+    rec = grid_receivers(n, n, sp, width, width, 32, 32)
+    return Problem(f"config3_crop_{n}cube", n, n, n, sp, dt, nt, vp, vs, rho,
+                   "force", src, np.array([0.0, 0.0, 1e10]),
+                   _wavelet_for("force", nt, dt, f0), rec, "sponge", width, f0)
+
+
 def config4(n: int = 192, nt: int = 1500, h: float = 15.0, width: int = 20,
             seed: int = SEED):
     """Adjoint case: returns (true, start) problems on n^3 (192), dx = 15 m.
