@@ -55,6 +55,14 @@ def parse_args():
                     help="skip the adjoint-gradient / forward time ratio")
     ap.add_argument("--adj-n", type=int, default=192)
     ap.add_argument("--adj-nt", type=int, default=1500)
+    ap.add_argument("--storage", choices=("f32", "bf16", "f16"), default="f32",
+                    help="wavefield storage of the main workload (FP32 arithmetic)")
+    ap.add_argument("--no-storage", action="store_true",
+                    help="skip the FP32 / BF16 / FP16 storage comparison")
+    ap.add_argument("--storage-nt", type=int, default=40,
+                    help="time steps timed per storage type on the large grid")
+    ap.add_argument("--crop-nt", type=int, default=1000,
+                    help="time steps of the 128^3 crop run against the oracle")
     return ap.parse_args()
 
 
@@ -142,17 +150,20 @@ class ClockSampler:
 
 # --- roofline bookkeeping ----------------------------------------------------
 
-def algorithmic_bytes(prob):
-    """Minimal DRAM bytes per launch of each pass (FP32):
-    velocity: read 6 sigma + rho, read+write 3 v           = 13 floats / cell
-    stress:   read 3 v + lambda + mu, read+write 6 sigma   = 17 floats / cell
-    C-PML: each pass reads and writes 3 memory variables per damped direction
-    of every slab cell (24 B per cell-direction and pass)."""
+def algorithmic_bytes(prob, es: int = 4):
+    """Minimal DRAM bytes per launch of each pass, for wavefields stored in
+    `es` bytes (the medium is FP32):
+    velocity: read 6 sigma + rho, read+write 3 v           = 12 es + 4 B / cell
+    stress:   read 3 v + lambda + mu, read+write 6 sigma   = 15 es + 8 B / cell
+    (FP32: 52 and 68 B).  C-PML: each pass reads and writes 3 FP32 memory
+    variables per damped direction of every slab cell (24 B per
+    cell-direction and pass).  The whole-step minimum reads and writes the 9
+    fields once and reads the medium once: 18 es + 12 B (84 B in FP32)."""
     n = prob.nx * prob.ny * prob.nz
     W = prob.width if prob.boundary == "cpml" else 0
     slab = 2 * W * (prob.ny * prob.nz + prob.nx * prob.nz + prob.nx * prob.ny)
-    return {"velocity": 52 * n + 24 * slab, "stress": 68 * n + 24 * slab,
-            "step_min": 84 * n + 48 * slab, "slab_cell_dirs": slab}
+    return {"velocity": (12 * es + 4) * n + 24 * slab, "stress": (15 * es + 8) * n + 24 * slab,
+            "step_min": (18 * es + 12) * n + 48 * slab, "slab_cell_dirs": slab}
 
 
 def kernel_source_sha() -> str:
@@ -201,6 +212,8 @@ def cpu_oracle_rate(prob, seconds: float):
     s = oracle.OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
     s.set_medium_vel(prob.vp, prob.vs, prob.rho)
     s.set_boundary(prob.boundary, prob.width, prob.dt, prob.f0)
+    s.forward(2, prob.dt, prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet,
+              prob.rec_pos)                      # first touch of the oracle's arrays
     t0 = time.perf_counter()
     s.forward(2, prob.dt, prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet,
               prob.rec_pos)
@@ -227,7 +240,7 @@ def run_ours(args, world, rank, local):
     prob = synth.config2(n=args.n, nt=args.nt)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    sim = ews.simulation_for(prob)
+    sim = ews.simulation_for(prob, storage=args.storage)
     sim.set_stream(stream.cuda_stream)
     seis = torch.zeros((3, sim.nrec, prob.nt), device=dev)
     for _ in range(args.warmup):
@@ -258,12 +271,13 @@ def run_ours(args, world, rank, local):
     # dominant kernel and its roofline
     names = ews.KERNEL_NAMES
     dom = int(np.argmax(kms[:len(names)]))
-    alg = algorithmic_bytes(prob)
+    alg = algorithmic_bytes(prob, 4 if args.storage == "f32" else 2)
     avg_ms = kms[dom] / max(klaunch[dom], 1)
     dom_bytes = alg.get(names[dom], 0)
     peak, peak_kind = peaks()
     achieved = dom_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
-    traffic = committed_traffic(f"k_{names[dom]}", f"{prob.nx}cube_cpml")
+    tag = f"{prob.nx}cube_cpml" + ("" if args.storage == "f32" else "_" + args.storage)
+    traffic = committed_traffic(f"k_{names[dom]}", tag)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "kernel": f"k_{names[dom]}", "peak_kind": peak_kind,
@@ -304,6 +318,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded layered + random model)",
         "config": {"workload": WORKLOAD, "grid": [prob.nx, prob.ny, prob.nz], "nt": prob.nt,
                    "dx_m": prob.spacing[0], "boundary": "cpml", "width": prob.width,
+                   "storage": args.storage,
                    "receivers": int(sim.nrec), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (9 fields + 3 medium arrays = 768 MiB "
                          "resident, 129 MB L2)"},
@@ -313,6 +328,8 @@ def run_ours(args, world, rank, local):
     }
     if not args.no_adjoint:
         out["adjoint"] = adjoint_ratio(args, local)
+    if not args.no_storage:
+        out["storage"] = storage_report(args, local, rank == 0 and world == 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
     sim.close()
@@ -363,6 +380,75 @@ def adjoint_ratio(args, local):
                         "L2 misfit vs 10% sphere model, checkpoints every 50",
             "forward_ms": round(fwd_ms, 2), "gradient_ms": round(grad_ms, 2),
             "ratio": round(grad_ms / fwd_ms, 3), "misfit": mis[0]}
+
+
+def storage_report(args, local, with_oracle: bool):
+    """Large forward case (1024 x 1024 x 512, dx = 50 m, sponge 20, point
+    force 2 Hz at 10 km, 32 x 32 receivers): throughput of the same loop with
+    the wavefields stored in FP32, BF16 and FP16, and the seismogram error of
+    each against the FP64 oracle on the 128^3 crop of the same recipe."""
+    import numpy as np
+    import torch
+    from paper_2112_15071_gb300 import ews, synth
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    nt = args.storage_nt
+    prob = synth.config3(nt=nt, device=dev)
+    peak, peak_kind = peaks()
+    es = {"f32": 4, "bf16": 2, "f16": 2}
+    out = {"workload": f"{prob.nx}x{prob.ny}x{prob.nz} dx=50 m, sponge 20, layered + random "
+                       "(device-generated), vertical force 2 Hz at 10 km, 32x32 receivers",
+           "timed_steps": nt, "peak_gbs": peak, "peak_kind": peak_kind}
+    for st in ("f32", "bf16", "f16"):
+        sim = ews.simulation_for(prob, storage=st)
+        sim.set_stream(stream.cuda_stream)
+        seis = torch.zeros((3, sim.nrec, nt), device=dev)
+        sim.run(nt, prob.dt, seis)                   # warm-up
+        torch.cuda.synchronize()
+        sim.profile(reset=True)
+        sim.set_profiling(True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.run(nt, prob.dt, seis)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        kms, kl = sim.profile(reset=True)
+        sim.set_profiling(False)
+        alg = algorithmic_bytes(prob, es[st])
+        v_ms = kms[0] / max(kl[0], 1)
+        s_ms = kms[1] / max(kl[1], 1)
+        step_ms = ms / nt
+        out[st] = {"gcells": round(prob.ncell * nt / (ms / 1e3) / 1e9, 3),
+                   "ms_per_time_step": round(step_ms, 4),
+                   "velocity_frac": round(alg["velocity"] / (v_ms / 1e3) / 1e9 / peak, 4),
+                   "stress_frac": round(alg["stress"] / (s_ms / 1e3) / 1e9 / peak, 4),
+                   "whole_step_frac": round(alg["step_min"] / (step_ms / 1e3) / 1e9 / peak, 4),
+                   "algorithmic_bytes_per_cell": 18 * es[st] + 12,
+                   "field_scales": [float(x) for x in sim.field_scales()]}
+        sim.close()
+        del seis
+    del prob
+    torch.cuda.empty_cache()
+    if with_oracle:
+        from oracle import oracle
+        oracle.build()
+        crop = synth.config3_crop(nt=args.crop_nt)
+        t0 = time.perf_counter()
+        want = oracle.run_problem(crop)
+        t_or = time.perf_counter() - t0
+        err = {"crop": f"{crop.nx}^3, same recipe, force at k={int(crop.src_pos[2] / 50)}, "
+                       f"{crop.rec_pos.shape[0]} receivers", "nt": crop.nt,
+               "metric": "relative L2 of all seismograms vs the FP64 oracle",
+               "oracle_seconds": round(t_or, 1)}
+        for st in ("f32", "bf16", "f16"):
+            sim = ews.simulation_for(crop, storage=st)
+            got = sim.run(crop.nt, crop.dt)
+            err[st] = float(np.linalg.norm(got.astype(np.float64) - want) / np.linalg.norm(want))
+            sim.close()
+        out["error_vs_oracle"] = err
+    return out
 
 
 # --- reference arm: the FP64 oracle on the host cores -------------------------

@@ -168,6 +168,40 @@ def layered_random(nx: int, ny: int, nz: int, spacing,
     return vp, vs, gardner(vp)
 
 
+def layered_random_device(nx: int, ny: int, nz: int, spacing, device,
+                          layer_vp=(2000.0, 3000.0, 4000.0, 5000.0, 6000.0),
+                          vpvs: float = 1.73, corr_len: float = 200.0,
+                          amp: float = 0.05, seed: int = SEED):
+    """The layered_random recipe generated directly in device memory with
+    torch (for grids whose host generation would take minutes): the same
+    layers, circular Gaussian filtering and Gardner density, drawn from
+    torch's seeded generator instead of numpy's.  Returns CUDA tensors."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    p = torch.randn((nz, ny, nx), generator=gen, device=device, dtype=torch.float32)
+    for axis, h in ((2, spacing[0]), (1, spacing[1]), (0, spacing[2])):
+        n = p.shape[axis]
+        x = torch.arange(n, device=device, dtype=torch.float64)
+        x = torch.minimum(x, n - x)
+        kf = torch.fft.rfft(torch.exp(-(x / (corr_len / h)) ** 2))
+        shape = [1, 1, 1]
+        shape[axis] = kf.shape[0]
+        pf = torch.fft.rfft(p, dim=axis)
+        pf *= kf.reshape(shape).to(pf.dtype)
+        p = torch.fft.irfft(pf, n=n, dim=axis).float()
+        del pf
+    p *= amp / p.abs().max()
+    nl = len(layer_vp)
+    layer = torch.clamp((torch.arange(nz, device=device) * nl) // nz, max=nl - 1)
+    vp1 = torch.tensor(layer_vp, device=device, dtype=torch.float32)[layer]
+    vp = (vp1[:, None, None] * (1.0 + p)).contiguous()
+    del p
+    vs = vp / vpvs
+    rho = (310.0 * vp.double() ** 0.25).float()
+    return vp, vs, rho
+
+
 def add_sphere(vp, vs, spacing, centre, radius: float, frac: float):
     """Multiply vp and vs by (1 + frac) inside a sphere; Gardner rho."""
     nz, ny, nx = vp.shape
@@ -290,11 +324,15 @@ def config2(n: int = 256, nt: int = 2000, h: float = 20.0, width: int = 20,
 
 
 def config3(nx: int = 1024, ny: int = 1024, nz: int = 512, nt: int = 3000,
-            h: float = 50.0, width: int = 20, seed: int = SEED) -> Problem:
+            h: float = 50.0, width: int = 20, seed: int = SEED, device=None) -> Problem:
     """Large forward case: 1024 x 1024 x 512, dx = 50 m, layered + random,
-    sponge 20, vertical point force at 10 km depth (2 Hz), 32 x 32 receivers."""
+    sponge 20, vertical point force at 10 km depth (2 Hz), 32 x 32 receivers.
+    With `device`, the model is generated in device memory (torch tensors)."""
     sp = (h, h, h)
-    vp, vs, rho = layered_random(nx, ny, nz, sp, seed=seed)
+    if device is not None:
+        vp, vs, rho = layered_random_device(nx, ny, nz, sp, device, seed=seed)
+    else:
+        vp, vs, rho = layered_random(nx, ny, nz, sp, seed=seed)
     dt = 0.5 * PAPER_CFL * h / (6000.0 * 1.05)
     ksrc = min(int(round(10000.0 / h)), nz - 3)
     src = np.array([(nx // 2) * h, (ny // 2) * h, ksrc * h])
