@@ -137,7 +137,8 @@ __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int fr
             if (mu > 0.0f) zsmin = sqrtf(r * mu);
         }
     }
-    // warp-level reduce, then one atomic per warp and quantity
+    // warp-level reduce, then across the 8 warps of the block, then one
+    // atomic per block and quantity
     for (int o = 16; o > 0; o >>= 1) {
         flag |= __shfl_xor_sync(0xffffffffu, flag, o);
         vp = fmaxf(vp, __shfl_xor_sync(0xffffffffu, vp, o));
@@ -145,7 +146,24 @@ __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int fr
         rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
         zsmin = fminf(zsmin, __shfl_xor_sync(0xffffffffu, zsmin, o));
     }
-    if ((threadIdx.x & 31) == 0) {
+    __shared__ float red[8][5];
+    const int w = threadIdx.y;                 // blockDim = (32, 8): one warp per row
+    if (threadIdx.x == 0) {
+        red[w][0] = __uint_as_float(flag);
+        red[w][1] = vp;
+        red[w][2] = rmin;
+        red[w][3] = zsmin;
+        red[w][4] = zp;
+    }
+    __syncthreads();
+    if (w == 0 && threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) {
+            flag |= __float_as_uint(red[q][0]);
+            vp = fmaxf(vp, red[q][1]);
+            rmin = fminf(rmin, red[q][2]);
+            zsmin = fminf(zsmin, red[q][3]);
+            zp = fmaxf(zp, red[q][4]);
+        }
         if (flag) atomicOr(flags, flag);
         atomicMax(flags + 1, __float_as_uint(vp));
         atomicMin(flags + 2, __float_as_uint(rmin));
