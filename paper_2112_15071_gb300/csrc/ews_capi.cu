@@ -74,6 +74,7 @@ struct ews_sim {
     bool model_set = false;
     float vpmax = 0.0f;
     float rho_min = 0.0f, zs_min = 0.0f, zp_max = 0.0f;   // medium bounds
+    bool has_fluid = false;       // some cell has mu == 0
     // per-field storage scales (16-bit storage holds scale[q] x value)
     float scale[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
     bool scale_user = false;      // set by ews_set_field_scales
@@ -119,6 +120,9 @@ struct ews_sim {
     size_t aux_cap = 0;
     float* gout = nullptr;                // gradient staging for host outputs
     double* dmisfit = nullptr;
+    StencilPlan* adj_plan = nullptr;      // stencil plan of the adjoint fields
+    const float* adj_hist = nullptr;      // history buffer the plan's map points at
+    int adj_hist_slots = 0;
 
     void* field(int q) const { return (char*)fields + (size_t)q * fstride * es; }
     DevFields F() const {
@@ -308,6 +312,7 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
     s->rho_min = bnd[1];
     s->zs_min = bnd[2];
     s->zp_max = bnd[3];
+    s->has_fluid = (hf[0] & 16u) != 0;
     s->model_set = true;
     s->pml_dt = -1.0;
     return EWS_OK;
@@ -429,20 +434,29 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
     ews_status st;
     if ((st = mark(s, -1)) != EWS_OK) return st;
     for (int n = n0; n < n0 + nsteps; ++n) {
-        CK(launch_velocity(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
+        if (vcap) {   // v^{n+1/2} also into the history slot of step n
+            VelExtra X{};
+            X.vcap = vcap + (size_t)(n - n0 + 1) * 3 * s->fstride;
+            X.fstride = (long long)s->fstride;
+            CK(launch_velocity_cap(s->plan, s->g, F, s->B, dto, X, s->err, s->stream));
+        } else {
+            CK(launch_velocity(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
+        }
         if ((st = mark(s, EWS_KERNEL_VELOCITY)) != EWS_OK) return st;
         if (S.kind == EWS_SOURCE_FORCE) {
             CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, stor, s->err, s->stream));
             if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
+            if (vcap) {   // the captured v^{n+1/2} includes the force term too
+                DevFields H = F;
+                for (int c = 0; c < 3; ++c)
+                    H.f[c] = vcap + (size_t)(n - n0 + 1) * 3 * s->fstride + c * s->fstride;
+                CK(launch_inject(s->g, H, M, s->B, S, s->wavelet, n, stor, s->err, s->stream));
+            }
         }
         if (s->nrec > 0 && dseis) {
             CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, stor, inv, s->stream));
             if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
         }
-        if (vcap)   // v^{n+1/2} into the history slot of step n (fields 0..2 are contiguous)
-            CK(cudaMemcpyAsync(vcap + (size_t)(n - n0 + 1) * 3 * s->fstride, s->fields,
-                               3 * s->fstride * sizeof(float), cudaMemcpyDeviceToDevice,
-                               s->stream));
         CK(launch_stress(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
         if ((st = mark(s, EWS_KERNEL_STRESS)) != EWS_OK) return st;
         if (S.kind == EWS_SOURCE_MOMENT) {
@@ -529,7 +543,51 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     CK(cudaMemsetAsync(s->adj, 0, 17 * fs * sizeof(float), s->stream));
     CK(cudaMemsetAsync(s->acc64, 0, 8 * fs * sizeof(double), s->stream));
     const float fdt = (float)dt;
-    for (int c = nck - 1; c >= 0; --c) {
+    const bool transformed = !s->has_fluid;
+    if (transformed) {
+        // Reverse sweep in (alpha, tau): the forward passes with -dt on the
+        // adjoint fields, gradient products fused into the velocity pass.
+        DevFields AF;
+        for (int q = 0; q < NFIELD; ++q) AF.f[q] = s->adj + q * fs;
+        if (!s->adj_plan) {
+            cudaError_t e = stencil_plan_create(s->g, AF, s->M(), s->B, EWS_STORAGE_F32, &s->adj_plan);
+            if (e != cudaSuccess) return fail(EWS_ECUDA, "adjoint stencil plan: %s", cudaGetErrorString(e));
+        }
+        if (s->adj_hist != s->vhist || s->adj_hist_slots != K + 1) {
+            CK(stencil_plan_set_history(s->adj_plan, s->g, s->vhist, (long long)fs, K + 1));
+            s->adj_hist = s->vhist;
+            s->adj_hist_slots = K + 1;
+        }
+        float mdt[NFIELD], one[NFIELD];
+        for (int q = 0; q < NFIELD; ++q) {
+            mdt[q] = -fdt;
+            one[q] = 1.0f;
+        }
+        for (int c = nck - 1; c >= 0; --c) {
+            const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
+            CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s->stream));
+            CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float), cudaMemcpyDeviceToDevice,
+                               s->stream));
+            if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK) return st;
+            for (int m = n1 - 1; m >= n0; --m) {
+                VelExtra X{};
+                for (int q = 0; q < 8; ++q) X.acc[q] = A.acc[q];
+                X.fstride = (long long)fs;
+                X.gdt = fdt;
+                X.hslot = m - n0 + 1;
+                X.vnext = m + 1 < n1 ? s->vhist + (size_t)(m - n0 + 2) * 3 * fs : nullptr;
+                CK(launch_velocity_grad(s->adj_plan, s->g, AF, s->B, mdt, X, s->err, s->stream));
+                if (s->nrec > 0 && sadj)
+                    CK(launch_adj_inject(s->g, A, s->M(), s->B, s->rtaps, s->nrec, sadj, nt, m,
+                                         s->stream));
+                CK(launch_stress(s->adj_plan, s->g, AF, s->B, mdt, one, s->err, s->stream));
+            }
+            CK(launch_rho_term(s->g, A, s->B, s->vhist + 3 * fs, s->vhist, (long long)fs, s->stream));
+            CK(launch_acc_flush(s->g, A, s->stream));
+        }
+    }
+    for (int c = transformed ? -1 : nck - 1; c >= 0; --c) {
         const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
         CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
                            cudaMemcpyDeviceToDevice, s->stream));
@@ -555,7 +613,10 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         gm = s->gout + ncell;
         gr = s->gout + 2 * ncell;
     }
-    CK(launch_grad_finalize(s->g, A, s->M(), gl, gm, gr, s->stream));
+    if (transformed)
+        CK(launch_grad_finalize_t(s->g, A, s->M(), gl, gm, gr, s->stream));
+    else
+        CK(launch_grad_finalize(s->g, A, s->M(), gl, gm, gr, s->stream));
     if (!g_on_device) {
         CK(cudaMemcpyAsync(g_lam, gl, ncell * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaMemcpyAsync(g_mu, gm, ncell * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
@@ -696,6 +757,7 @@ void ews_destroy(ews_sim* s) {
     cudaFree(s->flags);
     cudaFree(s->err);
     stencil_plan_destroy(s->plan);
+    stencil_plan_destroy(s->adj_plan);
     cudaFree(s->psi);
     cudaFree(s->wavelet);
     cudaFree(s->rtaps);

@@ -107,6 +107,7 @@ __global__ void k_field_in(DevGrid g, const float* __restrict__ d, float s, T* _
 // unsigned atomics order them).  flags[0]: bit0 non-finite, bit1 rho <= 0,
 // bit2 mu < 0, bit3 lambda + 2 mu <= 0;  flags[1]: max vp; flags[2]: min
 // rho; flags[3]: min sqrt(rho mu) over mu > 0; flags[4]: max sqrt(rho (lambda + 2 mu)).
+// flags[0] bit4 (16) marks a cell with mu == 0, which is valid.
 __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int from_vel,
                                unsigned* flags) {
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -135,6 +136,7 @@ __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int fr
             zp = sqrtf(r * (lam + 2.0f * mu));
             rmin = r;
             if (mu > 0.0f) zsmin = sqrtf(r * mu);
+            if (mu == 0.0f) flag |= 16u;       // a fluid cell (not an error)
         }
     }
     // warp-level reduce, then across the 8 warps of the block, then one

@@ -72,10 +72,11 @@ struct DevSource {
     Tap tap[kMaxSrcTaps]; // w already holds -dt M_c w_tri / V or dt F_c w_tri / V
 };
 
-// Adjoint state (ews_adjoint.cu): P velocity-like (true adjoint = G P),
-// Q stress-like, FP32 per-segment accumulators and FP64 totals:
-// acc[0] lambda, [1] mu at normal points, [2..4] mu at xy/xz/yz shear points,
-// [5..7] buoyancy at vx/vy/vz points.
+// Adjoint state (ews_adjoint.cu): p velocity-like, q stress-like, FP32
+// per-segment accumulators and FP64 totals (meaning per formulation in
+// ews_adjoint.cu; both keep lambda / normal-mu terms in acc[0..1], shear
+// terms at the xy/xz/yz points in acc[2..4], buoyancy terms at the vx/vy/vz
+// points in acc[5..7]).
 struct AdjFields {
     float* p[3];
     float* q[6];
@@ -96,12 +97,32 @@ cudaError_t launch_grad_finalize(const DevGrid& g, const AdjFields& A, const Dev
                                  float* glam, float* gmu, float* grho, cudaStream_t st);
 cudaError_t launch_residual(const float* seis, const float* obs, float* sadj, long long n,
                             float dt, double* misfit, cudaStream_t st);
+// Transformed formulation (p = alpha, q = tau; see ews_adjoint.cu).
+cudaError_t launch_adj_inject(const DevGrid& g, const AdjFields& A, const DevMedium& M,
+                              const DevBoundary& B, const Tap* taps, int nrec, const float* sadj,
+                              int ld, int n, cudaStream_t st);
+cudaError_t launch_rho_term(const DevGrid& g, const AdjFields& A, const DevBoundary& B,
+                            const float* vn, const float* vp, long long fstride, cudaStream_t st);
+cudaError_t launch_grad_finalize_t(const DevGrid& g, const AdjFields& A, const DevMedium& M,
+                                   float* glam, float* gmu, float* grho, cudaStream_t st);
 
 // Thread-local error message for ews_last_error() (ews_capi.cu).
 ews_status report(ews_status s, const char* fmt, ...);
 
 // Stencil passes (ews_stencil.cu): TMA tensor maps and launch geometry are
 // built once per simulation (the field and medium addresses never change).
+// Extra operands of the velocity pass when it captures the velocity history
+// (checkpoint recomputation) or runs as the reverse (adjoint) pass with the
+// gradient products fused in.
+struct VelExtra {
+    float* vcap;          // capture: destination of v^{n+1/2} (3 fields, fstride apart)
+    const float* vnext;   // reverse: v^{m+3/2} (3 fields) for the buoyancy term, or null
+    float* acc[8];        // reverse: FP32 gradient accumulators (AdjFields order)
+    long long fstride;    // elements between the fields of a history slot
+    float gdt;            // reverse: dt of the forward step
+    int hslot;            // reverse: history slot holding v^{m+1/2}
+};
+
 // The passes take, per field q, dto[q] = dt s_q (used for the fields they
 // write) and inv[q] = 1 / s_q (used for the 16-bit fields they read); with
 // FP32 storage s_q = 1.  *err collects bit 1 / 2 (a velocity / stress pipeline
@@ -120,6 +141,20 @@ cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFi
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                           const DevBoundary& B, const float dto[9], const float inv[9],
                           int* err, cudaStream_t st);
+// FP32 storage only.  Velocity pass that also writes v^{n+1/2} to X.vcap:
+cudaError_t launch_velocity_cap(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
+                                const DevBoundary& B, const float dto[9], const VelExtra& X,
+                                int* err, cudaStream_t st);
+// Reverse velocity pass on the adjoint fields F (dto = -dt) with the gradient
+// products of reverse step m accumulated into X.acc (history tiles from the
+// map set by stencil_plan_set_history; boundary none or sponge):
+cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
+                                 const DevBoundary& B, const float dto[9], const VelExtra& X,
+                                 int* err, cudaStream_t st);
+// History buffer of the reverse pass: nslot slots of 3 fields, slot s field c
+// at hist + (3 s + c) * fstride, pitched like the wavefields.
+cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const float* hist,
+                                     long long fstride, int nslot);
 
 // Sources, receivers, medium set-up and storage conversion (ews_forward.cu).
 // All run on `st`; `storage` is the EWS_STORAGE_* type of the wavefields.
@@ -131,7 +166,7 @@ cudaError_t launch_inject(const DevGrid& g, const DevFields& F, const DevMedium&
 cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps, int nrec,
                           float* seis, int ld, int n, int storage, const float inv[3],
                           cudaStream_t st);
-// flags[0]: validity bits; flags[1..4]: float bits of max vp, min rho,
+// flags[0]: validity bits (bit4: some mu == 0); flags[1..4]: float bits of max vp, min rho,
 // min sqrt(rho mu) over cells with mu > 0 (else FLT_MAX), max sqrt(rho (lambda + 2 mu)).
 cudaError_t launch_medium_setup(const DevGrid& g, float* a, float* b, float* rho,
                                 int from_velocities, unsigned* flags, cudaStream_t st);

@@ -116,21 +116,34 @@ struct Lay {
                   "TMA destinations must stay 128-byte aligned");
 };
 
+// Kernel modes of the velocity pass: plain forward; forward that also
+// copies v^{n+1/2} into a history slot (checkpoint recomputation); reverse
+// (adjoint) pass that also accumulates the gradient products, for which each
+// slot carries the three velocity-history halo tiles of the same plane.
+enum { M_FWD = 0, M_CAP = 1, M_GRAD = 2 };
+template <typename T, int MODE>
+__host__ __device__ constexpr int slot_bytes() {
+    return MODE == M_GRAD ? ((Lay<T>::V_BYTES + 3 * Lay<T>::HB > Lay<T>::SLOT
+                                  ? Lay<T>::V_BYTES + 3 * Lay<T>::HB
+                                  : Lay<T>::SLOT) + 127) / 128 * 128
+                          : Lay<T>::SLOT;
+}
+
 // C-PML memory variables of the output plane live in one extra buffer of 9
 // FP32 core tiles (3 terms for each damped direction), refilled for the next
 // output plane as soon as the current one has been consumed.
 constexpr int PSI_BYTES = 9 * CORE * 4;
-template <int BND, typename T>
+template <int BND, typename T, int MODE = M_FWD>
 constexpr size_t smem_bytes() {
-    return (size_t)NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0) + 8 * (NSLOT + 1);
+    return (size_t)NSLOT * slot_bytes<T, MODE>() + (BND == BND_CPML ? PSI_BYTES : 0) + 8 * (NSLOT + 1);
 }
 // CTAs per SM that the shared-memory footprint allows; the register budget of
 // the kernels is sized for exactly that many.
-template <int BND, typename T>
+template <int BND, typename T, int MODE = M_FWD>
 constexpr int min_blocks() {
-    return (227 * 1024) / (int)(smem_bytes<BND, T>() + 1024) < 1   ? 1
-           : (227 * 1024) / (int)(smem_bytes<BND, T>() + 1024) > 4 ? 4
-                                                                   : (227 * 1024) / (int)(smem_bytes<BND, T>() + 1024);
+    return (227 * 1024) / (int)(smem_bytes<BND, T, MODE>() + 1024) < 1   ? 1
+           : (227 * 1024) / (int)(smem_bytes<BND, T, MODE>() + 1024) > 4 ? 4
+                                                                         : (227 * 1024) / (int)(smem_bytes<BND, T, MODE>() + 1024);
 }
 
 // --- PTX wrappers -------------------------------------------------------------
@@ -190,12 +203,23 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z, int w) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z),
+        "r"(w)
+        : "memory");
+}
+
 // Tensor maps of one pass, in slot order: halo[] then core[] as listed in
 // the slot layout above, then the C-PML terms [3 * direction + term].
 struct Maps {
     CUtensorMap halo[MAXH];
     CUtensorMap core[MAXC];
     CUtensorMap psi[9];
+    CUtensorMap hist;     // velocity history [slot * 3 + component][nz][ny][pitch] (4D)
 };
 
 struct PassParams {
@@ -207,19 +231,25 @@ struct PassParams {
     int ntx, nty;
     int zchunk;           // planes per z-chunk
     int* err;
+    VelExtra X;           // history / gradient operands of the M_CAP and M_GRAD modes
 };
 
 // Issue the TMA loads of z-plane `z` of tile (x0, y0) into `slot`.
-template <typename T>
+template <typename T, int MODE>
 __device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, uint64_t* bar,
-                                          int x0, int y0, int z) {
+                                          int x0, int y0, int z, int hslot) {
     using L = Lay<T>;
-    mbar_expect_tx(bar, (uint32_t)L::V_BYTES);
+    mbar_expect_tx(bar, (uint32_t)(L::V_BYTES + (MODE == M_GRAD ? 3 * L::HB : 0)));
 #pragma unroll
     for (int h = 0; h < 5; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
     tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0 - 2, z);
 #pragma unroll
     for (int c = 0; c < 4; ++c) tma_load_3d(slot + L::V_CORE + c * L::CB, &m.core[c], bar, x0, y0, z);
+    if constexpr (MODE == M_GRAD)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            tma_load_4d(slot + L::V_BYTES + c * L::HB, &m.hist, bar, x0 - St<T>::HO, y0 - 2, z,
+                        3 * hslot + c);
 }
 template <typename T>
 __device__ __forceinline__ void issue_str(const Maps& m, unsigned char* slot, uint64_t* bar,
@@ -347,16 +377,18 @@ enum { VC_SZZ, VC_VX, VC_VY, VC_VZ };
 
 struct VelQ {
     float zz[ROWS][4], xz[ROWS][4], yz[ROWS][4];   // sigma_zz k-1..k+2, sigma_xz/yz k-2..k+1
+    float hx[ROWS][4], hy[ROWS][4], hz[ROWS][4];   // M_GRAD history: vx/vy k-1..k+2, vz k-2..k+1
 };
 
 // One arrival of the z-loop, ring position PH = m mod 4.  Returns false if
 // the CTA must stop (a wait gave up).
-template <int BND, typename T, int PH>
+template <int BND, typename T, int MODE, int PH>
 __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, VelQ& Q, unsigned char* sm,
                                          uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
     using L = Lay<T>;
     constexpr int HX = L::HX;
+    constexpr int SB = slot_bytes<T, MODE>();
     const DevGrid& g = P.g;
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
     const int k = G.z0 - 4 + m;                                    // output plane
@@ -366,11 +398,28 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     const float paz = sz ? __ldg(P.B.pa[2] + k) : 0.f, pbz = sz ? __ldg(P.B.pb[2] + k) : 0.f;
     const float G3 = (BND == BND_SPONGE && out) ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
     const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;   // damped dirs of k
+    // M_GRAD: gradient accumulators and v^{m+3/2} of the output cells, loaded
+    // before the wait so their latency overlaps it
+    float ga[ROWS][8], gv[ROWS][3];
+    if constexpr (MODE == M_GRAD) {
+#pragma unroll
+        for (int rr = 0; rr < ROWS; ++rr) {
+            const long long oo = (long long)k * g.plane + G.obase + rr * g.pitch;
+            const bool on = out && G.own[rr];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) ga[rr][q] = on ? P.X.acc[q][oo] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ga[rr][5 + c] = (on && P.X.vnext) ? P.X.acc[5 + c][oo] : 0.f;
+                gv[rr][c] = (on && P.X.vnext) ? __ldg(P.X.vnext + c * P.X.fstride + oo) : 0.f;
+            }
+        }
+    }
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
     if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
-    const unsigned char* sl0 = sm + S0 * L::SLOT;
-    const unsigned char* sl1 = sm + S1 * L::SLOT;
-    const unsigned char* sl2 = sm + S2 * L::SLOT;
+    const unsigned char* sl0 = sm + S0 * SB;
+    const unsigned char* sl1 = sm + S1 * SB;
+    const unsigned char* sl2 = sm + S2 * SB;
     // push own-column values: sigma_zz of plane p, sigma_xz / sigma_yz of p - 1
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr) {
@@ -378,6 +427,11 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         if (m > 0) {
             Q.xz[rr][PH] = F((const T*)(sl1 + VH_SXZ * L::HB), G.hc + rr * HX);
             Q.yz[rr][PH] = F((const T*)(sl1 + VH_SYZ * L::HB), G.hc + rr * HX);
+        }
+        if constexpr (MODE == M_GRAD) {   // history: vx, vy of plane p; vz of plane p - 1
+            Q.hx[rr][PH] = F((const T*)(sl0 + L::V_BYTES + 0 * L::HB), G.hc + rr * HX);
+            Q.hy[rr][PH] = F((const T*)(sl0 + L::V_BYTES + 1 * L::HB), G.hc + rr * HX);
+            if (m > 0) Q.hz[rr][PH] = F((const T*)(sl1 + L::V_BYTES + 2 * L::HB), G.hc + rr * HX);
         }
     }
     if (out && ok) {
@@ -418,7 +472,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             }
             if (BND == BND_CPML) {
                 // memory variables of plane k from the psi buffer, updated, stored
-                const float* ps = (const float*)(sm + NSLOT * L::SLOT) + G.cc + rr * TX;
+                const float* ps = (const float*)(sm + NSLOT * SB) + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
@@ -437,6 +491,44 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                 }
             }
             // buoyancy at the v points: 1 / mean of the two adjacent densities
+            if constexpr (MODE == M_GRAD) {
+                // Gradient products of this reverse step m (stress points of
+                // the cell; the medium enters at the end): strain rates E of
+                // the forward v^{m+1/2} (Eq. 2/3 operators) against u, the
+                // adjoint stress variable before this pass.
+                const T* vhx = (const T*)(sl2 + L::V_BYTES + 0 * L::HB) + G.hc;
+                const T* vhy = (const T*)(sl2 + L::V_BYTES + 1 * L::HB) + G.hc;
+                const T* vhz = (const T*)(sl2 + L::V_BYTES + 2 * L::HB) + G.hc;
+                const float* qhx = Q.hx[rr];
+                const float* qhy = Q.hy[rr];
+                const float* qhz = Q.hz[rr];
+                const float exx = g.c1x * (F(vhx, R) - F(vhx, R - 1)) + g.c2x * (F(vhx, R + 1) - F(vhx, R - 2));
+                const float eyy = g.c1y * (F(vhy, R) - F(vhy, R - HX)) + g.c2y * (F(vhy, R + HX) - F(vhy, R - 2 * HX));
+                const float ezz = g.c1z * (qhz[C] - qhz[B]) + g.c2z * (qhz[D] - qhz[A]);
+                const float gxy = g.c1y * (F(vhx, R + HX) - F(vhx, R)) + g.c2y * (F(vhx, R + 2 * HX) - F(vhx, R - HX)) +
+                                  g.c1x * (F(vhy, R + 1) - F(vhy, R)) + g.c2x * (F(vhy, R + 2) - F(vhy, R - 1));
+                const float gxz = g.c1z * (qhx[C] - qhx[B]) + g.c2z * (qhx[D] - qhx[A]) +
+                                  g.c1x * (F(vhz, R + 1) - F(vhz, R)) + g.c2x * (F(vhz, R + 2) - F(vhz, R - 1));
+                const float gyz = g.c1z * (qhy[C] - qhy[B]) + g.c2z * (qhy[D] - qhy[A]) +
+                                  g.c1y * (F(vhz, R + HX) - F(vhz, R)) + g.c2y * (F(vhz, R + 2 * HX) - F(vhz, R - HX));
+                const float uxx = F(hxx, R), uyy = F(hyy, R), uzz = F(vc, VC_SZZ * CORE + rr * TX);
+                const float gdt = P.X.gdt;
+                const long long oo = o + rr * g.pitch;
+                P.X.acc[0][oo] = ga[rr][0] + gdt * (exx + eyy + ezz) * (uxx + uyy + uzz);
+                P.X.acc[1][oo] = ga[rr][1] + gdt * (exx * uxx + eyy * uyy + ezz * uzz);
+                P.X.acc[2][oo] = ga[rr][2] + gdt * gxy * F(hxy, R);
+                P.X.acc[3][oo] = ga[rr][3] + gdt * gxz * F(hxz, R);
+                P.X.acc[4][oo] = ga[rr][4] + gdt * gyz * F(hyz, R);
+                if (P.X.vnext) {
+                    // buoyancy term of step m + 1: (v^{m+3/2} / G - v^{m+1/2}) times
+                    // the adjoint velocity variable before this pass
+                    const float Gs = (BND == BND_SPONGE) ? G3 * G.gy[rr] : 1.0f;
+                    const float iG = 1.0f / Gs;
+                    P.X.acc[5][oo] = ga[rr][5] + (gv[rr][0] * iG - F(vhx, R)) * F(vc, VC_VX * CORE + rr * TX);
+                    P.X.acc[6][oo] = ga[rr][6] + (gv[rr][1] * iG - F(vhy, R)) * F(vc, VC_VY * CORE + rr * TX);
+                    P.X.acc[7][oo] = ga[rr][7] + (gv[rr][2] * iG - F(vhz, R)) * F(vc, VC_VZ * CORE + rr * TX);
+                }
+            }
             const float r0 = hr[RF];
             const float bx = __fdividef(2.0f, r0 + hr[RF + G.cx]);
             const float by = __fdividef(2.0f, r0 + hr[RF + G.cy[rr]]);
@@ -453,6 +545,11 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             ((T*)P.F.f[VX])[oo] = St<T>::put(vx);
             ((T*)P.F.f[VY])[oo] = St<T>::put(vy);
             ((T*)P.F.f[VZ])[oo] = St<T>::put(vz);
+            if constexpr (MODE == M_CAP) {   // v^{n+1/2} into its history slot
+                P.X.vcap[oo] = vx;
+                P.X.vcap[P.X.fstride + oo] = vy;
+                P.X.vcap[2 * P.X.fstride + oo] = vz;
+            }
         }
     }
     if (__syncthreads_or(!ok)) {
@@ -466,38 +563,41 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         const int kn = k + 1;
         if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
             const unsigned dn = G.dirs(kn, g.nz);
-            if (dn) issue_psi(maps, (float*)(sm + NSLOT * L::SLOT), &bars[NSLOT], G.x0, G.y0, kn, dn);
+            if (dn) issue_psi(maps, (float*)(sm + NSLOT * SB), &bars[NSLOT], G.x0, G.y0, kn, dn);
         }
     }
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_vel<T>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
+        issue_vel<T, MODE>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m, P.X.hslot);
     return true;
 }
 
-template <int BND, typename T>
-__global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_velocity(const __grid_constant__ Maps maps,
-                                                                        const PassParams P) {
+template <int BND, typename T, int MODE>
+__global__ void __launch_bounds__(NTH, (min_blocks<BND, T, MODE>())) k_velocity(
+    const __grid_constant__ Maps maps, const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(
-        sm + NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0));
+    constexpr int SB = slot_bytes<T, MODE>();
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB + (BND == BND_CPML ? PSI_BYTES : 0));
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
     const Geo<BND, T> G(P);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_vel<T>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
+            issue_vel<T, MODE>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot);
     VelQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { Q.zz[rr][q] = 0.f; Q.xz[rr][q] = 0.f; Q.yz[rr][q] = 0.f; }
+        for (int q = 0; q < 4; ++q) {
+            Q.zz[rr][q] = 0.f; Q.xz[rr][q] = 0.f; Q.yz[rr][q] = 0.f;
+            Q.hx[rr][q] = 0.f; Q.hy[rr][q] = 0.f; Q.hz[rr][q] = 0.f;
+        }
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!vel_step<BND, T, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return;
-        if (m + 1 < G.P4 && !vel_step<BND, T, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return;
-        if (m + 2 < G.P4 && !vel_step<BND, T, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return;
-        if (m + 3 < G.P4 && !vel_step<BND, T, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return;
+        if (!vel_step<BND, T, MODE, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return;
+        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return;
+        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return;
+        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
@@ -705,9 +805,15 @@ cudaError_t prepare(K kern, size_t smem, int* blocks_per_sm) {
 
 template <int BND, typename T>
 cudaError_t occupancy(int* occ) {
-    int a = 0, b = 0;
-    cudaError_t e = prepare(k_velocity<BND, T>, smem_bytes<BND, T>(), &a);
+    int a = 0, b = 0, c = 0;
+    cudaError_t e = prepare(k_velocity<BND, T, M_FWD>, smem_bytes<BND, T>(), &a);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T>, smem_bytes<BND, T>(), &b);
+    if constexpr (std::is_same<T, float>::value) {     // history and reverse modes
+        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP>, smem_bytes<BND, T, M_CAP>(), &c);
+        if constexpr (BND != BND_CPML)
+            if (e == cudaSuccess)
+                e = prepare(k_velocity<BND, T, M_GRAD>, smem_bytes<BND, T, M_GRAD>(), &c);
+    }
     *occ = a < b ? a : b;
     return e;
 }
@@ -756,6 +862,7 @@ bool encode_maps(Maps* vm, Maps* smp, const DevGrid& g, const DevFields& F, cons
 
 struct StencilPlan {
     Maps vmaps, smaps;
+    bool has_hist = false;
     int kind = 0;
     int storage = EWS_STORAGE_F32;
     int grid = 0;
@@ -809,7 +916,7 @@ cudaError_t plan_build(StencilPlan* p, const DevGrid& g, const DevFields& F, con
 
 PassParams pass_params(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                        const DevBoundary& B, const float dto[9], const float inv[9], int* err) {
-    PassParams P;
+    PassParams P{};
     P.g = g;
     P.F = F;
     P.B = B;
@@ -824,18 +931,19 @@ PassParams pass_params(const StencilPlan* sp, const DevGrid& g, const DevFields&
     return P;
 }
 
-template <typename T>
+template <typename T, int MODE = M_FWD>
 void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     dim3 blk(TX, RY);
     switch (sp->kind) {
         case BND_SPONGE:
-            k_velocity<BND_SPONGE, T><<<sp->grid, blk, smem_bytes<BND_SPONGE, T>(), st>>>(sp->vmaps, P);
+            k_velocity<BND_SPONGE, T, MODE><<<sp->grid, blk, smem_bytes<BND_SPONGE, T, MODE>(), st>>>(sp->vmaps, P);
             break;
         case BND_CPML:
-            k_velocity<BND_CPML, T><<<sp->grid, blk, smem_bytes<BND_CPML, T>(), st>>>(sp->vmaps, P);
+            if constexpr (MODE != M_GRAD)
+                k_velocity<BND_CPML, T, MODE><<<sp->grid, blk, smem_bytes<BND_CPML, T, MODE>(), st>>>(sp->vmaps, P);
             break;
         default:
-            k_velocity<BND_NONE, T><<<sp->grid, blk, smem_bytes<BND_NONE, T>(), st>>>(sp->vmaps, P);
+            k_velocity<BND_NONE, T, MODE><<<sp->grid, blk, smem_bytes<BND_NONE, T, MODE>(), st>>>(sp->vmaps, P);
             break;
     }
 }
@@ -897,6 +1005,46 @@ cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFi
         default: launch_v<float>(sp, P, st); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_velocity_cap(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
+                                const DevBoundary& B, const float dto[9], const VelExtra& X,
+                                int* err, cudaStream_t st) {
+    if (sp->storage != EWS_STORAGE_F32) return cudaErrorInvalidValue;
+    const float one[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    PassParams P = pass_params(sp, g, F, B, dto, one, err);
+    P.X = X;
+    launch_v<float, M_CAP>(sp, P, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
+                                 const DevBoundary& B, const float dto[9], const VelExtra& X,
+                                 int* err, cudaStream_t st) {
+    if (sp->storage != EWS_STORAGE_F32 || sp->kind == BND_CPML || !sp->has_hist)
+        return cudaErrorInvalidValue;
+    const float one[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    PassParams P = pass_params(sp, g, F, B, dto, one, err);
+    P.X = X;
+    launch_v<float, M_GRAD>(sp, P, st);
+    return cudaGetLastError();
+}
+
+cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const float* hist,
+                                     long long fstride, int nslot) {
+    auto fn = encoder();
+    if (!fn) return cudaErrorInvalidValue;
+    cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
+                          (cuuint64_t)(3 * nslot)};
+    cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4,
+                             (cuuint64_t)fstride * 4};
+    cuuint32_t box[4] = {(cuuint32_t)HXF, (cuuint32_t)HY, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(&p->vmaps.hist, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(hist),
+                    dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, EWS_L2PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    p->has_hist = r == CUDA_SUCCESS;
+    return p->has_hist ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,

@@ -142,3 +142,19 @@ def test_autograd_function_matches_ews_gradient(ews, orc):
     assert float(loss) == pytest.approx(mis, rel=1e-5)
     for q, t in enumerate((lam, mu, rho)):
         assert rel(t.grad.cpu().numpy(), g[q]) <= 1e-5
+
+
+def test_fluid_cells_use_the_direct_formulation(ews, orc):
+    """With mu = 0 somewhere the stiffness has no inverse, so the transformed
+    reverse sweep cannot recover dJ/dmu there; the library then runs the
+    direct-variable adjoint.  Both must match the FP64 adjoint."""
+    p = problem((40, 36, 28), "sponge", "force", seed=77)
+    p.vs[:3] = 0.0                                   # a fluid top layer
+    A = np.random.default_rng(5).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    med = [a.astype(np.float64) for a in p.lame()]
+    want = orc.gradient(p, A.astype(np.float64), ckpt_every=30, medium=med)
+    sim = ews.simulation_for(p)
+    sim.set_model_lame(*p.lame())
+    got = sim.adjoint(p.nt, p.dt, A, ckpt_every=30)
+    for q in range(3):
+        assert rel(got[q], want[q]) <= TOL_ORACLE, (q, rel(got[q], want[q]))
