@@ -162,14 +162,24 @@ ews_status ews_advance(ews_sim* sim, int n0, int nsteps, double dt, float* seis,
  * device per adj_on_device), writes dL/dlambda, dL/dmu, dL/drho per cell
  * ([nz][ny][nx] float32 each, host or device per g_on_device).  Runs the
  * forward loop from rest storing the 9 wavefields every ckpt_every steps
- * (0: 50), then for each segment in reverse recomputes its states, keeps
- * v^{n+1/2}, and steps the adjoint back through the stress and velocity
- * passes.  Accumulation is FP32 within a segment and FP64 across segments.
- * Boundaries NONE and SPONGE (C-PML: EWS_EINVAL).  Extra device memory:
- * (nt / ckpt_every) x 9 + (ckpt_every + 1) x 3 + 17 fields + 8 FP64 fields. */
+ * (0: 50), then steps the adjoint back segment by segment, recomputing each
+ * segment's velocity history v^{n+1/2} from its checkpoint.  The trailing
+ * segments whose history fits in the history budget (see
+ * ews_set_history_budget; at least one segment) keep the history written
+ * by the first forward pass and are not recomputed.  Accumulation is FP32
+ * within ckpt_every steps and FP64 across them.  Boundaries NONE and SPONGE
+ * (C-PML: EWS_EINVAL); F32 storage only.  Extra device memory: checkpoints
+ * (nt / ckpt_every) x 9 fields, history max(ckpt_every + 1, budgeted
+ * slots) x 3 fields, 17 FP32 + 8 FP64 fields. */
 ews_status ews_adjoint(ews_sim* sim, int nt, double dt, const float* seis_adj,
                        int adj_on_device, float* g_lam, float* g_mu, float* g_rho,
                        int g_on_device, int ckpt_every);
+
+/* Device memory the adjoint may use for resident velocity history (bytes,
+ * >= 0; default 0 = one segment).  Each resident time step costs 3 fields
+ * (12 bytes per cell); with a budget covering all nt steps the gradient
+ * needs no recomputation.  Not in the paper. */
+ews_status ews_set_history_budget(ews_sim* sim, double bytes);
 
 /* Gradient of the L2 misfit J = dt/2 sum_(c,r,n) (seis - observed)^2 with
  * respect to lambda, mu, rho (one forward with checkpoints, then the

@@ -120,6 +120,7 @@ struct ews_sim {
     size_t aux_cap = 0;
     float* gout = nullptr;                // gradient staging for host outputs
     double* dmisfit = nullptr;
+    double hist_budget = 0;               // bytes of resident velocity history
     StencilPlan* adj_plan = nullptr;      // stencil plan of the adjoint fields
     const float* adj_hist = nullptr;      // history buffer the plan's map points at
     int adj_hist_slots = 0;
@@ -507,6 +508,18 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     const int K = ckpt_every > 0 ? (ckpt_every < nt ? ckpt_every : nt) : (nt < 50 ? nt : 50);
     const int nck = (nt + K - 1) / K;
     const size_t fs = s->fstride;
+    const bool transformed = !s->has_fluid;
+    // Resident history: the trailing segments [n_res, nt) whose velocity
+    // history fits the budget (at least the last segment) are captured by
+    // the first forward pass; earlier segments are recomputed into the same
+    // buffer from their checkpoints.
+    const double slot_bytes = 3.0 * fs * sizeof(float);
+    const long long budget_slots = (long long)(s->hist_budget / slot_bytes);
+    int c_res = nck - 1;                       // first resident segment
+    if (transformed)
+        while (c_res > 0 && (long long)(nt - (c_res - 1) * K) + 1 <= budget_slots) --c_res;
+    const int n_res = c_res * K;
+    const int hslots = std::max(K, nt - n_res) + 1;
     if (!s->adj) {
         cudaError_t e = cudaMalloc(&s->adj, 17 * fs * sizeof(float));
         if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint state: %s", cudaGetErrorString(e));
@@ -516,7 +529,9 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         if (e != cudaSuccess) return fail(EWS_ENOMEM, "misfit: %s", cudaGetErrorString(e));
     }
     if ((st = ensure_buf(&s->ckpt, &s->ckpt_cap, (size_t)nck * 9 * fs, "checkpoints")) != EWS_OK) return st;
-    if ((st = ensure_buf(&s->vhist, &s->vhist_cap, (size_t)(K + 1) * 3 * fs, "velocity history")) != EWS_OK) return st;
+    if ((st = ensure_buf(&s->vhist, &s->vhist_cap, (size_t)(transformed ? hslots : K + 1) * 3 * fs,
+                         "velocity history")) != EWS_OK)
+        return st;
     const size_t nseis = (size_t)3 * s->nrec * nt;
     if (obs_dev && (st = ensure_buf(&s->aux, &s->aux_cap, 2 * (nseis ? nseis : 1), "adjoint source")) != EWS_OK)
         return st;
@@ -524,14 +539,25 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     for (int c = 0; c < 3; ++c) A.p[c] = s->adj + c * fs;
     for (int c = 0; c < 6; ++c) A.q[c] = s->adj + (3 + c) * fs;
     for (int c = 0; c < 8; ++c) { A.acc[c] = s->adj + (9 + c) * fs; A.acc64[c] = s->acc64 + c * fs; }
-    // forward with checkpoints (and seismograms when a misfit is asked for)
+    // forward with checkpoints (and seismograms when a misfit is asked for);
+    // the resident segments also write their velocity history
     if ((st = ews_reset(s)) != EWS_OK) return st;
     float* dseis = obs_dev ? s->aux : nullptr;
     for (int c = 0; c < nck; ++c) {
         const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
-        CK(cudaMemcpyAsync(s->ckpt + (size_t)c * 9 * fs, s->fields, 9 * fs * sizeof(float),
-                           cudaMemcpyDeviceToDevice, s->stream));
-        if ((st = steps(s, s->src, n0, n1 - n0, dt, dseis, nt)) != EWS_OK) return st;
+        if (!transformed || c < c_res)   // resident segments are never restored
+            CK(cudaMemcpyAsync(s->ckpt + (size_t)c * 9 * fs, s->fields, 9 * fs * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s->stream));
+        if (transformed && c >= c_res) {
+            if (c == c_res)
+                CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, s->stream));
+            // steps() puts v^{n+1/2} at slot n - n0 + 1 of the buffer it is given
+            float* base = s->vhist + (size_t)(n0 - n_res) * 3 * fs;
+            if ((st = steps(s, s->src, n0, n1 - n0, dt, dseis, nt, base)) != EWS_OK) return st;
+        } else if ((st = steps(s, s->src, n0, n1 - n0, dt, dseis, nt)) != EWS_OK) {
+            return st;
+        }
     }
     const float* sadj = sadj_dev;
     if (obs_dev) {
@@ -543,7 +569,6 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     CK(cudaMemsetAsync(s->adj, 0, 17 * fs * sizeof(float), s->stream));
     CK(cudaMemsetAsync(s->acc64, 0, 8 * fs * sizeof(double), s->stream));
     const float fdt = (float)dt;
-    const bool transformed = !s->has_fluid;
     if (transformed) {
         // Reverse sweep in (alpha, tau): the forward passes with -dt on the
         // adjoint fields, gradient products fused into the velocity pass.
@@ -553,23 +578,29 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
             cudaError_t e = stencil_plan_create(s->g, AF, s->M(), s->B, EWS_STORAGE_F32, &s->adj_plan);
             if (e != cudaSuccess) return fail(EWS_ECUDA, "adjoint stencil plan: %s", cudaGetErrorString(e));
         }
-        if (s->adj_hist != s->vhist || s->adj_hist_slots != K + 1) {
-            CK(stencil_plan_set_history(s->adj_plan, s->g, s->vhist, (long long)fs, K + 1));
+        const int cap_slots = (int)(s->vhist_cap / (3 * fs));
+        if (s->adj_hist != s->vhist || s->adj_hist_slots != cap_slots) {
+            CK(stencil_plan_set_history(s->adj_plan, s->g, s->vhist, (long long)fs, cap_slots));
             s->adj_hist = s->vhist;
-            s->adj_hist_slots = K + 1;
+            s->adj_hist_slots = cap_slots;
         }
         float mdt[NFIELD], one[NFIELD];
         for (int q = 0; q < NFIELD; ++q) {
             mdt[q] = -fdt;
             one[q] = 1.0f;
         }
-        for (int c = nck - 1; c >= 0; --c) {
-            const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
-            CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
-                               cudaMemcpyDeviceToDevice, s->stream));
-            CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float), cudaMemcpyDeviceToDevice,
-                               s->stream));
-            if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK) return st;
+        // segment ranges in reverse: the resident range first, then the
+        // recomputed segments
+        for (int c = c_res; c >= 0; --c) {
+            const int n0 = c * K, n1 = c == c_res ? nt : n0 + K;
+            if (c < c_res) {
+                CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, s->stream));
+                CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, s->stream));
+                if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK)
+                    return st;
+            }
             for (int m = n1 - 1; m >= n0; --m) {
                 VelExtra X{};
                 for (int q = 0; q < 8; ++q) X.acc[q] = A.acc[q];
@@ -582,6 +613,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
                     CK(launch_adj_inject(s->g, A, s->M(), s->B, s->rtaps, s->nrec, sadj, nt, m,
                                          s->stream));
                 CK(launch_stress(s->adj_plan, s->g, AF, s->B, mdt, one, s->err, s->stream));
+                if ((m - n0) % K == 0 && m > n0) CK(launch_acc_flush(s->g, A, s->stream));
             }
             CK(launch_rho_term(s->g, A, s->B, s->vhist + 3 * fs, s->vhist, (long long)fs, s->stream));
             CK(launch_acc_flush(s->g, A, s->stream));
@@ -980,6 +1012,13 @@ ews_status ews_set_state(ews_sim* s, const float* in, int on_device) {
         CK(cudaStreamSynchronize(s->stream));
         return fail(EWS_ERANGE, "a state value exceeds the FP16 range at the field scales");
     }
+    return EWS_OK;
+}
+
+ews_status ews_set_history_budget(ews_sim* s, double bytes) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (!(bytes >= 0) || !std::isfinite(bytes)) return fail(EWS_EINVAL, "budget must be >= 0");
+    s->hist_budget = bytes;
     return EWS_OK;
 }
 

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("ews_get_state", _I, [_P, _P, _I]),
     ("ews_set_state", _I, [_P, _P, _I]),
     ("ews_set_field_scales", _I, [_P, _P]),
+    ("ews_set_history_budget", _I, [_P, _D]),
     ("ews_get_field_scales", _I, [_P, _P]),
     ("ews_adjoint", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _I, _I]),
     ("ews_gradient", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _P, _I, _I]),
@@ -236,6 +237,10 @@ def ews_get_field_scales(sim):
     return a
 
 
+def ews_set_history_budget(sim, nbytes: float):
+    _check(load().ews_set_history_budget(sim, float(nbytes)))
+
+
 def ews_adjoint(sim, nt: int, dt: float, seis_adj, g_lam, g_mu, g_rho, ckpt_every: int = 0):
     pa, da = _ptr(seis_adj)
     (pl, d0), (pm, d1), (pr, d2) = _ptr(g_lam), _ptr(g_mu), _ptr(g_rho)
@@ -378,6 +383,9 @@ class Simulation:
 
     def set_state(self, state):
         ews_set_state(self._h, state)
+
+    def set_history_budget(self, nbytes):
+        ews_set_history_budget(self._h, nbytes)
 
     def set_field_scales(self, scale):
         ews_set_field_scales(self._h, scale)

@@ -158,3 +158,24 @@ def test_fluid_cells_use_the_direct_formulation(ews, orc):
     got = sim.adjoint(p.nt, p.dt, A, ckpt_every=30)
     for q in range(3):
         assert rel(got[q], want[q]) <= TOL_ORACLE, (q, rel(got[q], want[q]))
+
+
+@pytest.mark.parametrize("kind", ["moment", "force"])
+def test_resident_history_matches_recomputation(ews, orc, kind):
+    """Keeping the velocity history of every segment in device memory (no
+    recomputation) gives the same gradient as recomputing every segment
+    from its checkpoint, and both match the FP64 adjoint."""
+    p = problem((37, 45, 33), "sponge", kind, nt=130, seed=12)
+    A = np.random.default_rng(6).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    sim = ews.simulation_for(p)
+    sim.set_model_lame(*p.lame())
+    g0 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
+    sim.set_history_budget(4e9)
+    g1 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
+    sim.set_history_budget(3 * 4 * 48 * 45 * 33 * 70.5)    # about half the run resident
+    g2 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
+    want = orc.gradient(p, A.astype(np.float64), ckpt_every=20,
+                        medium=[a.astype(np.float64) for a in p.lame()])
+    for q in range(3):
+        assert rel(g1[q], g0[q]) <= 1e-6 and rel(g2[q], g0[q]) <= 1e-6
+        assert rel(g1[q], want[q]) <= TOL_ORACLE
