@@ -63,6 +63,18 @@ ews_status report(ews_status s, const char* fmt, ...) {
 }
 }  // namespace ews
 
+// One captured time loop: a CUDA graph of steps n0 .. n0 + nsteps - 1 with
+// everything its kernel parameters depend on as the key.
+struct GraphEntry {
+    unsigned long long gen;
+    int n0, nsteps, ld;
+    double dt;
+    const float* dseis;
+    const float* vcap;
+    cudaGraphExec_t exec;
+    long long launches[EWS_NKERNEL];
+};
+
 struct ews_sim {
     ews_grid grid{};
     ews_options opt{};
@@ -121,6 +133,10 @@ struct ews_sim {
     float* gout = nullptr;                // gradient staging for host outputs
     double* dmisfit = nullptr;
     double hist_budget = 0;               // bytes of resident velocity history
+    // captured time loops (used when per-launch profiling is off)
+    std::vector<GraphEntry> graphs;
+    unsigned long long gen = 1;           // bumped when a kernel parameter source changes
+    cudaStream_t cap_stream = nullptr;    // private stream the loops are captured on
     StencilPlan* adj_plan = nullptr;      // stencil plan of the adjoint fields
     const float* adj_hist = nullptr;      // history buffer the plan's map points at
     int adj_hist_slots = 0;
@@ -393,12 +409,14 @@ void auto_scales(ews_sim* s, double dt) {
         const double bound = q < 3 ? vb : sb;
         double sc = (bound > 0 && std::isfinite(bound)) ? 8192.0 / bound : 1.0;
         sc = std::min(std::max(sc, 0x1p-100), 0x1p100);
-        s->scale[q] = pow2_floor(sc);
+        const float v = pow2_floor(sc);
+        if (v != s->scale[q]) s->gen++;
+        s->scale[q] = v;
     }
 }
 
-ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
-                 float* dseis, int ld, float* vcap = nullptr) {
+ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
+                        float* dseis, int ld, float* vcap) {
     DevFields F = s->F();
     DevMedium M = s->M();
     // fold dt and the cell volume into the source taps
@@ -465,6 +483,61 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
             if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
         }
     }
+    return EWS_OK;
+}
+
+// The time loop of steps_direct, captured once into a CUDA graph per
+// (state generation, step range, dt, output buffers) and replayed: one
+// graph launch per call instead of 4-5 kernel launches per step.  With
+// per-launch profiling on, the launches go out directly (events between
+// them).
+ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
+                 float* dseis, int ld, float* vcap = nullptr) {
+    if (s->profiling || nsteps <= 0) return steps_direct(s, src, n0, nsteps, dt, dseis, ld, vcap);
+    GraphEntry* hit = nullptr;
+    for (GraphEntry& ge : s->graphs)
+        if (ge.gen == s->gen && ge.n0 == n0 && ge.nsteps == nsteps && ge.ld == ld && ge.dt == dt &&
+            ge.dseis == dseis && ge.vcap == vcap)
+            hit = &ge;
+    if (!hit) {
+        if (!s->cap_stream) CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+        long long before[EWS_NKERNEL];
+        std::memcpy(before, s->launches, sizeof(before));
+        cudaStream_t user = s->stream;
+        s->stream = s->cap_stream;
+        CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const ews_status st = steps_direct(s, src, n0, nsteps, dt, dseis, ld, vcap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+        s->stream = user;
+        GraphEntry ge{};
+        for (int k = 0; k < EWS_NKERNEL; ++k) ge.launches[k] = s->launches[k] - before[k];
+        std::memcpy(s->launches, before, sizeof(before));
+        if (st != EWS_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (st != EWS_OK) return st;
+            return fail(EWS_ECUDA, "time-loop capture: %s", cudaGetErrorString(e));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return fail(EWS_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        ge.gen = s->gen;
+        ge.n0 = n0;
+        ge.nsteps = nsteps;
+        ge.ld = ld;
+        ge.dt = dt;
+        ge.dseis = dseis;
+        ge.vcap = vcap;
+        if (s->graphs.size() >= 16) {          // keep the 16 most recent loops
+            cudaGraphExecDestroy(s->graphs.front().exec);
+            s->graphs.erase(s->graphs.begin());
+        }
+        s->graphs.push_back(ge);
+        hit = &s->graphs.back();
+    }
+    CK(cudaGraphLaunch(hit->exec, s->stream));
+    for (int k = 0; k < EWS_NKERNEL; ++k) s->launches[k] += hit->launches[k];
+    s->fresh = false;
     return EWS_OK;
 }
 
@@ -803,6 +876,8 @@ void ews_destroy(ews_sim* s) {
     cudaFree(s->dmisfit);
     cudaFree(s->stage);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    for (GraphEntry& ge : s->graphs) cudaGraphExecDestroy(ge.exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
 }
 
@@ -845,6 +920,7 @@ ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const doubl
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->wavelet_nt = nt;
+    s->gen++;
     s->wsum = 0;
     for (int n = 0; n < nt; ++n) s->wsum += std::fabs((double)wavelet[n]);
     SourceSpec& sp = s->src;
@@ -875,6 +951,7 @@ ews_status ews_set_receivers(ews_sim* s, int nrec, const double* pos) {
         CK(cudaStreamSynchronize(s->stream));
     }
     s->nrec = nrec;
+    s->gen++;
     return EWS_OK;
 }
 
@@ -1027,6 +1104,7 @@ ews_status ews_set_field_scales(ews_sim* s, const float* scale) {
     if (!scale) {                      // back to the defaults
         for (int q = 0; q < NFIELD; ++q) s->scale[q] = 1.0f;
         s->scale_user = false;
+        s->gen++;
         return ews_reset(s);
     }
     for (int q = 0; q < NFIELD; ++q) {
@@ -1042,6 +1120,7 @@ ews_status ews_set_field_scales(ews_sim* s, const float* scale) {
     }
     for (int q = 0; q < NFIELD; ++q) s->scale[q] = scale[q];
     s->scale_user = true;
+    s->gen++;
     return ews_reset(s);
 }
 

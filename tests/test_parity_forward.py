@@ -223,3 +223,29 @@ def test_errors_are_reported(ews):
         sim.run(p.nt + 1, p.dt)                                   # longer than the wavelet
     assert e.value.status == ews.EWS_EINVAL
     sim.run(10, limit * 0.999)
+
+
+def test_graph_replay_equals_direct_launches(ews):
+    """The captured time loop (profiling off) and event-bracketed direct
+    launches (profiling on) give bitwise identical seismograms and states,
+    including chunked runs that capture several graphs and a changed dt."""
+    from paper_2112_15071_gb300 import synth
+    p = synth.small_problem(70, 45, 37, nt=80, boundary="cpml", width=6, kind="force", seed=9)
+    sim = ews.simulation_for(p)
+    a = sim.run(p.nt, p.dt)
+    sa = sim.get_state()
+    b = sim.run(p.nt, p.dt)                      # replay of the cached graph
+    sim.set_profiling(True)
+    c = sim.run(p.nt, p.dt)
+    sc = sim.get_state()
+    sim.set_profiling(False)
+    assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(sa, sc)
+    _, n = sim.profile(reset=True)
+    assert n[0] == 3 * p.nt                       # velocity launches counted on replay too
+    seis = np.zeros((3, p.rec_pos.shape[0], p.nt), np.float32)
+    sim.reset()
+    for n0 in range(0, p.nt, 30):
+        sim.advance(n0, min(30, p.nt - n0), p.dt, seis, p.nt)
+    assert np.array_equal(seis, a)
+    d = sim.run(p.nt, p.dt * 0.9)
+    assert not np.array_equal(d, a)
