@@ -266,6 +266,56 @@ ews_status ews_forward_noalloc(const ews_grid* grid, const ews_options* opt,
                                const float* wavelet, int nrec, const double* rec_pos,
                                int nt, double dt, float* seis, void* cuda_stream);
 
+/* ---- Batched shots (not in the paper, which runs one model at a time) ----
+ * Many independent shots, each a configured simulation (model, source and
+ * receivers set; F32 storage; boundary NONE or SPONGE, the same for all
+ * shots), run forward - and, when observed data are given, through the L2
+ * misfit gradient of ews_gradient - in ONE persistent kernel launch.  The
+ * launch takes work items (a 32 x 8 x zchunk tile of a pass, a chunk of
+ * cells, or a source/receiver step) of all shots from a device queue; an
+ * item waits (bounded, EWS_ETIMEOUT) until its shot's earlier stages are
+ * done, so shots of uneven size and step count share the GPU without a
+ * grid-wide barrier.  Results equal those of ews_run / ews_gradient on each
+ * simulation alone (bitwise for the forward, to accumulation order for the
+ * gradient). */
+typedef struct {
+    ews_sim* sim;             /* configured simulation, used exclusively by this call */
+    int nt;                   /* steps (<= the wavelet length)                        */
+    double dt;                /* time step (checked like ews_run)                     */
+    float* seis;              /* device [3][nrec][nt] output, or NULL                 */
+    const float* observed;    /* device [3][nrec][nt]: also compute the gradient      */
+    float* g_lam;             /* device dense [nz][ny][nx] outputs when observed set  */
+    float* g_mu;
+    float* g_rho;
+    double misfit;            /* out: J = dt/2 sum (seis - observed)^2                */
+} ews_batch_shot;
+
+enum { EWS_BATCH_PERSISTENT = 0, EWS_BATCH_SEQUENTIAL = 1 };
+
+typedef struct {
+    int mode;                 /* EWS_BATCH_PERSISTENT, or EWS_BATCH_SEQUENTIAL: each
+                               * shot through ews_run / ews_gradient in turn (the
+                               * one-by-one reference)                                 */
+    int ckpt_every;           /* gradient checkpoint interval (0: 50)                 */
+    int zchunk;               /* planes per tile in z; 0: picked per grid size by the
+                               * autotuner (timed trial launches, cached per process) */
+    int ctas_per_sm;          /* resident CTAs per SM to launch (0: as many as fit)   */
+    int dep_wait_ms;          /* give-up time of one dependency wait (0: 4000 ms)     */
+    int test_unsatisfiable;   /* testing only: the last item waits for an item that
+                               * never exists, so the launch must end in EWS_ETIMEOUT */
+} ews_batch_options;
+
+/* Run nshots shots; opt may be NULL (persistent, autotuned).  All device
+ * work runs on cuda_stream (NULL: default stream), which is synchronised
+ * before return.  Errors: EWS_EINVAL (mixed boundaries, C-PML, 16-bit
+ * storage, fluid cells for gradients, missing outputs), EWS_ECFL, EWS_ENOMEM,
+ * EWS_ETIMEOUT (a dependency or pipeline wait gave up), EWS_ECUDA. */
+ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
+                     void* cuda_stream);
+
+/* zchunk the autotuner picked for a grid (0 if not tuned yet). */
+int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int gradient);
+
 /* Time-step rule of Sec. 2.1.3, Eq. 5: 0.495 min(dx, dy, dz) / vmax. */
 double ews_cfl_dt(const ews_grid* grid, double vmax);
 

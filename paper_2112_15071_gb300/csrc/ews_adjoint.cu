@@ -37,6 +37,7 @@
 // segments; k_grad_finalize applies the chain rule of the staggered means
 // (mu: 4-cell shear means, rho: 2-cell means inverted).
 #include "ews_internal.cuh"
+#include "ews_ops.cuh"
 
 namespace ews {
 
@@ -212,12 +213,7 @@ __global__ void k_adj_record(DevGrid g, AdjFields A, const Tap* __restrict__ tap
 __global__ void k_acc_flush(DevGrid g, AdjFields A) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
     if (i >= g.nx || j >= g.ny) return;
-    const long long o = cidx(g, i, j, k);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        A.acc64[a][o] += (double)A.acc[a][o];
-        A.acc[a][o] = 0.0f;
-    }
+    ops::flush_cell(A, cidx(g, i, j, k));
 }
 
 // Chain rule of the staggered means; output dense [nz][ny][nx].
@@ -277,36 +273,21 @@ __global__ void k_grad_finalize(DevGrid g, AdjFields A, DevMedium M, float* __re
 
 // Transformed formulation: residual injection alpha += G B S^T sadj_n (one
 // thread per component and receiver, 8 taps each).
-template <int BND>
 __global__ void k_adj_inject(DevGrid g, AdjFields A, DevMedium M, DevBoundary B,
                              const Tap* __restrict__ taps, int nrec,
                              const float* __restrict__ sadj, int ld, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nrec) return;
-    const float a = __ldg(sadj + (long long)t * ld + n);
-    const Tap* tp = taps + 8 * t;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const Tap q = tp[m];
-        const float r0 = med(M.rho, g, q.i, q.j, q.k);
-        const float r1 = med(M.rho, g, q.i + (q.q == VX), q.j + (q.q == VY), q.k + (q.q == VZ));
-        atomicAdd(A.p[q.q] + cidx(g, q.i, q.j, q.k),
-                  gain<BND>(B, q.i, q.j, q.k) * 2.0f / (r0 + r1) * q.w * a);
-    }
+    ops::adj_inject_one(g, A, M, B, taps, sadj, ld, n, t);
 }
 
 // Transformed formulation: buoyancy term of step n0 (first step of a
 // segment), acc5..7 += (v^{n0+1/2} / G - v^{n0-1/2}) alpha.
-template <int BND>
 __global__ void k_rho_term(DevGrid g, AdjFields A, DevBoundary B, const float* __restrict__ vn,
                            const float* __restrict__ vp, long long fstride) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
     if (i >= g.nx || j >= g.ny) return;
-    const long long o = cidx(g, i, j, k);
-    const float iG = 1.0f / gain<BND>(B, i, j, k);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        A.acc[5 + c][o] += (__ldg(vn + c * fstride + o) * iG - __ldg(vp + c * fstride + o)) * A.p[c][o];
+    ops::rho_term_cell(A, B, vn, vp, fstride, cidx(g, i, j, k), i, j, k);
 }
 
 // Transformed formulation: pointwise inverses and the chain rule of the
@@ -315,61 +296,7 @@ __global__ void k_grad_finalize_t(DevGrid g, AdjFields A, DevMedium M, float* __
                                   float* __restrict__ gmu, float* __restrict__ grho) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
     if (i >= g.nx || j >= g.ny) return;
-    const long long o = cidx(g, i, j, k);
-    const double lam = __ldg(M.lam + o), mu0 = __ldg(M.mu + o);
-    const double kap = 3.0 * lam + 2.0 * mu0;
-    const double a0 = A.acc64[0][o];
-    double mu = (A.acc64[1][o] - lam * a0 / kap) / mu0;
-    double rho = 0.0;
-    // shear point (a, b) of a plane uses cells a, min(a+1), b, min(b+1)
-    for (int da = -1; da <= 0; ++da)
-        for (int db = -1; db <= 0; ++db) {
-            int a = i + da, b = j + db;
-            if (a >= 0 && b >= 0) {           // xy: (a, b, k)
-                const int ap = min(a + 1, g.nx - 1), bp = min(b + 1, g.ny - 1);
-                const int mult = (a == i && b == j) + (ap == i && b == j) + (a == i && bp == j) + (ap == i && bp == j);
-                if (mult) {
-                    const double mb = 0.25 * ((double)med(M.mu, g, a, b, k) + med(M.mu, g, ap, b, k) +
-                                              med(M.mu, g, a, bp, k) + med(M.mu, g, ap, bp, k));
-                    mu += 0.25 * mult * A.acc64[2][cidx(g, a, b, k)] / mb;
-                }
-            }
-            a = i + da; b = k + db;
-            if (a >= 0 && b >= 0) {           // xz: (a, j, b)
-                const int ap = min(a + 1, g.nx - 1), bp = min(b + 1, g.nz - 1);
-                const int mult = (a == i && b == k) + (ap == i && b == k) + (a == i && bp == k) + (ap == i && bp == k);
-                if (mult) {
-                    const double mb = 0.25 * ((double)med(M.mu, g, a, j, b) + med(M.mu, g, ap, j, b) +
-                                              med(M.mu, g, a, j, bp) + med(M.mu, g, ap, j, bp));
-                    mu += 0.25 * mult * A.acc64[3][cidx(g, a, j, b)] / mb;
-                }
-            }
-            a = j + da; b = k + db;
-            if (a >= 0 && b >= 0) {           // yz: (i, a, b)
-                const int ap = min(a + 1, g.ny - 1), bp = min(b + 1, g.nz - 1);
-                const int mult = (a == j && b == k) + (ap == j && b == k) + (a == j && bp == k) + (ap == j && bp == k);
-                if (mult) {
-                    const double mb = 0.25 * ((double)med(M.mu, g, i, a, b) + med(M.mu, g, i, ap, b) +
-                                              med(M.mu, g, i, a, bp) + med(M.mu, g, i, ap, bp));
-                    mu += 0.25 * mult * A.acc64[4][cidx(g, i, a, b)] / mb;
-                }
-            }
-        }
-    // v point (a) along axis c uses cells a and min(a+1): d rho_mean / d rho = 1/2 each
-    for (int c = 0; c < 3; ++c)
-        for (int d = -1; d <= 0; ++d) {
-            const int ii = i + (c == 0 ? d : 0), jj = j + (c == 1 ? d : 0), kk = k + (c == 2 ? d : 0);
-            if (ii < 0 || jj < 0 || kk < 0) continue;
-            const int a = c == 0 ? ii : (c == 1 ? jj : kk);
-            const int n = c == 0 ? g.nx : (c == 1 ? g.ny : g.nz);
-            const int self = c == 0 ? i : (c == 1 ? j : k);
-            const int mult = (a == self) + (min(a + 1, n - 1) == self);
-            if (mult) rho += -0.5 * mult * A.acc64[5 + c][cidx(g, ii, jj, kk)];
-        }
-    const long long od = ((long long)k * g.ny + j) * g.nx + i;
-    glam[od] = (float)(a0 / kap);
-    gmu[od] = (float)mu;
-    grho[od] = (float)rho;
+    ops::finalize_t_cell(g, A, M, glam, gmu, grho, i, j, k);
 }
 
 // L2 misfit: sadj = dt (s - d), misfit += dt / 2 (s - d)^2.
@@ -441,19 +368,13 @@ cudaError_t launch_adj_inject(const DevGrid& g, const AdjFields& A, const DevMed
                               int ld, int n, cudaStream_t st) {
     if (nrec <= 0) return cudaSuccess;
     const dim3 grid((3 * nrec + 127) / 128);
-    if (B.kind == BND_SPONGE)
-        k_adj_inject<BND_SPONGE><<<grid, 128, 0, st>>>(g, A, M, B, taps, nrec, sadj, ld, n);
-    else
-        k_adj_inject<BND_NONE><<<grid, 128, 0, st>>>(g, A, M, B, taps, nrec, sadj, ld, n);
+    k_adj_inject<<<grid, 128, 0, st>>>(g, A, M, B, taps, nrec, sadj, ld, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rho_term(const DevGrid& g, const AdjFields& A, const DevBoundary& B,
                             const float* vn, const float* vp, long long fstride, cudaStream_t st) {
-    if (B.kind == BND_SPONGE)
-        k_rho_term<BND_SPONGE><<<plane_grid(g), dim3(32, 8), 0, st>>>(g, A, B, vn, vp, fstride);
-    else
-        k_rho_term<BND_NONE><<<plane_grid(g), dim3(32, 8), 0, st>>>(g, A, B, vn, vp, fstride);
+    k_rho_term<<<plane_grid(g), dim3(32, 8), 0, st>>>(g, A, B, vn, vp, fstride);
     return cudaGetLastError();
 }
 

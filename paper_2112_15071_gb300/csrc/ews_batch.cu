@@ -1,0 +1,404 @@
+// ews_batch.cu -- host side of the batched executor (ews_batch in
+// include/ews.h): per-shot programs of stages, their merge into one entry
+// list, the z-chunk autotuner, and the one-by-one reference mode.  The
+// executor kernel itself is k_batch in ews_stencil.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "ews_sim.cuh"
+
+namespace ews {
+namespace {
+
+#define BCK(call)                                                                      \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return report(e_ == cudaErrorMemoryAllocation ? EWS_ENOMEM : EWS_ECUDA,    \
+                          "%s: %s", #call, cudaGetErrorString(e_));                    \
+    } while (0)
+
+struct Stage {
+    int kind, n, slot, flag, nitems;
+};
+
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+// One forward time step n: velocity pass (capturing v^{n+1/2} into history
+// slot `slot` when >= 0), force injection and receivers, stress pass,
+// moment injection.  Single-item stages that would do nothing are left out.
+void push_step(std::vector<Stage>& P, const BatchShot& B, int n, int slot, bool record) {
+    P.push_back({slot >= 0 ? BK_VEL_CAP : BK_VEL, n, slot, 0, B.items_pass});
+    if (B.S.kind == EWS_SOURCE_FORCE || (record && B.seis && B.nrec > 0))
+        P.push_back({BK_POSTV, n, slot, record ? 1 : 0, 1});
+    P.push_back({BK_STR, n, 0, 0, B.items_pass});
+    if (B.S.kind == EWS_SOURCE_MOMENT) P.push_back({BK_POSTS, n, 0, 0, 1});
+}
+
+// The stages of ews_run on one shot.
+void forward_program(std::vector<Stage>& P, const BatchShot& B, int nt) {
+    P.push_back({BK_ZERO_F, 0, 0, 0, B.items_elem});
+    for (int n = 0; n < nt; ++n) push_step(P, B, n, -1, true);
+}
+
+// The stages of ews_gradient on one shot (transformed reverse sweep):
+// forward with checkpoints (the resident range [c_res K, nt) writes its
+// history), residual, then per segment in reverse: restore and recompute
+// (not for the resident range), reverse steps, buoyancy term and flushes;
+// finally the gradients.
+void gradient_program(std::vector<Stage>& P, const BatchShot& B, int nt, int K, int c_res) {
+    const int nck = (nt + K - 1) / K;
+    const int n_res = c_res * K;
+    P.push_back({BK_ZERO_F, 0, 0, 0, B.items_elem});
+    for (int c = 0; c < nck; ++c) {
+        const int n0 = c * K, n1 = std::min(n0 + K, nt);
+        if (c < c_res) P.push_back({BK_SAVE, 0, c, 0, B.items_elem});
+        if (c == c_res) P.push_back({BK_HIST0, 0, 0, 0, B.items_elem});
+        for (int n = n0; n < n1; ++n) push_step(P, B, n, c >= c_res ? n - n_res + 1 : -1, true);
+    }
+    P.push_back({BK_RESID, 0, 0, 0, 1});
+    P.push_back({BK_ZERO_A, 0, 0, 0, B.items_elem});
+    for (int c = c_res; c >= 0; --c) {
+        const int n0 = c * K, n1 = c == c_res ? nt : n0 + K;
+        if (c < c_res) {
+            P.push_back({BK_LOAD, 0, c, 0, B.items_elem});
+            P.push_back({BK_HIST0, 0, 0, 0, B.items_elem});
+            for (int n = n0; n < n1; ++n) push_step(P, B, n, n - n0 + 1, false);
+        }
+        for (int m = n1 - 1; m >= n0; --m) {
+            P.push_back({BK_VEL_GRAD, m + 1 < n1 ? 1 : 0, m - n0 + 1, 0, B.items_pass});
+            if (B.nrec > 0) P.push_back({BK_ADJINJ, m, 0, 0, 1});
+            P.push_back({BK_STR_ADJ, m, 0, 0, B.items_pass});
+            if ((m - n0) % K == 0 && m > n0) P.push_back({BK_FLUSH, 0, 0, 0, B.items_elem});
+        }
+        P.push_back({BK_RHO, 0, 0, 0, B.items_elem});
+        P.push_back({BK_FLUSH, 0, 0, 0, B.items_elem});
+    }
+    P.push_back({BK_FINAL, 0, 0, 0, B.items_elem});
+}
+
+// First resident segment of the history budget (as in the adjoint of
+// ews_capi.cu): the trailing segments whose history fits, at least one.
+int resident_from(const ews_sim* s, int nt, int K) {
+    const int nck = (nt + K - 1) / K;
+    const long long slots = (long long)(s->hist_budget / (3.0 * s->fstride * sizeof(float)));
+    int c_res = nck - 1;
+    while (c_res > 0 && (long long)(nt - (c_res - 1) * K) + 1 <= slots) --c_res;
+    return c_res;
+}
+
+// Everything the executor needs about one shot.
+ews_status fill_shot(BatchShot& B, ews_sim* s, const ews_batch_shot& in, int zchunk, int* err,
+                     bool grad) {
+    std::memset(&B, 0, sizeof(B));
+    const size_t fs = s->fstride;
+    int ntx, nty, zc, items;
+    stencil_plan_export(s->plan, &B.vf, &B.sf, &ntx, &nty, &zc, &items);
+    const int nz = s->g.nz;
+    zc = std::min(std::max(zchunk, 1), nz);
+    B.items_pass = ntx * nty * (int)ceil_div(nz, zc);
+    B.items_elem = (int)ceil_div((long long)fs, kBatchElem);
+    PassParams& P = B.pf;
+    P.g = s->g;
+    P.F = s->F();
+    P.B = s->B;
+    for (int q = 0; q < NFIELD; ++q) {
+        P.dto[q] = (float)in.dt;
+        P.inv[q] = 1.0f;
+    }
+    P.ntx = ntx;
+    P.nty = nty;
+    P.zchunk = zc;
+    P.err = err;
+    B.M = s->M();
+    B.S = sim_source(s, in.dt);
+    B.wavelet = s->wavelet;
+    B.rtaps = s->rtaps;
+    B.nrec = s->nrec;
+    B.nt = in.nt;
+    B.seis = in.seis;
+    B.fs = (long long)fs;
+    B.dt = (float)in.dt;
+    if (!grad) return EWS_OK;
+    int a, b, c, d;
+    stencil_plan_export(s->adj_plan, &B.va, &B.sa, &a, &b, &c, &d);
+    PassParams& Q = B.pa;
+    Q = P;
+    for (int q = 0; q < NFIELD; ++q) {
+        Q.F.f[q] = s->adj + q * fs;
+        Q.dto[q] = -(float)in.dt;
+    }
+    for (int q = 0; q < 3; ++q) B.A.p[q] = s->adj + q * fs;
+    for (int q = 0; q < 6; ++q) B.A.q[q] = s->adj + (3 + q) * fs;
+    for (int q = 0; q < 8; ++q) {
+        B.A.acc[q] = s->adj + (9 + q) * fs;
+        B.A.acc64[q] = s->acc64 + q * fs;
+        Q.X.acc[q] = B.A.acc[q];
+    }
+    Q.X.fstride = (long long)fs;
+    Q.X.gdt = (float)in.dt;
+    B.vhist = s->vhist;
+    B.ckpt = s->ckpt;
+    B.obs = in.observed;
+    const size_t nseis = (size_t)3 * s->nrec * in.nt;
+    if (!B.seis) B.seis = s->aux;                 // forward seismograms for the residual
+    B.sadj = s->aux + nseis;
+    B.misfit = s->dmisfit;
+    B.gl = in.g_lam;
+    B.gm = in.g_mu;
+    B.gr = in.g_rho;
+    return EWS_OK;
+}
+
+struct Entry {
+    double key;
+    BatchEntry e;
+};
+
+// Run the programs of `shots` in one persistent launch.
+ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector<Stage>>& progs,
+                          int bnd, bool grad, int ctas_per_sm, int* d_err, cudaStream_t st,
+                          float* ms_out, unsigned long long wait_ns = 0, bool stall = false) {
+    const int ns = (int)shots.size();
+    std::vector<Entry> all;
+    size_t total = 0;
+    for (const auto& p : progs) total += p.size();
+    all.reserve(total);
+    for (int s = 0; s < ns; ++s) {
+        long long need = 0;
+        const double R = (double)progs[s].size();
+        for (size_t r = 0; r < progs[s].size(); ++r) {
+            const Stage& g = progs[s][r];
+            BatchEntry e{};
+            e.shot = s;
+            e.kind = g.kind;
+            e.n = g.n;
+            e.slot = g.slot;
+            e.flag = g.flag;
+            e.need = need;
+            e.nitems = g.nitems;
+            all.push_back({(r + 0.5) / R, e});
+            need += g.nitems;
+        }
+    }
+    // every shot advances through its program at the same relative pace
+    std::stable_sort(all.begin(), all.end(), [](const Entry& a, const Entry& b) {
+        return a.key < b.key || (a.key == b.key && a.e.shot < b.e.shot);
+    });
+    std::vector<BatchEntry> ent(all.size());
+    for (size_t i = 0; i < all.size(); ++i) ent[i] = all[i].e;
+    if (stall && !ent.empty()) ent.back().need += 1;   // waits for an item that never exists
+    const int nent = (int)ent.size();
+
+    int dev = 0, sms = 0, per_sm = 0;
+    BCK(cudaGetDevice(&dev));
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BCK(batch_occupancy(bnd, grad, &per_sm));
+    if (per_sm < 1) return report(EWS_ECUDA, "batched executor does not fit on an SM");
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+
+    BatchShot* d_shots = nullptr;
+    BatchEntry* d_ent = nullptr;
+    unsigned* d_cnt = nullptr;       // cur, taken[nent]
+    unsigned long long* d_done = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_shots);
+        cudaFree(d_ent);
+        cudaFree(d_cnt);
+        cudaFree(d_done);
+    };
+    cudaError_t e = cudaMalloc(&d_shots, sizeof(BatchShot) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ent, sizeof(BatchEntry) * nent);
+    if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(unsigned) * (nent + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_done, sizeof(unsigned long long) * ns);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_shots, shots.data(), sizeof(BatchShot) * ns, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(BatchEntry) * nent, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * (nent + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_done, 0, sizeof(unsigned long long) * ns, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess && ms_out) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess && ms_out) e = cudaEventCreate(&t1);
+    if (e == cudaSuccess && ms_out) e = cudaEventRecord(t0, st);
+    if (e == cudaSuccess)
+        e = launch_batch(bnd, grad, sms * per_sm, d_shots, d_ent, nent, d_cnt, d_cnt + 1, d_done,
+                         d_err, wait_ns ? wait_ns : 4000000000ull, st);
+    if (e == cudaSuccess && ms_out) e = cudaEventRecord(t1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && ms_out) e = cudaEventElapsedTime(ms_out, t0, t1);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess)
+        return report(e == cudaErrorMemoryAllocation ? EWS_ENOMEM : EWS_ECUDA, "batched launch: %s",
+                      cudaGetErrorString(e));
+    if (herr)
+        return report(EWS_ETIMEOUT, "batched executor: a %s wait gave up (flags %d)",
+                      (herr & 8) ? "dependency" : "pipeline", herr);
+    return EWS_OK;
+}
+
+// ---- autotuner: planes per tile in z, per grid size ----
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
+
+ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, bool grad, int ctas,
+                       int* d_err, cudaStream_t st, int* out) {
+    const auto key = std::make_tuple(s->g.nx, s->g.ny, s->g.nz, bnd, grad ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *out = it->second;
+            return EWS_OK;
+        }
+    }
+    const int nz = s->g.nz;
+    std::vector<int> cand;
+    for (int z : {8, 12, 16, 24, 32, 48, 64, 96, 128})
+        if (z <= nz) cand.push_back(z);
+    if (cand.empty() || cand.back() != nz) cand.push_back(nz);
+    const int T = std::min(in.nt, 6);                 // trial: a few forward steps
+    int best = cand.front();
+    float best_ms = 1e30f;
+    for (int z : cand) {
+        std::vector<BatchShot> shots(1);
+        ews_batch_shot probe = in;
+        probe.seis = nullptr;
+        probe.nt = T;
+        ews_status r = fill_shot(shots[0], s, probe, z, d_err, false);
+        if (r != EWS_OK) return r;
+        std::vector<std::vector<Stage>> progs(1);
+        for (int n = 0; n < T; ++n) push_step(progs[0], shots[0], n, -1, false);
+        float ms = 0, ms2 = 0;
+        if ((r = run_persistent(shots, progs, bnd, grad, ctas, d_err, st, &ms)) != EWS_OK) return r;
+        if ((r = run_persistent(shots, progs, bnd, grad, ctas, d_err, st, &ms2)) != EWS_OK) return r;
+        ms = std::min(ms, ms2);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = z;
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    *out = best;
+    return EWS_OK;
+}
+
+}  // namespace
+}  // namespace ews
+
+extern "C" {
+
+int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int gradient) {
+    if (!grid) return 0;
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    auto it = ews::g_tuned.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary,
+                                                gradient ? 1 : 0));
+    return it == ews::g_tuned.end() ? 0 : it->second;
+}
+
+ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
+                     void* cuda_stream) {
+    using namespace ews;
+    if (nshots <= 0 || !shots) return report(EWS_EINVAL, "no shots");
+    ews_batch_options o{};
+    if (opt) o = *opt;
+    if (o.mode != EWS_BATCH_PERSISTENT && o.mode != EWS_BATCH_SEQUENTIAL)
+        return report(EWS_EINVAL, "unknown batch mode %d", o.mode);
+    if (o.ckpt_every < 0 || o.zchunk < 0 || o.ctas_per_sm < 0 || o.dep_wait_ms < 0)
+        return report(EWS_EINVAL, "negative batch option");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int bnd = shots[0].sim ? shots[0].sim->opt.boundary : -1;
+    bool grad = false;
+    for (int i = 0; i < nshots; ++i) {
+        const ews_batch_shot& b = shots[i];
+        ews_sim* s = b.sim;
+        if (!s) return report(EWS_EINVAL, "shot %d: null simulation", i);
+        for (int j = 0; j < i; ++j)
+            if (shots[j].sim == s) return report(EWS_EINVAL, "shot %d: simulation used twice", i);
+        if (s->opt.boundary != bnd) return report(EWS_EINVAL, "shot %d: boundary differs", i);
+        if (bnd == EWS_BOUNDARY_CPML) return report(EWS_EINVAL, "batched shots take NONE or SPONGE");
+        if (s->opt.storage != EWS_STORAGE_F32) return report(EWS_EINVAL, "shot %d: F32 storage only", i);
+        if (b.nt <= 0) return report(EWS_EINVAL, "shot %d: nt must be positive", i);
+        if (b.observed) {
+            grad = true;
+            if (!b.g_lam || !b.g_mu || !b.g_rho)
+                return report(EWS_EINVAL, "shot %d: gradient outputs missing", i);
+        }
+        ews_status r = sim_ready(s, b.nt, b.dt);
+        if (r != EWS_OK) return r;
+        if (b.observed && s->has_fluid)
+            return report(EWS_EINVAL, "shot %d: fluid cells (mu = 0) are not batched", i);
+    }
+    const int K0 = o.ckpt_every > 0 ? o.ckpt_every : 50;
+
+    if (o.mode == EWS_BATCH_SEQUENTIAL) {      // one shot after the other
+        for (int i = 0; i < nshots; ++i) {
+            ews_batch_shot& b = shots[i];
+            ews_sim* s = b.sim;
+            ews_status r = ews_set_stream(s, st);
+            if (r != EWS_OK) return r;
+            if (b.observed) {
+                r = ews_gradient(s, b.nt, b.dt, b.observed, 1, &b.misfit, b.g_lam, b.g_mu,
+                                 b.g_rho, 1, K0);
+                if (r == EWS_OK && b.seis && s->nrec > 0)
+                    BCK(cudaMemcpyAsync(b.seis, s->aux, (size_t)3 * s->nrec * b.nt * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, st));
+            } else {
+                r = ews_run(s, b.nt, b.dt, b.seis, 1, nullptr);
+            }
+            if (r != EWS_OK) return r;
+        }
+        BCK(cudaStreamSynchronize(st));
+        return EWS_OK;
+    }
+
+    int* d_err = shots[0].sim->err;            // any of the shots' error flags
+    std::vector<BatchShot> bs(nshots);
+    std::vector<std::vector<Stage>> progs(nshots);
+    for (int i = 0; i < nshots; ++i) {
+        ews_batch_shot& b = shots[i];
+        ews_sim* s = b.sim;
+        const int K = std::min(K0, b.nt);
+        int c_res = 0;
+        if (b.observed) {
+            c_res = resident_from(s, b.nt, K);
+            const int hslots = std::max(K, b.nt - c_res * K) + 1;
+            ews_status r = sim_adjoint_buffers(s, b.nt, K, hslots, true);
+            if (r == EWS_OK) r = sim_adjoint_plan(s);
+            if (r != EWS_OK) return r;
+        }
+        int zc = o.zchunk;
+        if (zc == 0) {
+            ews_status r = tune_zchunk(s, b, bnd, grad, o.ctas_per_sm, d_err, st, &zc);
+            if (r != EWS_OK) return r;
+        }
+        ews_status r = fill_shot(bs[i], s, b, zc, d_err, b.observed != nullptr);
+        if (r != EWS_OK) return r;
+        if (b.observed) gradient_program(progs[i], bs[i], b.nt, K, c_res);
+        else forward_program(progs[i], bs[i], b.nt);
+    }
+    ews_status r = run_persistent(bs, progs, bnd, grad, o.ctas_per_sm, d_err, st, nullptr,
+                                  (unsigned long long)o.dep_wait_ms * 1000000ull,
+                                  o.test_unsatisfiable != 0);
+    if (r != EWS_OK) return r;
+    for (int i = 0; i < nshots; ++i) {
+        ews_sim* s = shots[i].sim;
+        s->fresh = false;
+        if (shots[i].observed)
+            BCK(cudaMemcpy(&shots[i].misfit, s->dmisfit, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return EWS_OK;
+}
+
+}  // extern "C"

@@ -13,6 +13,7 @@
 
 #include "../../include/ews.h"
 #include "ews_internal.cuh"
+#include "ews_sim.cuh"
 
 using namespace ews;
 
@@ -43,13 +44,6 @@ constexpr double kC2 = -1.0 / 24.0;
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Host-side description of the point source (taps are rebuilt per dt).
-struct SourceSpec {
-    int kind = -1;
-    double pos[3] = {0, 0, 0};
-    double comp[6] = {0, 0, 0, 0, 0, 0};
-};
-
 }  // namespace
 
 namespace ews {
@@ -62,101 +56,6 @@ ews_status report(ews_status s, const char* fmt, ...) {
     return s;
 }
 }  // namespace ews
-
-// One captured time loop: a CUDA graph of steps n0 .. n0 + nsteps - 1 with
-// everything its kernel parameters depend on as the key.
-struct GraphEntry {
-    unsigned long long gen;
-    int n0, nsteps, ld;
-    double dt;
-    const float* dseis;
-    const float* vcap;
-    cudaGraphExec_t exec;
-    long long launches[EWS_NKERNEL];
-};
-
-struct ews_sim {
-    ews_grid grid{};
-    ews_options opt{};
-    DevGrid g{};
-    size_t fstride = 0;           // elements between fields (and medium arrays)
-    int es = 4;                   // bytes per stored wavefield element
-    float* fields = nullptr;      // 9 * fstride elements of the storage type
-    float* medium = nullptr;      // 3 * fstride floats: lambda, mu, rho
-    bool model_set = false;
-    float vpmax = 0.0f;
-    float rho_min = 0.0f, zs_min = 0.0f, zp_max = 0.0f;   // medium bounds
-    bool has_fluid = false;       // some cell has mu == 0
-    // per-field storage scales (16-bit storage holds scale[q] x value)
-    float scale[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
-    bool scale_user = false;      // set by ews_set_field_scales
-    bool fresh = true;            // wavefields are all zero
-    float* stage = nullptr;       // dense float32 staging for 16-bit state I/O
-    size_t stage_cap = 0;
-    // boundary
-    float* prof = nullptr;        // g[3][n], pa[3][n], pb[3][n] packed
-    float* psi = nullptr;         // C-PML memory variables
-    size_t psi_floats = 0;
-    DevBoundary B{};
-    double pml_dt = -1.0;
-    // source
-    SourceSpec src;
-    double wsum = 0;              // sum of |wavelet|
-    DevSource S{};
-    float* wavelet = nullptr;
-    int wavelet_nt = 0;
-    // receivers
-    int nrec = 0;
-    Tap* rtaps = nullptr;         // [3 * nrec][8]
-    float* seis_buf = nullptr;    // internal [3][nrec][cap] when caller is on host
-    size_t seis_cap = 0;
-    unsigned* flags = nullptr;    // device scratch for medium checks
-    int* err = nullptr;           // device flag: bounded waits that gave up
-    StencilPlan* plan = nullptr;
-    cudaStream_t stream = nullptr;
-    // launch accounting and optional per-launch event timing
-    long long launches[EWS_NKERNEL] = {};
-    double kernel_ms[EWS_NKERNEL] = {};
-    bool profiling = false;
-    std::vector<cudaEvent_t> ev_pool;     // reused across calls
-    std::vector<int> ev_class;            // class of the launch ending at event m
-    size_t ev_used = 0;
-    // adjoint buffers (allocated on first use)
-    float* adj = nullptr;                 // P (3), Q (6), FP32 accumulators (8)
-    double* acc64 = nullptr;              // FP64 accumulators (8)
-    float* ckpt = nullptr;                // checkpoints, nck x 9 fields
-    size_t ckpt_cap = 0;                  // fields' worth of floats
-    float* vhist = nullptr;               // velocity history, (K + 1) x 3 fields
-    size_t vhist_cap = 0;
-    float* aux = nullptr;                 // seismogram-sized adjoint source + observed
-    size_t aux_cap = 0;
-    float* gout = nullptr;                // gradient staging for host outputs
-    double* dmisfit = nullptr;
-    double hist_budget = 0;               // bytes of resident velocity history
-    // captured time loops (used when per-launch profiling is off)
-    std::vector<GraphEntry> graphs;
-    unsigned long long gen = 1;           // bumped when a kernel parameter source changes
-    cudaStream_t cap_stream = nullptr;    // private stream the loops are captured on
-    StencilPlan* adj_plan = nullptr;      // stencil plan of the adjoint fields
-    const float* adj_hist = nullptr;      // history buffer the plan's map points at
-    int adj_hist_slots = 0;
-
-    void* field(int q) const { return (char*)fields + (size_t)q * fstride * es; }
-    DevFields F() const {
-        DevFields f;
-        for (int q = 0; q < NFIELD; ++q) f.f[q] = (float*)field(q);
-        return f;
-    }
-    bool wide() const { return opt.storage == EWS_STORAGE_F32; }
-    DevMedium M() const {
-        DevMedium m;
-        m.lam = medium;
-        m.mu = medium + fstride;
-        m.rho = medium + 2 * fstride;
-        return m;
-    }
-    long long ncell() const { return (long long)grid.nx * grid.ny * grid.nz; }
-};
 
 namespace {
 
@@ -415,11 +314,9 @@ void auto_scales(ews_sim* s, double dt) {
     }
 }
 
-ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
-                        float* dseis, int ld, float* vcap) {
-    DevFields F = s->F();
-    DevMedium M = s->M();
-    // fold dt and the cell volume into the source taps
+// Source taps for this dt: dt, the cell volume and the field scale folded
+// into the trilinear weights (Sec. 2.4 reading).
+DevSource source_taps(const ews_sim* s, const SourceSpec& src, double dt) {
     DevSource S{};
     S.kind = -1;
     if (src.kind >= 0 && s->wavelet) {
@@ -442,6 +339,14 @@ ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, d
             }
         }
     }
+    return S;
+}
+
+ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
+                        float* dseis, int ld, float* vcap) {
+    DevFields F = s->F();
+    DevMedium M = s->M();
+    const DevSource S = source_taps(s, src, dt);
     // dt x scale of each output field, 1 / scale of each input field
     float dto[NFIELD], inv[NFIELD];
     for (int q = 0; q < NFIELD; ++q) {
@@ -593,21 +498,9 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         while (c_res > 0 && (long long)(nt - (c_res - 1) * K) + 1 <= budget_slots) --c_res;
     const int n_res = c_res * K;
     const int hslots = std::max(K, nt - n_res) + 1;
-    if (!s->adj) {
-        cudaError_t e = cudaMalloc(&s->adj, 17 * fs * sizeof(float));
-        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint state: %s", cudaGetErrorString(e));
-        e = cudaMalloc(&s->acc64, 8 * fs * sizeof(double));
-        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint accumulators: %s", cudaGetErrorString(e));
-        e = cudaMalloc(&s->dmisfit, sizeof(double));
-        if (e != cudaSuccess) return fail(EWS_ENOMEM, "misfit: %s", cudaGetErrorString(e));
-    }
-    if ((st = ensure_buf(&s->ckpt, &s->ckpt_cap, (size_t)nck * 9 * fs, "checkpoints")) != EWS_OK) return st;
-    if ((st = ensure_buf(&s->vhist, &s->vhist_cap, (size_t)(transformed ? hslots : K + 1) * 3 * fs,
-                         "velocity history")) != EWS_OK)
+    if ((st = sim_adjoint_buffers(s, nt, K, transformed ? hslots : K + 1, obs_dev != nullptr)) != EWS_OK)
         return st;
     const size_t nseis = (size_t)3 * s->nrec * nt;
-    if (obs_dev && (st = ensure_buf(&s->aux, &s->aux_cap, 2 * (nseis ? nseis : 1), "adjoint source")) != EWS_OK)
-        return st;
     AdjFields A;
     for (int c = 0; c < 3; ++c) A.p[c] = s->adj + c * fs;
     for (int c = 0; c < 6; ++c) A.q[c] = s->adj + (3 + c) * fs;
@@ -647,16 +540,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         // adjoint fields, gradient products fused into the velocity pass.
         DevFields AF;
         for (int q = 0; q < NFIELD; ++q) AF.f[q] = s->adj + q * fs;
-        if (!s->adj_plan) {
-            cudaError_t e = stencil_plan_create(s->g, AF, s->M(), s->B, EWS_STORAGE_F32, &s->adj_plan);
-            if (e != cudaSuccess) return fail(EWS_ECUDA, "adjoint stencil plan: %s", cudaGetErrorString(e));
-        }
-        const int cap_slots = (int)(s->vhist_cap / (3 * fs));
-        if (s->adj_hist != s->vhist || s->adj_hist_slots != cap_slots) {
-            CK(stencil_plan_set_history(s->adj_plan, s->g, s->vhist, (long long)fs, cap_slots));
-            s->adj_hist = s->vhist;
-            s->adj_hist_slots = cap_slots;
-        }
+        if ((st = sim_adjoint_plan(s)) != EWS_OK) return st;
         float mdt[NFIELD], one[NFIELD];
         for (int q = 0; q < NFIELD; ++q) {
             mdt[q] = -fdt;
@@ -746,6 +630,52 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+
+namespace ews {
+
+ews_status sim_ready(ews_sim* s, int n_end, double dt) { return ensure_ready(s, n_end, dt); }
+
+DevSource sim_source(const ews_sim* s, double dt) { return source_taps(s, s->src, dt); }
+
+ews_status sim_adjoint_buffers(ews_sim* s, int nt, int K, int hslots, bool with_obs) {
+    const size_t fs = s->fstride;
+    const int nck = (nt + K - 1) / K;
+    if (!s->adj) {
+        cudaError_t e = cudaMalloc(&s->adj, 17 * fs * sizeof(float));
+        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint state: %s", cudaGetErrorString(e));
+        e = cudaMalloc(&s->acc64, 8 * fs * sizeof(double));
+        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint accumulators: %s", cudaGetErrorString(e));
+        e = cudaMalloc(&s->dmisfit, sizeof(double));
+        if (e != cudaSuccess) return fail(EWS_ENOMEM, "misfit: %s", cudaGetErrorString(e));
+    }
+    ews_status st;
+    if ((st = ensure_buf(&s->ckpt, &s->ckpt_cap, (size_t)nck * 9 * fs, "checkpoints")) != EWS_OK) return st;
+    if ((st = ensure_buf(&s->vhist, &s->vhist_cap, (size_t)hslots * 3 * fs, "velocity history")) != EWS_OK)
+        return st;
+    const size_t nseis = (size_t)3 * s->nrec * nt;
+    if (with_obs && (st = ensure_buf(&s->aux, &s->aux_cap, 2 * (nseis ? nseis : 1), "adjoint source")) != EWS_OK)
+        return st;
+    return EWS_OK;
+}
+
+ews_status sim_adjoint_plan(ews_sim* s) {
+    const size_t fs = s->fstride;
+    DevFields AF;
+    for (int q = 0; q < NFIELD; ++q) AF.f[q] = s->adj + q * fs;
+    if (!s->adj_plan) {
+        cudaError_t e = stencil_plan_create(s->g, AF, s->M(), s->B, EWS_STORAGE_F32, &s->adj_plan);
+        if (e != cudaSuccess) return fail(EWS_ECUDA, "adjoint stencil plan: %s", cudaGetErrorString(e));
+    }
+    const int cap_slots = (int)(s->vhist_cap / (3 * fs));
+    if (s->adj_hist != s->vhist || s->adj_hist_slots != cap_slots) {
+        CK(stencil_plan_set_history(s->adj_plan, s->g, s->vhist, (long long)fs, cap_slots));
+        s->adj_hist = s->vhist;
+        s->adj_hist_slots = cap_slots;
+    }
+    return EWS_OK;
+}
+
+}  // namespace ews
 
 extern "C" {
 

@@ -9,61 +9,23 @@
 #include <type_traits>
 
 #include "ews_internal.cuh"
+#include "ews_ops.cuh"
 
 namespace ews {
 
 namespace {
 
-__device__ __forceinline__ float med(const float* __restrict__ m, const DevGrid& g,
-                                     int i, int j, int k) {
-    i = min(i, g.nx - 1);
-    j = min(j, g.ny - 1);
-    k = min(k, g.nz - 1);
-    return __ldg(m + (long long)k * g.plane + (long long)j * g.pitch + i);
-}
-
-template <typename T> struct Io;
-template <> struct Io<float> {
-    __device__ static float get(const float* p) { return *p; }
-    __device__ static float put(float x) { return x; }
-};
-template <> struct Io<__nv_bfloat16> {
-    __device__ static float get(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-    __device__ static __nv_bfloat16 put(float x) { return __float2bfloat16_rn(x); }
-};
-template <> struct Io<__half> {
-    __device__ static float get(const __half* p) { return __half2float(*p); }
-    __device__ static __half put(float x) { return __float2half_rn(x); }
-};
+using ops::Io;
+using ops::med;
 
 // Point-source injection (one thread per tap).  Runs after the pass it
-// belongs to; the sponge gain is applied to the injected amount, which
-// equals injecting before the gain.  Tap weights include the field scale.
+// belongs to.
 template <typename T>
 __global__ void k_inject(DevGrid g, DevFields F, DevMedium M, DevBoundary B, DevSource S,
                          const float* __restrict__ wavelet, int n, int* err) {
     const int t = threadIdx.x;
     if (t >= S.ntap) return;
-    const Tap tp = S.tap[t];
-    const long long c = (long long)tp.k * g.plane + (long long)tp.j * g.pitch + tp.i;
-    float amp = tp.w * __ldg(wavelet + n);
-    if (S.kind == 1) {
-        const float r0 = med(M.rho, g, tp.i, tp.j, tp.k);
-        const float r1 = med(M.rho, g, tp.i + (tp.q == VX), tp.j + (tp.q == VY),
-                             tp.k + (tp.q == VZ));
-        amp *= 2.0f / (r0 + r1);
-    }
-    if (B.kind == BND_SPONGE)
-        amp *= __ldg(B.g[0] + tp.i) * __ldg(B.g[1] + tp.j) * __ldg(B.g[2] + tp.k);
-    // several taps may hit the same element (e.g. a source on a grid point)
-    T* f = reinterpret_cast<T*>(F.f[tp.q]) + c;
-    if constexpr (sizeof(T) == 4) {
-        atomicAdd(f, amp);
-    } else {
-        const float now = Io<T>::get(f) + amp;    // estimate for the range check
-        atomicAdd(f, Io<T>::put(amp));
-        if (std::is_same<T, __half>::value && fabsf(now) > 65504.0f) atomicOr(err, 4);
-    }
+    ops::inject_tap<T>(g, F, M, B, S, wavelet, n, t, err);
 }
 
 // Receiver sampling: one thread per (component, receiver), 8 taps each.
@@ -72,14 +34,7 @@ __global__ void k_record(DevGrid g, DevFields F, const Tap* __restrict__ taps, i
                          float* __restrict__ seis, int ld, int n, float i0, float i1, float i2) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nrec) return;
-    const Tap* tp = taps + 8 * t;
-    float acc = 0.0f;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const Tap q = tp[m];
-        acc += q.w * Io<T>::get(reinterpret_cast<const T*>(F.f[q.q]) +
-                                (long long)q.k * g.plane + (long long)q.j * g.pitch + q.i);
-    }
+    float acc = ops::record_one<T>(g, F, taps, t);
     if constexpr (sizeof(T) == 2) acc *= (t < nrec ? i0 : t < 2 * nrec ? i1 : i2);
     seis[(long long)t * ld + n] = acc;
 }

@@ -17,6 +17,7 @@
 //       them in with the same TMA boxes as the fields.
 //   * seismograms [3][nrec][nt] float32; wavelet [nt] float32.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -122,6 +123,113 @@ struct VelExtra {
     float gdt;            // reverse: dt of the forward step
     int hslot;            // reverse: history slot holding v^{m+1/2}
 };
+
+struct StencilPlan;
+
+// Tensor maps of one pass (ews_stencil.cu), in the order of its shared-memory
+// slot layout: halo tiles, core tiles, C-PML terms [3 * direction + term],
+// and the velocity-history map of the reverse pass.
+static constexpr int kMapsHalo = 6, kMapsCore = 7;
+struct Maps {
+    CUtensorMap halo[kMapsHalo];
+    CUtensorMap core[kMapsCore];
+    CUtensorMap psi[9];
+    CUtensorMap hist;     // velocity history [slot * 3 + component][nz][ny][pitch] (4D)
+};
+
+// Parameters of one pass launch (or one batched work item).
+struct PassParams {
+    DevGrid g;
+    DevFields F;
+    DevBoundary B;
+    float dto[9];         // per output field: dt x its storage scale
+    float inv[9];         // per input field: 1 / its storage scale (16-bit storage)
+    int ntx, nty;
+    int zchunk;           // planes per z-chunk
+    int* err;
+    VelExtra X;           // history / gradient operands of the capture and reverse modes
+};
+
+// ---- batched executor (ews_stencil.cu kernel, ews_batch.cu programs) ----
+//
+// One persistent launch runs the programs of many independent shots.  A
+// program is a sequence of stages; a stage is a set of work items (tiles x
+// z-chunks of a pass, chunks of cells of an elementwise step, or a single
+// item).  Stages of all shots are merged into one list of entries ordered by
+// the fraction of its program a stage completes, so shots progress together.
+// CTAs claim items entry by entry (an entry's items are handed out only
+// after every item of the previous entries was), and an item of stage r of
+// shot s starts once every item of stages < r of s has finished (per-shot
+// done counter, bounded wait).  Claims follow the entry order, so every
+// awaited item was claimed earlier by a running CTA: no deadlock, whatever
+// the number of resident CTAs.
+enum BatchKind {
+    BK_VEL = 0,       // forward velocity pass
+    BK_VEL_CAP,       // forward velocity pass writing history slot `slot`
+    BK_VEL_GRAD,      // reverse velocity pass, history slot `slot`, n != 0: buoyancy term
+    BK_STR,           // forward stress pass
+    BK_STR_ADJ,       // reverse stress pass
+    BK_POSTV,         // step n: force injection (also into history slot `slot` if >= 0); receivers if flag
+    BK_POSTS,         // step n: moment injection
+    BK_ADJINJ,        // reverse step n: residual injection
+    BK_SAVE,          // fields -> checkpoint `slot`
+    BK_LOAD,          // checkpoint `slot` -> fields
+    BK_HIST0,         // v -> history slot 0
+    BK_ZERO_F,        // fields (and C-PML-free state) := 0
+    BK_ZERO_A,        // adjoint fields and accumulators := 0
+    BK_RESID,         // residual dt (s - d) and misfit
+    BK_FLUSH,         // FP64 accumulators += FP32 ones; FP32 := 0
+    BK_RHO,           // buoyancy term of a segment's first reverse step
+    BK_FINAL,         // gradients from the accumulators
+    BK_NKIND
+};
+
+struct BatchEntry {
+    int shot, kind, n, slot;
+    long long need;       // items of the shot's earlier stages
+    int nitems;
+    int flag;             // BK_POSTV: record the receivers
+};
+
+struct alignas(64) BatchShot {
+    Maps vf, sf;          // forward field maps
+    Maps va, sa;          // adjoint field maps (va.hist: velocity history)
+    PassParams pf;        // forward passes (dto = dt)
+    PassParams pa;        // reverse passes (dto = -dt; X.acc, X.fstride, X.gdt set)
+    DevMedium M;
+    DevSource S;          // tap weights hold dt and 1 / V
+    const float* wavelet;
+    const Tap* rtaps;
+    int nrec, nt;         // receivers; steps (seismogram leading dimension)
+    float* seis;          // [3][nrec][nt] or null
+    AdjFields A;
+    float* vhist;         // history slots of 3 fields
+    float* ckpt;          // checkpoints of 9 fields
+    long long fs;         // elements per field (padded)
+    const float* obs;     // observed seismograms (gradient shots)
+    float* sadj;          // residual dt (s - d)
+    double* misfit;
+    float *gl, *gm, *gr;  // dense gradients
+    int items_pass;       // tiles x z-chunks of one pass
+    int items_elem;       // cell chunks of one elementwise stage
+    float dt;
+    int pad;
+};
+static constexpr int kBatchElem = 8192;   // cells per elementwise work item
+
+// Launch the executor over `nentries` entries (device tables; the counters
+// cur/taken/done start at zero).  grid: CTAs to launch; grad: whether any
+// stage uses the reverse modes (larger slots).  err bits: 1 / 2 stencil
+// waits, 8 a dependency wait gave up.
+cudaError_t launch_batch(int bnd, bool grad, int grid, const BatchShot* shots,
+                         const BatchEntry* entries, int nentries, unsigned* cur,
+                         unsigned* taken, unsigned long long* done, int* err,
+                         unsigned long long wait_ns, cudaStream_t st);
+// CTAs per SM the executor achieves (sets its shared-memory attribute).
+cudaError_t batch_occupancy(int bnd, bool grad, int* per_sm);
+// The plan's tensor maps and pass parameters, for a BatchShot.
+void stencil_plan_export(const StencilPlan* p, Maps* vmaps, Maps* smaps, int* ntx, int* nty,
+                         int* zchunk, int* items);
 
 // The passes take, per field q, dto[q] = dt s_q (used for the fields they
 // write) and inv[q] = 1 / s_q (used for the 16-bit fields they read); with

@@ -37,6 +37,7 @@
 #include <type_traits>
 
 #include "ews_internal.cuh"
+#include "ews_ops.cuh"
 #ifndef EWS_L2PROMO
 #define EWS_L2PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_256B
 #endif
@@ -215,24 +216,7 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
 
 // Tensor maps of one pass, in slot order: halo[] then core[] as listed in
 // the slot layout above, then the C-PML terms [3 * direction + term].
-struct Maps {
-    CUtensorMap halo[MAXH];
-    CUtensorMap core[MAXC];
-    CUtensorMap psi[9];
-    CUtensorMap hist;     // velocity history [slot * 3 + component][nz][ny][pitch] (4D)
-};
-
-struct PassParams {
-    DevGrid g;
-    DevFields F;
-    DevBoundary B;
-    float dto[9];         // per output field: dt x its storage scale
-    float inv[9];         // per input field: 1 / its storage scale (16-bit storage)
-    int ntx, nty;
-    int zchunk;           // planes per z-chunk
-    int* err;
-    VelExtra X;           // history / gradient operands of the M_CAP and M_GRAD modes
-};
+static_assert(MAXH == kMapsHalo && MAXC == kMapsCore, "tensor-map counts of Maps");
 
 // Issue the TMA loads of z-plane `z` of tile (x0, y0) into `slot`.
 template <typename T, int MODE>
@@ -309,12 +293,14 @@ struct Geo {
     float pax, pbx, pay[ROWS], pby[ROWS];            // C-PML a, b of the x and y slabs
     long long obase;                                  // j0 * pitch + i
 
-    __device__ __forceinline__ Geo(const PassParams& P) {
+    // item = (z-chunk) * ntile + tile: the CTA index of a pass launch, or a
+    // work item of the batched executor
+    __device__ __forceinline__ Geo(const PassParams& P, int item) {
         const DevGrid& g = P.g;
         const int tx = threadIdx.x, ty = threadIdx.y;
         const int ntile = P.ntx * P.nty;
-        const int t = (int)(blockIdx.x % ntile);
-        z0 = (int)(blockIdx.x / ntile) * P.zchunk;
+        const int t = item % ntile;
+        z0 = (item / ntile) * P.zchunk;
         const int z1 = min(g.nz, z0 + P.zchunk);
         P4 = z1 - z0 + 4;                             // planes z0-2 .. z1+1
         x0 = (t % P.ntx) * TX;
@@ -411,7 +397,9 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 ga[rr][5 + c] = (on && P.X.vnext) ? P.X.acc[5 + c][oo] : 0.f;
-                gv[rr][c] = (on && P.X.vnext) ? __ldg(P.X.vnext + c * P.X.fstride + oo) : 0.f;
+                // plain (coherent) load: the batched executor rewrites the
+                // history within one launch
+                gv[rr][c] = (on && P.X.vnext) ? P.X.vnext[c * P.X.fstride + oo] : 0.f;
             }
         }
     }
@@ -572,14 +560,13 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     return true;
 }
 
+// One (tile, z-chunk) of the velocity pass; the ring barriers must be freshly
+// initialised.  Returns false if a wait gave up (the error is recorded).
 template <int BND, typename T, int MODE>
-__global__ void __launch_bounds__(NTH, (min_blocks<BND, T, MODE>())) k_velocity(
-    const __grid_constant__ Maps maps, const PassParams P) {
-    extern __shared__ __align__(128) unsigned char sm[];
+__device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, int item,
+                                         unsigned char* sm, uint64_t* bars) {
     constexpr int SB = slot_bytes<T, MODE>();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB + (BND == BND_CPML ? PSI_BYTES : 0));
-    ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    const Geo<BND, T> G(P);
+    const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
             issue_vel<T, MODE>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot);
@@ -594,13 +581,24 @@ __global__ void __launch_bounds__(NTH, (min_blocks<BND, T, MODE>())) k_velocity(
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!vel_step<BND, T, MODE, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return;
-        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return;
-        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return;
-        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return;
+        if (!vel_step<BND, T, MODE, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
+        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
+        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
+        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
+    return true;
+}
+
+template <int BND, typename T, int MODE>
+__global__ void __launch_bounds__(NTH, (min_blocks<BND, T, MODE>())) k_velocity(
+    const __grid_constant__ Maps maps, const PassParams P) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    constexpr int SB = slot_bytes<T, MODE>();
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB + (BND == BND_CPML ? PSI_BYTES : 0));
+    ring_init(bars, threadIdx.y * TX + threadIdx.x);
+    vel_tile<BND, T, MODE>(maps, P, (int)blockIdx.x, sm, bars);
 }
 
 // ------------------------------------------------------------------------------
@@ -740,13 +738,9 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
 }
 
 template <int BND, typename T>
-__global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_stress(const __grid_constant__ Maps maps,
-                                                                      const PassParams P) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(
-        sm + NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0));
-    ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    const Geo<BND, T> G(P);
+__device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, int item,
+                                         unsigned char* sm, uint64_t* bars) {
+    const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
             issue_str<T>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
@@ -758,13 +752,271 @@ __global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_stress(const __gr
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!str_step<BND, T, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return;
-        if (m + 1 < G.P4 && !str_step<BND, T, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return;
-        if (m + 2 < G.P4 && !str_step<BND, T, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return;
-        if (m + 3 < G.P4 && !str_step<BND, T, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return;
+        if (!str_step<BND, T, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
+        if (m + 1 < G.P4 && !str_step<BND, T, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
+        if (m + 2 < G.P4 && !str_step<BND, T, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
+        if (m + 3 < G.P4 && !str_step<BND, T, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
+    return true;
+}
+
+template <int BND, typename T>
+__global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_stress(const __grid_constant__ Maps maps,
+                                                                      const PassParams P) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+        sm + NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0));
+    ring_init(bars, threadIdx.y * TX + threadIdx.x);
+    str_tile<BND, T>(maps, P, (int)blockIdx.x, sm, bars);
+}
+
+// ------------------------------------------------------------------------------
+// Batched executor: one persistent launch over the work items of many shots
+// (see BatchShot / BatchEntry).  Each CTA claims an item, waits (bounded) for
+// the shot's earlier stages, runs it, and counts it done.
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Re-arm the ring for the next item: every copy of the previous item has
+// been waited for, so the barriers can be invalidated and initialised again.
+__device__ __forceinline__ void ring_rearm(uint64_t* bars, int tid) {
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s <= NSLOT; ++s)
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[s])) : "memory");
+        for (int s = 0; s <= NSLOT; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// The executor's tensor maps live in global memory, written by the host
+// before the launch: acquire them for the tensor-map proxy before the
+// issuing thread's first copy through them.
+__device__ __forceinline__ void acquire_maps(const Maps* m) {
+    const CUtensorMap* t = reinterpret_cast<const CUtensorMap*>(m);
+    for (int k = 0; k < (int)(sizeof(Maps) / sizeof(CUtensorMap)); ++k)
+        asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(t + k)
+                     : "memory");
+}
+
+// Stage the pass parameters of an item in shared memory.
+__device__ __forceinline__ void stage_params(PassParams* dst, const PassParams& src, int tid) {
+    static_assert(sizeof(PassParams) % 4 == 0, "PassParams is copied as words");
+    const int* a = reinterpret_cast<const int*>(&src);
+    int* b = reinterpret_cast<int*>(dst);
+    for (int w = tid; w < (int)(sizeof(PassParams) / 4); w += NTH) b[w] = a[w];
+}
+
+template <int BND, bool GRAD>
+__global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
+    k_batch(const BatchShot* __restrict__ shots, const BatchEntry* __restrict__ entries,
+            int nentries, unsigned* cur, unsigned* taken, unsigned long long* done, int* err,
+            unsigned long long wait_ns) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    constexpr int SB = GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>();
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB);
+    __shared__ PassParams sP;
+    __shared__ int s_e, s_it, s_stop;
+    __shared__ double s_red[NTH / 32];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    ring_init(bars, tid);
+    while (true) {
+        if (tid == 0) {
+            int e = -1, it = 0, stop = 0;
+            while (true) {               // claim the next item in entry order
+                if (ld_relaxed(err)) break;
+                const unsigned c = ld_relaxed_u(cur);
+                if (c >= (unsigned)nentries) break;
+                const unsigned t = atomicAdd(&taken[c], 1u);
+                if (t < (unsigned)entries[c].nitems) {
+                    e = (int)c;
+                    it = (int)t;
+                    break;
+                }
+                atomicCAS(cur, c, c + 1);
+            }
+            if (e >= 0) {                // wait for the shot's earlier stages
+                const int shot = entries[e].shot;
+                const unsigned long long need = (unsigned long long)entries[e].need;
+                const unsigned long long t0 = now_ns();
+                while (ld_acquire(&done[shot]) < need) {
+                    if (ld_relaxed(err)) { stop = 1; break; }
+                    if (now_ns() - t0 > wait_ns) { atomicOr(err, 8); stop = 1; break; }
+                    __nanosleep(100);
+                }
+            }
+            s_e = e;
+            s_it = it;
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_e < 0 || s_stop) break;
+        const int it = s_it;
+        const BatchEntry E = entries[s_e];
+        const BatchShot& B = shots[E.shot];
+        // results of the awaited items (generic stores of other CTAs) are
+        // visible to this CTA's loads and to its TMA (async proxy) reads
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const DevGrid& g = B.pf.g;
+        const long long fs = B.fs;
+        bool ok = true;
+        switch (E.kind) {
+            case BK_VEL:
+            case BK_VEL_CAP:
+            case BK_VEL_GRAD:
+            case BK_STR:
+            case BK_STR_ADJ: {
+                const bool adj = E.kind == BK_VEL_GRAD || E.kind == BK_STR_ADJ;
+                stage_params(&sP, adj ? B.pa : B.pf, tid);
+                __syncthreads();
+                if (tid == 0) {
+                    if (E.kind == BK_VEL_CAP) {
+                        sP.X.vcap = B.vhist + (long long)E.slot * 3 * fs;
+                        sP.X.fstride = fs;
+                    } else if (E.kind == BK_VEL_GRAD) {
+                        sP.X.hslot = E.slot;
+                        sP.X.vnext = E.n ? B.vhist + (long long)(E.slot + 1) * 3 * fs : nullptr;
+                    }
+                }
+                if (tid == 0)
+                    acquire_maps(E.kind == BK_VEL || E.kind == BK_VEL_CAP ? &B.vf
+                                 : E.kind == BK_STR                       ? &B.sf
+                                 : E.kind == BK_STR_ADJ                   ? &B.sa
+                                                                          : &B.va);
+                ring_rearm(bars, tid);
+                if (E.kind == BK_VEL)
+                    ok = vel_tile<BND, float, M_FWD>(B.vf, sP, it, sm, bars);
+                else if (E.kind == BK_VEL_CAP)
+                    ok = vel_tile<BND, float, M_CAP>(B.vf, sP, it, sm, bars);
+                else if (E.kind == BK_STR)
+                    ok = str_tile<BND, float>(B.sf, sP, it, sm, bars);
+                else if (E.kind == BK_STR_ADJ)
+                    ok = str_tile<BND, float>(B.sa, sP, it, sm, bars);
+                else if constexpr (GRAD)
+                    ok = vel_tile<BND, float, M_GRAD>(B.va, sP, it, sm, bars);
+                break;
+            }
+            case BK_POSTV: {
+                const DevFields& F = B.pf.F;
+                if (B.S.kind == 1 && tid < B.S.ntap) {
+                    ops::inject_tap<float>(g, F, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
+                    if (E.slot >= 0) {           // the captured v^{n+1/2} includes the force
+                        DevFields H = F;
+                        for (int c = 0; c < 3; ++c) H.f[c] = B.vhist + ((long long)E.slot * 3 + c) * fs;
+                        ops::inject_tap<float>(g, H, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
+                    }
+                }
+                __threadfence();
+                __syncthreads();
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                if (B.seis && E.flag)
+                    for (int t = tid; t < 3 * B.nrec; t += NTH)
+                        B.seis[(long long)t * B.nt + E.n] = ops::record_one<float>(g, F, B.rtaps, t);
+                break;
+            }
+            case BK_POSTS:
+                if (B.S.kind == 0 && tid < B.S.ntap)
+                    ops::inject_tap<float>(g, B.pf.F, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
+                break;
+            case BK_ADJINJ:
+                for (int t = tid; t < 3 * B.nrec; t += NTH)
+                    ops::adj_inject_one(g, B.A, B.M, B.pf.B, B.rtaps, B.sadj, B.nt, E.n, t);
+                break;
+            case BK_RESID: {
+                double acc = 0.0;
+                const long long n = 3LL * B.nrec * B.nt;
+                for (long long t = tid; t < n; t += NTH) {
+                    const float r = B.seis[t] - B.obs[t];
+                    B.sadj[t] = B.dt * r;
+                    acc += 0.5 * (double)B.dt * (double)r * (double)r;
+                }
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if ((tid & 31) == 0) s_red[tid >> 5] = acc;
+                __syncthreads();
+                if (tid == 0) {
+                    double sum = 0.0;
+                    for (int w = 0; w < NTH / 32; ++w) sum += s_red[w];
+                    *B.misfit = sum;
+                }
+                break;
+            }
+            default: {                       // elementwise stages over a cell range
+                const long long o0 = (long long)it * kBatchElem;
+                const long long o1 = o0 + kBatchElem < fs ? o0 + kBatchElem : fs;
+                const DevFields& F = B.pf.F;
+                for (long long o = o0 + tid; o < o1; o += NTH) {
+                    switch (E.kind) {
+                        case BK_SAVE:
+                            for (int q = 0; q < NFIELD; ++q)
+                                B.ckpt[((long long)E.slot * NFIELD + q) * fs + o] = F.f[q][o];
+                            break;
+                        case BK_LOAD:
+                            for (int q = 0; q < NFIELD; ++q)
+                                F.f[q][o] = B.ckpt[((long long)E.slot * NFIELD + q) * fs + o];
+                            break;
+                        case BK_HIST0:
+                            for (int q = 0; q < 3; ++q) B.vhist[q * fs + o] = F.f[q][o];
+                            break;
+                        case BK_ZERO_F:
+                            for (int q = 0; q < NFIELD; ++q) F.f[q][o] = 0.0f;
+                            break;
+                        case BK_ZERO_A:
+                            for (int q = 0; q < 3; ++q) B.A.p[q][o] = 0.0f;
+                            for (int q = 0; q < 6; ++q) B.A.q[q][o] = 0.0f;
+                            for (int q = 0; q < 8; ++q) {
+                                B.A.acc[q][o] = 0.0f;
+                                B.A.acc64[q][o] = 0.0;
+                            }
+                            break;
+                        case BK_FLUSH:
+                            ops::flush_cell(B.A, o);
+                            break;
+                        case BK_RHO:
+                        case BK_FINAL: {
+                            const int k = (int)(o / g.plane);
+                            const long long r = o - (long long)k * g.plane;
+                            const int j = (int)(r / g.pitch), i = (int)(r - (long long)j * g.pitch);
+                            if (i >= g.nx || k >= g.nz) break;
+                            if (E.kind == BK_RHO)
+                                ops::rho_term_cell(B.A, B.pf.B, B.vhist + 3 * fs, B.vhist, fs, o, i, j, k);
+                            else
+                                ops::finalize_t_cell(g, B.A, B.M, B.gl, B.gm, B.gr, i, j, k);
+                            break;
+                        }
+                        default:
+                            break;
+                    }
+                }
+                break;
+            }
+        }
+        __syncthreads();
+        if (!ok) break;                      // a pipeline wait gave up (recorded)
+        if (tid == 0) {                      // release: this item's stores, then the count
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __threadfence();
+            atomicAdd(&done[E.shot], 1ull);
+        }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
@@ -1045,6 +1297,54 @@ cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const flo
                     CU_TENSOR_MAP_SWIZZLE_NONE, EWS_L2PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     p->has_hist = r == CUDA_SUCCESS;
     return p->has_hist ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BND, bool GRAD>
+constexpr size_t batch_smem() {
+    return (size_t)NSLOT * (GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>()) +
+           8 * (NSLOT + 1);
+}
+
+template <int BND, bool GRAD>
+cudaError_t batch_prepare(int* per_sm) {
+    return prepare(k_batch<BND, GRAD>, batch_smem<BND, GRAD>(), per_sm);
+}
+
+cudaError_t batch_occupancy(int bnd, bool grad, int* per_sm) {
+    if (bnd == BND_SPONGE) return grad ? batch_prepare<BND_SPONGE, true>(per_sm) : batch_prepare<BND_SPONGE, false>(per_sm);
+    if (bnd == BND_NONE) return grad ? batch_prepare<BND_NONE, true>(per_sm) : batch_prepare<BND_NONE, false>(per_sm);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch(int bnd, bool grad, int grid, const BatchShot* shots,
+                         const BatchEntry* entries, int nentries, unsigned* cur,
+                         unsigned* taken, unsigned long long* done, int* err,
+                         unsigned long long wait_ns, cudaStream_t st) {
+    const dim3 blk(TX, RY);
+    if (bnd == BND_SPONGE) {
+        if (grad)
+            k_batch<BND_SPONGE, true><<<grid, blk, batch_smem<BND_SPONGE, true>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
+        else
+            k_batch<BND_SPONGE, false><<<grid, blk, batch_smem<BND_SPONGE, false>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
+    } else if (bnd == BND_NONE) {
+        if (grad)
+            k_batch<BND_NONE, true><<<grid, blk, batch_smem<BND_NONE, true>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
+        else
+            k_batch<BND_NONE, false><<<grid, blk, batch_smem<BND_NONE, false>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+void stencil_plan_export(const StencilPlan* p, Maps* vmaps, Maps* smaps, int* ntx, int* nty,
+                         int* zchunk, int* items) {
+    *vmaps = p->vmaps;
+    *smaps = p->smaps;
+    *ntx = p->ntx;
+    *nty = p->nty;
+    *zchunk = p->zchunk;
+    *items = p->grid;
 }
 
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,

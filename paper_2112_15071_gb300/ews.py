@@ -53,6 +53,20 @@ class ews_options(C.Structure):
                 ("sponge_alpha", C.c_double), ("pml_R", C.c_double), ("pml_f0", C.c_double)]
 
 
+class ews_batch_shot(C.Structure):
+    _fields_ = [("sim", C.c_void_p), ("nt", C.c_int), ("dt", C.c_double),
+                ("seis", C.c_void_p), ("observed", C.c_void_p), ("g_lam", C.c_void_p),
+                ("g_mu", C.c_void_p), ("g_rho", C.c_void_p), ("misfit", C.c_double)]
+
+
+class ews_batch_options(C.Structure):
+    _fields_ = [("mode", C.c_int), ("ckpt_every", C.c_int), ("zchunk", C.c_int),
+                ("ctas_per_sm", C.c_int), ("dep_wait_ms", C.c_int),
+                ("test_unsatisfiable", C.c_int)]
+
+
+EWS_BATCH_PERSISTENT, EWS_BATCH_SEQUENTIAL = 0, 1
+
 _lock = threading.Lock()
 _lib = None
 
@@ -80,6 +94,8 @@ SIGNATURES = [
     ("ews_get_profile", _I, [_P, _P, _P, _I]),
     ("ews_forward_noalloc", _I, [C.POINTER(ews_grid), C.POINTER(ews_options), _P, _P, _P, _I,
                              _P, _P, _P, _I, _P, _I, _D, _P, _P]),
+    ("ews_batch", _I, [_I, C.POINTER(ews_batch_shot), C.POINTER(ews_batch_options), _P]),
+    ("ews_batch_tuned_zchunk", _I, [C.POINTER(ews_grid), _I, _I]),
     ("ews_cfl_dt", _D, [C.POINTER(ews_grid), _D]),
     ("ews_max_freq", _D, [C.POINTER(ews_grid), _D]),
     ("ews_last_error", C.c_char_p, []),
@@ -257,6 +273,34 @@ def ews_gradient(sim, nt: int, dt: float, observed, g_lam, g_mu, g_rho, ckpt_eve
     _check(load().ews_gradient(sim, int(nt), float(dt), po, do, C.byref(mis), pl, pm, pr, d0,
                                int(ckpt_every)))
     return mis.value
+
+
+def ews_batch(shots, mode: int = EWS_BATCH_PERSISTENT, ckpt_every: int = 0, zchunk: int = 0,
+              ctas_per_sm: int = 0, dep_wait_ms: int = 0, test_unsatisfiable: bool = False,
+              stream_handle: int = 0):
+    """Run shots in one batched launch.  Each shot is a dict with keys
+    sim (Simulation), nt, dt and optional seis (CUDA tensor [3][nrec][nt]),
+    observed, g_lam, g_mu, g_rho (CUDA tensors).  Returns the misfits."""
+    arr = (ews_batch_shot * len(shots))()
+    for i, d in enumerate(shots):
+        b = arr[i]
+        b.sim = d["sim"].handle.value if hasattr(d["sim"], "handle") else d["sim"]
+        b.nt = int(d["nt"])
+        b.dt = float(d["dt"])
+        for key in ("seis", "observed", "g_lam", "g_mu", "g_rho"):
+            t = d.get(key)
+            if t is not None:
+                p, dev = _ptr(t)
+                assert dev == 1, f"{key} must be a CUDA tensor"
+                setattr(b, key, p.value)
+    opt = ews_batch_options(int(mode), int(ckpt_every), int(zchunk), int(ctas_per_sm),
+                            int(dep_wait_ms), int(bool(test_unsatisfiable)))
+    _check(load().ews_batch(len(shots), arr, C.byref(opt), C.c_void_p(stream_handle)))
+    return [arr[i].misfit for i in range(len(shots))]
+
+
+def ews_batch_tuned_zchunk(grid: ews_grid, boundary: int, gradient: bool) -> int:
+    return load().ews_batch_tuned_zchunk(C.byref(grid), int(boundary), int(bool(gradient)))
 
 
 def ews_set_profiling(sim, on: bool):

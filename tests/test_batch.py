@@ -1,0 +1,142 @@
+"""Batched shots in one persistent launch (ews_batch).
+
+The executor runs the same stencil, source, receiver and adjoint work items
+as ews_run / ews_gradient, scheduled by per-shot dependency counters; so
+each shot's seismograms and gradients must agree with the one-by-one path
+(the forward up to FP32 rounding order of separately compiled copies of the
+same arithmetic; the gradient to accumulation order), for uneven shot sizes
+and step counts, any number of resident CTAs and any z-chunk.  A dependency
+that can never be met ends in EWS_ETIMEOUT after the bounded wait, and the
+context stays usable.
+"""
+import numpy as np
+import pytest
+
+from paper_2112_15071_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ews():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_15071_gb300 import ews as E
+    E.load()
+    return E
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def shots_for(ews, probs, grad=False, obs=None):
+    import torch
+    out = []
+    for i, p in enumerate(probs):
+        sim = ews.simulation_for(p)
+        d = {"sim": sim, "nt": p.nt, "dt": p.dt,
+             "seis": torch.zeros((3, p.rec_pos.shape[0], p.nt), device="cuda")}
+        if grad:
+            d["observed"] = torch.from_numpy(obs[i]).cuda()
+            for k in ("g_lam", "g_mu", "g_rho"):
+                d[k] = torch.zeros((p.nz, p.ny, p.nx), device="cuda")
+        out.append(d)
+    return out
+
+
+def problems(kinds=("moment", "force", "moment"), nts=(70, 45, 90)):
+    dims = [(40, 36, 28), (70, 45, 37), (33, 65, 40)]
+    return [synth.small_problem(*dims[i], nt=nts[i], boundary="sponge", width=5, kind=kinds[i],
+                                nrec=6, seed=30 + i) for i in range(len(kinds))]
+
+
+@pytest.mark.parametrize("zchunk,ctas", [(0, 0), (8, 1), (13, 2)])
+def test_forward_batch_matches_run(ews, zchunk, ctas):
+    import torch
+    probs = problems()
+    shots = shots_for(ews, probs)
+    ews.ews_batch(shots, zchunk=zchunk, ctas_per_sm=ctas)
+    torch.cuda.synchronize()
+    for p, d in zip(probs, shots):
+        want = ews.simulation_for(p).run(p.nt, p.dt)
+        got = d["seis"].cpu().numpy()
+        assert rel(got, want) <= 1e-6, rel(got, want)
+        # the batched run leaves the shot's final state in its simulation
+        ref = ews.simulation_for(p)
+        ref.run(p.nt, p.dt)
+        assert rel(d["sim"].get_state(), ref.get_state()) <= 1e-6
+
+
+def test_gradient_batch_matches_one_by_one(ews, orc):
+    import torch
+    probs = problems(kinds=("moment", "force"), nts=(60, 75))
+    rng = np.random.default_rng(2)
+    obs = [(orc.run_problem(p) * (1 + 0.2 * rng.standard_normal((3, p.rec_pos.shape[0], p.nt))))
+           .astype(np.float32) for p in probs]
+    a = shots_for(ews, probs, grad=True, obs=obs)
+    b = shots_for(ews, probs, grad=True, obs=obs)
+    ma = ews.ews_batch(a, ckpt_every=20)
+    mb = ews.ews_batch(b, mode=ews.EWS_BATCH_SEQUENTIAL, ckpt_every=20)
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        assert ma[i] == pytest.approx(mb[i], rel=1e-6)
+        assert rel(a[i]["seis"].cpu().numpy(), b[i]["seis"].cpu().numpy()) <= 1e-6
+        for k in ("g_lam", "g_mu", "g_rho"):
+            assert rel(a[i][k].cpu().numpy(), b[i][k].cpu().numpy()) <= 1e-5, (i, k)
+    # and against the FP64 adjoint of the oracle for the first shot
+    p = probs[0]
+    seis = orc.run_problem(p)
+    want = orc.gradient(p, p.dt * (seis - obs[0].astype(np.float64)), ckpt_every=20)
+    for q, k in enumerate(("g_lam", "g_mu", "g_rho")):
+        assert rel(a[0][k].cpu().numpy(), want[q]) <= 1e-4
+
+
+def test_mixed_forward_and_gradient_shots(ews, orc):
+    import torch
+    probs = problems(kinds=("moment", "force"), nts=(50, 40))
+    obs = [orc.run_problem(probs[0]).astype(np.float32) * 1.1]
+    shots = shots_for(ews, probs[:1], grad=True, obs=obs) + shots_for(ews, probs[1:])
+    ews.ews_batch(shots, ckpt_every=16)
+    torch.cuda.synchronize()
+    want = ews.simulation_for(probs[1]).run(probs[1].nt, probs[1].dt)
+    assert rel(shots[1]["seis"].cpu().numpy(), want) <= 1e-6
+    sim = ews.simulation_for(probs[0])
+    mis, g = sim.gradient(probs[0].nt, probs[0].dt, obs[0], ckpt_every=16)
+    for q, k in enumerate(("g_lam", "g_mu", "g_rho")):
+        assert rel(shots[0][k].cpu().numpy(), g[q]) <= 1e-5
+
+
+def test_validation(ews):
+    p = problems()[0]
+    a = ews.simulation_for(p)
+    c = synth.small_problem(40, 36, 28, nt=20, boundary="cpml", width=5)
+    with pytest.raises(ews.EwsError) as e:
+        ews.ews_batch([{"sim": a, "nt": p.nt, "dt": p.dt}, {"sim": a, "nt": p.nt, "dt": p.dt}])
+    assert e.value.status == ews.EWS_EINVAL
+    with pytest.raises(ews.EwsError) as e:
+        ews.ews_batch([{"sim": ews.simulation_for(c), "nt": c.nt, "dt": c.dt}])
+    assert e.value.status == ews.EWS_EINVAL
+    with pytest.raises(ews.EwsError) as e:
+        ews.ews_batch([{"sim": a, "nt": p.nt, "dt": p.dt * 10}])
+    assert e.value.status == ews.EWS_ECFL
+
+
+def test_unsatisfiable_dependency_times_out(ews):
+    """The last item waits for an item that never exists: the bounded wait
+    gives up, every CTA leaves, the call returns EWS_ETIMEOUT, and the next
+    batch on the same context runs normally."""
+    import torch
+    probs = problems(nts=(10, 10, 10))
+    shots = shots_for(ews, probs)
+    with pytest.raises(ews.EwsError) as e:
+        ews.ews_batch(shots, zchunk=16, dep_wait_ms=200, test_unsatisfiable=True)
+    assert e.value.status == ews.EWS_ETIMEOUT
+    shots = shots_for(ews, probs)
+    ews.ews_batch(shots, zchunk=16)
+    torch.cuda.synchronize()
+    want = ews.simulation_for(probs[0]).run(probs[0].nt, probs[0].dt)
+    assert rel(shots[0]["seis"].cpu().numpy(), want) <= 1e-6
