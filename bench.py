@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--adj-nt", type=int, default=1500)
     ap.add_argument("--storage", choices=("f32", "bf16", "f16"), default="f32",
                     help="wavefield storage of the main workload (FP32 arithmetic)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-shot comparison")
+    ap.add_argument("--batch-shots", type=int, default=12,
+                    help="shots of the 48-shot batched workload to run (first k)")
     ap.add_argument("--no-storage", action="store_true",
                     help="skip the FP32 / BF16 / FP16 storage comparison")
     ap.add_argument("--storage-nt", type=int, default=40,
@@ -340,6 +344,8 @@ def run_ours(args, world, rank, local):
         out["adjoint"] = adjoint_ratio(args, local)
     if not args.no_storage:
         out["storage"] = storage_report(args, local, rank == 0 and world == 1)
+    if not args.no_batch:
+        out["batch"] = batch_report(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
     sim.close()
@@ -468,6 +474,69 @@ def storage_report(args, local, with_oracle: bool):
             err[st] = float(np.linalg.norm(got.astype(np.float64) - want) / np.linalg.norm(want))
             sim.close()
         out["error_vs_oracle"] = err
+    return out
+
+
+def batch_report(args, local):
+    """Batched shots (48-shot recipe: cubes 96..224, 800..1600 steps, 5..15 Hz,
+    own layered + random model each, sponge 16, explosion at nz/3, 8 x 8
+    receivers; the first --batch-shots of them): forward, and forward plus L2
+    gradient against data from a +5 % sphere variant, as one persistent
+    launch and one shot after another.  Aggregate Gcell-updates/s counts
+    cells x steps of every shot over the wall time of the whole job."""
+    import torch
+    from paper_2112_15071_gb300 import ews, synth
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    probs = synth.config5_shots(48, device=dev)[:args.batch_shots]
+    cells = sum(p.ncell * p.nt for p in probs)
+    sims = [ews.simulation_for(p) for p in probs]
+    seis = [torch.zeros((3, s.nrec, p.nt), device=dev) for s, p in zip(sims, probs)]
+    # observed data: the same shots on the anomaly variants, batched
+    obs = [torch.zeros_like(x) for x in seis]
+    vsims = []
+    for p in probs:
+        v = ews.simulation_for(p)
+        v.set_model_vel(*synth.sphere_anomaly_device(p.vp, p.vs, p.spacing))
+        vsims.append(v)
+    ews.ews_batch([{"sim": v, "nt": p.nt, "dt": p.dt, "seis": o}
+                   for v, p, o in zip(vsims, probs, obs)], stream_handle=stream.cuda_stream)
+    for v in vsims:
+        v.close()
+    grads = [torch.zeros((3, p.nz, p.ny, p.nx), device=dev) for p in probs]
+
+    def job(mode, gradient):
+        shots = []
+        for s, p, x, o, g in zip(sims, probs, seis, obs, grads):
+            d = {"sim": s, "nt": p.nt, "dt": p.dt, "seis": x}
+            if gradient:
+                d.update(observed=o, g_lam=g[0], g_mu=g[1], g_rho=g[2])
+            shots.append(d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ews.ews_batch(shots, mode=mode, ckpt_every=50, stream_handle=stream.cuda_stream)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    out = {"workload": f"first {len(probs)} of the 48-shot recipe (cubes "
+                       f"{min(p.nx for p in probs)}..{max(p.nx for p in probs)}, "
+                       f"{min(p.nt for p in probs)}..{max(p.nt for p in probs)} steps, sponge 16, "
+                       "explosion, 64 receivers; device-generated models)",
+           "cell_steps": cells}
+    for name, gradient in (("forward", False), ("forward_gradient", True)):
+        job(ews.EWS_BATCH_PERSISTENT, gradient)              # warm-up, autotune
+        tp = job(ews.EWS_BATCH_PERSISTENT, gradient)
+        job(ews.EWS_BATCH_SEQUENTIAL, gradient)
+        ts = job(ews.EWS_BATCH_SEQUENTIAL, gradient)
+        out[name] = {"persistent_s": round(tp, 3), "one_by_one_s": round(ts, 3),
+                     "persistent_gcells": round(cells / tp / 1e9, 3),
+                     "one_by_one_gcells": round(cells / ts / 1e9, 3),
+                     "speedup": round(ts / tp, 3)}
+    out["tuned_zchunk"] = {f"{p.nx}^3": ews.ews_batch_tuned_zchunk(s.grid, 1, False)
+                           for s, p in zip(sims, probs)}
+    for s in sims:
+        s.close()
+    torch.cuda.empty_cache()
     return out
 
 

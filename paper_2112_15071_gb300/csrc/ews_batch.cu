@@ -32,14 +32,11 @@ struct Stage {
 long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
 // One forward time step n: velocity pass (capturing v^{n+1/2} into history
-// slot `slot` when >= 0), force injection and receivers, stress pass,
-// moment injection.  Single-item stages that would do nothing are left out.
+// slot `slot` when >= 0) and stress pass; the source and receiver terms ride
+// on their items.
 void push_step(std::vector<Stage>& P, const BatchShot& B, int n, int slot, bool record) {
     P.push_back({slot >= 0 ? BK_VEL_CAP : BK_VEL, n, slot, 0, B.items_pass});
-    if (B.S.kind == EWS_SOURCE_FORCE || (record && B.seis && B.nrec > 0))
-        P.push_back({BK_POSTV, n, slot, record ? 1 : 0, 1});
-    P.push_back({BK_STR, n, 0, 0, B.items_pass});
-    if (B.S.kind == EWS_SOURCE_MOMENT) P.push_back({BK_POSTS, n, 0, 0, 1});
+    P.push_back({BK_STR, n, 0, record ? 1 : 0, B.items_pass});
 }
 
 // The stages of ews_run on one shot.
@@ -48,12 +45,14 @@ void forward_program(std::vector<Stage>& P, const BatchShot& B, int nt) {
     for (int n = 0; n < nt; ++n) push_step(P, B, n, -1, true);
 }
 
-// The stages of ews_gradient on one shot (transformed reverse sweep):
-// forward with checkpoints (the resident range [c_res K, nt) writes its
-// history), residual, then per segment in reverse: restore and recompute
-// (not for the resident range), reverse steps, buoyancy term and flushes;
-// finally the gradients.
-void gradient_program(std::vector<Stage>& P, const BatchShot& B, int nt, int K, int c_res) {
+// The stages of ews_gradient on one shot (transformed reverse sweep), in
+// two parts.  Forward part: forward with checkpoints (the resident range
+// [c_res K, nt) writes its history) and the residual.  Reverse part: per
+// segment in reverse, restore and recompute (not for the resident range),
+// reverse steps, buoyancy term and flushes; finally the gradients.  The
+// forward part runs in the lean executor (3 CTAs per SM), the reverse part
+// in the one with the reverse velocity pass (larger slots, 2 per SM).
+void gradient_forward_program(std::vector<Stage>& P, const BatchShot& B, int nt, int K, int c_res) {
     const int nck = (nt + K - 1) / K;
     const int n_res = c_res * K;
     P.push_back({BK_ZERO_F, 0, 0, 0, B.items_elem});
@@ -64,6 +63,9 @@ void gradient_program(std::vector<Stage>& P, const BatchShot& B, int nt, int K, 
         for (int n = n0; n < n1; ++n) push_step(P, B, n, c >= c_res ? n - n_res + 1 : -1, true);
     }
     P.push_back({BK_RESID, 0, 0, 0, 1});
+}
+
+void gradient_reverse_program(std::vector<Stage>& P, const BatchShot& B, int nt, int K, int c_res) {
     P.push_back({BK_ZERO_A, 0, 0, 0, B.items_elem});
     for (int c = c_res; c >= 0; --c) {
         const int n0 = c * K, n1 = c == c_res ? nt : n0 + K;
@@ -73,8 +75,7 @@ void gradient_program(std::vector<Stage>& P, const BatchShot& B, int nt, int K, 
             for (int n = n0; n < n1; ++n) push_step(P, B, n, n - n0 + 1, false);
         }
         for (int m = n1 - 1; m >= n0; --m) {
-            P.push_back({BK_VEL_GRAD, m + 1 < n1 ? 1 : 0, m - n0 + 1, 0, B.items_pass});
-            if (B.nrec > 0) P.push_back({BK_ADJINJ, m, 0, 0, 1});
+            P.push_back({BK_VEL_GRAD, m, m - n0 + 1, m + 1 < n1 ? 1 : 0, B.items_pass});
             P.push_back({BK_STR_ADJ, m, 0, 0, B.items_pass});
             if ((m - n0) % K == 0 && m > n0) P.push_back({BK_FLUSH, 0, 0, 0, B.items_elem});
         }
@@ -365,7 +366,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
 
     int* d_err = shots[0].sim->err;            // any of the shots' error flags
     std::vector<BatchShot> bs(nshots);
-    std::vector<std::vector<Stage>> progs(nshots);
+    std::vector<std::vector<Stage>> progs(nshots), rprogs(nshots);
     for (int i = 0; i < nshots; ++i) {
         ews_batch_shot& b = shots[i];
         ews_sim* s = b.sim;
@@ -380,17 +381,23 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         }
         int zc = o.zchunk;
         if (zc == 0) {
-            ews_status r = tune_zchunk(s, b, bnd, grad, o.ctas_per_sm, d_err, st, &zc);
+            ews_status r = tune_zchunk(s, b, bnd, false, o.ctas_per_sm, d_err, st, &zc);
             if (r != EWS_OK) return r;
         }
         ews_status r = fill_shot(bs[i], s, b, zc, d_err, b.observed != nullptr);
         if (r != EWS_OK) return r;
-        if (b.observed) gradient_program(progs[i], bs[i], b.nt, K, c_res);
-        else forward_program(progs[i], bs[i], b.nt);
+        if (b.observed) {
+            gradient_forward_program(progs[i], bs[i], b.nt, K, c_res);
+            gradient_reverse_program(rprogs[i], bs[i], b.nt, K, c_res);
+        } else {
+            forward_program(progs[i], bs[i], b.nt);
+        }
     }
-    ews_status r = run_persistent(bs, progs, bnd, grad, o.ctas_per_sm, d_err, st, nullptr,
-                                  (unsigned long long)o.dep_wait_ms * 1000000ull,
+    const unsigned long long wait = (unsigned long long)o.dep_wait_ms * 1000000ull;
+    ews_status r = run_persistent(bs, progs, bnd, false, o.ctas_per_sm, d_err, st, nullptr, wait,
                                   o.test_unsatisfiable != 0);
+    if (r == EWS_OK && grad)
+        r = run_persistent(bs, rprogs, bnd, true, o.ctas_per_sm, d_err, st, nullptr, wait, false);
     if (r != EWS_OK) return r;
     for (int i = 0; i < nshots; ++i) {
         ews_sim* s = shots[i].sim;

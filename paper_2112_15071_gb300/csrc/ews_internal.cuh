@@ -163,15 +163,17 @@ struct PassParams {
 // done counter, bounded wait).  Claims follow the entry order, so every
 // awaited item was claimed earlier by a running CTA: no deadlock, whatever
 // the number of resident CTAs.
+// Point terms ride on the pass items that own their cells: the force of
+// step n on the velocity-pass items (also into the history when capturing),
+// the moment on the stress-pass items, the residual on the reverse
+// velocity-pass items, and the receivers (when flag) on the stress-pass
+// items holding their first tap.
 enum BatchKind {
-    BK_VEL = 0,       // forward velocity pass
-    BK_VEL_CAP,       // forward velocity pass writing history slot `slot`
-    BK_VEL_GRAD,      // reverse velocity pass, history slot `slot`, n != 0: buoyancy term
-    BK_STR,           // forward stress pass
+    BK_VEL = 0,       // forward velocity pass of step n
+    BK_VEL_CAP,       // forward velocity pass of step n writing history slot `slot`
+    BK_VEL_GRAD,      // reverse velocity pass of step n, history slot `slot`; flag: buoyancy term
+    BK_STR,           // forward stress pass of step n; flag: record the receivers
     BK_STR_ADJ,       // reverse stress pass
-    BK_POSTV,         // step n: force injection (also into history slot `slot` if >= 0); receivers if flag
-    BK_POSTS,         // step n: moment injection
-    BK_ADJINJ,        // reverse step n: residual injection
     BK_SAVE,          // fields -> checkpoint `slot`
     BK_LOAD,          // checkpoint `slot` -> fields
     BK_HIST0,         // v -> history slot 0
@@ -188,7 +190,7 @@ struct BatchEntry {
     int shot, kind, n, slot;
     long long need;       // items of the shot's earlier stages
     int nitems;
-    int flag;             // BK_POSTV: record the receivers
+    int flag;             // see BatchKind
 };
 
 struct alignas(64) BatchShot {

@@ -91,8 +91,16 @@ __device__ __forceinline__ float record_one(const DevGrid& g, const DevFields& F
     return acc;
 }
 
-// Reverse sweep in transformed variables: residual sample t injected into
-// alpha (alpha += G B S^T sadj_n).
+// Reverse sweep in transformed variables: one tap of a residual sample a
+// injected into alpha (alpha += G B S^T sadj_n).
+__device__ __forceinline__ void adj_inject_tap(const DevGrid& g, const AdjFields& A,
+                                               const DevMedium& M, const DevBoundary& B,
+                                               const Tap& q, float a) {
+    atomicAdd(A.p[q.q] + cidx(g, q.i, q.j, q.k),
+              gain(B, q.i, q.j, q.k) * buoy(M, g, q.q - VX, q.i, q.j, q.k) * q.w * a);
+}
+
+// All 8 taps of residual sample t.
 __device__ __forceinline__ void adj_inject_one(const DevGrid& g, const AdjFields& A,
                                                const DevMedium& M, const DevBoundary& B,
                                                const Tap* __restrict__ taps,
@@ -100,11 +108,7 @@ __device__ __forceinline__ void adj_inject_one(const DevGrid& g, const AdjFields
     const float a = sadj[(long long)t * ld + n];
     const Tap* tp = taps + 8 * t;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const Tap q = tp[m];
-        atomicAdd(A.p[q.q] + cidx(g, q.i, q.j, q.k),
-                  gain(B, q.i, q.j, q.k) * buoy(M, g, q.q - VX, q.i, q.j, q.k) * q.w * a);
-    }
+    for (int m = 0; m < 8; ++m) adj_inject_tap(g, A, M, B, tp[m], a);
 }
 
 // Buoyancy term of a segment's first reverse step at element o of cell

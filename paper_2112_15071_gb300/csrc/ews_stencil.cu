@@ -825,6 +825,22 @@ __device__ __forceinline__ void stage_params(PassParams* dst, const PassParams& 
     for (int w = tid; w < (int)(sizeof(PassParams) / 4); w += NTH) b[w] = a[w];
 }
 
+// Cell box of a pass item (the same decomposition as Geo).
+struct ItemBox {
+    int x0, y0, z0, z1;
+    __device__ __forceinline__ ItemBox(const PassParams& P, int item) {
+        const int ntile = P.ntx * P.nty;
+        const int t = item % ntile;
+        z0 = (item / ntile) * P.zchunk;
+        z1 = min(P.g.nz, z0 + P.zchunk);
+        x0 = (t % P.ntx) * TX;
+        y0 = (t / P.ntx) * TY;
+    }
+    __device__ __forceinline__ bool has(int i, int j, int k) const {
+        return i >= x0 && i < x0 + TX && j >= y0 && j < y0 + TY && k >= z0 && k < z1;
+    }
+};
+
 template <int BND, bool GRAD>
 __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
     k_batch(const BatchShot* __restrict__ shots, const BatchEntry* __restrict__ entries,
@@ -834,10 +850,15 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
     constexpr int SB = GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>();
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB);
     __shared__ PassParams sP;
-    __shared__ int s_e, s_it, s_stop;
+    __shared__ int s_e, s_it, s_stop, s_key;
+    __shared__ unsigned long long s_fenced[4];   // map sets acquired, bit per shot < 64
     __shared__ double s_red[NTH / 32];
     const int tid = threadIdx.y * TX + threadIdx.x;
     ring_init(bars, tid);
+    if (tid == 0) {
+        s_key = -1;
+        for (int q = 0; q < 4; ++q) s_fenced[q] = 0;
+    }
     while (true) {
         if (tid == 0) {
             int e = -1, it = 0, stop = 0;
@@ -853,15 +874,17 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                 }
                 atomicCAS(cur, c, c + 1);
             }
-            if (e >= 0) {                // wait for the shot's earlier stages
+            if (e >= 0) {                // wait for the shot's earlier stages (acquire)
                 const int shot = entries[e].shot;
                 const unsigned long long need = (unsigned long long)entries[e].need;
                 const unsigned long long t0 = now_ns();
                 while (ld_acquire(&done[shot]) < need) {
                     if (ld_relaxed(err)) { stop = 1; break; }
                     if (now_ns() - t0 > wait_ns) { atomicOr(err, 8); stop = 1; break; }
-                    __nanosleep(100);
+                    __nanosleep(64);
                 }
+                // the awaited generic stores are visible to this thread's TMA copies
+                asm volatile("fence.proxy.async.global;" ::: "memory");
             }
             s_e = e;
             s_it = it;
@@ -872,10 +895,6 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
         const int it = s_it;
         const BatchEntry E = entries[s_e];
         const BatchShot& B = shots[E.shot];
-        // results of the awaited items (generic stores of other CTAs) are
-        // visible to this CTA's loads and to its TMA (async proxy) reads
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        asm volatile("fence.proxy.async.global;" ::: "memory");
         const DevGrid& g = B.pf.g;
         const long long fs = B.fs;
         bool ok = true;
@@ -886,22 +905,30 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
             case BK_STR:
             case BK_STR_ADJ: {
                 const bool adj = E.kind == BK_VEL_GRAD || E.kind == BK_STR_ADJ;
-                stage_params(&sP, adj ? B.pa : B.pf, tid);
-                __syncthreads();
+                const int key = 2 * E.shot + (adj ? 1 : 0);
+                if (s_key != key) {          // stage this shot's pass parameters once
+                    stage_params(&sP, adj ? B.pa : B.pf, tid);
+                    __syncthreads();
+                    if (tid == 0) s_key = key;
+                }
+                const int set = E.kind == BK_VEL || E.kind == BK_VEL_CAP ? 0
+                                : E.kind == BK_STR                     ? 1
+                                : E.kind == BK_STR_ADJ                 ? 2
+                                                                       : 3;
                 if (tid == 0) {
                     if (E.kind == BK_VEL_CAP) {
                         sP.X.vcap = B.vhist + (long long)E.slot * 3 * fs;
                         sP.X.fstride = fs;
                     } else if (E.kind == BK_VEL_GRAD) {
                         sP.X.hslot = E.slot;
-                        sP.X.vnext = E.n ? B.vhist + (long long)(E.slot + 1) * 3 * fs : nullptr;
+                        sP.X.vnext = E.flag ? B.vhist + (long long)(E.slot + 1) * 3 * fs : nullptr;
+                    }
+                    const Maps* mp = set == 0 ? &B.vf : set == 1 ? &B.sf : set == 2 ? &B.sa : &B.va;
+                    if (E.shot >= 64 || !((s_fenced[set] >> E.shot) & 1ull)) {
+                        acquire_maps(mp);
+                        if (E.shot < 64) s_fenced[set] |= 1ull << E.shot;
                     }
                 }
-                if (tid == 0)
-                    acquire_maps(E.kind == BK_VEL || E.kind == BK_VEL_CAP ? &B.vf
-                                 : E.kind == BK_STR                       ? &B.sf
-                                 : E.kind == BK_STR_ADJ                   ? &B.sa
-                                                                          : &B.va);
                 ring_rearm(bars, tid);
                 if (E.kind == BK_VEL)
                     ok = vel_tile<BND, float, M_FWD>(B.vf, sP, it, sm, bars);
@@ -913,34 +940,49 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                     ok = str_tile<BND, float>(B.sa, sP, it, sm, bars);
                 else if constexpr (GRAD)
                     ok = vel_tile<BND, float, M_GRAD>(B.va, sP, it, sm, bars);
-                break;
-            }
-            case BK_POSTV: {
-                const DevFields& F = B.pf.F;
-                if (B.S.kind == 1 && tid < B.S.ntap) {
-                    ops::inject_tap<float>(g, F, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
-                    if (E.slot >= 0) {           // the captured v^{n+1/2} includes the force
-                        DevFields H = F;
-                        for (int c = 0; c < 3; ++c) H.f[c] = B.vhist + ((long long)E.slot * 3 + c) * fs;
-                        ops::inject_tap<float>(g, H, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
+                if (!ok) break;
+                // Point terms of this step inside the item's cells, after its
+                // stores (the next pass starts only when every item is done):
+                // the force after the velocity pass (also into the captured
+                // history), the moment after the stress pass, the residual
+                // after the reverse velocity pass; and, at the stress pass,
+                // the receivers whose first tap lies in the item (v^{n+1/2}
+                // is final once the stress pass may start).
+                __syncthreads();
+                const ItemBox box(sP, it);
+                if ((E.kind == BK_VEL || E.kind == BK_VEL_CAP) && B.S.kind == 1 && tid < B.S.ntap) {
+                    const Tap& q = B.S.tap[tid];
+                    if (box.has(q.i, q.j, q.k)) {
+                        ops::inject_tap<float>(g, B.pf.F, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
+                        if (E.kind == BK_VEL_CAP) {
+                            DevFields H = B.pf.F;
+                            for (int c = 0; c < 3; ++c)
+                                H.f[c] = B.vhist + ((long long)E.slot * 3 + c) * fs;
+                            ops::inject_tap<float>(g, H, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
+                        }
                     }
                 }
-                __threadfence();
-                __syncthreads();
-                asm volatile("fence.acq_rel.gpu;" ::: "memory");
-                if (B.seis && E.flag)
-                    for (int t = tid; t < 3 * B.nrec; t += NTH)
-                        B.seis[(long long)t * B.nt + E.n] = ops::record_one<float>(g, F, B.rtaps, t);
+                if (E.kind == BK_STR && B.S.kind == 0 && tid < B.S.ntap) {
+                    const Tap& q = B.S.tap[tid];
+                    if (box.has(q.i, q.j, q.k))
+                        ops::inject_tap<float>(g, B.pf.F, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
+                }
+                if (E.kind == BK_STR && E.flag && B.seis)
+                    for (int t = tid; t < 3 * B.nrec; t += NTH) {
+                        const Tap& q = B.rtaps[8 * t];
+                        if (box.has(q.i, q.j, q.k))
+                            B.seis[(long long)t * B.nt + E.n] = ops::record_one<float>(g, B.pf.F, B.rtaps, t);
+                    }
+                if (E.kind == BK_VEL_GRAD && B.nrec > 0)
+                    for (int t = tid; t < 3 * B.nrec; t += NTH) {
+                        const float a = B.sadj[(long long)t * B.nt + E.n];
+                        for (int m = 0; m < 8; ++m) {
+                            const Tap& q = B.rtaps[8 * t + m];
+                            if (box.has(q.i, q.j, q.k)) ops::adj_inject_tap(g, B.A, B.M, B.pf.B, q, a);
+                        }
+                    }
                 break;
             }
-            case BK_POSTS:
-                if (B.S.kind == 0 && tid < B.S.ntap)
-                    ops::inject_tap<float>(g, B.pf.F, B.M, B.pf.B, B.S, B.wavelet, E.n, tid, err);
-                break;
-            case BK_ADJINJ:
-                for (int t = tid; t < 3 * B.nrec; t += NTH)
-                    ops::adj_inject_one(g, B.A, B.M, B.pf.B, B.rtaps, B.sadj, B.nt, E.n, t);
-                break;
             case BK_RESID: {
                 double acc = 0.0;
                 const long long n = 3LL * B.nrec * B.nt;
@@ -1012,7 +1054,6 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
         __syncthreads();
         if (!ok) break;                      // a pipeline wait gave up (recorded)
         if (tid == 0) {                      // release: this item's stores, then the count
-            asm volatile("fence.proxy.async.global;" ::: "memory");
             __threadfence();
             atomicAdd(&done[E.shot], 1ull);
         }

@@ -343,6 +343,23 @@ def config3(nx: int = 1024, ny: int = 1024, nz: int = 512, nt: int = 3000,
                    _wavelet_for("force", nt, dt, f0), rec, "sponge", width, f0)
 
 
+def sphere_anomaly_device(vp, vs, spacing, frac: float = 0.05):
+    """+frac on vp and vs inside a centred sphere of a quarter of the cube
+    side (device tensors); Gardner density.  The 'observed' variant of a
+    batched shot."""
+    import torch
+    nz, ny, nx = vp.shape
+    dev = vp.device
+    z = torch.arange(nz, device=dev, dtype=torch.float32)[:, None, None] - nz // 2
+    y = torch.arange(ny, device=dev, dtype=torch.float32)[None, :, None] - ny // 2
+    x = torch.arange(nx, device=dev, dtype=torch.float32)[None, None, :] - nx // 2
+    inside = (x * x + y * y + z * z) <= (min(nx, ny, nz) / 4.0) ** 2
+    f = torch.where(inside, torch.tensor(1.0 + frac, device=dev), torch.tensor(1.0, device=dev))
+    vp2 = (vp * f).contiguous()
+    vs2 = (vs * f).contiguous()
+    return vp2, vs2, (310.0 * vp2.double() ** 0.25).float()
+
+
 def config3_crop(n: int = 128, nt: int = 1000, h: float = 50.0, width: int = 20,
                  seed: int = SEED) -> Problem:
     """The large forward recipe re-instantiated on an n^3 crop (128^3) for the
@@ -389,10 +406,11 @@ def config4(n: int = 192, nt: int = 1500, h: float = 15.0, width: int = 20,
     return true, start
 
 
-def config5_shots(nshots: int = 48, seed: int = SEED):
+def config5_shots(nshots: int = 48, seed: int = SEED, device=None):
     """Batched case: seeded cube sizes in {96, 104, ..., 224}, nt in
     [800, 1600], f0 in [5, 15] Hz, dx = vs_min / (12.5 f0) rounded down to
-    0.5 m; each shot has its own layered + random model (seed + shot)."""
+    0.5 m; each shot has its own layered + random model (seed + shot).
+    With `device`, the models are generated in device memory (torch)."""
     rng = np.random.default_rng(seed)
     sizes = rng.choice(np.arange(96, 225, 8), size=nshots)
     nts = rng.integers(800, 1601, size=nshots)
@@ -403,8 +421,12 @@ def config5_shots(nshots: int = 48, seed: int = SEED):
         vs_min = 2000.0 * 0.95 / 1.73
         h = math.floor(vs_min / (12.5 * f0) * 2.0) / 2.0
         sp = (h, h, h)
-        vp, vs, rho = layered_random(n, n, n, sp, corr_len=max(200.0, 4 * h),
-                                     seed=seed + s)
+        if device is not None:
+            vp, vs, rho = layered_random_device(n, n, n, sp, device,
+                                                corr_len=max(200.0, 4 * h), seed=seed + s)
+        else:
+            vp, vs, rho = layered_random(n, n, n, sp, corr_len=max(200.0, 4 * h),
+                                         seed=seed + s)
         dt = 0.5 * PAPER_CFL * h / (6000.0 * 1.05)
         src = np.array([(n // 2) * h, (n // 2) * h, (n // 3) * h])
         rec = grid_receivers(n, n, sp, 16, 16, 8, 8)
