@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--adj-nt", type=int, default=1500)
     ap.add_argument("--storage", choices=("f32", "bf16", "f16"), default="f32",
                     help="wavefield storage of the main workload (FP32 arithmetic)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the timing sweep over the paper's 11 grid levels")
+    ap.add_argument("--sweep-nt", type=int, default=100,
+                    help="time steps timed per level of the sweep")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-shot comparison")
     ap.add_argument("--batch-shots", type=int, default=12,
@@ -346,6 +350,8 @@ def run_ours(args, world, rank, local):
         out["storage"] = storage_report(args, local, rank == 0 and world == 1)
     if not args.no_batch:
         out["batch"] = batch_report(args, local)
+    if not args.no_sweep:
+        out["paper_sweep"] = paper_sweep(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
     sim.close()
@@ -538,6 +544,46 @@ def batch_report(args, local):
         s.close()
     torch.cuda.empty_cache()
     return out
+
+
+# The paper's GL timings (Sec. 4, total-time table divided by cells x steps):
+# Mcell-updates/s per level on its integrated Vega GPU.  Context only.
+PAPER_GPU_MCELLS = [74, 111, 127, 99, 58, 105, 97, 99, 112, 79, 77]
+
+
+def paper_sweep(args, local):
+    """The 11 grid levels of the paper's level-of-detail table with its 1D
+    crustal model and moment tensor: Gcell-updates/s of --sweep-nt steps per
+    level (time only), beside the paper's own GL figures for context."""
+    import torch
+    from paper_2112_15071_gb300 import ews, synth
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for lv in range(len(synth.PAPER_LEVELS)):
+        p = synth.paper_level(lv, nt=args.sweep_nt)
+        sim = ews.simulation_for(p)
+        sim.set_stream(stream.cuda_stream)
+        seis = torch.zeros((3, sim.nrec, p.nt), device=dev)
+        sim.run(p.nt, p.dt, seis)                     # warm-up (graph capture)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.run(p.nt, p.dt, seis)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        g = p.ncell * p.nt / (ms / 1e3) / 1e9
+        rows.append({"level": lv, "grid": [p.nx, p.ny, p.nz], "ms_per_step": round(ms / p.nt, 4),
+                     "gcells": round(g, 3), "paper_gl_mcells": PAPER_GPU_MCELLS[lv],
+                     "x_paper": round(g * 1e3 / PAPER_GPU_MCELLS[lv], 1)})
+        sim.close()
+    return {"workload": "paper level table (Sec. 3.2.1): grids, spacings and dt as printed, 1D "
+                        "crustal model, Eq. 7 moment tensor, sponge, 8 receivers; "
+                        f"{args.sweep_nt} timed steps per level",
+            "paper_hardware": "AMD Ryzen 7 4700U integrated Vega GPU, OpenGL (context only)",
+            "levels": rows}
 
 
 # --- reference arm: the FP64 oracle on the host cores -------------------------

@@ -343,6 +343,48 @@ def config3(nx: int = 1024, ny: int = 1024, nz: int = 512, nt: int = 3000,
                    _wavelet_for("force", nt, dt, f0), rec, "sponge", width, f0)
 
 
+# Grid spacings (km) and time steps (s) of the level-of-detail table (Sec.
+# 3.2.1, "Simulation details"), level by level.
+PAPER_LEVEL_SPACING = [
+    (6.67, 10.61, 3.75, 0.1), (6.67, 10.61, 1.87, 0.1), (3.33, 10.61, 1.87, 0.1),
+    (3.33, 5.30, 1.87, 0.1), (3.33, 5.30, 0.93, 0.05), (1.66, 5.30, 0.93, 0.05),
+    (1.66, 2.65, 0.93, 0.05), (1.66, 2.65, 0.46, 0.01), (0.83, 2.65, 0.46, 0.01),
+    (0.83, 1.32, 0.46, 0.01), (0.83, 1.32, 0.23, 0.01),
+]
+
+
+def paper_level(level: int, nt: int | None = None) -> Problem:
+    """Level `level` of the paper's level-of-detail table as a synthetic
+    input: the grid, spacing and time step of the table, the 1D crustal
+    model of Sec. 3.1.2 (layer tops measured from 30 km below the top of the
+    grid, whose depth range is -30..90 km; cells above depth 0 take the top
+    layer), the moment tensor of Eq. 7 at the centroid depth (7 km) in the
+    centre of (x, y), a Ricker at the table's maximum frequency, a sponge of a quarter of the thinnest axis (at most
+    16 cells) and 8 receivers on a line at the top of the interior.  Timing
+    workload only (the real seismograms are not available)."""
+    nx, ny, nz, steps = PAPER_LEVELS[level]
+    dxk, dyk, dzk, dt = PAPER_LEVEL_SPACING[level]
+    sp = (dxk * 1e3, dyk * 1e3, dzk * 1e3)
+    nt = steps if nt is None else nt
+    depth = (np.arange(nz) * sp[2]) / 1e3 - 30.0            # km, cell tops
+    li = np.clip(np.searchsorted(PAPER_LAYERS[:, 0], depth, side="right") - 1, 0, None)
+    vp1, vs1, rho1 = (PAPER_LAYERS[li, c] * 1e3 for c in (1, 2, 3))
+    shp = (nz, ny, nx)
+    vp = np.broadcast_to(vp1[:, None, None], shp).astype(np.float32)
+    vs = np.broadcast_to(vs1[:, None, None], shp).astype(np.float32)
+    rho = np.broadcast_to(rho1[:, None, None], shp).astype(np.float32)
+    width = max(4, min(16, min(nx, ny, nz) // 4))
+    M = PAPER_MOMENT_TENSOR
+    comp = np.array([M[0, 0], M[1, 1], M[2, 2], M[0, 1], M[0, 2], M[1, 2]])
+    ks = min(int(round((30.0 + 7.0) * 1e3 / sp[2])), nz - width - 2)
+    src = np.array([(nx // 2) * sp[0], (ny // 2) * sp[1], ks * sp[2]])
+    fmax = 0.037 if level < 3 else 0.075 if level < 6 else 0.15 if level < 9 else 0.30
+    rec = grid_receivers(nx, ny, sp, width, width, 8, 1)
+    return Problem(f"paper_level{level}_{nx}x{ny}x{nz}", nx, ny, nz, sp, dt, nt, vp, vs, rho,
+                   "moment", src, comp, _wavelet_for("moment", nt, dt, fmax), rec, "sponge",
+                   width, fmax)
+
+
 def sphere_anomaly_device(vp, vs, spacing, frac: float = 0.05):
     """+frac on vp and vs inside a centred sphere of a quarter of the cube
     side (device tensors); Gardner density.  The 'observed' variant of a
