@@ -77,14 +77,19 @@ def parse_args():
 # --- distributed plumbing ----------------------------------------------------
 
 def dist_setup(want: int):
+    """Rank, world and local device from the torchrun environment; NCCL
+    process group on GPUs (gloo when no GPU is present, e.g. CPU tests)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return world, rank, local
@@ -97,13 +102,21 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values (each rank's timed region)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, steps: int, ms: float, world: int) -> float:
+    """Whole-job throughput: the units all ranks processed (replicas, the
+    same work on every rank) over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms / 1e3)
 
 
 # --- clocks ------------------------------------------------------------------
@@ -273,7 +286,7 @@ def run_ours(args, world, rank, local):
     ms = max_over_ranks(t_start.elapsed_time(t_end), world)
     _, klaunch = sim.profile(reset=True)
     cells = prob.ncell * prob.nt
-    value = world * cells * args.steps / (ms / 1e3) / 1e9
+    value = aggregate_rate(cells, args.steps, ms, world) / 1e9
 
     # per-kernel durations: the same runs with CUDA events between launches
     # (direct launches instead of the graph), on the launching stream
