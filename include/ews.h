@@ -313,6 +313,26 @@ typedef struct {
 ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
                      void* cuda_stream);
 
+/* One iteration of multi-shot full-waveform inversion on one model (not
+ * in the paper, which only runs the forward model; its case study is many
+ * stations for one earthquake).  All shots share one grid; each shot's
+ * simulation has its source and receivers set and `observed` data
+ * (device [3][nrec][nt]); their g_* and seis fields are ignored.  lam, mu,
+ * rho: device dense [nz][ny][nx], the current model, replaced by the
+ * updated one.  The iteration: L2 misfit and gradients of all shots in one
+ * batched launch (ews_batch), their sum g, the direction d = -s_p g_p with
+ * s_p = max|m_p| / max|g_p| per parameter, misfits of batched forward runs
+ * at steps max_rel_step and max_rel_step / 2 and at the minimum of the
+ * parabola through those and J(0) (within [0.1, 2] max_rel_step), and the
+ * model of the smallest misfit, if smaller than J(0) (else the model is
+ * kept and *step = 0).  Trial models keep rho and mu at least half, and the
+ * bulk modulus at least half, of their current values.  Outputs: *misfit0
+ * = J at the current model, *misfit1 = J at the returned model, *step = the
+ * accepted step.  Every simulation ends holding the returned model. */
+ews_status ews_fwi_iteration(int nshots, ews_batch_shot* shots, float* lam, float* mu,
+                             float* rho, double max_rel_step, int ckpt_every, double* misfit0,
+                             double* misfit1, double* step, void* cuda_stream);
+
 /* zchunk the autotuner picked for a grid (0 if not tuned yet). */
 int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int gradient);
 

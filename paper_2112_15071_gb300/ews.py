@@ -96,6 +96,8 @@ SIGNATURES = [
                              _P, _P, _P, _I, _P, _I, _D, _P, _P]),
     ("ews_batch", _I, [_I, C.POINTER(ews_batch_shot), C.POINTER(ews_batch_options), _P]),
     ("ews_batch_tuned_zchunk", _I, [C.POINTER(ews_grid), _I, _I]),
+    ("ews_fwi_iteration", _I, [_I, C.POINTER(ews_batch_shot), _P, _P, _P, _D, _I, _P, _P, _P,
+                               _P]),
     ("ews_cfl_dt", _D, [C.POINTER(ews_grid), _D]),
     ("ews_max_freq", _D, [C.POINTER(ews_grid), _D]),
     ("ews_last_error", C.c_char_p, []),
@@ -297,6 +299,31 @@ def ews_batch(shots, mode: int = EWS_BATCH_PERSISTENT, ckpt_every: int = 0, zchu
                             int(dep_wait_ms), int(bool(test_unsatisfiable)))
     _check(load().ews_batch(len(shots), arr, C.byref(opt), C.c_void_p(stream_handle)))
     return [arr[i].misfit for i in range(len(shots))]
+
+
+def ews_fwi_iteration(shots, lam, mu, rho, max_rel_step: float = 0.02, ckpt_every: int = 0,
+                      stream_handle: int = 0):
+    """One multi-shot inversion iteration.  shots: dicts with sim, nt, dt and
+    observed (CUDA tensor); lam, mu, rho: CUDA tensors [nz][ny][nx] updated
+    in place.  Returns (misfit before, misfit after, accepted step)."""
+    arr = (ews_batch_shot * len(shots))()
+    for i, d in enumerate(shots):
+        arr[i].sim = d["sim"].handle.value if hasattr(d["sim"], "handle") else d["sim"]
+        arr[i].nt = int(d["nt"])
+        arr[i].dt = float(d["dt"])
+        p, dev = _ptr(d["observed"])
+        assert dev == 1, "observed must be a CUDA tensor"
+        arr[i].observed = p.value
+    ptrs = []
+    for t in (lam, mu, rho):
+        p, dev = _ptr(t)
+        assert dev == 1, "the model must be CUDA tensors"
+        ptrs.append(p)
+    j0, j1, a = C.c_double(), C.c_double(), C.c_double()
+    _check(load().ews_fwi_iteration(len(shots), arr, ptrs[0], ptrs[1], ptrs[2],
+                                    float(max_rel_step), int(ckpt_every), C.byref(j0),
+                                    C.byref(j1), C.byref(a), C.c_void_p(stream_handle)))
+    return j0.value, j1.value, a.value
 
 
 def ews_batch_tuned_zchunk(grid: ews_grid, boundary: int, gradient: bool) -> int:
