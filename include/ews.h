@@ -165,8 +165,9 @@ ews_status ews_advance(ews_sim* sim, int n0, int nsteps, double dt, float* seis,
  * (0: 50), then steps the adjoint back segment by segment, recomputing each
  * segment's velocity history v^{n+1/2} from its checkpoint.  The trailing
  * segments whose history fits in the history budget (see
- * ews_set_history_budget; at least one segment) keep the history written
- * by the first forward pass and are not recomputed.  Accumulation is FP32
+ * ews_set_history_budget; by default half the free device memory; at
+ * least one segment) keep the history written by the first forward pass
+ * and are not recomputed.  Accumulation is FP32
  * within ckpt_every steps and FP64 across them.  Boundaries NONE and SPONGE
  * (C-PML: EWS_EINVAL); F32 storage only.  Extra device memory: checkpoints
  * (nt / ckpt_every) x 9 fields, history max(ckpt_every + 1, budgeted
@@ -175,10 +176,13 @@ ews_status ews_adjoint(ews_sim* sim, int nt, double dt, const float* seis_adj,
                        int adj_on_device, float* g_lam, float* g_mu, float* g_rho,
                        int g_on_device, int ckpt_every);
 
-/* Device memory the adjoint may use for resident velocity history (bytes,
- * >= 0; default 0 = one segment).  Each resident time step costs 3 fields
- * (12 bytes per cell); with a budget covering all nt steps the gradient
- * needs no recomputation.  Not in the paper. */
+/* Device memory the adjoint may use for resident velocity history, in
+ * bytes.  Each resident time step costs 3 fields (12 bytes per cell); with a
+ * budget covering all nt steps the gradient needs no recomputation.  0: one
+ * segment (every earlier segment recomputed from its checkpoint).  < 0
+ * (the default): automatic, half of the device memory free at the call
+ * (for ews_batch, that half shared among the gradient shots).  Not in the
+ * paper. */
 ews_status ews_set_history_budget(ews_sim* sim, double bytes);
 
 /* Gradient of the L2 misfit J = dt/2 sum_(c,r,n) (seis - observed)^2 with

@@ -87,9 +87,10 @@ void gradient_reverse_program(std::vector<Stage>& P, const BatchShot& B, int nt,
 
 // First resident segment of the history budget (as in the adjoint of
 // ews_capi.cu): the trailing segments whose history fits, at least one.
-int resident_from(const ews_sim* s, int nt, int K) {
+int resident_from(const ews_sim* s, int nt, int K, int nshots) {
     const int nck = (nt + K - 1) / K;
-    const long long slots = (long long)(s->hist_budget / (3.0 * s->fstride * sizeof(float)));
+    const double budget = sim_history_budget(s, 0.5 / nshots);   // automatic: a share per shot
+    const long long slots = (long long)(budget / (3.0 * s->fstride * sizeof(float)));
     int c_res = nck - 1;
     while (c_res > 0 && (long long)(nt - (c_res - 1) * K) + 1 <= slots) --c_res;
     return c_res;
@@ -373,7 +374,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         const int K = std::min(K0, b.nt);
         int c_res = 0;
         if (b.observed) {
-            c_res = resident_from(s, b.nt, K);
+            c_res = resident_from(s, b.nt, K, nshots);
             const int hslots = std::max(K, b.nt - c_res * K) + 1;
             ews_status r = sim_adjoint_buffers(s, b.nt, K, hslots, true);
             if (r == EWS_OK) r = sim_adjoint_plan(s);

@@ -492,7 +492,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     // the first forward pass; earlier segments are recomputed into the same
     // buffer from their checkpoints.
     const double slot_bytes = 3.0 * fs * sizeof(float);
-    const long long budget_slots = (long long)(s->hist_budget / slot_bytes);
+    const long long budget_slots = (long long)(sim_history_budget(s, 0.5) / slot_bytes);
     int c_res = nck - 1;                       // first resident segment
     if (transformed)
         while (c_res > 0 && (long long)(nt - (c_res - 1) * K) + 1 <= budget_slots) --c_res;
@@ -656,6 +656,13 @@ ews_status sim_adjoint_buffers(ews_sim* s, int nt, int K, int hslots, bool with_
     if (with_obs && (st = ensure_buf(&s->aux, &s->aux_cap, 2 * (nseis ? nseis : 1), "adjoint source")) != EWS_OK)
         return st;
     return EWS_OK;
+}
+
+double sim_history_budget(const ews_sim* s, double share) {
+    if (s->hist_budget >= 0) return s->hist_budget;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0.0;
+    return share * ((double)free_b + (double)s->vhist_cap * sizeof(float));
 }
 
 ews_status sim_adjoint_plan(ews_sim* s) {
@@ -1024,8 +1031,8 @@ ews_status ews_set_state(ews_sim* s, const float* in, int on_device) {
 
 ews_status ews_set_history_budget(ews_sim* s, double bytes) {
     if (!s) return fail(EWS_EINVAL, "null simulation");
-    if (!(bytes >= 0) || !std::isfinite(bytes)) return fail(EWS_EINVAL, "budget must be >= 0");
-    s->hist_budget = bytes;
+    if (std::isnan(bytes) || !std::isfinite(bytes)) return fail(EWS_EINVAL, "budget must be finite");
+    s->hist_budget = bytes < 0 ? -1.0 : bytes;
     return EWS_OK;
 }
 

@@ -93,7 +93,7 @@ struct ews_sim {
     size_t aux_cap = 0;
     float* gout = nullptr;                // gradient staging for host outputs
     double* dmisfit = nullptr;
-    double hist_budget = 0;               // bytes of resident velocity history
+    double hist_budget = -1;              // bytes of resident velocity history (< 0: auto)
     // captured time loops (used when per-launch profiling is off)
     std::vector<GraphEntry> graphs;
     unsigned long long gen = 1;           // bumped when a kernel parameter source changes
@@ -131,5 +131,8 @@ DevSource sim_source(const ews_sim* s, double dt);             // source taps fo
 ews_status sim_adjoint_buffers(ews_sim* s, int nt, int K, int hslots, bool with_obs);
 // Stencil plan of the adjoint fields with its history map on s->vhist.
 ews_status sim_adjoint_plan(ews_sim* s);
+// History budget in bytes: the set value, or (automatic) `share` of the
+// device memory free now plus what the history buffer already holds.
+double sim_history_budget(const ews_sim* s, double share);
 
 }  // namespace ews

@@ -79,6 +79,7 @@ def test_gradient_batch_matches_one_by_one(ews, orc):
            .astype(np.float32) for p in probs]
     a = shots_for(ews, probs, grad=True, obs=obs)
     b = shots_for(ews, probs, grad=True, obs=obs)
+    a[1]["sim"].set_history_budget(0)         # one shot recomputes its segments
     ma = ews.ews_batch(a, ckpt_every=20)
     mb = ews.ews_batch(b, mode=ews.EWS_BATCH_SEQUENTIAL, ckpt_every=20)
     torch.cuda.synchronize()

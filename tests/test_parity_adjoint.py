@@ -45,10 +45,12 @@ def test_adjoint_matches_oracle(ews, orc, boundary, kind, dims):
     want = orc.gradient(p, A.astype(np.float64), ckpt_every=25, medium=[a.astype(np.float64) for a in p.lame()])
     sim = ews.simulation_for(p)
     sim.set_model_lame(*p.lame())
-    got = sim.adjoint(p.nt, p.dt, A, ckpt_every=25)
-    for q in range(3):
-        assert np.abs(want[q]).max() > 0
-        assert rel(got[q], want[q]) <= TOL_ORACLE, (q, rel(got[q], want[q]))
+    for budget in (-1, 0):              # history resident (automatic) / recomputed per segment
+        sim.set_history_budget(budget)
+        got = sim.adjoint(p.nt, p.dt, A, ckpt_every=25)
+        for q in range(3):
+            assert np.abs(want[q]).max() > 0
+            assert rel(got[q], want[q]) <= TOL_ORACLE, (budget, q, rel(got[q], want[q]))
 
 
 def test_checkpoint_interval_invariance(ews):
@@ -169,6 +171,7 @@ def test_resident_history_matches_recomputation(ews, orc, kind):
     A = np.random.default_rng(6).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
     sim = ews.simulation_for(p)
     sim.set_model_lame(*p.lame())
+    sim.set_history_budget(0)                                # one segment resident
     g0 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
     sim.set_history_budget(4e9)
     g1 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
