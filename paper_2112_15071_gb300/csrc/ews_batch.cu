@@ -243,9 +243,10 @@ ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector
     if (e != cudaSuccess)
         return report(e == cudaErrorMemoryAllocation ? EWS_ENOMEM : EWS_ECUDA, "batched launch: %s",
                       cudaGetErrorString(e));
-    if (herr)
+    if (herr & 11)
         return report(EWS_ETIMEOUT, "batched executor: a %s wait gave up (flags %d)",
                       (herr & 8) ? "dependency" : "pipeline", herr);
+    if (herr & 16) return report(EWS_ENONFINITE, "batched executor: a receiver recorded NaN or Inf");
     return EWS_OK;
 }
 

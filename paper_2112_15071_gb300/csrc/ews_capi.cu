@@ -378,7 +378,7 @@ ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, d
             }
         }
         if (s->nrec > 0 && dseis) {
-            CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, stor, inv, s->stream));
+            CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, stor, inv, s->err, s->stream));
             if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
         }
         CK(launch_stress(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
@@ -619,7 +619,8 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     CK(cudaGetLastError());
     if (herr) {
         CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
-        return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up");
+        if (herr & 3) return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up");
+        return fail(EWS_ENONFINITE, "a receiver recorded NaN or Inf during the gradient's forward run");
     }
     if (s->profiling && (st = collect_profile(s)) != EWS_OK) return st;
     return EWS_OK;
@@ -940,6 +941,9 @@ ews_status ews_advance(ews_sim* s, int n0, int nsteps, double dt, float* seis, i
         if (herr & 3)
             return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up (flags %d)",
                         herr);
+        if (herr & 16)
+            return fail(EWS_ENONFINITE, "a receiver recorded NaN or Inf in steps %d..%d: the "
+                                        "wavefield is not finite", n0, n0 + nsteps - 1);
         return fail(EWS_ERANGE, "a wavefield value exceeded the FP16 range: lower the field "
                                 "scales (ews_set_field_scales)");
     }

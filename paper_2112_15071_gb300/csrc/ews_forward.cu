@@ -29,13 +29,17 @@ __global__ void k_inject(DevGrid g, DevFields F, DevMedium M, DevBoundary B, Dev
 }
 
 // Receiver sampling: one thread per (component, receiver), 8 taps each.
+// A non-finite sample means the wavefield has blown up or was given a
+// NaN / Inf: flag bit 16 of *err (a watchdog that costs no extra traffic).
 template <typename T>
 __global__ void k_record(DevGrid g, DevFields F, const Tap* __restrict__ taps, int nrec,
-                         float* __restrict__ seis, int ld, int n, float i0, float i1, float i2) {
+                         float* __restrict__ seis, int ld, int n, float i0, float i1, float i2,
+                         int* err) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nrec) return;
     float acc = ops::record_one<T>(g, F, taps, t);
     if constexpr (sizeof(T) == 2) acc *= (t < nrec ? i0 : t < 2 * nrec ? i1 : i2);
+    if (!isfinite(acc)) atomicOr(err, 16);
     seis[(long long)t * ld + n] = acc;
 }
 
@@ -154,20 +158,20 @@ cudaError_t launch_inject(const DevGrid& g, const DevFields& F, const DevMedium&
 }
 
 cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps, int nrec,
-                          float* seis, int ld, int n, int storage, const float inv[3],
+                          float* seis, int ld, int n, int storage, const float inv[3], int* err,
                           cudaStream_t st) {
     if (nrec <= 0) return cudaSuccess;
     const int nt = 3 * nrec;
     const dim3 grid((nt + 127) / 128);
     switch (storage) {
         case EWS_STORAGE_BF16:
-            k_record<__nv_bfloat16><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2]);
+            k_record<__nv_bfloat16><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2], err);
             break;
         case EWS_STORAGE_F16:
-            k_record<__half><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2]);
+            k_record<__half><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2], err);
             break;
         default:
-            k_record<float><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, 1.f, 1.f, 1.f);
+            k_record<float><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, 1.f, 1.f, 1.f, err);
             break;
     }
     return cudaGetLastError();

@@ -236,7 +236,8 @@ void stencil_plan_export(const StencilPlan* p, Maps* vmaps, Maps* smaps, int* nt
 // The passes take, per field q, dto[q] = dt s_q (used for the fields they
 // write) and inv[q] = 1 / s_q (used for the 16-bit fields they read); with
 // FP32 storage s_q = 1.  *err collects bit 1 / 2 (a velocity / stress pipeline
-// wait gave up) and bit 4 (a value beyond the FP16 range was stored).
+// wait gave up), bit 4 (a value beyond the FP16 range was stored) and bit
+// 16 (a receiver recorded a NaN or Inf).
 struct StencilPlan;
 cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevMedium& M,
                                 const DevBoundary& B, int storage, StencilPlan** out);
@@ -274,7 +275,7 @@ cudaError_t launch_inject(const DevGrid& g, const DevFields& F, const DevMedium&
                           const DevBoundary& B, const DevSource& S, const float* wavelet,
                           int n, int storage, int* err, cudaStream_t st);
 cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps, int nrec,
-                          float* seis, int ld, int n, int storage, const float inv[3],
+                          float* seis, int ld, int n, int storage, const float inv[3], int* err,
                           cudaStream_t st);
 // flags[0]: validity bits (bit4: some mu == 0); flags[1..4]: float bits of max vp, min rho,
 // min sqrt(rho mu) over cells with mu > 0 (else FLT_MAX), max sqrt(rho (lambda + 2 mu)).

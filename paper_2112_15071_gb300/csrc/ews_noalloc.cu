@@ -266,13 +266,14 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
     for (int n = 0; n < nt; ++n) {
         NA_CK(launch_velocity(plan, g, F, B, dto, inv, err, stream));
         if (src_kind == EWS_SOURCE_FORCE) NA_CK(launch_inject(g, F, M, B, S, wavelet, n, f32, err, stream));
-        if (nrec > 0) NA_CK(launch_record(g, F, rtaps, nrec, seis, nt, n, f32, inv, stream));
+        if (nrec > 0) NA_CK(launch_record(g, F, rtaps, nrec, seis, nt, n, f32, inv, err, stream));
         NA_CK(launch_stress(plan, g, F, B, dto, inv, err, stream));
         if (src_kind == EWS_SOURCE_MOMENT) NA_CK(launch_inject(g, F, M, B, S, wavelet, n, f32, err, stream));
     }
     int herr = 0;
     NA_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     NA_CK(cudaStreamSynchronize(stream));
-    if (herr) return report(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up");
+    if (herr & 3) return report(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up");
+    if (herr) return report(EWS_ENONFINITE, "a receiver recorded NaN or Inf");
     return EWS_OK;
 }

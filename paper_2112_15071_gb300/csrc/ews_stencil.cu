@@ -971,7 +971,11 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                     for (int t = tid; t < 3 * B.nrec; t += NTH) {
                         const Tap& q = B.rtaps[8 * t];
                         if (box.has(q.i, q.j, q.k))
-                            B.seis[(long long)t * B.nt + E.n] = ops::record_one<float>(g, B.pf.F, B.rtaps, t);
+                        {
+                            const float v = ops::record_one<float>(g, B.pf.F, B.rtaps, t);
+                            if (!isfinite(v)) atomicOr(err, 16);
+                            B.seis[(long long)t * B.nt + E.n] = v;
+                        }
                     }
                 if (E.kind == BK_VEL_GRAD && B.nrec > 0)
                     for (int t = tid; t < 3 * B.nrec; t += NTH) {

@@ -249,3 +249,22 @@ def test_graph_replay_equals_direct_launches(ews):
     assert np.array_equal(seis, a)
     d = sim.run(p.nt, p.dt * 0.9)
     assert not np.array_equal(d, a)
+
+
+def test_nonfinite_wavefield_is_reported(ews):
+    """Watchdog: a NaN placed in the state (host-side fault injection)
+    reaches the receivers and the run returns EWS_ENONFINITE; the next run
+    from rest is clean."""
+    from paper_2112_15071_gb300 import synth
+    p = synth.small_problem(40, 36, 28, nt=40, boundary="sponge", width=5, kind="moment", seed=3)
+    sim = ews.simulation_for(p)
+    st = np.zeros((9, p.nz, p.ny, p.nx), np.float32)
+    c = np.round(p.rec_pos[0] / np.array(p.spacing)).astype(int)
+    st[3, c[2], c[1], c[0]] = np.nan
+    sim.set_state(st)
+    seis = np.zeros((3, p.rec_pos.shape[0], p.nt), np.float32)
+    with pytest.raises(ews.EwsError) as e:
+        sim.advance(0, 10, p.dt, seis, p.nt)
+    assert e.value.status == ews.EWS_ENONFINITE
+    out = sim.run(p.nt, p.dt)
+    assert np.all(np.isfinite(out))
