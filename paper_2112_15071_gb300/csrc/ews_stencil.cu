@@ -53,7 +53,10 @@ namespace {
 #define EWS_ROWS 1
 #endif
 #ifndef EWS_WAVES
-#define EWS_WAVES 4
+#define EWS_WAVES 4            // waves of (tile, z-chunk) CTAs per pass
+#endif
+#ifndef EWS_WAVES_CPML
+#define EWS_WAVES_CPML 8       // C-PML: tiles carry uneven work, finer chunks balance it
 #endif
 constexpr int TX = 32, TY = EWS_TILE_Y;
 constexpr int HY = TY + 4;                        // halo rows: y0-2 .. y0+TY+1
@@ -1196,13 +1199,17 @@ cudaError_t plan_build(StencilPlan* p, const DevGrid& g, const DevFields& F, con
     // Launch geometry: every tile column is cut into the same z-chunks and
     // chunk c of all tiles is resident at once, so neighbouring tiles march
     // through z together and the halo planes one CTA loads are still in L2
-    // when its neighbours load them.  Use as many chunks as the resident
-    // slots allow (at least 8 planes each); past one wave, whole columns.
+    // when its neighbours load them.  Use as many chunks as a few waves of
+    // the resident slots allow (at least 8 planes each).  With C-PML the
+    // slab tiles carry more work, so more, shorter chunks balance the SMs
+    // better (measured on 256^3: 8 waves 3 % faster than 4; without C-PML 4
+    // waves are 4 % faster than 8).
     p->ntx = (g.nx + TX - 1) / TX;
     p->nty = (g.ny + TY - 1) / TY;
     const long long ntile = (long long)p->ntx * p->nty;
     const long long slots = (long long)sms * occ;
-    long long nchunk = (slots * EWS_WAVES) / ntile;
+    const long long waves = B.kind == BND_CPML ? EWS_WAVES_CPML : EWS_WAVES;
+    long long nchunk = (slots * waves) / ntile;
     if (nchunk > g.nz / 8) nchunk = g.nz / 8;
     if (nchunk < 1) nchunk = 1;
     p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
