@@ -1203,12 +1203,14 @@ cudaError_t plan_build(StencilPlan* p, const DevGrid& g, const DevFields& F, con
     // the resident slots allow (at least 8 planes each).  With C-PML the
     // slab tiles carry more work, so more, shorter chunks balance the SMs
     // better (measured on 256^3: 8 waves 3 % faster than 4; without C-PML 4
-    // waves are 4 % faster than 8).
+    // waves are 4 % faster than 8).  16-bit storage fits 4 CTAs per SM, so
+    // 4 waves already give chunks that short (measured: 8 waves 7 % slower).
     p->ntx = (g.nx + TX - 1) / TX;
     p->nty = (g.ny + TY - 1) / TY;
     const long long ntile = (long long)p->ntx * p->nty;
     const long long slots = (long long)sms * occ;
-    const long long waves = B.kind == BND_CPML ? EWS_WAVES_CPML : EWS_WAVES;
+    const long long waves =
+        B.kind == BND_CPML && storage == EWS_STORAGE_F32 ? EWS_WAVES_CPML : EWS_WAVES;
     long long nchunk = (slots * waves) / ntile;
     if (nchunk > g.nz / 8) nchunk = g.nz / 8;
     if (nchunk < 1) nchunk = 1;
