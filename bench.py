@@ -63,8 +63,11 @@ def parse_args():
                     help="time steps timed per level of the sweep")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-shot comparison")
-    ap.add_argument("--batch-shots", type=int, default=12,
-                    help="shots of the 48-shot batched workload to run (first k)")
+    ap.add_argument("--batch-shots", type=int, default=48,
+                    help="shots of the 48-shot batched workload run forward (first k)")
+    ap.add_argument("--batch-grad-shots", type=int, default=12,
+                    help="shots of it run forward + gradient (first k; the gradient "
+                         "state of all 48 at once does not fit one GPU)")
     ap.add_argument("--no-storage", action="store_true",
                     help="skip the FP32 / BF16 / FP16 storage comparison")
     ap.add_argument("--storage-nt", type=int, default=40,
@@ -503,37 +506,45 @@ def storage_report(args, local, with_oracle: bool):
 def batch_report(args, local):
     """Batched shots (48-shot recipe: cubes 96..224, 800..1600 steps, 5..15 Hz,
     own layered + random model each, sponge 16, explosion at nz/3, 8 x 8
-    receivers; the first --batch-shots of them): forward, and forward plus L2
-    gradient against data from a +5 % sphere variant, as one persistent
-    launch and one shot after another.  Aggregate Gcell-updates/s counts
-    cells x steps of every shot over the wall time of the whole job."""
+    receivers): the forward of the first --batch-shots shots, and forward plus
+    L2 gradient (data from a +5 % sphere variant) of the first
+    --batch-grad-shots, each as one persistent launch and as one shot after
+    another.  Aggregate Gcell-updates/s counts cells x steps of every shot
+    over the wall time of the whole job."""
     import torch
     from paper_2112_15071_gb300 import ews, synth
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     probs = synth.config5_shots(48, device=dev)[:args.batch_shots]
-    cells = sum(p.ncell * p.nt for p in probs)
+    gprobs = probs[:args.batch_grad_shots]
     sims = [ews.simulation_for(p) for p in probs]
     seis = [torch.zeros((3, s.nrec, p.nt), device=dev) for s, p in zip(sims, probs)]
-    # observed data: the same shots on the anomaly variants, batched
-    obs = [torch.zeros_like(x) for x in seis]
+    # observed data of the gradient shots: the anomaly variants, batched
+    obs = [torch.zeros_like(x) for x in seis[:len(gprobs)]]
     vsims = []
-    for p in probs:
+    for p in gprobs:
         v = ews.simulation_for(p)
         v.set_model_vel(*synth.sphere_anomaly_device(p.vp, p.vs, p.spacing))
         vsims.append(v)
     ews.ews_batch([{"sim": v, "nt": p.nt, "dt": p.dt, "seis": o}
-                   for v, p, o in zip(vsims, probs, obs)], stream_handle=stream.cuda_stream)
+                   for v, p, o in zip(vsims, gprobs, obs)], stream_handle=stream.cuda_stream)
     for v in vsims:
         v.close()
-    grads = [torch.zeros((3, p.nz, p.ny, p.nx), device=dev) for p in probs]
+    grads = [torch.zeros((3, p.nz, p.ny, p.nx), device=dev) for p in gprobs]
+    # Both modes recompute every checkpoint segment (history budget 0): run
+    # alone, each shot could keep its whole history resident, which a batch
+    # of shots sharing the GPU cannot; this compares the scheduling alone.
+    for s in sims[:len(gprobs)]:
+        s.set_history_budget(0)
 
     def job(mode, gradient):
         shots = []
-        for s, p, x, o, g in zip(sims, probs, seis, obs, grads):
-            d = {"sim": s, "nt": p.nt, "dt": p.dt, "seis": x}
+        n = len(gprobs) if gradient else len(probs)
+        for i in range(n):
+            d = {"sim": sims[i], "nt": probs[i].nt, "dt": probs[i].dt, "seis": seis[i]}
             if gradient:
-                d.update(observed=o, g_lam=g[0], g_mu=g[1], g_rho=g[2])
+                g = grads[i]
+                d.update(observed=obs[i], g_lam=g[0], g_mu=g[1], g_rho=g[2])
             shots.append(d)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -541,22 +552,29 @@ def batch_report(args, local):
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
-    out = {"workload": f"first {len(probs)} of the 48-shot recipe (cubes "
-                       f"{min(p.nx for p in probs)}..{max(p.nx for p in probs)}, "
-                       f"{min(p.nt for p in probs)}..{max(p.nt for p in probs)} steps, sponge 16, "
-                       "explosion, 64 receivers; device-generated models)",
-           "cell_steps": cells}
-    for name, gradient in (("forward", False), ("forward_gradient", True)):
+    def cells_of(ps):
+        return sum(p.ncell * p.nt for p in ps)
+
+    out = {"workload": "48-shot recipe: cubes 96..224, 800..1600 steps, sponge 16, explosion, "
+                       "64 receivers, device-generated models",
+           "forward_shots": len(probs), "gradient_shots": len(gprobs),
+           "gradient_history": "checkpoints every 50 steps, every segment recomputed (budget 0)"}
+    for name, gradient, ps in (("forward", False, probs), ("forward_gradient", True, gprobs)):
         job(ews.EWS_BATCH_PERSISTENT, gradient)              # warm-up, autotune
         tp = job(ews.EWS_BATCH_PERSISTENT, gradient)
         job(ews.EWS_BATCH_SEQUENTIAL, gradient)
         ts = job(ews.EWS_BATCH_SEQUENTIAL, gradient)
-        out[name] = {"persistent_s": round(tp, 3), "one_by_one_s": round(ts, 3),
-                     "persistent_gcells": round(cells / tp / 1e9, 3),
-                     "one_by_one_gcells": round(cells / ts / 1e9, 3),
+        c = cells_of(ps)
+        out[name] = {"cell_steps": c, "persistent_s": round(tp, 3), "one_by_one_s": round(ts, 3),
+                     "persistent_gcells": round(c / tp / 1e9, 3),
+                     "one_by_one_gcells": round(c / ts / 1e9, 3),
                      "speedup": round(ts / tp, 3)}
-    out["tuned_zchunk"] = {f"{p.nx}^3": ews.ews_batch_tuned_zchunk(s.grid, 1, False)
-                           for s, p in zip(sims, probs)}
+        if gradient:
+            for s in sims[:len(gprobs)]:
+                s.release_workspace()
+    sizes = sorted({p.nx for p in probs})
+    out["tuned_zchunk"] = {f"{n}^3": ews.ews_batch_tuned_zchunk(
+        next(s.grid for s, p in zip(sims, probs) if p.nx == n), 1, False) for n in sizes}
     for s in sims:
         s.close()
     torch.cuda.empty_cache()

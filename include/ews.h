@@ -194,6 +194,13 @@ ews_status ews_gradient(ews_sim* sim, int nt, double dt, const float* observed,
                         int obs_on_device, double* misfit, float* g_lam, float* g_mu,
                         float* g_rho, int g_on_device, int ckpt_every);
 
+/* Free the working memory the simulation keeps between calls: adjoint
+ * state and accumulators, checkpoints, velocity history, seismogram and
+ * state staging, the adjoint stencil plan and captured time-loop graphs
+ * (the wavefields, medium, source and receivers stay).  Later calls
+ * allocate again as needed.  Synchronises the simulation's stream. */
+ews_status ews_release_workspace(ews_sim* sim);
+
 /* Zero the wavefields and C-PML memory variables. */
 ews_status ews_reset(ews_sim* sim);
 

@@ -377,7 +377,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         if (b.observed) {
             c_res = resident_from(s, b.nt, K, nshots);
             const int hslots = std::max(K, b.nt - c_res * K) + 1;
-            ews_status r = sim_adjoint_buffers(s, b.nt, K, hslots, true);
+            ews_status r = sim_adjoint_buffers(s, b.nt, c_res, hslots, true);
             if (r == EWS_OK) r = sim_adjoint_plan(s);
             if (r != EWS_OK) return r;
         }

@@ -498,7 +498,9 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         while (c_res > 0 && (long long)(nt - (c_res - 1) * K) + 1 <= budget_slots) --c_res;
     const int n_res = c_res * K;
     const int hslots = std::max(K, nt - n_res) + 1;
-    if ((st = sim_adjoint_buffers(s, nt, K, transformed ? hslots : K + 1, obs_dev != nullptr)) != EWS_OK)
+    // checkpoints only for the segments that will be recomputed
+    if ((st = sim_adjoint_buffers(s, nt, transformed ? c_res : nck, transformed ? hslots : K + 1,
+                                  obs_dev != nullptr)) != EWS_OK)
         return st;
     const size_t nseis = (size_t)3 * s->nrec * nt;
     AdjFields A;
@@ -638,9 +640,9 @@ ews_status sim_ready(ews_sim* s, int n_end, double dt) { return ensure_ready(s, 
 
 DevSource sim_source(const ews_sim* s, double dt) { return source_taps(s, s->src, dt); }
 
-ews_status sim_adjoint_buffers(ews_sim* s, int nt, int K, int hslots, bool with_obs) {
+ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool with_obs) {
     const size_t fs = s->fstride;
-    const int nck = (nt + K - 1) / K;
+    const int nck = nckpt > 0 ? nckpt : 1;
     if (!s->adj) {
         cudaError_t e = cudaMalloc(&s->adj, 17 * fs * sizeof(float));
         if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint state: %s", cudaGetErrorString(e));
@@ -1030,6 +1032,29 @@ ews_status ews_set_state(ews_sim* s, const float* in, int on_device) {
         CK(cudaStreamSynchronize(s->stream));
         return fail(EWS_ERANGE, "a state value exceeds the FP16 range at the field scales");
     }
+    return EWS_OK;
+}
+
+ews_status ews_release_workspace(ews_sim* s) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (s->stream) CK(cudaStreamSynchronize(s->stream));
+    else CK(cudaDeviceSynchronize());
+    for (GraphEntry& ge : s->graphs) cudaGraphExecDestroy(ge.exec);
+    s->graphs.clear();
+    stencil_plan_destroy(s->adj_plan);
+    s->adj_plan = nullptr;
+    s->adj_hist = nullptr;
+    s->adj_hist_slots = 0;
+    float** fbufs[] = {&s->adj, &s->ckpt, &s->vhist, &s->aux, &s->gout, &s->stage, &s->seis_buf};
+    for (float** b : fbufs) {
+        cudaFree(*b);
+        *b = nullptr;
+    }
+    cudaFree(s->acc64);
+    s->acc64 = nullptr;
+    cudaFree(s->dmisfit);
+    s->dmisfit = nullptr;
+    s->ckpt_cap = s->vhist_cap = s->aux_cap = s->stage_cap = s->seis_cap = 0;
     return EWS_OK;
 }
 

@@ -126,9 +126,9 @@ namespace ews {
 // error message (ews_last_error) and return its status on failure.
 ews_status sim_ready(ews_sim* s, int n_end, double dt);        // model, dt, boundary profiles
 DevSource sim_source(const ews_sim* s, double dt);             // source taps for this dt
-// Adjoint buffers for nt steps with checkpoints every K and `hslots`
+// Adjoint buffers for nt steps with `nckpt` checkpoints and `hslots`
 // history slots (allocated once, grown when needed).
-ews_status sim_adjoint_buffers(ews_sim* s, int nt, int K, int hslots, bool with_obs);
+ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool with_obs);
 // Stencil plan of the adjoint fields with its history map on s->vhist.
 ews_status sim_adjoint_plan(ews_sim* s);
 // History budget in bytes: the set value, or (automatic) `share` of the

@@ -87,6 +87,7 @@ SIGNATURES = [
     ("ews_set_state", _I, [_P, _P, _I]),
     ("ews_set_field_scales", _I, [_P, _P]),
     ("ews_set_history_budget", _I, [_P, _D]),
+    ("ews_release_workspace", _I, [_P]),
     ("ews_get_field_scales", _I, [_P, _P]),
     ("ews_adjoint", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _I, _I]),
     ("ews_gradient", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _P, _I, _I]),
@@ -257,6 +258,10 @@ def ews_get_field_scales(sim):
 
 def ews_set_history_budget(sim, nbytes: float):
     _check(load().ews_set_history_budget(sim, float(nbytes)))
+
+
+def ews_release_workspace(sim):
+    _check(load().ews_release_workspace(sim))
 
 
 def ews_adjoint(sim, nt: int, dt: float, seis_adj, g_lam, g_mu, g_rho, ckpt_every: int = 0):
@@ -454,6 +459,9 @@ class Simulation:
 
     def set_state(self, state):
         ews_set_state(self._h, state)
+
+    def release_workspace(self):
+        ews_release_workspace(self._h)
 
     def set_history_budget(self, nbytes):
         ews_set_history_budget(self._h, nbytes)

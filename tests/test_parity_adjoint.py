@@ -182,3 +182,15 @@ def test_resident_history_matches_recomputation(ews, orc, kind):
     for q in range(3):
         assert rel(g1[q], g0[q]) <= 1e-6 and rel(g2[q], g0[q]) <= 1e-6
         assert rel(g1[q], want[q]) <= TOL_ORACLE
+
+
+def test_release_workspace_and_run_again(ews):
+    p = problem((40, 36, 28), "sponge", "force", nt=60, seed=3)
+    A = np.random.default_rng(8).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    sim = ews.simulation_for(p)
+    g1 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
+    s1 = sim.run(p.nt, p.dt)
+    sim.release_workspace()
+    g2 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
+    s2 = sim.run(p.nt, p.dt)
+    assert np.array_equal(g1, g2) and np.array_equal(s1, s2)
