@@ -653,3 +653,136 @@ done:
     for (int q = 0; q < 8; ++q) free(acc[q]);
     return rc;
 }
+
+/* ---------------------------------------------------------------------------
+ * Tangent-linear model (forward-mode derivative of the discrete loop), for
+ * the dot-product test of the adjoint: for a model perturbation dm =
+ * (dlam, dmu, drho) it returns dseis = J dm exactly (to rounding), so that
+ * <J dm, A> = <dm, J^T A> pins orc_gradient.  Each step differentiates the
+ * operations of the forward step in order:
+ *   v' = G (v + dt B Dsig(sigma) + f_n)
+ *     -> dv' = G (dv + dt B Dsig(dsigma) + dt dB Dsig(sigma) + df_n),
+ *        dB = -B^2 drho_mean at the v points, df_n the force term with dB;
+ *   sigma' = G (sigma + dt C Dv(v') - m_n)
+ *     -> dsigma' = G (dsigma + dt C Dv(dv') + dt dC Dv(v')),
+ *        dC from dlam, dmu and the 4-cell means of dmu;
+ *   seis_n = S v' -> dseis_n = S dv'.
+ * Boundaries NONE and SPONGE (C-PML returns -3).
+ * ------------------------------------------------------------------------- */
+
+/* dv += dt dB Dsig(sigma) with the base state's stresses. */
+static void velocity_tangent_extra(const orc_sim *base, orc_sim *t, double dt, const double *dbx,
+                                   const double *dby, const double *dbz) {
+    double *const *f = base->f;
+    long nx = base->nx, ny = base->ny, nz = base->nz;
+    #pragma omp parallel for
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(base, i, j, k);
+                double sx = d_plus(base, f[SXX], 0, i, j, k) + d_minus(base, f[SXY], 1, i, j, k)
+                            + d_minus(base, f[SXZ], 2, i, j, k);
+                double sy = d_minus(base, f[SXY], 0, i, j, k) + d_plus(base, f[SYY], 1, i, j, k)
+                            + d_minus(base, f[SYZ], 2, i, j, k);
+                double sz = d_minus(base, f[SXZ], 0, i, j, k) + d_minus(base, f[SYZ], 1, i, j, k)
+                            + d_plus(base, f[SZZ], 2, i, j, k);
+                t->f[VX][c] += dt * dbx[c] * sx;
+                t->f[VY][c] += dt * dby[c] * sy;
+                t->f[VZ][c] += dt * dbz[c] * sz;
+            }
+}
+
+/* dsigma += dt dC Dv(v') with the base state's velocities. */
+static void stress_tangent_extra(const orc_sim *base, orc_sim *t, double dt, const double *dlam,
+                                 const double *dl2m, const double *dmxy, const double *dmxz,
+                                 const double *dmyz) {
+    double *const *f = base->f;
+    long nx = base->nx, ny = base->ny, nz = base->nz;
+    #pragma omp parallel for
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(base, i, j, k);
+                double exx = d_minus(base, f[VX], 0, i, j, k);
+                double eyy = d_minus(base, f[VY], 1, i, j, k);
+                double ezz = d_minus(base, f[VZ], 2, i, j, k);
+                t->f[SXX][c] += dt * (dl2m[c] * exx + dlam[c] * (eyy + ezz));
+                t->f[SYY][c] += dt * (dl2m[c] * eyy + dlam[c] * (exx + ezz));
+                t->f[SZZ][c] += dt * (dl2m[c] * ezz + dlam[c] * (exx + eyy));
+                t->f[SXY][c] += dt * dmxy[c] * (d_plus(base, f[VX], 1, i, j, k) + d_plus(base, f[VY], 0, i, j, k));
+                t->f[SXZ][c] += dt * dmxz[c] * (d_plus(base, f[VX], 2, i, j, k) + d_plus(base, f[VZ], 0, i, j, k));
+                t->f[SYZ][c] += dt * dmyz[c] * (d_plus(base, f[VY], 2, i, j, k) + d_plus(base, f[VZ], 1, i, j, k));
+            }
+}
+
+/* dseis [3][nrec][nt] of the model perturbation (dlam, dmu, drho), from rest,
+ * for the forward loop of orc_forward with the medium already set on s. */
+int orc_tangent(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
+                const double *comp, const double *wavelet, int nrec, const double *rpos,
+                const double *dlam, const double *dmu, const double *drho, double *dseis) {
+    if (s->boundary == BND_CPML) return -3;
+    long nx = s->nx, ny = s->ny, nz = s->nz, n = s->n;
+    orc_sim *t = orc_create(nx, ny, nz, s->h[0], s->h[1], s->h[2]);
+    /* the tangent propagates with the base medium and boundary */
+    memcpy(t->bx, s->bx, sizeof(double) * n); memcpy(t->by, s->by, sizeof(double) * n);
+    memcpy(t->bz, s->bz, sizeof(double) * n); memcpy(t->lam, s->lam, sizeof(double) * n);
+    memcpy(t->lp2m, s->lp2m, sizeof(double) * n); memcpy(t->mxy, s->mxy, sizeof(double) * n);
+    memcpy(t->mxz, s->mxz, sizeof(double) * n); memcpy(t->myz, s->myz, sizeof(double) * n);
+    t->boundary = s->boundary; t->width = s->width;
+    for (int a = 0; a < 3; ++a) {
+        long na = a == 0 ? nx : a == 1 ? ny : nz;
+        memcpy(t->g[a], s->g[a], sizeof(double) * na);
+    }
+    /* medium perturbations at the staggered points (the means of reading R4) */
+    double *dbx = zalloc(n), *dby = zalloc(n), *dbz = zalloc(n), *dl2m = zalloc(n);
+    double *dmxy = zalloc(n), *dmxz = zalloc(n), *dmyz = zalloc(n);
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(s, i, j, k);
+                long ip = clampi(i + 1, nx), jp = clampi(j + 1, ny), kp = clampi(k + 1, nz);
+                dbx[c] = -s->bx[c] * s->bx[c] * 0.5 * (drho[c] + drho[IDX(s, ip, j, k)]);
+                dby[c] = -s->by[c] * s->by[c] * 0.5 * (drho[c] + drho[IDX(s, i, jp, k)]);
+                dbz[c] = -s->bz[c] * s->bz[c] * 0.5 * (drho[c] + drho[IDX(s, i, j, kp)]);
+                dl2m[c] = dlam[c] + 2.0 * dmu[c];
+                dmxy[c] = 0.25 * (dmu[c] + dmu[IDX(s, ip, j, k)] + dmu[IDX(s, i, jp, k)] + dmu[IDX(s, ip, jp, k)]);
+                dmxz[c] = 0.25 * (dmu[c] + dmu[IDX(s, ip, j, k)] + dmu[IDX(s, i, j, kp)] + dmu[IDX(s, ip, j, kp)]);
+                dmyz[c] = 0.25 * (dmu[c] + dmu[IDX(s, i, jp, k)] + dmu[IDX(s, i, j, kp)] + dmu[IDX(s, i, jp, kp)]);
+            }
+    for (int q = 0; q < NFIELD; ++q) memset(s->f[q], 0, sizeof(double) * n);
+    double *tmp = (double *)malloc(sizeof(double) * 3 * (nrec > 0 ? nrec : 1));
+    double vol = s->h[0] * s->h[1] * s->h[2];
+    const double *db[3] = {dbx, dby, dbz};
+    int rc = 0;
+    for (int it = 0; it < nt && rc == 0; ++it) {
+        /* velocity: base terms of the tangent first (they use sigma^n), then the base step */
+        velocity_update(t, dt);
+        velocity_tangent_extra(s, t, dt, dbx, dby, dbz);
+        if (src_kind == 1)
+            for (int q = 0; q < 3; ++q) {
+                long idx[8]; double w[8];
+                if (!trilinear(s, q, pos, idx, w)) { rc = -1; break; }
+                for (int m = 0; m < 8; ++m)
+                    if (idx[m] >= 0) t->f[q][idx[m]] += w[m] * dt * db[q][idx[m]] * comp[q] * wavelet[it] / vol;
+            }
+        apply_sponge(t, VX, VZ + 1);
+        if (rc == 0 && orc_step_velocity(s, dt, src_kind, pos, comp, wavelet[it]) != 0) rc = -1;
+        if (rc == 0 && nrec > 0) {
+            if (orc_sample(t, nrec, rpos, tmp) != 0) { rc = -2; break; }
+            for (int q = 0; q < 3; ++q)
+                for (int r = 0; r < nrec; ++r)
+                    dseis[((long)q * nrec + r) * nt + it] = tmp[q * nrec + r];
+        }
+        /* stress: the tangent uses v' of the base (already stepped) */
+        if (rc == 0) {
+            stress_update(t, dt);
+            stress_tangent_extra(s, t, dt, dlam, dl2m, dmxy, dmxz, dmyz);
+            apply_sponge(t, SXX, SYZ + 1);
+            if (orc_step_stress(s, dt, src_kind, pos, comp, wavelet[it]) != 0) rc = -1;
+        }
+    }
+    free(tmp);
+    free(dbx); free(dby); free(dbz); free(dl2m); free(dmxy); free(dmxz); free(dmyz);
+    orc_destroy(t);
+    return rc;
+}

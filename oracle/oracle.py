@@ -75,6 +75,8 @@ def lib():
             L.orc_energy.argtypes = [P, P]
             L.orc_gradient.restype = I
             L.orc_gradient.argtypes = [P, I, D, I, P, P, P, I, P, P, I, P, P, P]
+            L.orc_tangent.restype = I
+            L.orc_tangent.argtypes = [P, I, D, I, P, P, P, I, P, P, P, P, P]
             _lib = L
     return _lib
 
@@ -228,6 +230,29 @@ def gradient(prob, sadj, ckpt_every=0, nt=None, medium=None):
     if rc != 0:
         raise ValueError(f"oracle gradient failed ({rc})")
     return g.reshape(3, s.nz, s.ny, s.nx)
+
+
+def tangent(prob, dmodel, nt=None, medium=None):
+    """Seismogram perturbation [3][nrec][nt] of the model perturbation
+    dmodel = (dlambda, dmu, drho) (forward-mode derivative of the loop),
+    FP64.  `medium` optionally overrides (lambda, mu, rho)."""
+    nt = prob.nt if nt is None else nt
+    s = OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
+    if medium is None:
+        s.set_medium_vel(prob.vp, prob.vs, prob.rho)
+    else:
+        s.set_medium_lame(*medium)
+    s.set_boundary(prob.boundary, prob.width, prob.dt, prob.f0)
+    k, p, c = s._src(prob.src_kind, prob.src_pos, prob.src_comp)
+    w = np.ascontiguousarray(prob.wavelet, np.float64)
+    r = np.ascontiguousarray(prob.rec_pos, np.float64).reshape(-1, 3)
+    d = [np.ascontiguousarray(a, np.float64).reshape(-1) for a in dmodel]
+    out = np.zeros((3, r.shape[0], nt))
+    rc = s._L.orc_tangent(s._h, int(nt), float(prob.dt), k, _p(p), _p(c), _p(w), r.shape[0],
+                          _p(r), _p(d[0]), _p(d[1]), _p(d[2]), _p(out))
+    if rc != 0:
+        raise ValueError(f"oracle tangent failed ({rc})")
+    return out
 
 
 def run_problem(prob, nt=None, state=None, boundary=None, snap_every=0, snap_mask=0,

@@ -93,3 +93,36 @@ def test_cpml_adjoint_is_refused(orc):
     p = synth.small_problem(12, 12, 12, nt=10, boundary="cpml", width=3)
     with pytest.raises(ValueError):
         orc.gradient(p, np.zeros((3, p.rec_pos.shape[0], p.nt)))
+
+
+@pytest.mark.parametrize("boundary", ["none", "sponge"])
+@pytest.mark.parametrize("kind", ["moment", "force"])
+def test_dot_product_with_the_tangent_model(orc, boundary, kind):
+    """<J dm, A> = <dm, J^T A>: the oracle's adjoint gradient against its
+    tangent-linear (forward-mode) model, to rounding, per parameter."""
+    p, m, A, _ = _setup(orc, boundary, kind, seed=17)
+    g = orc.gradient(p, A, ckpt_every=13, medium=m)
+    rng = np.random.default_rng(23)
+    for idx in range(3):
+        dm = [np.zeros_like(m[0]) for _ in range(3)]
+        dm[idx] = rng.standard_normal(m[0].shape) * np.abs(m[idx]).mean()
+        ds = orc.tangent(p, dm, medium=m)
+        lhs = float(np.sum(ds * A))
+        rhs = float(np.sum(dm[idx] * g[idx]))
+        assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs)), (idx, lhs, rhs)
+
+
+def test_tangent_matches_finite_differences(orc):
+    """The tangent model itself against central differences of the forward."""
+    p, m, A, L = _setup(orc, "sponge", "force", seed=29)
+    rng = np.random.default_rng(31)
+    dm = [rng.standard_normal(m[0].shape) * np.abs(a).mean() for a in m]
+    ds = orc.tangent(p, dm, medium=m)
+    h = 1e-5
+    def run(sign):
+        s = orc.OracleSim(p.nx, p.ny, p.nz, p.spacing)
+        s.set_medium_lame(*[a + sign * h * d for a, d in zip(m, dm)])
+        s.set_boundary("sponge", p.width, p.dt, p.f0)
+        return s.forward(p.nt, p.dt, p.src_kind, p.src_pos, p.src_comp, p.wavelet, p.rec_pos)
+    fd = (run(1) - run(-1)) / (2 * h)
+    assert np.linalg.norm(ds - fd) <= 1e-6 * np.linalg.norm(fd)
