@@ -943,11 +943,11 @@ ews_status ews_advance(ews_sim* s, int n0, int nsteps, double dt, float* seis, i
         if (herr & 3)
             return fail(EWS_ETIMEOUT, "a pipeline wait in the stencil kernels gave up (flags %d)",
                         herr);
-        if (herr & 16)
-            return fail(EWS_ENONFINITE, "a receiver recorded NaN or Inf in steps %d..%d: the "
-                                        "wavefield is not finite", n0, n0 + nsteps - 1);
-        return fail(EWS_ERANGE, "a wavefield value exceeded the FP16 range: lower the field "
-                                "scales (ews_set_field_scales)");
+        if (herr & 4)   // an FP16 overflow is the cause of any Inf the receivers saw
+            return fail(EWS_ERANGE, "a wavefield value exceeded the FP16 range: lower the "
+                                    "field scales (ews_set_field_scales)");
+        return fail(EWS_ENONFINITE, "a receiver recorded NaN or Inf in steps %d..%d: the "
+                                    "wavefield is not finite", n0, n0 + nsteps - 1);
     }
     if (s->profiling && (st = collect_profile(s)) != EWS_OK) return st;
     return EWS_OK;
