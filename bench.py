@@ -68,6 +68,10 @@ def parse_args():
     ap.add_argument("--batch-grad-shots", type=int, default=12,
                     help="shots of it run forward + gradient (first k; the gradient "
                          "state of all 48 at once does not fit one GPU)")
+    ap.add_argument("--no-free-surface", action="store_true",
+                    help="skip the free-surface (vacuum formulation) timing")
+    ap.add_argument("--fs-nt", type=int, default=200,
+                    help="time steps timed with and without the free surface")
     ap.add_argument("--no-storage", action="store_true",
                     help="skip the FP32 / BF16 / FP16 storage comparison")
     ap.add_argument("--storage-nt", type=int, default=40,
@@ -368,6 +372,8 @@ def run_ours(args, world, rank, local):
         out["batch"] = batch_report(args, local)
     if not args.no_sweep:
         out["paper_sweep"] = paper_sweep(args, local)
+    if not args.no_free_surface:
+        out["free_surface"] = free_surface_report(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
     sim.close()
@@ -619,6 +625,44 @@ def paper_sweep(args, local):
                         f"{args.sweep_nt} timed steps per level",
             "paper_hardware": "AMD Ryzen 7 4700U integrated Vega GPU, OpenGL (context only)",
             "levels": rows}
+
+
+def free_surface_report(args, local):
+    """The main workload with a vacuum free surface on the plane below the
+    top damping zone (ks = W; the paper's surface boundary, Sec. 2.5) and
+    the receivers on it, timed beside the same workload without it."""
+    import torch
+    from paper_2112_15071_gb300 import ews, synth
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    rows = {}
+    for fs in (False, True):
+        p = synth.config2(n=args.n, nt=args.fs_nt)
+        if fs:
+            ks = p.width
+            p.free_surface = (ks, 1e-3)
+            p.rec_pos = p.rec_pos.copy()
+            p.rec_pos[:, 2] = (ks - 0.5) * p.spacing[2]
+        sim = ews.simulation_for(p)
+        sim.set_stream(stream.cuda_stream)
+        seis = torch.zeros((3, sim.nrec, p.nt), device=dev)
+        sim.run(p.nt, p.dt, seis)                     # warm-up (graph capture)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.run(p.nt, p.dt, seis)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        rows["surface" if fs else "plain"] = {
+            "gcells": round(p.ncell * p.nt / (ms / 1e3) / 1e9, 3),
+            "ms_per_step": round(ms / p.nt, 4)}
+        sim.close()
+    rows["ratio"] = round(rows["surface"]["gcells"] / rows["plain"]["gcells"], 4)
+    rows["workload"] = (f"{args.n}^3 C-PML workload, {args.fs_nt} timed steps; surface at "
+                        "ks = W (vacuum eps = 1e-3 above), receivers on the surface plane")
+    return rows
 
 
 # --- reference arm: the FP64 oracle on the host cores -------------------------

@@ -121,6 +121,22 @@ ews_status ews_set_model_lame(ews_sim* sim, const float* lam, const float* mu,
 ews_status ews_set_model_vel(ews_sim* sim, const float* vp, const float* vs,
                              const float* rho, int on_device);
 
+/* Free surface by the vacuum formulation (Sec. 2.5, surface boundary):
+ * the cells above plane ks (k < ks) take eps times lambda, mu and rho of the
+ * cell (i, j, ks) below the surface in their column (the values the model
+ * arrays hold there are ignored); the shear modulus at the xz and yz shear
+ * points on the surface plane z = (ks - 1/2) dz is the harmonic mean of
+ * their 4 cells (arithmetic means elsewhere); and every z-derivative whose
+ * Eq. 4 stencil would take samples on both sides of that plane uses the
+ * 2nd-order difference (f(+1/2) - f(-1/2)) / dz instead: outputs at
+ * integer z on planes ks-1 and ks, at half-integer z on planes ks-2 .. ks.  ks < 0 removes the surface; 0 <= ks < nz; eps in
+ * (0, 1] (1e-3 is a usual value).  The damping of the top face still
+ * applies, so the surface is normally placed at or below it (ks >= width).
+ * The medium must be set (again) after this call: until then runs return
+ * EWS_ESTATE.  Forward runs and batched forward shots support the surface;
+ * gradients return EWS_EINVAL. */
+ews_status ews_set_free_surface(ews_sim* sim, int ks, double eps);
+
 /* Point source.  kind MOMENT: comp = (Mxx, Myy, Mzz, Mxy, Mxz, Myz) in N m
  * (Sec. 3.1.1, Eq. 7 gives such a tensor); each step n the stress pass does
  * sigma_ij -= dt M_ij wavelet[n] / (dx dy dz), spread over the 8 trilinear

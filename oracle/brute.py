@@ -22,27 +22,36 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def staggered_weights() -> np.ndarray:
-    """Weights w of f'(0) ~ sum_m w_m f(o_m) / h, o = (-3/2, -1/2, 1/2, 3/2),
-    exact for polynomials of degree <= 3 (solve the moment conditions)."""
-    o = np.array([-1.5, -0.5, 0.5, 1.5])
-    A = np.vstack([o ** p for p in range(4)])
-    rhs = np.array([0.0, 1.0, 0.0, 0.0])
+def staggered_weights(offsets=(-1.5, -0.5, 0.5, 1.5)) -> np.ndarray:
+    """Weights w of f'(0) ~ sum_m w_m f(o_m) / h on the given offsets, exact
+    for polynomials of the highest degree they allow (solve the moment
+    conditions).  Four offsets give Eq. 4; two give the 2nd-order difference
+    the free surface of Sec. 2.5 switches to."""
+    o = np.asarray(offsets, np.float64)
+    A = np.vstack([o ** p for p in range(o.size)])
+    rhs = np.zeros(o.size)
+    rhs[1] = 1.0
     return np.linalg.solve(A, rhs)
 
 
-def d1(n: int, h: float, shifted_output: bool) -> sp.csr_matrix:
+def d1(n: int, h: float, shifted_output: bool, surface: float | None = None) -> sp.csr_matrix:
     """1-D staggered derivative, n x n, zero outside the grid.
 
     shifted_output=True : input on integer points, output at i + 1/2.
     shifted_output=False: input on half points (element m at m + 1/2),
                           output at integer point i.
+    surface: position (in cells) of a free-surface plane; an output whose
+    four taps lie on both sides of it uses the two inner taps only.
     """
-    w = staggered_weights()
+    wide = (-1.5, -0.5, 0.5, 1.5)
     rows, cols, vals = [], [], []
     for i in range(n):
         out_pos = i + 0.5 if shifted_output else float(i)
-        for m, off in enumerate((-1.5, -0.5, 0.5, 1.5)):
+        offs = wide
+        if surface is not None and out_pos + wide[0] < surface < out_pos + wide[-1]:
+            offs = (-0.5, 0.5)
+        w = staggered_weights(offs)
+        for m, off in enumerate(offs):
             in_pos = out_pos + off
             col = int(round(in_pos)) if shifted_output else int(round(in_pos - 0.5))
             if 0 <= col < n:
@@ -77,7 +86,13 @@ class Brute:
     }
     NAMES = ("vx", "vy", "vz", "sxx", "syy", "szz", "sxy", "sxz", "syz")
 
-    def __init__(self, nx, ny, nz, spacing, lam, mu, rho):
+    def __init__(self, nx, ny, nz, spacing, lam, mu, rho, surface=None):
+        """surface: optional (ks, eps), a free surface by the vacuum
+        formulation of Sec. 2.5: the cells above plane ks get eps times the
+        medium of the cell below the surface in their column, the xz / yz
+        shear points on the plane z = ks - 1/2 take the harmonic mean of
+        their 4 cells, and the z-derivatives whose stencil straddles that
+        plane drop to 2nd order."""
         self.nx, self.ny, self.nz = nx, ny, nz
         self.h = spacing
         self.N = nx * ny * nz
@@ -92,12 +107,19 @@ class Brute:
         self.Mx = kron3(Iz, Iy, d1(nx, hx, False))
         self.Py = kron3(Iz, d1(ny, hy, True), Ix)
         self.My = kron3(Iz, d1(ny, hy, False), Ix)
-        self.Pz = kron3(d1(nz, hz, True), Iy, Ix)
-        self.Mz = kron3(d1(nz, hz, False), Iy, Ix)
+        zs = None if surface is None else surface[0] - 0.5
+        self.Pz = kron3(d1(nz, hz, True, zs), Iy, Ix)
+        self.Mz = kron3(d1(nz, hz, False, zs), Iy, Ix)
 
-        lam = np.asarray(lam, np.float64).ravel()
-        mu = np.asarray(mu, np.float64).ravel()
-        rho = np.asarray(rho, np.float64).ravel()
+        arrs = []
+        for a in (lam, mu, rho):
+            a = np.array(a, np.float64).reshape(nz, ny, nx)
+            if surface is not None:
+                ks, eps = surface
+                a[:ks] = eps * a[ks]
+            arrs.append(a.ravel())
+        lam, mu, rho = arrs
+        self._rho = rho
         Ax = kron3(Iz, Iy, avg1(nx))
         Ay = kron3(Iz, avg1(ny), Ix)
         Az = kron3(avg1(nz), Iy, Ix)
@@ -105,6 +127,13 @@ class Brute:
         self.lam = lam
         self.mu = mu
         self.mu_s = {"sxy": Ax @ (Ay @ mu), "sxz": Ax @ (Az @ mu), "syz": Ay @ (Az @ mu)}
+        if surface is not None and surface[0] >= 1:
+            # harmonic means on the surface plane: 4 / (sum of 1/mu) is the
+            # reciprocal of the arithmetic mean of 1/mu
+            on = (np.arange(self.N) // (nx * ny)) == surface[0] - 1
+            inv = 1.0 / mu
+            for key, A in (("sxz", Ax @ Az), ("syz", Ay @ Az)):
+                self.mu_s[key] = np.where(on, 1.0 / (A @ inv), self.mu_s[key])
         self.gain = np.ones(self.N)
         self.pml = None
         self.f = {k: np.zeros(self.N) for k in self.NAMES}
@@ -228,12 +257,10 @@ class Brute:
             self.f[k] = np.asarray(st[q], np.float64).ravel().copy()
 
 
-def from_velocities(nx, ny, nz, spacing, vp, vs, rho) -> Brute:
+def from_velocities(nx, ny, nz, spacing, vp, vs, rho, surface=None) -> Brute:
     vp = np.asarray(vp, np.float64)
     vs = np.asarray(vs, np.float64)
     rho = np.asarray(rho, np.float64)
     mu = rho * vs ** 2
     lam = rho * vp ** 2 - 2 * mu
-    b = Brute(nx, ny, nz, spacing, lam, mu, rho)
-    b.set_rho_cells(rho)
-    return b
+    return Brute(nx, ny, nz, spacing, lam, mu, rho, surface)

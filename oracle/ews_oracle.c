@@ -43,6 +43,15 @@
  *   R8  moment source: sigma_ij -= dt M_ij s_n / (dx dy dz), spread by the
  *       transposed trilinear weights on the sigma_ij grid; force source:
  *       v_i += dt b F_i s_n / (dx dy dz) on the v_i grid.
+ *   R16 free surface (Sec. 2.5, vacuum formulation): cells above plane ks
+ *       hold eps times lambda, mu and rho of cell (i, j, ks) below them
+ *       ("low values"); the shear modulus at the xz and yz shear points on
+ *       the surface plane z = ks - 1/2 is the harmonic mean of its 4 cells
+ *       (the vacuum formulation's averaging; the arithmetic mean there
+ *       couples light vacuum points to the rock and is unstable); a
+ *       z-difference whose Eq. 4 taps (z0 +- 1/2, z0 +- 3/2) would lie on
+ *       both sides of the surface plane takes the 2nd-order form
+ *       (f(z0 + 1/2) - f(z0 - 1/2)) / dz instead.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -75,6 +84,9 @@ typedef struct orc_sim {
     double *g[3];                    /* 1-D sponge profiles */
     double *pa[3], *pb[3];           /* 1-D C-PML coefficients */
     double *psi[18];                 /* C-PML memory variables (full size) */
+    /* free surface (reading R16): first cell plane below it, -1 without */
+    long fs;
+    double fs_eps;
 } orc_sim;
 
 static inline long IDX(const orc_sim *s, long i, long j, long k) {
@@ -88,6 +100,15 @@ static inline double fetch(const orc_sim *s, const double *f, long i, long j, lo
     return f[IDX(s, i, j, k)];
 }
 
+/* Reading R16: does a z-difference at output position z0 (in cells) take
+ * the 2nd-order form?  Yes when its outer taps z0 - 3/2 and z0 + 3/2 lie on
+ * both sides of the surface plane ks - 1/2. */
+static inline int second_order_z(const orc_sim *s, double z0) {
+    if (s->fs < 0) return 0;
+    double zs = (double)s->fs - 0.5;
+    return z0 - 1.5 < zs && zs < z0 + 1.5;
+}
+
 /* Eq. 4 evaluated at a half-integer position (index + 1/2) along axis a:
  * samples at index-1, index, index+1, index+2 (positions -3/2 .. +3/2). */
 static inline double d_plus(const orc_sim *s, const double *f, int a, long i, long j, long k) {
@@ -96,6 +117,7 @@ static inline double d_plus(const orc_sim *s, const double *f, int a, long i, lo
     double f0 = fetch(s, f, i, j, k);
     double fp1 = fetch(s, f, i + di, j + dj, k + dk);
     double fp2 = fetch(s, f, i + 2 * di, j + 2 * dj, k + 2 * dk);
+    if (a == 2 && second_order_z(s, (double)k + 0.5)) return (fp1 - f0) / s->h[a];
     return (ORC_C1 * (fp1 - f0) + ORC_C2 * (fp2 - fm1)) / s->h[a];
 }
 
@@ -107,6 +129,7 @@ static inline double d_minus(const orc_sim *s, const double *f, int a, long i, l
     double fm1 = fetch(s, f, i - di, j - dj, k - dk);
     double f0 = fetch(s, f, i, j, k);
     double fp1 = fetch(s, f, i + di, j + dj, k + dk);
+    if (a == 2 && second_order_z(s, (double)k)) return (f0 - fm1) / s->h[a];
     return (ORC_C1 * (f0 - fm1) + ORC_C2 * (fp1 - fm2)) / s->h[a];
 }
 
@@ -130,7 +153,15 @@ orc_sim *orc_create(long nx, long ny, long nz, double dx, double dy, double dz) 
         for (long i = 0; i < dims[a]; ++i) s->g[a][i] = 1.0;
     }
     s->boundary = BND_NONE;
+    s->fs = -1;
     return s;
+}
+
+/* Reading R16.  ks < 0: no surface.  Takes effect at the next
+ * orc_set_medium, which overwrites the medium above plane ks. */
+void orc_set_free_surface(orc_sim *s, long ks, double eps) {
+    s->fs = ks;
+    s->fs_eps = eps;
 }
 
 void orc_destroy(orc_sim *s) {
@@ -145,9 +176,28 @@ void orc_destroy(orc_sim *s) {
 
 /* Effective medium at the staggered points (Sec. 2.2.1, reading R4).
  * Input: Lame parameters and density per cell, [nz][ny][nx]. */
-void orc_set_medium(orc_sim *s, const double *lam, const double *mu, const double *rho) {
+void orc_set_medium(orc_sim *s, const double *lam_in, const double *mu_in,
+                    const double *rho_in) {
     long nx = s->nx, ny = s->ny, nz = s->nz;
     double vpmax = 0.0;
+    /* vacuum above a free surface (reading R16): eps times the column's
+     * medium at plane ks */
+    double *lam = zalloc(s->n), *mu = zalloc(s->n), *rho = zalloc(s->n);
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(s, i, j, k);
+                if (s->fs >= 0 && k < s->fs) {
+                    long b = IDX(s, i, j, s->fs);
+                    lam[c] = s->fs_eps * lam_in[b];
+                    mu[c] = s->fs_eps * mu_in[b];
+                    rho[c] = s->fs_eps * rho_in[b];
+                } else {
+                    lam[c] = lam_in[c];
+                    mu[c] = mu_in[c];
+                    rho[c] = rho_in[c];
+                }
+            }
     for (long k = 0; k < nz; ++k)
         for (long j = 0; j < ny; ++j)
             for (long i = 0; i < nx; ++i) {
@@ -166,10 +216,19 @@ void orc_set_medium(orc_sim *s, const double *lam, const double *mu, const doubl
                                     + mu[IDX(s, ip, j, kp)]);
                 s->myz[c] = 0.25 * (mu[c] + mu[IDX(s, i, jp, k)] + mu[IDX(s, i, j, kp)]
                                     + mu[IDX(s, i, jp, kp)]);
+                if (s->fs >= 1 && k == s->fs - 1) {
+                    /* shear points on the surface plane (reading R16):
+                     * harmonic mean of the 4 cells around them */
+                    s->mxz[c] = 4.0 / (1.0 / mu[c] + 1.0 / mu[IDX(s, ip, j, k)]
+                                       + 1.0 / mu[IDX(s, i, j, kp)] + 1.0 / mu[IDX(s, ip, j, kp)]);
+                    s->myz[c] = 4.0 / (1.0 / mu[c] + 1.0 / mu[IDX(s, i, jp, k)]
+                                       + 1.0 / mu[IDX(s, i, j, kp)] + 1.0 / mu[IDX(s, i, jp, kp)]);
+                }
                 double vp = sqrt((lam[c] + 2.0 * mu[c]) / rho[c]);
                 if (vp > vpmax) vpmax = vp;
             }
     s->vpmax = vpmax;
+    free(lam); free(mu); free(rho);
 }
 
 double orc_vpmax(const orc_sim *s) { return s->vpmax; }
@@ -497,7 +556,7 @@ static void grad_q(const orc_sim *s, double *const q[3], long i, long j, long k,
 int orc_gradient(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                  const double *comp, const double *wavelet, int nrec, const double *rpos,
                  const double *sadj, int ckpt_every, double *g_lam, double *g_mu, double *g_rho) {
-    if (s->boundary == BND_CPML) return -3;
+    if (s->boundary == BND_CPML || s->fs >= 0) return -3;
     const long N = s->n, nx = s->nx, ny = s->ny, nz = s->nz;
     const int K = ckpt_every > 0 ? ckpt_every : nt;
     const int nck = (nt + K - 1) / K;
@@ -720,7 +779,7 @@ static void stress_tangent_extra(const orc_sim *base, orc_sim *t, double dt, con
 int orc_tangent(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                 const double *comp, const double *wavelet, int nrec, const double *rpos,
                 const double *dlam, const double *dmu, const double *drho, double *dseis) {
-    if (s->boundary == BND_CPML) return -3;
+    if (s->boundary == BND_CPML || s->fs >= 0) return -3;
     long nx = s->nx, ny = s->ny, nz = s->nz, n = s->n;
     orc_sim *t = orc_create(nx, ny, nz, s->h[0], s->h[1], s->h[2]);
     /* the tangent propagates with the base medium and boundary */

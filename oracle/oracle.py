@@ -55,6 +55,7 @@ def lib():
             L.orc_create.argtypes = [L_, L_, L_, D, D, D]
             L.orc_destroy.argtypes = [P]
             L.orc_set_medium.argtypes = [P, P, P, P]
+            L.orc_set_free_surface.argtypes = [P, L_, D]
             L.orc_vpmax.restype = D
             L.orc_vpmax.argtypes = [P]
             L.orc_set_boundary.argtypes = [P, I, I, D, D, D, D]
@@ -113,6 +114,11 @@ class OracleSim:
             self._h = None
 
     # --- medium -------------------------------------------------------
+    def set_free_surface(self, ks: int, eps: float = 1e-3):
+        """Vacuum free surface above plane ks (reading R16); ks < 0 removes
+        it.  Takes effect at the next set_medium_*."""
+        self._L.orc_set_free_surface(self._h, int(ks), float(eps))
+
     def set_medium_lame(self, lam, mu, rho):
         arrs = [np.ascontiguousarray(a, np.float64).reshape(-1) for a in (lam, mu, rho)]
         for a in arrs:
@@ -260,6 +266,8 @@ def run_problem(prob, nt=None, state=None, boundary=None, snap_every=0, snap_mas
     """Run a ``synth.Problem`` through the oracle; returns seis [3][nrec][nt]."""
     nt = prob.nt if nt is None else nt
     s = OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
+    if prob.free_surface is not None:
+        s.set_free_surface(*prob.free_surface)
     s.set_medium_vel(prob.vp, prob.vs, prob.rho)
     s.set_boundary(boundary or prob.boundary, prob.width, prob.dt, prob.f0)
     if state is not None:

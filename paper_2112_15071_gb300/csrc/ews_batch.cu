@@ -166,7 +166,7 @@ struct Entry {
 
 // Run the programs of `shots` in one persistent launch.
 ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector<Stage>>& progs,
-                          int bnd, bool grad, int ctas_per_sm, int* d_err, cudaStream_t st,
+                          int bnd, int exec, int ctas_per_sm, int* d_err, cudaStream_t st,
                           float* ms_out, unsigned long long wait_ns = 0, bool stall = false) {
     const int ns = (int)shots.size();
     std::vector<Entry> all;
@@ -202,7 +202,7 @@ ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector
     int dev = 0, sms = 0, per_sm = 0;
     BCK(cudaGetDevice(&dev));
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BCK(batch_occupancy(bnd, grad, &per_sm));
+    BCK(batch_occupancy(bnd, exec, &per_sm));
     if (per_sm < 1) return report(EWS_ECUDA, "batched executor does not fit on an SM");
     if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
 
@@ -230,7 +230,7 @@ ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector
     if (e == cudaSuccess && ms_out) e = cudaEventCreate(&t1);
     if (e == cudaSuccess && ms_out) e = cudaEventRecord(t0, st);
     if (e == cudaSuccess)
-        e = launch_batch(bnd, grad, sms * per_sm, d_shots, d_ent, nent, d_cnt, d_cnt + 1, d_done,
+        e = launch_batch(bnd, exec, sms * per_sm, d_shots, d_ent, nent, d_cnt, d_cnt + 1, d_done,
                          d_err, wait_ns ? wait_ns : 4000000000ull, st);
     if (e == cudaSuccess && ms_out) e = cudaEventRecord(t1, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -254,9 +254,9 @@ ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
 
-ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, bool grad, int ctas,
+ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, int exec, int ctas,
                        int* d_err, cudaStream_t st, int* out) {
-    const auto key = std::make_tuple(s->g.nx, s->g.ny, s->g.nz, bnd, grad ? 1 : 0);
+    const auto key = std::make_tuple(s->g.nx, s->g.ny, s->g.nz, bnd, exec);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -283,8 +283,8 @@ ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, bool grad,
         std::vector<std::vector<Stage>> progs(1);
         for (int n = 0; n < T; ++n) push_step(progs[0], shots[0], n, -1, false);
         float ms = 0, ms2 = 0;
-        if ((r = run_persistent(shots, progs, bnd, grad, ctas, d_err, st, &ms)) != EWS_OK) return r;
-        if ((r = run_persistent(shots, progs, bnd, grad, ctas, d_err, st, &ms2)) != EWS_OK) return r;
+        if ((r = run_persistent(shots, progs, bnd, exec, ctas, d_err, st, &ms)) != EWS_OK) return r;
+        if ((r = run_persistent(shots, progs, bnd, exec, ctas, d_err, st, &ms2)) != EWS_OK) return r;
         ms = std::min(ms, ms2);
         if (ms < best_ms) {
             best_ms = ms;
@@ -306,7 +306,10 @@ int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int gradient) {
     if (!grid) return 0;
     std::lock_guard<std::mutex> lk(ews::g_tune_mu);
     auto it = ews::g_tuned.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary,
-                                                gradient ? 1 : 0));
+                                                gradient ? (int)ews::BX_GRAD : (int)ews::BX_LEAN));
+    if (it == ews::g_tuned.end() && !gradient)      // grids with a free surface
+        it = ews::g_tuned.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary,
+                                               (int)ews::BX_LEAN_FS));
     return it == ews::g_tuned.end() ? 0 : it->second;
 }
 
@@ -322,7 +325,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         return report(EWS_EINVAL, "negative batch option");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int bnd = shots[0].sim ? shots[0].sim->opt.boundary : -1;
-    bool grad = false;
+    bool grad = false, any_fs = false;
     for (int i = 0; i < nshots; ++i) {
         const ews_batch_shot& b = shots[i];
         ews_sim* s = b.sim;
@@ -342,6 +345,9 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         if (r != EWS_OK) return r;
         if (b.observed && s->has_fluid)
             return report(EWS_EINVAL, "shot %d: fluid cells (mu = 0) are not batched", i);
+        if (b.observed && s->g.fs != kNoSurface)
+            return report(EWS_EINVAL, "shot %d: gradients with a free surface are not built", i);
+        if (s->g.fs != kNoSurface) any_fs = true;
     }
     const int K0 = o.ckpt_every > 0 ? o.ckpt_every : 50;
 
@@ -383,7 +389,8 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         }
         int zc = o.zchunk;
         if (zc == 0) {
-            ews_status r = tune_zchunk(s, b, bnd, false, o.ctas_per_sm, d_err, st, &zc);
+            ews_status r = tune_zchunk(s, b, bnd, s->g.fs != kNoSurface ? BX_LEAN_FS : BX_LEAN,
+                                       o.ctas_per_sm, d_err, st, &zc);
             if (r != EWS_OK) return r;
         }
         ews_status r = fill_shot(bs[i], s, b, zc, d_err, b.observed != nullptr);
@@ -396,10 +403,10 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         }
     }
     const unsigned long long wait = (unsigned long long)o.dep_wait_ms * 1000000ull;
-    ews_status r = run_persistent(bs, progs, bnd, false, o.ctas_per_sm, d_err, st, nullptr, wait,
-                                  o.test_unsatisfiable != 0);
+    ews_status r = run_persistent(bs, progs, bnd, any_fs ? BX_LEAN_FS : BX_LEAN, o.ctas_per_sm,
+                                  d_err, st, nullptr, wait, o.test_unsatisfiable != 0);
     if (r == EWS_OK && grad)
-        r = run_persistent(bs, rprogs, bnd, true, o.ctas_per_sm, d_err, st, nullptr, wait, false);
+        r = run_persistent(bs, rprogs, bnd, BX_GRAD, o.ctas_per_sm, d_err, st, nullptr, wait, false);
     if (r != EWS_OK) return r;
     for (int i = 0; i < nshots; ++i) {
         ews_sim* s = shots[i].sim;

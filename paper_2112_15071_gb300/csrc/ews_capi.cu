@@ -210,6 +210,8 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
     if ((st = copy_field_in(s, (float*)M.lam, a, on_device)) != EWS_OK) return st;
     if ((st = copy_field_in(s, (float*)M.mu, b, on_device)) != EWS_OK) return st;
     if ((st = copy_field_in(s, (float*)M.rho, rho, on_device)) != EWS_OK) return st;
+    CK(launch_vacuum(s->g, (float*)M.lam, (float*)M.mu, (float*)M.rho, from_vel,
+                     (float)s->fs_eps, s->stream));
     CK(cudaMemsetAsync(s->flags, 0, 5 * sizeof(unsigned), s->stream));
     CK(cudaMemsetAsync(s->flags + 2, 0x7F, 2 * sizeof(unsigned), s->stream));   // min slots: 3.4e38
     CK(launch_medium_setup(s->g, (float*)M.lam, (float*)M.mu, (float*)M.rho, from_vel,
@@ -483,6 +485,8 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     if (s->opt.boundary == EWS_BOUNDARY_CPML)
         return fail(EWS_EINVAL, "the adjoint supports the none and sponge boundaries");
     if (!s->wide()) return fail(EWS_EINVAL, "the adjoint needs F32 wavefield storage");
+    if (s->g.fs != kNoSurface)
+        return fail(EWS_EINVAL, "the adjoint of the free-surface differences is not built");
     const int K = ckpt_every > 0 ? (ckpt_every < nt ? ckpt_every : nt) : (nt < 50 ? nt : 50);
     const int nck = (nt + K - 1) / K;
     const size_t fs = s->fstride;
@@ -752,6 +756,8 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
     g.c2y = (float)(kC2 / grid->dy);
     g.c1z = (float)(kC1 / grid->dz);
     g.c2z = (float)(kC2 / grid->dz);
+    g.fs = kNoSurface;
+    g.c1z2 = (float)(1.0 / grid->dz);
     s->fstride = (size_t)((g.plane * g.nz + 63) / 64 * 64);
     s->es = o.storage == EWS_STORAGE_F32 ? 4 : 2;
     s->B.kind = o.boundary;
@@ -868,6 +874,18 @@ ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const doubl
     for (int a = 0; a < 3; ++a) sp.pos[a] = pos[a];
     for (int c = 0; c < 6; ++c) sp.comp[c] = c < nc ? comp[c] : 0.0;
     s->S.kind = kind;
+    return EWS_OK;
+}
+
+ews_status ews_set_free_surface(ews_sim* s, int ks, double eps) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (ks >= s->g.nz) return fail(EWS_EINVAL, "surface plane %d outside the grid (nz = %d)", ks, s->g.nz);
+    if (ks >= 0 && !(eps > 0.0 && eps <= 1.0))
+        return fail(EWS_EINVAL, "vacuum fraction %g outside (0, 1]", eps);
+    s->g.fs = ks < 0 ? kNoSurface : ks;
+    s->fs_eps = ks < 0 ? 0.0 : eps;
+    s->model_set = false;          // the medium above the surface must be set again
+    s->gen++;
     return EWS_OK;
 }
 

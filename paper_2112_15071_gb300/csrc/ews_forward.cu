@@ -93,8 +93,10 @@ __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int fr
         if (flag == 0) {
             vp = sqrtf((lam + 2.0f * mu) / r);
             zp = sqrtf(r * (lam + 2.0f * mu));
-            rmin = r;
-            if (mu > 0.0f) zsmin = sqrtf(r * mu);
+            if (k >= g.fs) {                   // the medium below a free surface
+                rmin = r;
+                if (mu > 0.0f) zsmin = sqrtf(r * mu);
+            }
             if (mu == 0.0f) flag |= 16u;       // a fluid cell (not an error)
         }
     }
@@ -131,6 +133,22 @@ __global__ void k_medium_setup(DevGrid g, float* a, float* b, float* rho, int fr
         atomicMin(flags + 3, __float_as_uint(zsmin));
         atomicMax(flags + 4, __float_as_uint(zp));
     }
+}
+
+// Vacuum formulation of the free surface (Sec. 2.5 reading): every cell
+// above plane ks takes eps times the Lame parameters and density of the
+// first cell below the surface in its column.  Velocity input (vp, vs, rho):
+// the speeds are kept and rho is scaled, which gives the same Lame values.
+__global__ void k_vacuum(DevGrid g, float* a, float* b, float* rho, int from_vel, float eps) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.fs) return;
+    const long long c = (long long)k * g.plane + (long long)j * g.pitch + i;
+    const long long src = (long long)g.fs * g.plane + (long long)j * g.pitch + i;
+    rho[c] = eps * rho[src];
+    a[c] = from_vel ? a[src] : eps * a[src];
+    b[c] = from_vel ? b[src] : eps * b[src];
 }
 
 }  // namespace
@@ -174,6 +192,14 @@ cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps,
             k_record<float><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, 1.f, 1.f, 1.f, err);
             break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vacuum(const DevGrid& g, float* a, float* b, float* rho, int from_velocities,
+                          float eps, cudaStream_t st) {
+    if (g.fs <= 0 || g.fs >= g.nz) return cudaSuccess;
+    const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.fs);
+    k_vacuum<<<grid, dim3(32, 8), 0, st>>>(g, a, b, rho, from_velocities, eps);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,32 @@ struct DevGrid {
     long long plane;      // elements per z-plane = pitch * ny
     // Eq. 4 weights divided by the axis spacing (reading: the 1/h factor)
     float c1x, c2x, c1y, c2y, c1z, c2z;
+    // free surface (Sec. 2.5, vacuum formulation): plane index ks of the
+    // first cell below the surface (kNoSurface without one) and the weight
+    // 1/dz of the 2nd-order z-difference used next to it
+    int fs;
+    float c1z2;
 };
+constexpr int kNoSurface = -(1 << 28);
+
+// z-difference weights at output plane k (free-surface reading): a
+// z-derivative whose Eq. 4 stencil would take samples on both sides of the
+// surface plane z = (ks - 1/2) dz uses the 2nd-order difference: outputs at
+// integer z (planes ks-1, ks) and at half-integer z (planes ks-2 .. ks).
+// Without a surface (FS false) callers use the DevGrid weights directly.
+struct ZW {
+    float c1i, c2i, c1h, c2h;
+};
+template <bool FS>
+__host__ __device__ __forceinline__ ZW zweights(const DevGrid& g, int k) {
+    if constexpr (FS) {
+        const bool i2 = (unsigned)(k - g.fs + 1) < 2u;
+        const bool h2 = (unsigned)(k - g.fs + 2) < 3u;
+        return ZW{i2 ? g.c1z2 : g.c1z, i2 ? 0.0f : g.c2z, h2 ? g.c1z2 : g.c1z, h2 ? 0.0f : g.c2z};
+    } else {
+        return ZW{0.0f, 0.0f, 0.0f, 0.0f};   // callers take the DevGrid weights
+    }
+}
 
 struct DevFields {
     float* f[NFIELD];
@@ -219,16 +244,21 @@ struct alignas(64) BatchShot {
 };
 static constexpr int kBatchElem = 8192;   // cells per elementwise work item
 
-// Launch the executor over `nentries` entries (device tables; the counters
-// cur/taken/done start at zero).  grid: CTAs to launch; grad: whether any
-// stage uses the reverse modes (larger slots).  err bits: 1 / 2 stencil
-// waits, 8 a dependency wait gave up.
-cudaError_t launch_batch(int bnd, bool grad, int grid, const BatchShot* shots,
+// Executor forms: the lean one (forward stages, 3 CTAs per SM), the one with
+// the reverse passes (larger slots, 2 per SM), and the lean one whose passes
+// take the free-surface z-differences (grids with a surface; the others
+// unchanged).
+enum { BX_LEAN = 0, BX_GRAD = 1, BX_LEAN_FS = 2 };
+
+// Launch the executor `exec` over `nentries` entries (device tables; the
+// counters cur/taken/done start at zero).  grid: CTAs to launch.  err bits:
+// 1 / 2 stencil waits, 8 a dependency wait gave up.
+cudaError_t launch_batch(int bnd, int exec, int grid, const BatchShot* shots,
                          const BatchEntry* entries, int nentries, unsigned* cur,
                          unsigned* taken, unsigned long long* done, int* err,
                          unsigned long long wait_ns, cudaStream_t st);
 // CTAs per SM the executor achieves (sets its shared-memory attribute).
-cudaError_t batch_occupancy(int bnd, bool grad, int* per_sm);
+cudaError_t batch_occupancy(int bnd, int exec, int* per_sm);
 // The plan's tensor maps and pass parameters, for a BatchShot.
 void stencil_plan_export(const StencilPlan* p, Maps* vmaps, Maps* smaps, int* ntx, int* nty,
                          int* zchunk, int* items);
@@ -278,7 +308,12 @@ cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps,
                           float* seis, int ld, int n, int storage, const float inv[3], int* err,
                           cudaStream_t st);
 // flags[0]: validity bits (bit4: some mu == 0); flags[1..4]: float bits of max vp, min rho,
-// min sqrt(rho mu) over cells with mu > 0 (else FLT_MAX), max sqrt(rho (lambda + 2 mu)).
+// min sqrt(rho mu) over cells with mu > 0 (else FLT_MAX), max sqrt(rho (lambda + 2 mu));
+// the two minima only over cells below a free surface.
+// launch_vacuum: the cells above the free surface g.fs take eps times the medium
+// of the cell below the surface (raw input arrays, before launch_medium_setup).
+cudaError_t launch_vacuum(const DevGrid& g, float* a, float* b, float* rho, int from_velocities,
+                          float eps, cudaStream_t st);
 cudaError_t launch_medium_setup(const DevGrid& g, float* a, float* b, float* rho,
                                 int from_velocities, unsigned* flags, cudaStream_t st);
 // One field between its stored form (pitched, `storage` type, scaled by s)

@@ -172,6 +172,8 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
     g.c2y = (float)(-1.0 / 24.0 / gr.dy);
     g.c1z = (float)(9.0 / 8.0 / gr.dz);
     g.c2z = (float)(-1.0 / 24.0 / gr.dz);
+    g.fs = kNoSurface;
+    g.c1z2 = (float)(1.0 / gr.dz);
     DevFields F;
     for (int q = 0; q < NFIELD; ++q) F.f[q] = base + kOffFields + q * (size_t)kMaxCells;
     float* mlam = base + kOffMedium;

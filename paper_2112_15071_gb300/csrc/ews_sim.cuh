@@ -47,6 +47,7 @@ struct ews_sim {
     bool model_set = false;
     float vpmax = 0.0f;
     float rho_min = 0.0f, zs_min = 0.0f, zp_max = 0.0f;   // medium bounds
+    double fs_eps = 0.0;          // vacuum fraction above the free surface (g.fs)
     bool has_fluid = false;       // some cell has mu == 0
     // per-field storage scales (16-bit storage holds scale[q] x value)
     float scale[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};

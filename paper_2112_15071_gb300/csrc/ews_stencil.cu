@@ -371,7 +371,7 @@ struct VelQ {
 
 // One arrival of the z-loop, ring position PH = m mod 4.  Returns false if
 // the CTA must stop (a wait gave up).
-template <int BND, typename T, int MODE, int PH>
+template <int BND, typename T, int MODE, int PH, bool FS>
 __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, VelQ& Q, unsigned char* sm,
                                          uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
@@ -436,6 +436,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         const float* hr1 = (const float*)(sl1 + L::V_RHO) + G.hf;   // plane k + 1
         const T* vc = (const T*)(sl2 + L::V_CORE) + G.cc;
         const bool ktop = k + 1 < g.nz;
+        const ZW zw = zweights<FS>(g, k);   // used only with a free surface
         const long long o = (long long)k * g.plane + G.obase;
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
@@ -447,15 +448,15 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             // vx at (i+1/2, j, k)
             float dxx = g.c1x * (F(hxx, R + 1) - F(hxx, R)) + g.c2x * (F(hxx, R + 2) - F(hxx, R - 1));
             float dxy = g.c1y * (F(hxy, R) - F(hxy, R - HX)) + g.c2y * (F(hxy, R + HX) - F(hxy, R - 2 * HX));
-            float dxz = g.c1z * (qxz[C] - qxz[B]) + g.c2z * (qxz[D] - qxz[A]);
+            float dxz = (FS ? zw.c1i : g.c1z) * (qxz[C] - qxz[B]) + (FS ? zw.c2i : g.c2z) * (qxz[D] - qxz[A]);
             // vy at (i, j+1/2, k)
             float dyx = g.c1x * (F(hxy, R) - F(hxy, R - 1)) + g.c2x * (F(hxy, R + 1) - F(hxy, R - 2));
             float dyy = g.c1y * (F(hyy, R + HX) - F(hyy, R)) + g.c2y * (F(hyy, R + 2 * HX) - F(hyy, R - HX));
-            float dyz = g.c1z * (qyz[C] - qyz[B]) + g.c2z * (qyz[D] - qyz[A]);
+            float dyz = (FS ? zw.c1i : g.c1z) * (qyz[C] - qyz[B]) + (FS ? zw.c2i : g.c2z) * (qyz[D] - qyz[A]);
             // vz at (i, j, k+1/2)
             float dzx = g.c1x * (F(hxz, R) - F(hxz, R - 1)) + g.c2x * (F(hxz, R + 1) - F(hxz, R - 2));
             float dzy = g.c1y * (F(hyz, R) - F(hyz, R - HX)) + g.c2y * (F(hyz, R + HX) - F(hyz, R - 2 * HX));
-            float dzz = g.c1z * (qzz[C] - qzz[B]) + g.c2z * (qzz[D] - qzz[A]);
+            float dzz = (FS ? zw.c1h : g.c1z) * (qzz[C] - qzz[B]) + (FS ? zw.c2h : g.c2z) * (qzz[D] - qzz[A]);
             if constexpr (kScaled<T>) {     // stored -> physical units
                 dxx *= P.inv[SXX]; dxy *= P.inv[SXY]; dxz *= P.inv[SXZ];
                 dyx *= P.inv[SXY]; dyy *= P.inv[SYY]; dyz *= P.inv[SYZ];
@@ -565,7 +566,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
 
 // One (tile, z-chunk) of the velocity pass; the ring barriers must be freshly
 // initialised.  Returns false if a wait gave up (the error is recorded).
-template <int BND, typename T, int MODE>
+template <int BND, typename T, int MODE, bool FS = false>
 __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, int item,
                                          unsigned char* sm, uint64_t* bars) {
     constexpr int SB = slot_bytes<T, MODE>();
@@ -584,24 +585,24 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!vel_step<BND, T, MODE, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
-        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
-        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
-        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
+        if (!vel_step<BND, T, MODE, 0, FS>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
+        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1, FS>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
+        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2, FS>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
+        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3, FS>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
     return true;
 }
 
-template <int BND, typename T, int MODE>
+template <int BND, typename T, int MODE, bool FS = false>
 __global__ void __launch_bounds__(NTH, (min_blocks<BND, T, MODE>())) k_velocity(
     const __grid_constant__ Maps maps, const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int SB = slot_bytes<T, MODE>();
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB + (BND == BND_CPML ? PSI_BYTES : 0));
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    vel_tile<BND, T, MODE>(maps, P, (int)blockIdx.x, sm, bars);
+    vel_tile<BND, T, MODE, FS>(maps, P, (int)blockIdx.x, sm, bars);
 }
 
 // ------------------------------------------------------------------------------
@@ -614,7 +615,7 @@ struct StrQ {
     float vx[ROWS][4], vy[ROWS][4], vz[ROWS][4];   // vx/vy k-1..k+2, vz k-2..k+1
 };
 
-template <int BND, typename T, int PH>
+template <int BND, typename T, int PH, bool FS>
 __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, StrQ& Q, unsigned char* sm,
                                          uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
@@ -650,6 +651,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
         const float* lc = (const float*)(sl2 + L::S_LAM) + G.cc;
         const T* cr = (const T*)(sl2 + L::S_CORE) + G.cc;
         const long long o = (long long)k * g.plane + G.obase;
+        const ZW zw = zweights<FS>(g, k);   // used only with a free surface
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
             if (!G.own[rr]) continue;
@@ -660,13 +662,13 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
             // normal strain rates at (i, j, k)
             float exx = g.c1x * (F(hvx, R) - F(hvx, R - 1)) + g.c2x * (F(hvx, R + 1) - F(hvx, R - 2));
             float eyy = g.c1y * (F(hvy, R) - F(hvy, R - HX)) + g.c2y * (F(hvy, R + HX) - F(hvy, R - 2 * HX));
-            float ezz = g.c1z * (qvz[C] - qvz[B]) + g.c2z * (qvz[D] - qvz[A]);
+            float ezz = (FS ? zw.c1i : g.c1z) * (qvz[C] - qvz[B]) + (FS ? zw.c2i : g.c2z) * (qvz[D] - qvz[A]);
             // shear terms at the shear points
             float vxy = g.c1y * (F(hvx, R + HX) - F(hvx, R)) + g.c2y * (F(hvx, R + 2 * HX) - F(hvx, R - HX));
             float vyx = g.c1x * (F(hvy, R + 1) - F(hvy, R)) + g.c2x * (F(hvy, R + 2) - F(hvy, R - 1));
-            float vxz = g.c1z * (qvx[C] - qvx[B]) + g.c2z * (qvx[D] - qvx[A]);
+            float vxz = (FS ? zw.c1h : g.c1z) * (qvx[C] - qvx[B]) + (FS ? zw.c2h : g.c2z) * (qvx[D] - qvx[A]);
             float vzx = g.c1x * (F(hvz, R + 1) - F(hvz, R)) + g.c2x * (F(hvz, R + 2) - F(hvz, R - 1));
-            float vyz = g.c1z * (qvy[C] - qvy[B]) + g.c2z * (qvy[D] - qvy[A]);
+            float vyz = (FS ? zw.c1h : g.c1z) * (qvy[C] - qvy[B]) + (FS ? zw.c2h : g.c2z) * (qvy[D] - qvy[A]);
             float vzy = g.c1y * (F(hvz, R + HX) - F(hvz, R)) + g.c2y * (F(hvz, R + 2 * HX) - F(hvz, R - HX));
             if constexpr (kScaled<T>) {     // stored -> physical units
                 exx *= P.inv[VX]; vxy *= P.inv[VX]; vxz *= P.inv[VX];
@@ -698,8 +700,16 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
             const float mu0 = hmu[RF], mxp = hmu[RF + G.cx], myp = hmu[RF + cyr];
             const float mzp = hmu1[RF];
             const float mxy = 0.25f * (mu0 + mxp + myp + hmu[RF + G.cx + cyr]);
-            const float mxz = 0.25f * (mu0 + mxp + mzp + hmu1[RF + G.cx]);
-            const float myz = 0.25f * (mu0 + myp + mzp + hmu1[RF + cyr]);
+            float mxz = 0.25f * (mu0 + mxp + mzp + hmu1[RF + G.cx]);
+            float myz = 0.25f * (mu0 + myp + mzp + hmu1[RF + cyr]);
+            if constexpr (FS) {
+                // xz / yz shear points on the free-surface plane z = ks - 1/2:
+                // harmonic mean of the 4 cells (vacuum-formulation reading)
+                if (k == g.fs - 1) {
+                    mxz = 4.0f / (1.0f / mu0 + 1.0f / mxp + 1.0f / mzp + 1.0f / hmu1[RF + G.cx]);
+                    myz = 4.0f / (1.0f / mu0 + 1.0f / myp + 1.0f / mzp + 1.0f / hmu1[RF + cyr]);
+                }
+            }
             const float l2m = lam + 2.0f * mu0;
             float s0 = F(cr, SC_SXX * CORE + rr * TX) + P.dto[SXX] * (l2m * exx + lam * (eyy + ezz));
             float s1 = F(cr, SC_SYY * CORE + rr * TX) + P.dto[SYY] * (l2m * eyy + lam * (exx + ezz));
@@ -740,7 +750,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
     return true;
 }
 
-template <int BND, typename T>
+template <int BND, typename T, bool FS = false>
 __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, int item,
                                          unsigned char* sm, uint64_t* bars) {
     const Geo<BND, T> G(P, item);
@@ -755,24 +765,24 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!str_step<BND, T, 0>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
-        if (m + 1 < G.P4 && !str_step<BND, T, 1>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
-        if (m + 2 < G.P4 && !str_step<BND, T, 2>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
-        if (m + 3 < G.P4 && !str_step<BND, T, 3>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
+        if (!str_step<BND, T, 0, FS>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
+        if (m + 1 < G.P4 && !str_step<BND, T, 1, FS>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
+        if (m + 2 < G.P4 && !str_step<BND, T, 2, FS>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
+        if (m + 3 < G.P4 && !str_step<BND, T, 3, FS>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
     return true;
 }
 
-template <int BND, typename T>
+template <int BND, typename T, bool FS = false>
 __global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_stress(const __grid_constant__ Maps maps,
                                                                       const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(
         sm + NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0));
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    str_tile<BND, T>(maps, P, (int)blockIdx.x, sm, bars);
+    str_tile<BND, T, FS>(maps, P, (int)blockIdx.x, sm, bars);
 }
 
 // ------------------------------------------------------------------------------
@@ -844,7 +854,7 @@ struct ItemBox {
     }
 };
 
-template <int BND, bool GRAD>
+template <int BND, bool GRAD, bool FS = false>
 __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
     k_batch(const BatchShot* __restrict__ shots, const BatchEntry* __restrict__ entries,
             int nentries, unsigned* cur, unsigned* taken, unsigned long long* done, int* err,
@@ -934,11 +944,11 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                 }
                 ring_rearm(bars, tid);
                 if (E.kind == BK_VEL)
-                    ok = vel_tile<BND, float, M_FWD>(B.vf, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_FWD, FS>(B.vf, sP, it, sm, bars);
                 else if (E.kind == BK_VEL_CAP)
-                    ok = vel_tile<BND, float, M_CAP>(B.vf, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_CAP, FS>(B.vf, sP, it, sm, bars);
                 else if (E.kind == BK_STR)
-                    ok = str_tile<BND, float>(B.sf, sP, it, sm, bars);
+                    ok = str_tile<BND, float, FS>(B.sf, sP, it, sm, bars);
                 else if (E.kind == BK_STR_ADJ)
                     ok = str_tile<BND, float>(B.sa, sP, it, sm, bars);
                 else if constexpr (GRAD)
@@ -1108,8 +1118,12 @@ cudaError_t occupancy(int* occ) {
     int a = 0, b = 0, c = 0;
     cudaError_t e = prepare(k_velocity<BND, T, M_FWD>, smem_bytes<BND, T>(), &a);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T>, smem_bytes<BND, T>(), &b);
+    // free-surface variants: same slots, occupancy taken from the plain ones
+    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, true>, smem_bytes<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_stress<BND, T, true>, smem_bytes<BND, T>(), &c);
     if constexpr (std::is_same<T, float>::value) {     // history and reverse modes
         if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP>, smem_bytes<BND, T, M_CAP>(), &c);
+        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP, true>, smem_bytes<BND, T, M_CAP>(), &c);
         if constexpr (BND != BND_CPML)
             if (e == cudaSuccess)
                 e = prepare(k_velocity<BND, T, M_GRAD>, smem_bytes<BND, T, M_GRAD>(), &c);
@@ -1237,37 +1251,52 @@ PassParams pass_params(const StencilPlan* sp, const DevGrid& g, const DevFields&
     return P;
 }
 
-template <typename T, int MODE = M_FWD>
-void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
+template <typename T, int MODE, bool FS>
+void launch_v_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     dim3 blk(TX, RY);
     switch (sp->kind) {
         case BND_SPONGE:
-            k_velocity<BND_SPONGE, T, MODE><<<sp->grid, blk, smem_bytes<BND_SPONGE, T, MODE>(), st>>>(sp->vmaps, P);
+            k_velocity<BND_SPONGE, T, MODE, FS><<<sp->grid, blk, smem_bytes<BND_SPONGE, T, MODE>(), st>>>(sp->vmaps, P);
             break;
         case BND_CPML:
             if constexpr (MODE != M_GRAD)
-                k_velocity<BND_CPML, T, MODE><<<sp->grid, blk, smem_bytes<BND_CPML, T, MODE>(), st>>>(sp->vmaps, P);
+                k_velocity<BND_CPML, T, MODE, FS><<<sp->grid, blk, smem_bytes<BND_CPML, T, MODE>(), st>>>(sp->vmaps, P);
             break;
         default:
-            k_velocity<BND_NONE, T, MODE><<<sp->grid, blk, smem_bytes<BND_NONE, T, MODE>(), st>>>(sp->vmaps, P);
+            k_velocity<BND_NONE, T, MODE, FS><<<sp->grid, blk, smem_bytes<BND_NONE, T, MODE>(), st>>>(sp->vmaps, P);
+            break;
+    }
+}
+
+// The reverse (M_GRAD) pass has no free-surface form: the host rejects
+// gradients of grids with a surface.
+template <typename T, int MODE = M_FWD>
+void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
+    if constexpr (MODE != M_GRAD)
+        if (P.g.fs != kNoSurface) return launch_v_fs<T, MODE, true>(sp, P, st);
+    launch_v_fs<T, MODE, false>(sp, P, st);
+}
+
+template <typename T, bool FS>
+void launch_s_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
+    dim3 blk(TX, RY);
+    switch (sp->kind) {
+        case BND_SPONGE:
+            k_stress<BND_SPONGE, T, FS><<<sp->grid, blk, smem_bytes<BND_SPONGE, T>(), st>>>(sp->smaps, P);
+            break;
+        case BND_CPML:
+            k_stress<BND_CPML, T, FS><<<sp->grid, blk, smem_bytes<BND_CPML, T>(), st>>>(sp->smaps, P);
+            break;
+        default:
+            k_stress<BND_NONE, T, FS><<<sp->grid, blk, smem_bytes<BND_NONE, T>(), st>>>(sp->smaps, P);
             break;
     }
 }
 
 template <typename T>
 void launch_s(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
-    dim3 blk(TX, RY);
-    switch (sp->kind) {
-        case BND_SPONGE:
-            k_stress<BND_SPONGE, T><<<sp->grid, blk, smem_bytes<BND_SPONGE, T>(), st>>>(sp->smaps, P);
-            break;
-        case BND_CPML:
-            k_stress<BND_CPML, T><<<sp->grid, blk, smem_bytes<BND_CPML, T>(), st>>>(sp->smaps, P);
-            break;
-        default:
-            k_stress<BND_NONE, T><<<sp->grid, blk, smem_bytes<BND_NONE, T>(), st>>>(sp->smaps, P);
-            break;
-    }
+    if (P.g.fs != kNoSurface) return launch_s_fs<T, true>(sp, P, st);
+    launch_s_fs<T, false>(sp, P, st);
 }
 
 }  // namespace
@@ -1359,36 +1388,58 @@ constexpr size_t batch_smem() {
            8 * (NSLOT + 1);
 }
 
-template <int BND, bool GRAD>
+template <int BND, bool GRAD, bool FS>
 cudaError_t batch_prepare(int* per_sm) {
-    return prepare(k_batch<BND, GRAD>, batch_smem<BND, GRAD>(), per_sm);
+    return prepare(k_batch<BND, GRAD, FS>, batch_smem<BND, GRAD>(), per_sm);
 }
 
-cudaError_t batch_occupancy(int bnd, bool grad, int* per_sm) {
-    if (bnd == BND_SPONGE) return grad ? batch_prepare<BND_SPONGE, true>(per_sm) : batch_prepare<BND_SPONGE, false>(per_sm);
-    if (bnd == BND_NONE) return grad ? batch_prepare<BND_NONE, true>(per_sm) : batch_prepare<BND_NONE, false>(per_sm);
+template <int BND>
+cudaError_t batch_occupancy_b(int exec, int* per_sm) {
+    switch (exec) {
+        case BX_LEAN: return batch_prepare<BND, false, false>(per_sm);
+        case BX_GRAD: return batch_prepare<BND, true, false>(per_sm);
+        case BX_LEAN_FS: return batch_prepare<BND, false, true>(per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t batch_occupancy(int bnd, int exec, int* per_sm) {
+    if (bnd == BND_SPONGE) return batch_occupancy_b<BND_SPONGE>(exec, per_sm);
+    if (bnd == BND_NONE) return batch_occupancy_b<BND_NONE>(exec, per_sm);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batch(int bnd, bool grad, int grid, const BatchShot* shots,
+template <int BND, bool GRAD, bool FS>
+void batch_go(int grid, const BatchShot* shots, const BatchEntry* entries, int nentries,
+              unsigned* cur, unsigned* taken, unsigned long long* done, int* err,
+              unsigned long long wait_ns, cudaStream_t st) {
+    k_batch<BND, GRAD, FS><<<grid, dim3(TX, RY), batch_smem<BND, GRAD>(), st>>>(
+        shots, entries, nentries, cur, taken, done, err, wait_ns);
+}
+
+template <int BND>
+cudaError_t launch_batch_b(int exec, int grid, const BatchShot* shots, const BatchEntry* entries,
+                           int nentries, unsigned* cur, unsigned* taken,
+                           unsigned long long* done, int* err, unsigned long long wait_ns,
+                           cudaStream_t st) {
+    switch (exec) {
+        case BX_LEAN: batch_go<BND, false, false>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
+        case BX_GRAD: batch_go<BND, true, false>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
+        case BX_LEAN_FS: batch_go<BND, false, true>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(int bnd, int exec, int grid, const BatchShot* shots,
                          const BatchEntry* entries, int nentries, unsigned* cur,
                          unsigned* taken, unsigned long long* done, int* err,
                          unsigned long long wait_ns, cudaStream_t st) {
-    const dim3 blk(TX, RY);
-    if (bnd == BND_SPONGE) {
-        if (grad)
-            k_batch<BND_SPONGE, true><<<grid, blk, batch_smem<BND_SPONGE, true>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
-        else
-            k_batch<BND_SPONGE, false><<<grid, blk, batch_smem<BND_SPONGE, false>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
-    } else if (bnd == BND_NONE) {
-        if (grad)
-            k_batch<BND_NONE, true><<<grid, blk, batch_smem<BND_NONE, true>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
-        else
-            k_batch<BND_NONE, false><<<grid, blk, batch_smem<BND_NONE, false>(), st>>>(shots, entries, nentries, cur, taken, done, err, wait_ns);
-    } else {
-        return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    if (bnd == BND_SPONGE)
+        return launch_batch_b<BND_SPONGE>(exec, grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st);
+    if (bnd == BND_NONE)
+        return launch_batch_b<BND_NONE>(exec, grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st);
+    return cudaErrorInvalidValue;
 }
 
 void stencil_plan_export(const StencilPlan* p, Maps* vmaps, Maps* smaps, int* ntx, int* nty,

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("ews_set_model_vel", _I, [_P, _P, _P, _P, _I]),
     ("ews_set_source", _I, [_P, _I, _P, _P, _P, _I]),
     ("ews_set_receivers", _I, [_P, _I, _P]),
+    ("ews_set_free_surface", _I, [_P, _I, _D]),
     ("ews_run", _I, [_P, _I, _D, _P, _I, _P]),
     ("ews_advance", _I, [_P, _I, _I, _D, _P, _I, _I]),
     ("ews_reset", _I, [_P]),
@@ -212,6 +213,10 @@ def ews_set_receivers(sim, pos):
     r = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
     _check(load().ews_set_receivers(sim, int(r.shape[0]),
                                     r.ctypes.data_as(C.c_void_p) if r.size else None))
+
+
+def ews_set_free_surface(sim, ks: int, eps: float = 1e-3):
+    _check(load().ews_set_free_surface(sim, int(ks), float(eps)))
 
 
 def ews_run(sim, nt: int, dt: float, seis, snapshots=None):
@@ -415,6 +420,10 @@ class Simulation:
         ews_set_source(self._h, SOURCE[kind] if isinstance(kind, str) else kind, pos, comp,
                        wavelet)
 
+    def set_free_surface(self, ks, eps=1e-3):
+        """Vacuum free surface above plane ks (set the model afterwards)."""
+        ews_set_free_surface(self._h, ks, eps)
+
     def set_receivers(self, pos):
         ews_set_receivers(self._h, pos)
         self.nrec = int(np.asarray(pos).reshape(-1, 3).shape[0])
@@ -477,6 +486,8 @@ def simulation_for(prob, **kw) -> Simulation:
     """Simulation set up from a ``synth.Problem`` (model, source, receivers)."""
     sim = Simulation(prob.nx, prob.ny, prob.nz, prob.spacing, boundary=prob.boundary,
                      width=prob.width, f0=prob.f0, **kw)
+    if prob.free_surface is not None:
+        sim.set_free_surface(*prob.free_surface)
     sim.set_model_vel(prob.vp, prob.vs, prob.rho)
     sim.set_source(prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet)
     sim.set_receivers(prob.rec_pos)

@@ -248,6 +248,7 @@ class Problem:
     width: int = 16
     f0: float = 10.0
     extra: dict = field(default_factory=dict)
+    free_surface: tuple | None = None   # (ks, eps): vacuum above plane ks
 
     @property
     def ncell(self) -> int:
