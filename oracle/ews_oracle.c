@@ -526,11 +526,16 @@ double orc_energy(const orc_sim *s, const double *vprev) {
  * (the sponge gain is diagonal, so its transpose is itself).  The forward
  * step n is
  *     V: v' = G (v + dt B Dsig(sigma) + f_n),   R: s_n = S v',
- *     T: sigma' = G (sigma + dt C Dv(v') - m_n),
- * with Dv = -Dsig^T (zero exterior).  Going back through T then V:
- *     w = G a_sig;  g_C += dt Dv(v') (x) w;  a_v += -dt Dsig(C w) + S^T sadj_n;
+ *     T: sigma' = G (sigma + dt C Dv(v') - m_n).
+ * Going back through T then V:
+ *     w = G a_sig;  g_C += dt Dv(v') (x) w;  a_v += dt Dv^T(C w) + S^T sadj_n;
  *     a_sig = w;  u = G a_v;  g_B += (dt Dsig(sigma) + f_n / B) (x) u;
- *     a_sig += -dt Dv(B u);  a_v = u.
+ *     a_sig += dt Dsig^T(B u);  a_v = u.
+ * The transposes are taken column by column from the differences' own
+ * weights (grad_q_T, div_tau_T), so they hold with the free-surface switch
+ * of R16 too; with the zero exterior alone Dv^T = -Dsig.  The medium chain
+ * rule follows the means of R4 (harmonic on the surface plane, R16) and
+ * folds the vacuum cells into the surface cell of their column.
  * The forward states of each segment are recomputed from checkpoints.
  * ------------------------------------------------------------------------ */
 
@@ -553,10 +558,94 @@ static void grad_q(const orc_sim *s, double *const q[3], long i, long j, long k,
     e[5] = d_plus(s, q[1], 2, i, j, k) + d_plus(s, q[2], 1, i, j, k);
 }
 
+/* Weight of the sample at offset d (cells along axis a) in the difference
+ * at output index o: d_plus (output at o + 1/2) samples o-1 .. o+2,
+ * d_minus (output at o) samples o-2 .. o+1; Eq. 4 weights, or the 2nd-order
+ * pair where reading R16 switches the z-difference. */
+static double tap_weight(const orc_sim *s, int a, int plus, long o, long d) {
+    int second = a == 2 && second_order_z(s, plus ? (double)o + 0.5 : (double)o);
+    long in0 = plus ? 0 : -1;             /* the inner samples are in0, in0 + 1 */
+    double w = 0.0;
+    if (d == in0) w = second ? -1.0 : -ORC_C1;
+    else if (d == in0 + 1) w = second ? 1.0 : ORC_C1;
+    else if (d == in0 - 1) w = second ? 0.0 : -ORC_C2;
+    else if (d == in0 + 2) w = second ? 0.0 : ORC_C2;
+    return w / s->h[a];
+}
+
+/* Transpose of d_plus (plus = 1) or d_minus (plus = 0) along axis a,
+ * applied to y and evaluated at element (i, j, k): the sum over the outputs
+ * o along a whose samples include the element, of that sample's weight
+ * times y at o (column (i, j, k) of the difference operator). */
+static double d_transpose(const orc_sim *s, const double *y, int a, int plus, long i, long j,
+                          long k) {
+    long dims[3] = {s->nx, s->ny, s->nz};
+    long p = a == 0 ? i : (a == 1 ? j : k);
+    double acc = 0.0;
+    for (long o = p - 2; o <= p + 2; ++o) {
+        if (o < 0 || o >= dims[a]) continue;
+        double w = tap_weight(s, a, plus, o, p - o);
+        if (w == 0.0) continue;
+        long oi = a == 0 ? o : i, oj = a == 1 ? o : j, ok = a == 2 ? o : k;
+        acc += w * y[IDX(s, oi, oj, ok)];
+    }
+    return acc;
+}
+
+/* Transpose of grad_q: 6 strain-like components y -> 3 velocity-like. */
+static void grad_q_T(const orc_sim *s, double *const y[6], long i, long j, long k, double out[3]) {
+    out[0] = d_transpose(s, y[0], 0, 0, i, j, k) + d_transpose(s, y[3], 1, 1, i, j, k)
+             + d_transpose(s, y[4], 2, 1, i, j, k);
+    out[1] = d_transpose(s, y[1], 1, 0, i, j, k) + d_transpose(s, y[3], 0, 1, i, j, k)
+             + d_transpose(s, y[5], 2, 1, i, j, k);
+    out[2] = d_transpose(s, y[2], 2, 0, i, j, k) + d_transpose(s, y[4], 0, 1, i, j, k)
+             + d_transpose(s, y[5], 1, 1, i, j, k);
+}
+
+/* Transpose of div_tau: 3 velocity-like components y -> 6 stress-like. */
+static void div_tau_T(const orc_sim *s, double *const y[3], long i, long j, long k, double out[6]) {
+    out[0] = d_transpose(s, y[0], 0, 1, i, j, k);
+    out[1] = d_transpose(s, y[1], 1, 1, i, j, k);
+    out[2] = d_transpose(s, y[2], 2, 1, i, j, k);
+    out[3] = d_transpose(s, y[0], 1, 0, i, j, k) + d_transpose(s, y[1], 0, 0, i, j, k);
+    out[4] = d_transpose(s, y[0], 2, 0, i, j, k) + d_transpose(s, y[2], 0, 0, i, j, k);
+    out[5] = d_transpose(s, y[1], 2, 0, i, j, k) + d_transpose(s, y[2], 1, 0, i, j, k);
+}
+
+/* mu at the cell from the stored lambda and lambda + 2 mu. */
+static double cell_mu(const orc_sim *s, long c) { return 0.5 * (s->lp2m[c] - s->lam[c]); }
+
+/* d(shear mean)/d(mu of cell m) for the 4 cells c4 of one xz or yz shear
+ * point on plane k: 1/4 (arithmetic, R4), or mean^2 / (4 mu_m^2) on the
+ * surface plane (harmonic, R16). */
+static double shear_weight(const orc_sim *s, long k, const long c4[4], int m, double mean) {
+    if (s->fs >= 1 && k == s->fs - 1) {
+        double mu = cell_mu(s, c4[m]);
+        return mean * mean / (4.0 * mu * mu);
+    }
+    return 0.25;
+}
+
+/* Reading R16: the medium above the surface is eps times the surface cell
+ * of its column, so a derivative with respect to the effective medium there
+ * belongs to that cell (times eps); the input values above it are unused. */
+static void fold_vacuum(const orc_sim *s, double *g) {
+    if (s->fs < 1) return;
+    for (long j = 0; j < s->ny; ++j)
+        for (long i = 0; i < s->nx; ++i) {
+            double sum = 0.0;
+            for (long k = 0; k < s->fs; ++k) {
+                sum += g[IDX(s, i, j, k)];
+                g[IDX(s, i, j, k)] = 0.0;
+            }
+            g[IDX(s, i, j, s->fs)] += s->fs_eps * sum;
+        }
+}
+
 int orc_gradient(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                  const double *comp, const double *wavelet, int nrec, const double *rpos,
                  const double *sadj, int ckpt_every, double *g_lam, double *g_mu, double *g_rho) {
-    if (s->boundary == BND_CPML || s->fs >= 0) return -3;
+    if (s->boundary == BND_CPML) return -3;
     const long N = s->n, nx = s->nx, ny = s->ny, nz = s->nz;
     const int K = ckpt_every > 0 ? ckpt_every : nt;
     const int nck = (nt + K - 1) / K;
@@ -625,16 +714,17 @@ int orc_gradient(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                     as[4][cc] = s->mxz[cc] * w[4][cc];
                     as[5][cc] = s->myz[cc] * w[5][cc];
                 }
+                #pragma omp parallel for
                 for (long k = 0; k < nz; ++k)
                     for (long j = 0; j < ny; ++j)
                         for (long i = 0; i < nx; ++i) {
                             long cc = IDX(s, i, j, k);
                             double dv[3];
-                            div_tau(s, as, i, j, k, dv);
+                            grad_q_T(s, as, i, j, k, dv);
                             for (int q = 0; q < 3; ++q) tmp[q][cc] = dv[q];
                         }
                 for (int q = 0; q < 3; ++q)
-                    for (long cc = 0; cc < N; ++cc) av[q][cc] -= dt * tmp[q][cc];
+                    for (long cc = 0; cc < N; ++cc) av[q][cc] += dt * tmp[q][cc];
             }
             /* receivers: a_v += S^T sadj_n */
             for (int r = 0; r < nrec; ++r)
@@ -671,16 +761,17 @@ int orc_gradient(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                             acc[5 + q][idx[m]] += wt[m] * dt * comp[q] * wavelet[n] / vol * av[q][idx[m]];
                 }
             }
+            #pragma omp parallel for
             for (long k = 0; k < nz; ++k)
                 for (long j = 0; j < ny; ++j)
                     for (long i = 0; i < nx; ++i) {
                         long cc = IDX(s, i, j, k);
                         double e[6];
-                        grad_q(s, tmp, i, j, k, e);
+                        div_tau_T(s, tmp, i, j, k, e);
                         for (int q = 0; q < 6; ++q) w[q][cc] = e[q];
                     }
             for (int q = 0; q < 6; ++q)
-                for (long cc = 0; cc < N; ++cc) as[q][cc] -= dt * w[q][cc];
+                for (long cc = 0; cc < N; ++cc) as[q][cc] += dt * w[q][cc];
         }
     }
     /* medium chain rule: lambda direct; mu normal + 1/4 of each shear mean;
@@ -696,8 +787,8 @@ int orc_gradient(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                 long yz[4] = {cc, IDX(s, i, jp, k), IDX(s, i, j, kp), IDX(s, i, jp, kp)};
                 for (int m = 0; m < 4; ++m) {
                     g_mu[xy[m]] += 0.25 * acc[2][cc];
-                    g_mu[xz[m]] += 0.25 * acc[3][cc];
-                    g_mu[yz[m]] += 0.25 * acc[4][cc];
+                    g_mu[xz[m]] += shear_weight(s, k, xz, m, s->mxz[cc]) * acc[3][cc];
+                    g_mu[yz[m]] += shear_weight(s, k, yz, m, s->myz[cc]) * acc[4][cc];
                 }
                 double bx = s->bx[cc], by = s->by[cc], bz = s->bz[cc];
                 g_rho[cc] += -0.5 * bx * bx * acc[5][cc] - 0.5 * by * by * acc[6][cc] - 0.5 * bz * bz * acc[7][cc];
@@ -705,6 +796,9 @@ int orc_gradient(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                 g_rho[IDX(s, i, jp, k)] += -0.5 * by * by * acc[6][cc];
                 g_rho[IDX(s, i, j, kp)] += -0.5 * bz * bz * acc[7][cc];
             }
+    fold_vacuum(s, g_lam);
+    fold_vacuum(s, g_mu);
+    fold_vacuum(s, g_rho);
 done:
     free(ck); free(hist);
     for (int q = 0; q < 3; ++q) { free(av[q]); free(tmp[q]); }
@@ -778,10 +872,26 @@ static void stress_tangent_extra(const orc_sim *base, orc_sim *t, double dt, con
  * for the forward loop of orc_forward with the medium already set on s. */
 int orc_tangent(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                 const double *comp, const double *wavelet, int nrec, const double *rpos,
-                const double *dlam, const double *dmu, const double *drho, double *dseis) {
-    if (s->boundary == BND_CPML || s->fs >= 0) return -3;
+                const double *dlam_in, const double *dmu_in, const double *drho_in,
+                double *dseis) {
+    if (s->boundary == BND_CPML) return -3;
     long nx = s->nx, ny = s->ny, nz = s->nz, n = s->n;
     orc_sim *t = orc_create(nx, ny, nz, s->h[0], s->h[1], s->h[2]);
+    t->fs = s->fs;
+    t->fs_eps = s->fs_eps;
+    /* perturbation of the effective medium: above a free surface, eps times
+     * the perturbation of the column's surface cell (reading R16) */
+    double *dlam = zalloc(n), *dmu = zalloc(n), *drho = zalloc(n);
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                long c = IDX(s, i, j, k);
+                long b = (s->fs >= 0 && k < s->fs) ? IDX(s, i, j, s->fs) : c;
+                double e = b == c ? 1.0 : s->fs_eps;
+                dlam[c] = e * dlam_in[b];
+                dmu[c] = e * dmu_in[b];
+                drho[c] = e * drho_in[b];
+            }
     /* the tangent propagates with the base medium and boundary */
     memcpy(t->bx, s->bx, sizeof(double) * n); memcpy(t->by, s->by, sizeof(double) * n);
     memcpy(t->bz, s->bz, sizeof(double) * n); memcpy(t->lam, s->lam, sizeof(double) * n);
@@ -805,8 +915,13 @@ int orc_tangent(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
                 dbz[c] = -s->bz[c] * s->bz[c] * 0.5 * (drho[c] + drho[IDX(s, i, j, kp)]);
                 dl2m[c] = dlam[c] + 2.0 * dmu[c];
                 dmxy[c] = 0.25 * (dmu[c] + dmu[IDX(s, ip, j, k)] + dmu[IDX(s, i, jp, k)] + dmu[IDX(s, ip, jp, k)]);
-                dmxz[c] = 0.25 * (dmu[c] + dmu[IDX(s, ip, j, k)] + dmu[IDX(s, i, j, kp)] + dmu[IDX(s, ip, j, kp)]);
-                dmyz[c] = 0.25 * (dmu[c] + dmu[IDX(s, i, jp, k)] + dmu[IDX(s, i, j, kp)] + dmu[IDX(s, i, jp, kp)]);
+                long xz[4] = {c, IDX(s, ip, j, k), IDX(s, i, j, kp), IDX(s, ip, j, kp)};
+                long yz[4] = {c, IDX(s, i, jp, k), IDX(s, i, j, kp), IDX(s, i, jp, kp)};
+                dmxz[c] = dmyz[c] = 0.0;
+                for (int m = 0; m < 4; ++m) {
+                    dmxz[c] += shear_weight(s, k, xz, m, s->mxz[c]) * dmu[xz[m]];
+                    dmyz[c] += shear_weight(s, k, yz, m, s->myz[c]) * dmu[yz[m]];
+                }
             }
     for (int q = 0; q < NFIELD; ++q) memset(s->f[q], 0, sizeof(double) * n);
     double *tmp = (double *)malloc(sizeof(double) * 3 * (nrec > 0 ? nrec : 1));
@@ -842,6 +957,7 @@ int orc_tangent(orc_sim *s, int nt, double dt, int src_kind, const double *pos,
     }
     free(tmp);
     free(dbx); free(dby); free(dbz); free(dl2m); free(dmxy); free(dmxz); free(dmyz);
+    free(dlam); free(dmu); free(drho);
     orc_destroy(t);
     return rc;
 }

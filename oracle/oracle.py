@@ -220,6 +220,8 @@ def gradient(prob, sadj, ckpt_every=0, nt=None, medium=None):
     FP64.  `medium` optionally overrides (lambda, mu, rho)."""
     nt = prob.nt if nt is None else nt
     s = OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
+    if prob.free_surface is not None:
+        s.set_free_surface(*prob.free_surface)
     if medium is None:
         s.set_medium_vel(prob.vp, prob.vs, prob.rho)
     else:
@@ -244,6 +246,8 @@ def tangent(prob, dmodel, nt=None, medium=None):
     FP64.  `medium` optionally overrides (lambda, mu, rho)."""
     nt = prob.nt if nt is None else nt
     s = OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
+    if prob.free_surface is not None:
+        s.set_free_surface(*prob.free_surface)
     if medium is None:
         s.set_medium_vel(prob.vp, prob.vs, prob.rho)
     else:

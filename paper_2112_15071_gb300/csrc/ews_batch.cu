@@ -345,8 +345,6 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         if (r != EWS_OK) return r;
         if (b.observed && s->has_fluid)
             return report(EWS_EINVAL, "shot %d: fluid cells (mu = 0) are not batched", i);
-        if (b.observed && s->g.fs != kNoSurface)
-            return report(EWS_EINVAL, "shot %d: gradients with a free surface are not built", i);
         if (s->g.fs != kNoSurface) any_fs = true;
     }
     const int K0 = o.ckpt_every > 0 ? o.ckpt_every : 50;
@@ -406,7 +404,8 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
     ews_status r = run_persistent(bs, progs, bnd, any_fs ? BX_LEAN_FS : BX_LEAN, o.ctas_per_sm,
                                   d_err, st, nullptr, wait, o.test_unsatisfiable != 0);
     if (r == EWS_OK && grad)
-        r = run_persistent(bs, rprogs, bnd, BX_GRAD, o.ctas_per_sm, d_err, st, nullptr, wait, false);
+        r = run_persistent(bs, rprogs, bnd, any_fs ? BX_GRAD_FS : BX_GRAD, o.ctas_per_sm, d_err,
+                           st, nullptr, wait, false);
     if (r != EWS_OK) return r;
     for (int i = 0; i < nshots; ++i) {
         ews_sim* s = shots[i].sim;

@@ -485,8 +485,8 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     if (s->opt.boundary == EWS_BOUNDARY_CPML)
         return fail(EWS_EINVAL, "the adjoint supports the none and sponge boundaries");
     if (!s->wide()) return fail(EWS_EINVAL, "the adjoint needs F32 wavefield storage");
-    if (s->g.fs != kNoSurface)
-        return fail(EWS_EINVAL, "the adjoint of the free-surface differences is not built");
+    if (s->g.fs != kNoSurface && s->has_fluid)
+        return fail(EWS_EINVAL, "gradients with a free surface need mu > 0 below it");
     const int K = ckpt_every > 0 ? (ckpt_every < nt ? ckpt_every : nt) : (nt < 50 ? nt : 50);
     const int nck = (nt + K - 1) / K;
     const size_t fs = s->fstride;
@@ -575,7 +575,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
                 if (s->nrec > 0 && sadj)
                     CK(launch_adj_inject(s->g, A, s->M(), s->B, s->rtaps, s->nrec, sadj, nt, m,
                                          s->stream));
-                CK(launch_stress(s->adj_plan, s->g, AF, s->B, mdt, one, s->err, s->stream));
+                CK(launch_stress(s->adj_plan, s->g, AF, s->B, mdt, one, s->err, s->stream, true));
                 if ((m - n0) % K == 0 && m > n0) CK(launch_acc_flush(s->g, A, s->stream));
             }
             CK(launch_rho_term(s->g, A, s->B, s->vhist + 3 * fs, s->vhist, (long long)fs, s->stream));
@@ -758,6 +758,7 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
     g.c2z = (float)(kC2 / grid->dz);
     g.fs = kNoSurface;
     g.c1z2 = (float)(1.0 / grid->dz);
+    g.fs_eps = 0.0f;
     s->fstride = (size_t)((g.plane * g.nz + 63) / 64 * 64);
     s->es = o.storage == EWS_STORAGE_F32 ? 4 : 2;
     s->B.kind = o.boundary;
@@ -884,6 +885,7 @@ ews_status ews_set_free_surface(ews_sim* s, int ks, double eps) {
         return fail(EWS_EINVAL, "vacuum fraction %g outside (0, 1]", eps);
     s->g.fs = ks < 0 ? kNoSurface : ks;
     s->fs_eps = ks < 0 ? 0.0 : eps;
+    s->g.fs_eps = (float)s->fs_eps;
     s->model_set = false;          // the medium above the surface must be set again
     s->gen++;
     return EWS_OK;

@@ -39,25 +39,64 @@ struct DevGrid {
     // 1/dz of the 2nd-order z-difference used next to it
     int fs;
     float c1z2;
+    float fs_eps;         // vacuum fraction above the surface
 };
 constexpr int kNoSurface = -(1 << 28);
+
+// Forms of the passes' z-differences: no free surface; the forward form
+// with a surface; the transposed form of the reverse sweep with a surface.
+enum { ZS_NONE = 0, ZS_FWD = 1, ZS_ADJ = 2 };
 
 // z-difference weights at output plane k (free-surface reading): a
 // z-derivative whose Eq. 4 stencil would take samples on both sides of the
 // surface plane z = (ks - 1/2) dz uses the 2nd-order difference: outputs at
 // integer z (planes ks-1, ks) and at half-integer z (planes ks-2 .. ks).
-// Without a surface (FS false) callers use the DevGrid weights directly.
+// c1i, c2i: integer-z outputs; c1h, c2h: half-integer-z outputs.  Without a
+// surface (FS = ZS_NONE) callers use the DevGrid weights directly.
 struct ZW {
     float c1i, c2i, c1h, c2h;
 };
-template <bool FS>
+template <int FS>
 __host__ __device__ __forceinline__ ZW zweights(const DevGrid& g, int k) {
-    if constexpr (FS) {
+    if constexpr (FS != ZS_NONE) {
         const bool i2 = (unsigned)(k - g.fs + 1) < 2u;
         const bool h2 = (unsigned)(k - g.fs + 2) < 3u;
         return ZW{i2 ? g.c1z2 : g.c1z, i2 ? 0.0f : g.c2z, h2 ? g.c1z2 : g.c1z, h2 ? 0.0f : g.c2z};
     } else {
         return ZW{0.0f, 0.0f, 0.0f, 0.0f};   // callers take the DevGrid weights
+    }
+}
+
+// Transposed z-weights at output plane k, per tap (A..D = the four samples
+// from the lowest plane up), for the reverse sweep with a surface.  The
+// transpose of the forward difference that maps half-z samples to integer-z
+// outputs is the map from integer-z samples to half-z outputs whose row k
+// holds, at each sample, the weight that sample's own output row gives to
+// plane k: an integer-z output at k (samples on half planes k-2 .. k+1)
+// takes the half-output weights of those planes, and a half-z output at k
+// (samples on integer planes k-1 .. k+2) the integer-output weights.
+struct ZT {
+    float iA, iB, iC, iD, hA, hB, hC, hD;
+};
+__host__ __device__ __forceinline__ ZT ztransposed(const DevGrid& g, int k) {
+    const ZW m2 = zweights<ZS_FWD>(g, k - 2), m1 = zweights<ZS_FWD>(g, k - 1);
+    const ZW z0 = zweights<ZS_FWD>(g, k), p1 = zweights<ZS_FWD>(g, k + 1);
+    const ZW p2 = zweights<ZS_FWD>(g, k + 2);
+    return ZT{-m2.c2h, -m1.c1h, z0.c1h, p1.c2h, -m1.c2i, -z0.c1i, p1.c1i, p2.c2i};
+}
+
+// One z-difference from the four samples a..d (lowest plane first) of an
+// integer-z (HALF false) or half-integer-z (HALF true) output.
+template <int FS, bool HALF>
+__device__ __forceinline__ float zdiff(const DevGrid& g, const ZW& zw, const ZT& zt, float a,
+                                       float b, float c, float d) {
+    if constexpr (FS == ZS_ADJ) {
+        return HALF ? zt.hA * a + zt.hB * b + zt.hC * c + zt.hD * d
+                    : zt.iA * a + zt.iB * b + zt.iC * c + zt.iD * d;
+    } else if constexpr (FS == ZS_FWD) {
+        return HALF ? zw.c1h * (c - b) + zw.c2h * (d - a) : zw.c1i * (c - b) + zw.c2i * (d - a);
+    } else {
+        return g.c1z * (c - b) + g.c2z * (d - a);
     }
 }
 
@@ -245,10 +284,10 @@ struct alignas(64) BatchShot {
 static constexpr int kBatchElem = 8192;   // cells per elementwise work item
 
 // Executor forms: the lean one (forward stages, 3 CTAs per SM), the one with
-// the reverse passes (larger slots, 2 per SM), and the lean one whose passes
-// take the free-surface z-differences (grids with a surface; the others
-// unchanged).
-enum { BX_LEAN = 0, BX_GRAD = 1, BX_LEAN_FS = 2 };
+// the reverse passes (larger slots, 2 per SM), and both again with the
+// free-surface z-differences (grids with a surface; shots without one run
+// unchanged in them).
+enum { BX_LEAN = 0, BX_GRAD = 1, BX_LEAN_FS = 2, BX_GRAD_FS = 3 };
 
 // Launch the executor `exec` over `nentries` entries (device tables; the
 // counters cur/taken/done start at zero).  grid: CTAs to launch.  err bits:
@@ -281,7 +320,7 @@ cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFi
                             int* err, cudaStream_t st);
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                           const DevBoundary& B, const float dto[9], const float inv[9],
-                          int* err, cudaStream_t st);
+                          int* err, cudaStream_t st, bool reverse = false);
 // FP32 storage only.  Velocity pass that also writes v^{n+1/2} to X.vcap:
 cudaError_t launch_velocity_cap(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                                 const DevBoundary& B, const float dto[9], const VelExtra& X,

@@ -174,6 +174,7 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
     g.c2z = (float)(-1.0 / 24.0 / gr.dz);
     g.fs = kNoSurface;
     g.c1z2 = (float)(1.0 / gr.dz);
+    g.fs_eps = 0.0f;
     DevFields F;
     for (int q = 0; q < NFIELD; ++q) F.f[q] = base + kOffFields + q * (size_t)kMaxCells;
     float* mlam = base + kOffMedium;

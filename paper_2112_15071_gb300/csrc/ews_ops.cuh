@@ -131,16 +131,33 @@ __device__ __forceinline__ void flush_cell(const AdjFields& A, long long o) {
     }
 }
 
-// Gradients of cell (i, j, k) from the transformed-variable accumulators:
+// Derivative of a 4-cell shear mean with respect to one of its cells, which
+// occurs mult times among the 4 (top edge clamped): mult / 4 for the
+// arithmetic mean; mult mean^2 / (4 mu_cell^2) for the harmonic mean of the
+// xz / yz points on a free-surface plane (reading of Sec. 2.5).
+__device__ __forceinline__ double shear_d(double mean, double mu_cell, int mult, bool harmonic) {
+    return harmonic ? mult * mean * mean / (4.0 * mu_cell * mu_cell) : 0.25 * mult;
+}
+
+// 4-cell shear mean of mu, harmonic on a free-surface plane.
+__device__ __forceinline__ double shear_mean(double a, double b, double c, double d,
+                                             bool harmonic) {
+    return harmonic ? 4.0 / (1.0 / a + 1.0 / b + 1.0 / c + 1.0 / d) : 0.25 * (a + b + c + d);
+}
+
+struct Grad3 {
+    double lam, mu, rho;
+};
+
+// Gradients with respect to the medium of cell (i, j, k) as the passes use
+// it, from the transformed-variable accumulators:
 // dJ/dlambda = acc0 / (3 lambda + 2 mu);
 // dJ/dmu = (acc1 - lambda acc0 / (3 lambda + 2 mu)) / mu + the shear sums
-//          over the 4-cell means (each point / its mean, weight 1/4, top
-//          edge clamped);
+//          over the 4-cell means (each point / its mean times the mean's
+//          derivative, top edge clamped);
 // dJ/drho = -1/2 sum over the 2-cell v points of the cell of acc5..7.
-// Output dense [nz][ny][nx].
-__device__ __forceinline__ void finalize_t_cell(const DevGrid& g, const AdjFields& A,
-                                                const DevMedium& M, float* glam, float* gmu,
-                                                float* grho, int i, int j, int k) {
+__device__ __forceinline__ Grad3 grad_t_cell(const DevGrid& g, const AdjFields& A,
+                                             const DevMedium& M, int i, int j, int k) {
     const long long o = cidx(g, i, j, k);
     const double lam = __ldg(M.lam + o), mu0 = __ldg(M.mu + o);
     const double kap = 3.0 * lam + 2.0 * mu0;
@@ -164,9 +181,10 @@ __device__ __forceinline__ void finalize_t_cell(const DevGrid& g, const AdjField
                 const int ap = min(a + 1, g.nx - 1), bp = min(b + 1, g.nz - 1);
                 const int mult = (a == i && b == k) + (ap == i && b == k) + (a == i && bp == k) + (ap == i && bp == k);
                 if (mult) {
-                    const double mb = 0.25 * ((double)med(M.mu, g, a, j, b) + med(M.mu, g, ap, j, b) +
-                                              med(M.mu, g, a, j, bp) + med(M.mu, g, ap, j, bp));
-                    mu += 0.25 * mult * A.acc64[3][cidx(g, a, j, b)] / mb;
+                    const bool h = b == g.fs - 1;
+                    const double mb = shear_mean(med(M.mu, g, a, j, b), med(M.mu, g, ap, j, b),
+                                                 med(M.mu, g, a, j, bp), med(M.mu, g, ap, j, bp), h);
+                    mu += shear_d(mb, mu0, mult, h) * A.acc64[3][cidx(g, a, j, b)] / mb;
                 }
             }
             a = j + da; b = k + db;
@@ -174,9 +192,10 @@ __device__ __forceinline__ void finalize_t_cell(const DevGrid& g, const AdjField
                 const int ap = min(a + 1, g.ny - 1), bp = min(b + 1, g.nz - 1);
                 const int mult = (a == j && b == k) + (ap == j && b == k) + (a == j && bp == k) + (ap == j && bp == k);
                 if (mult) {
-                    const double mb = 0.25 * ((double)med(M.mu, g, i, a, b) + med(M.mu, g, i, ap, b) +
-                                              med(M.mu, g, i, a, bp) + med(M.mu, g, i, ap, bp));
-                    mu += 0.25 * mult * A.acc64[4][cidx(g, i, a, b)] / mb;
+                    const bool h = b == g.fs - 1;
+                    const double mb = shear_mean(med(M.mu, g, i, a, b), med(M.mu, g, i, ap, b),
+                                                 med(M.mu, g, i, a, bp), med(M.mu, g, i, ap, bp), h);
+                    mu += shear_d(mb, mu0, mult, h) * A.acc64[4][cidx(g, i, a, b)] / mb;
                 }
             }
         }
@@ -190,10 +209,32 @@ __device__ __forceinline__ void finalize_t_cell(const DevGrid& g, const AdjField
             const int mult = (a == self) + (min(a + 1, n - 1) == self);
             if (mult) rho += -0.5 * mult * A.acc64[5 + c][cidx(g, ii, jj, kk)];
         }
+    return Grad3{a0 / kap, mu, rho};
+}
+
+// Gradients of the input model at cell (i, j, k), dense [nz][ny][nx]
+// output.  With a free surface the cells above it hold eps times the
+// surface cell of their column (reading of Sec. 2.5): their own input
+// values are unused (gradient 0) and the surface cell collects eps times
+// their gradients.
+__device__ __forceinline__ void finalize_t_cell(const DevGrid& g, const AdjFields& A,
+                                                const DevMedium& M, float* glam, float* gmu,
+                                                float* grho, int i, int j, int k) {
     const long long od = ((long long)k * g.ny + j) * g.nx + i;
-    glam[od] = (float)(a0 / kap);
-    gmu[od] = (float)mu;
-    grho[od] = (float)rho;
+    Grad3 r{0.0, 0.0, 0.0};
+    if (k >= g.fs) {
+        r = grad_t_cell(g, A, M, i, j, k);
+        if (k == g.fs)
+            for (int kk = 0; kk < k; ++kk) {
+                const Grad3 v = grad_t_cell(g, A, M, i, j, kk);
+                r.lam += g.fs_eps * v.lam;
+                r.mu += g.fs_eps * v.mu;
+                r.rho += g.fs_eps * v.rho;
+            }
+    }
+    glam[od] = (float)r.lam;
+    gmu[od] = (float)r.mu;
+    grho[od] = (float)r.rho;
 }
 
 }  // namespace ops

@@ -371,7 +371,7 @@ struct VelQ {
 
 // One arrival of the z-loop, ring position PH = m mod 4.  Returns false if
 // the CTA must stop (a wait gave up).
-template <int BND, typename T, int MODE, int PH, bool FS>
+template <int BND, typename T, int MODE, int PH, int FS>
 __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, VelQ& Q, unsigned char* sm,
                                          uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
@@ -436,7 +436,8 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         const float* hr1 = (const float*)(sl1 + L::V_RHO) + G.hf;   // plane k + 1
         const T* vc = (const T*)(sl2 + L::V_CORE) + G.cc;
         const bool ktop = k + 1 < g.nz;
-        const ZW zw = zweights<FS>(g, k);   // used only with a free surface
+        const ZW zw = zweights<FS == ZS_NONE ? ZS_NONE : ZS_FWD>(g, k);   // surface forms only
+        const ZT zt = FS == ZS_ADJ ? ztransposed(g, k) : ZT{};
         const long long o = (long long)k * g.plane + G.obase;
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
@@ -448,15 +449,15 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             // vx at (i+1/2, j, k)
             float dxx = g.c1x * (F(hxx, R + 1) - F(hxx, R)) + g.c2x * (F(hxx, R + 2) - F(hxx, R - 1));
             float dxy = g.c1y * (F(hxy, R) - F(hxy, R - HX)) + g.c2y * (F(hxy, R + HX) - F(hxy, R - 2 * HX));
-            float dxz = (FS ? zw.c1i : g.c1z) * (qxz[C] - qxz[B]) + (FS ? zw.c2i : g.c2z) * (qxz[D] - qxz[A]);
+            float dxz = zdiff<FS, false>(g, zw, zt, qxz[A], qxz[B], qxz[C], qxz[D]);
             // vy at (i, j+1/2, k)
             float dyx = g.c1x * (F(hxy, R) - F(hxy, R - 1)) + g.c2x * (F(hxy, R + 1) - F(hxy, R - 2));
             float dyy = g.c1y * (F(hyy, R + HX) - F(hyy, R)) + g.c2y * (F(hyy, R + 2 * HX) - F(hyy, R - HX));
-            float dyz = (FS ? zw.c1i : g.c1z) * (qyz[C] - qyz[B]) + (FS ? zw.c2i : g.c2z) * (qyz[D] - qyz[A]);
+            float dyz = zdiff<FS, false>(g, zw, zt, qyz[A], qyz[B], qyz[C], qyz[D]);
             // vz at (i, j, k+1/2)
             float dzx = g.c1x * (F(hxz, R) - F(hxz, R - 1)) + g.c2x * (F(hxz, R + 1) - F(hxz, R - 2));
             float dzy = g.c1y * (F(hyz, R) - F(hyz, R - HX)) + g.c2y * (F(hyz, R + HX) - F(hyz, R - 2 * HX));
-            float dzz = (FS ? zw.c1h : g.c1z) * (qzz[C] - qzz[B]) + (FS ? zw.c2h : g.c2z) * (qzz[D] - qzz[A]);
+            float dzz = zdiff<FS, true>(g, zw, zt, qzz[A], qzz[B], qzz[C], qzz[D]);
             if constexpr (kScaled<T>) {     // stored -> physical units
                 dxx *= P.inv[SXX]; dxy *= P.inv[SXY]; dxz *= P.inv[SXZ];
                 dyx *= P.inv[SXY]; dyy *= P.inv[SYY]; dyz *= P.inv[SYZ];
@@ -496,12 +497,13 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                 const float* qhz = Q.hz[rr];
                 const float exx = g.c1x * (F(vhx, R) - F(vhx, R - 1)) + g.c2x * (F(vhx, R + 1) - F(vhx, R - 2));
                 const float eyy = g.c1y * (F(vhy, R) - F(vhy, R - HX)) + g.c2y * (F(vhy, R + HX) - F(vhy, R - 2 * HX));
-                const float ezz = g.c1z * (qhz[C] - qhz[B]) + g.c2z * (qhz[D] - qhz[A]);
+                constexpr int FW = FS == ZS_NONE ? ZS_NONE : ZS_FWD;   // forward strain rates
+                const float ezz = zdiff<FW, false>(g, zw, zt, qhz[A], qhz[B], qhz[C], qhz[D]);
                 const float gxy = g.c1y * (F(vhx, R + HX) - F(vhx, R)) + g.c2y * (F(vhx, R + 2 * HX) - F(vhx, R - HX)) +
                                   g.c1x * (F(vhy, R + 1) - F(vhy, R)) + g.c2x * (F(vhy, R + 2) - F(vhy, R - 1));
-                const float gxz = g.c1z * (qhx[C] - qhx[B]) + g.c2z * (qhx[D] - qhx[A]) +
+                const float gxz = zdiff<FW, true>(g, zw, zt, qhx[A], qhx[B], qhx[C], qhx[D]) +
                                   g.c1x * (F(vhz, R + 1) - F(vhz, R)) + g.c2x * (F(vhz, R + 2) - F(vhz, R - 1));
-                const float gyz = g.c1z * (qhy[C] - qhy[B]) + g.c2z * (qhy[D] - qhy[A]) +
+                const float gyz = zdiff<FW, true>(g, zw, zt, qhy[A], qhy[B], qhy[C], qhy[D]) +
                                   g.c1y * (F(vhz, R + HX) - F(vhz, R)) + g.c2y * (F(vhz, R + 2 * HX) - F(vhz, R - HX));
                 const float uxx = F(hxx, R), uyy = F(hyy, R), uzz = F(vc, VC_SZZ * CORE + rr * TX);
                 const float gdt = P.X.gdt;
@@ -566,7 +568,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
 
 // One (tile, z-chunk) of the velocity pass; the ring barriers must be freshly
 // initialised.  Returns false if a wait gave up (the error is recorded).
-template <int BND, typename T, int MODE, bool FS = false>
+template <int BND, typename T, int MODE, int FS = ZS_NONE>
 __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, int item,
                                          unsigned char* sm, uint64_t* bars) {
     constexpr int SB = slot_bytes<T, MODE>();
@@ -595,7 +597,7 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
     return true;
 }
 
-template <int BND, typename T, int MODE, bool FS = false>
+template <int BND, typename T, int MODE, int FS = ZS_NONE>
 __global__ void __launch_bounds__(NTH, (min_blocks<BND, T, MODE>())) k_velocity(
     const __grid_constant__ Maps maps, const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
@@ -615,7 +617,7 @@ struct StrQ {
     float vx[ROWS][4], vy[ROWS][4], vz[ROWS][4];   // vx/vy k-1..k+2, vz k-2..k+1
 };
 
-template <int BND, typename T, int PH, bool FS>
+template <int BND, typename T, int PH, int FS>
 __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, StrQ& Q, unsigned char* sm,
                                          uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
@@ -651,7 +653,8 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
         const float* lc = (const float*)(sl2 + L::S_LAM) + G.cc;
         const T* cr = (const T*)(sl2 + L::S_CORE) + G.cc;
         const long long o = (long long)k * g.plane + G.obase;
-        const ZW zw = zweights<FS>(g, k);   // used only with a free surface
+        const ZW zw = zweights<FS == ZS_NONE ? ZS_NONE : ZS_FWD>(g, k);   // surface forms only
+        const ZT zt = FS == ZS_ADJ ? ztransposed(g, k) : ZT{};
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
             if (!G.own[rr]) continue;
@@ -662,13 +665,13 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
             // normal strain rates at (i, j, k)
             float exx = g.c1x * (F(hvx, R) - F(hvx, R - 1)) + g.c2x * (F(hvx, R + 1) - F(hvx, R - 2));
             float eyy = g.c1y * (F(hvy, R) - F(hvy, R - HX)) + g.c2y * (F(hvy, R + HX) - F(hvy, R - 2 * HX));
-            float ezz = (FS ? zw.c1i : g.c1z) * (qvz[C] - qvz[B]) + (FS ? zw.c2i : g.c2z) * (qvz[D] - qvz[A]);
+            float ezz = zdiff<FS, false>(g, zw, zt, qvz[A], qvz[B], qvz[C], qvz[D]);
             // shear terms at the shear points
             float vxy = g.c1y * (F(hvx, R + HX) - F(hvx, R)) + g.c2y * (F(hvx, R + 2 * HX) - F(hvx, R - HX));
             float vyx = g.c1x * (F(hvy, R + 1) - F(hvy, R)) + g.c2x * (F(hvy, R + 2) - F(hvy, R - 1));
-            float vxz = (FS ? zw.c1h : g.c1z) * (qvx[C] - qvx[B]) + (FS ? zw.c2h : g.c2z) * (qvx[D] - qvx[A]);
+            float vxz = zdiff<FS, true>(g, zw, zt, qvx[A], qvx[B], qvx[C], qvx[D]);
             float vzx = g.c1x * (F(hvz, R + 1) - F(hvz, R)) + g.c2x * (F(hvz, R + 2) - F(hvz, R - 1));
-            float vyz = (FS ? zw.c1h : g.c1z) * (qvy[C] - qvy[B]) + (FS ? zw.c2h : g.c2z) * (qvy[D] - qvy[A]);
+            float vyz = zdiff<FS, true>(g, zw, zt, qvy[A], qvy[B], qvy[C], qvy[D]);
             float vzy = g.c1y * (F(hvz, R + HX) - F(hvz, R)) + g.c2y * (F(hvz, R + 2 * HX) - F(hvz, R - HX));
             if constexpr (kScaled<T>) {     // stored -> physical units
                 exx *= P.inv[VX]; vxy *= P.inv[VX]; vxz *= P.inv[VX];
@@ -702,7 +705,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
             const float mxy = 0.25f * (mu0 + mxp + myp + hmu[RF + G.cx + cyr]);
             float mxz = 0.25f * (mu0 + mxp + mzp + hmu1[RF + G.cx]);
             float myz = 0.25f * (mu0 + myp + mzp + hmu1[RF + cyr]);
-            if constexpr (FS) {
+            if constexpr (FS != ZS_NONE) {
                 // xz / yz shear points on the free-surface plane z = ks - 1/2:
                 // harmonic mean of the 4 cells (vacuum-formulation reading)
                 if (k == g.fs - 1) {
@@ -750,7 +753,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
     return true;
 }
 
-template <int BND, typename T, bool FS = false>
+template <int BND, typename T, int FS = ZS_NONE>
 __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, int item,
                                          unsigned char* sm, uint64_t* bars) {
     const Geo<BND, T> G(P, item);
@@ -775,7 +778,7 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
     return true;
 }
 
-template <int BND, typename T, bool FS = false>
+template <int BND, typename T, int FS = ZS_NONE>
 __global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_stress(const __grid_constant__ Maps maps,
                                                                       const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
@@ -943,16 +946,17 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                     }
                 }
                 ring_rearm(bars, tid);
+                constexpr int ZF = FS ? ZS_FWD : ZS_NONE, ZA = FS ? ZS_ADJ : ZS_NONE;
                 if (E.kind == BK_VEL)
-                    ok = vel_tile<BND, float, M_FWD, FS>(B.vf, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_FWD, ZF>(B.vf, sP, it, sm, bars);
                 else if (E.kind == BK_VEL_CAP)
-                    ok = vel_tile<BND, float, M_CAP, FS>(B.vf, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_CAP, ZF>(B.vf, sP, it, sm, bars);
                 else if (E.kind == BK_STR)
-                    ok = str_tile<BND, float, FS>(B.sf, sP, it, sm, bars);
+                    ok = str_tile<BND, float, ZF>(B.sf, sP, it, sm, bars);
                 else if (E.kind == BK_STR_ADJ)
-                    ok = str_tile<BND, float>(B.sa, sP, it, sm, bars);
+                    ok = str_tile<BND, float, ZA>(B.sa, sP, it, sm, bars);
                 else if constexpr (GRAD)
-                    ok = vel_tile<BND, float, M_GRAD>(B.va, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_GRAD, ZA>(B.va, sP, it, sm, bars);
                 if (!ok) break;
                 // Point terms of this step inside the item's cells, after its
                 // stores (the next pass starts only when every item is done):
@@ -1119,14 +1123,18 @@ cudaError_t occupancy(int* occ) {
     cudaError_t e = prepare(k_velocity<BND, T, M_FWD>, smem_bytes<BND, T>(), &a);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T>, smem_bytes<BND, T>(), &b);
     // free-surface variants: same slots, occupancy taken from the plain ones
-    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, true>, smem_bytes<BND, T>(), &c);
-    if (e == cudaSuccess) e = prepare(k_stress<BND, T, true>, smem_bytes<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, ZS_FWD>, smem_bytes<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_FWD>, smem_bytes<BND, T>(), &c);
     if constexpr (std::is_same<T, float>::value) {     // history and reverse modes
         if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP>, smem_bytes<BND, T, M_CAP>(), &c);
-        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP, true>, smem_bytes<BND, T, M_CAP>(), &c);
-        if constexpr (BND != BND_CPML)
+        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP, ZS_FWD>, smem_bytes<BND, T, M_CAP>(), &c);
+        if constexpr (BND != BND_CPML) {
             if (e == cudaSuccess)
                 e = prepare(k_velocity<BND, T, M_GRAD>, smem_bytes<BND, T, M_GRAD>(), &c);
+            if (e == cudaSuccess)
+                e = prepare(k_velocity<BND, T, M_GRAD, ZS_ADJ>, smem_bytes<BND, T, M_GRAD>(), &c);
+            if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_ADJ>, smem_bytes<BND, T>(), &c);
+        }
     }
     *occ = a < b ? a : b;
     return e;
@@ -1251,7 +1259,7 @@ PassParams pass_params(const StencilPlan* sp, const DevGrid& g, const DevFields&
     return P;
 }
 
-template <typename T, int MODE, bool FS>
+template <typename T, int MODE, int FS>
 void launch_v_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     dim3 blk(TX, RY);
     switch (sp->kind) {
@@ -1268,16 +1276,20 @@ void launch_v_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     }
 }
 
-// The reverse (M_GRAD) pass has no free-surface form: the host rejects
-// gradients of grids with a surface.
+// With a free surface the reverse (M_GRAD) pass takes the transposed
+// z-weights, the others the forward ones.
 template <typename T, int MODE = M_FWD>
 void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
-    if constexpr (MODE != M_GRAD)
-        if (P.g.fs != kNoSurface) return launch_v_fs<T, MODE, true>(sp, P, st);
-    launch_v_fs<T, MODE, false>(sp, P, st);
+    if (P.g.fs != kNoSurface) {
+        if constexpr (MODE == M_GRAD)
+            return launch_v_fs<T, MODE, ZS_ADJ>(sp, P, st);
+        else
+            return launch_v_fs<T, MODE, ZS_FWD>(sp, P, st);
+    }
+    launch_v_fs<T, MODE, ZS_NONE>(sp, P, st);
 }
 
-template <typename T, bool FS>
+template <typename T, int FS>
 void launch_s_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     dim3 blk(TX, RY);
     switch (sp->kind) {
@@ -1293,10 +1305,16 @@ void launch_s_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     }
 }
 
+// reverse: the stress pass of the reverse sweep (transposed z-weights with
+// a free surface; FP32 storage only).
 template <typename T>
-void launch_s(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
-    if (P.g.fs != kNoSurface) return launch_s_fs<T, true>(sp, P, st);
-    launch_s_fs<T, false>(sp, P, st);
+void launch_s(const StencilPlan* sp, const PassParams& P, cudaStream_t st, bool reverse) {
+    if (P.g.fs != kNoSurface) {
+        if constexpr (std::is_same<T, float>::value)
+            if (reverse) return launch_s_fs<T, ZS_ADJ>(sp, P, st);
+        return launch_s_fs<T, ZS_FWD>(sp, P, st);
+    }
+    launch_s_fs<T, ZS_NONE>(sp, P, st);
 }
 
 }  // namespace
@@ -1399,6 +1417,7 @@ cudaError_t batch_occupancy_b(int exec, int* per_sm) {
         case BX_LEAN: return batch_prepare<BND, false, false>(per_sm);
         case BX_GRAD: return batch_prepare<BND, true, false>(per_sm);
         case BX_LEAN_FS: return batch_prepare<BND, false, true>(per_sm);
+        case BX_GRAD_FS: return batch_prepare<BND, true, true>(per_sm);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1426,6 +1445,7 @@ cudaError_t launch_batch_b(int exec, int grid, const BatchShot* shots, const Bat
         case BX_LEAN: batch_go<BND, false, false>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
         case BX_GRAD: batch_go<BND, true, false>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
         case BX_LEAN_FS: batch_go<BND, false, true>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
+        case BX_GRAD_FS: batch_go<BND, true, true>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -1454,12 +1474,12 @@ void stencil_plan_export(const StencilPlan* p, Maps* vmaps, Maps* smaps, int* nt
 
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                           const DevBoundary& B, const float dto[9], const float inv[9],
-                          int* err, cudaStream_t st) {
+                          int* err, cudaStream_t st, bool reverse) {
     const PassParams P = pass_params(sp, g, F, B, dto, inv, err);
     switch (sp->storage) {
-        case EWS_STORAGE_BF16: launch_s<__nv_bfloat16>(sp, P, st); break;
-        case EWS_STORAGE_F16: launch_s<__half>(sp, P, st); break;
-        default: launch_s<float>(sp, P, st); break;
+        case EWS_STORAGE_BF16: launch_s<__nv_bfloat16>(sp, P, st, false); break;
+        case EWS_STORAGE_F16: launch_s<__half>(sp, P, st, false); break;
+        default: launch_s<float>(sp, P, st, reverse); break;
     }
     return cudaGetLastError();
 }

@@ -211,20 +211,84 @@ def test_stable_at_the_bound_with_surface(orc):
     assert max(peaks[4:]) <= 4.0 * max(peaks[:4]), peaks
 
 
-def test_adjoint_rejects_surface(orc):
-    p = synth.small_problem(8, 8, 8, nt=5, width=2, nrec=2)
-    p.free_surface = (3, 1e-3)
-    s = orc.OracleSim(p.nx, p.ny, p.nz, p.spacing)
-    s.set_free_surface(3, 1e-3)
-    s.set_medium_vel(p.vp, p.vs, p.rho)
-    s.set_boundary("sponge", 2, p.dt, p.f0)
-    import ctypes as C
-    g = np.zeros((3, s.n))
-    w = np.ascontiguousarray(p.wavelet, np.float64)
-    r = np.ascontiguousarray(p.rec_pos, np.float64)
-    a = np.zeros((3, 2, 5))
-    k, pp, c = s._src(p.src_kind, p.src_pos, p.src_comp)
-    ptr = lambda x: x.ctypes.data_as(C.c_void_p)
-    rc = s._L.orc_gradient(s._h, 5, float(p.dt), k, ptr(pp), ptr(c), ptr(w), 2, ptr(r), ptr(a),
-                           0, ptr(g[0]), ptr(g[1]), ptr(g[2]))
-    assert rc == -3
+def _surface_setup(orc, boundary, kind, seed=3, dims=(14, 12, 16), nt=70, ks=5, eps=1e-2):
+    """Adjoint set-up with a surface: source below it, receivers on it and
+    below it; L = <A, seis> for a fixed random A."""
+    p = synth.small_problem(*dims, nt=nt, boundary=boundary, width=3, kind=kind, nrec=4,
+                            seed=seed)
+    h = p.spacing[2]
+    p.free_surface = (ks, eps)
+    p.src_pos = p.src_pos.copy()
+    p.src_pos[2] = (ks + 3.4) * h
+    p.rec_pos = p.rec_pos.copy()
+    p.rec_pos[::2, 2] = (ks - 0.5) * h
+    p.rec_pos[1::2, 2] = (ks + 1.3) * h
+    lam, mu, rho = [a.astype(np.float64) for a in p.lame()]
+    rng = np.random.default_rng(seed + 100)
+    A = rng.standard_normal((3, p.rec_pos.shape[0], p.nt))
+
+    def L(l, m, r):
+        s = orc.OracleSim(p.nx, p.ny, p.nz, p.spacing)
+        s.set_free_surface(*p.free_surface)
+        s.set_medium_lame(l, m, r)
+        s.set_boundary(boundary, p.width, p.dt, p.f0)
+        seis = s.forward(p.nt, p.dt, p.src_kind, p.src_pos, p.src_comp, p.wavelet, p.rec_pos)
+        return float(np.sum(A * seis))
+
+    return p, (lam, mu, rho), A, L
+
+
+@pytest.mark.parametrize("boundary", ["none", "sponge"])
+@pytest.mark.parametrize("kind", ["moment", "force"])
+def test_surface_dot_product(orc, boundary, kind):
+    """<J dm, A> = <dm, J^T A> with the surface: the adjoint's transposed
+    differences (column by column from the switched weights), harmonic-mean
+    chain rule and vacuum folding against the tangent model, to rounding."""
+    p, m, A, _ = _surface_setup(orc, boundary, kind, seed=17)
+    g = orc.gradient(p, A, ckpt_every=13, medium=m)
+    rng = np.random.default_rng(23)
+    for idx in range(3):
+        dm = [np.zeros_like(m[0]) for _ in range(3)]
+        dm[idx] = rng.standard_normal(m[0].shape) * np.abs(m[idx]).mean()
+        ds = orc.tangent(p, dm, medium=m)
+        lhs = float(np.sum(ds * A))
+        rhs = float(np.sum(dm[idx] * g[idx]))
+        assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs)), (idx, lhs, rhs)
+
+
+@pytest.mark.parametrize("kind", ["moment", "force"])
+def test_surface_gradient_matches_central_fd(orc, kind):
+    """The adjoint gradient with the surface against central differences of
+    the forward oracle (directional, each parameter); the model values above
+    the surface are unused, so their gradient is zero."""
+    p, m, A, L = _surface_setup(orc, "sponge", kind, seed=9)
+    g = orc.gradient(p, A, ckpt_every=16, medium=m)
+    ks = p.free_surface[0]
+    for idx in range(3):
+        assert np.all(g[idx][:ks] == 0.0)
+    rng = np.random.default_rng(7)
+    for idx in range(3):
+        d = rng.standard_normal(m[0].shape)
+        h = 1e-4 * np.abs(m[idx]).mean() / np.abs(d).mean()
+        plus = [a + (h * d if i == idx else 0) for i, a in enumerate(m)]
+        minus = [a - (h * d if i == idx else 0) for i, a in enumerate(m)]
+        fd = (L(*plus) - L(*minus)) / (2 * h)
+        an = float(np.sum(g[idx] * d))
+        assert abs(fd - an) <= 1e-6 * abs(fd), (idx, fd, an)
+
+
+def test_surface_tangent_matches_finite_differences(orc):
+    p, m, A, L = _surface_setup(orc, "sponge", "moment", seed=29)
+    rng = np.random.default_rng(31)
+    dm = [rng.standard_normal(m[0].shape) * np.abs(a).mean() for a in m]
+    ds = orc.tangent(p, dm, medium=m)
+    h = 1e-5
+
+    def run(sign):
+        s = orc.OracleSim(p.nx, p.ny, p.nz, p.spacing)
+        s.set_free_surface(*p.free_surface)
+        s.set_medium_lame(*[a + sign * h * d for a, d in zip(m, dm)])
+        s.set_boundary("sponge", p.width, p.dt, p.f0)
+        return s.forward(p.nt, p.dt, p.src_kind, p.src_pos, p.src_comp, p.wavelet, p.rec_pos)
+    fd = (run(1) - run(-1)) / (2 * h)
+    assert np.linalg.norm(ds - fd) <= 1e-6 * np.linalg.norm(fd)
