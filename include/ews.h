@@ -121,6 +121,25 @@ ews_status ews_set_model_lame(ews_sim* sim, const float* lam, const float* mu,
 ews_status ews_set_model_vel(ews_sim* sim, const float* vp, const float* vs,
                              const float* rho, int on_device);
 
+/* Medium on its own, usually coarser, grid of mx x my x mz cells covering
+ * the same box (Sec. 2.2.1: medium textures smaller than the wavefield
+ * textures, read with trilinear interpolation).  a, b, rho are dense
+ * [mz][my][mx] float32 (host, or device with on_device = 1): lambda, mu if
+ * from_velocities = 0, else vp, vs (converted on the device).  The passes
+ * sample it at every staggered point instead of reading medium arrays of
+ * the wavefield grid: a wavefield-grid position x (cells, per axis) maps to
+ * the medium coordinate c = (x + 1/2) m / n - 1/2, clamped to [0, m - 1],
+ * and the value is the linear interpolation of the two medium cells around
+ * c on each axis (1 / rho at the v points, lambda and mu at the cells, mu
+ * at the shear points).  With m = n this equals ews_set_model_lame / _vel.
+ * Same validity rules (EWS_EINVAL / EWS_ENONFINITE); vp_max for the
+ * stability check is taken over the medium cells.  A later
+ * ews_set_model_lame / _vel returns to the wavefield-grid medium.  Not
+ * combined with a free surface, gradients or batched shots (EWS_EINVAL). */
+ews_status ews_set_model_coarse(ews_sim* sim, int mx, int my, int mz, const float* a,
+                                const float* b, const float* rho, int from_velocities,
+                                int on_device);
+
 /* Free surface by the vacuum formulation (Sec. 2.5, surface boundary):
  * the cells above plane ks (k < ks) take eps times lambda, mu and rho of the
  * cell (i, j, ks) below the surface in their column (the values the model

@@ -233,6 +233,72 @@ void orc_set_medium(orc_sim *s, const double *lam_in, const double *mu_in,
 
 double orc_vpmax(const orc_sim *s) { return s->vpmax; }
 
+/* Reading R17 (Sec. 2.2.1: the medium textures may be much smaller than
+ * the wavefield textures and are sampled with trilinear interpolation): a
+ * medium grid of m = (mx, my, mz) cells covers the same box as the n cells
+ * of the wavefield grid.  A fine-grid position x (in cells, per axis) maps
+ * to the medium coordinate c = (x + 1/2) m / n - 1/2 (texel centres of both
+ * grids at their cell centres), clamped to [0, m - 1]; the value there is
+ * the linear interpolation of the two neighbouring medium cells, per axis.
+ * With m = n this is reading R4 (means of 2 or 4 cells, top edge clamped). */
+static double coarse_at(const double *a, const long m[3], const long n[3], const double x[3]) {
+    long i0[3];
+    double fr[3];
+    for (int d = 0; d < 3; ++d) {
+        double c = (x[d] + 0.5) * (double)m[d] / (double)n[d] - 0.5;
+        if (c < 0.0) c = 0.0;
+        if (c > (double)(m[d] - 1)) c = (double)(m[d] - 1);
+        i0[d] = (long)floor(c);
+        if (i0[d] > m[d] - 2) i0[d] = m[d] - 2 < 0 ? 0 : m[d] - 2;
+        fr[d] = c - (double)i0[d];
+    }
+    double v = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double w = (dx ? fr[0] : 1.0 - fr[0]) * (dy ? fr[1] : 1.0 - fr[1])
+                           * (dz ? fr[2] : 1.0 - fr[2]);
+                if (w == 0.0) continue;
+                long ix = i0[0] + dx, iy = i0[1] + dy, iz = i0[2] + dz;
+                v += w * a[(iz * m[1] + iy) * m[0] + ix];
+            }
+    return v;
+}
+
+/* Effective medium of the staggered points from a medium grid of mx x my x
+ * mz cells (reading R17): 1 / rho at the v points, lambda and lambda + 2 mu
+ * at the normal points, mu at the shear points, each interpolated at its
+ * own position.  vp_max is taken over the medium cells (an upper bound of
+ * the interpolated speeds).  No free surface. */
+void orc_set_medium_coarse(orc_sim *s, long mx, long my, long mz, const double *lam,
+                           const double *mu, const double *rho) {
+    const long m[3] = {mx, my, mz}, n[3] = {s->nx, s->ny, s->nz};
+    double vpmax = 0.0;
+    for (long c = 0; c < mx * my * mz; ++c) {
+        double vp = sqrt((lam[c] + 2.0 * mu[c]) / rho[c]);
+        if (vp > vpmax) vpmax = vp;
+    }
+    for (long k = 0; k < s->nz; ++k)
+        for (long j = 0; j < s->ny; ++j)
+            for (long i = 0; i < s->nx; ++i) {
+                long c = IDX(s, i, j, k);
+                double I = (double)i, J = (double)j, K = (double)k;
+                double px[3] = {I + 0.5, J, K}, py[3] = {I, J + 0.5, K}, pz[3] = {I, J, K + 0.5};
+                double p0[3] = {I, J, K};
+                double pxy[3] = {I + 0.5, J + 0.5, K}, pxz[3] = {I + 0.5, J, K + 0.5};
+                double pyz[3] = {I, J + 0.5, K + 0.5};
+                s->bx[c] = 1.0 / coarse_at(rho, m, n, px);
+                s->by[c] = 1.0 / coarse_at(rho, m, n, py);
+                s->bz[c] = 1.0 / coarse_at(rho, m, n, pz);
+                s->lam[c] = coarse_at(lam, m, n, p0);
+                s->lp2m[c] = s->lam[c] + 2.0 * coarse_at(mu, m, n, p0);
+                s->mxy[c] = coarse_at(mu, m, n, pxy);
+                s->mxz[c] = coarse_at(mu, m, n, pxz);
+                s->myz[c] = coarse_at(mu, m, n, pyz);
+            }
+    s->vpmax = vpmax;
+}
+
 /* Damping layers (Sec. 2.5 for the sponge; C-PML is reading R7).
  * Must be called after orc_set_medium (C-PML uses vpmax) and whenever dt
  * changes (C-PML coefficients depend on dt). */

@@ -56,6 +56,7 @@ def lib():
             L.orc_destroy.argtypes = [P]
             L.orc_set_medium.argtypes = [P, P, P, P]
             L.orc_set_free_surface.argtypes = [P, L_, D]
+            L.orc_set_medium_coarse.argtypes = [P, L_, L_, L_, P, P, P]
             L.orc_vpmax.restype = D
             L.orc_vpmax.argtypes = [P]
             L.orc_set_boundary.argtypes = [P, I, I, D, D, D, D]
@@ -127,6 +128,15 @@ class OracleSim:
 
     def set_medium_vel(self, vp, vs, rho):
         self.set_medium_lame(*lame_from_velocities(vp, vs, rho))
+
+    def set_medium_coarse(self, lam, mu, rho):
+        """Medium on its own grid of [mz][my][mx] cells over the same box
+        (reading R17: trilinear sampling at the staggered positions)."""
+        arrs = [np.ascontiguousarray(a, np.float64) for a in (lam, mu, rho)]
+        mz, my, mx = arrs[0].shape
+        for a in arrs:
+            assert a.shape == (mz, my, mx)
+        self._L.orc_set_medium_coarse(self._h, mx, my, mz, *[_p(a) for a in arrs])
 
     @property
     def vpmax(self) -> float:
@@ -272,7 +282,10 @@ def run_problem(prob, nt=None, state=None, boundary=None, snap_every=0, snap_mas
     s = OracleSim(prob.nx, prob.ny, prob.nz, prob.spacing)
     if prob.free_surface is not None:
         s.set_free_surface(*prob.free_surface)
-    s.set_medium_vel(prob.vp, prob.vs, prob.rho)
+    if prob.coarse_medium is not None:
+        s.set_medium_coarse(*prob.coarse_medium)
+    else:
+        s.set_medium_vel(prob.vp, prob.vs, prob.rho)
     s.set_boundary(boundary or prob.boundary, prob.width, prob.dt, prob.f0)
     if state is not None:
         s.set_state(state)

@@ -346,6 +346,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         if (b.observed && s->has_fluid)
             return report(EWS_EINVAL, "shot %d: fluid cells (mu = 0) are not batched", i);
         if (s->g.fs != kNoSurface) any_fs = true;
+        if (s->g.cm[0]) return report(EWS_EINVAL, "shot %d: coarse medium grids are not batched", i);
     }
     const int K0 = o.ckpt_every > 0 ? o.ckpt_every : 50;
 

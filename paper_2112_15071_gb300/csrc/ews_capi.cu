@@ -205,6 +205,10 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
                      int on_device, int from_vel) {
     if (!s) return fail(EWS_EINVAL, "null simulation");
     if (!a || !b || !rho) return fail(EWS_EINVAL, "null model array");
+    if (s->g.cm[0]) {                          // back from a coarse medium grid
+        for (int q = 0; q < 3; ++q) s->g.cm[q] = nullptr;
+        s->gen++;
+    }
     DevMedium M = s->M();
     ews_status st;
     if ((st = copy_field_in(s, (float*)M.lam, a, on_device)) != EWS_OK) return st;
@@ -487,6 +491,8 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     if (!s->wide()) return fail(EWS_EINVAL, "the adjoint needs F32 wavefield storage");
     if (s->g.fs != kNoSurface && s->has_fluid)
         return fail(EWS_EINVAL, "gradients with a free surface need mu > 0 below it");
+    if (s->g.cm[0])
+        return fail(EWS_EINVAL, "gradients with a coarse medium grid are not built");
     const int K = ckpt_every > 0 ? (ckpt_every < nt ? ckpt_every : nt) : (nt < 50 ? nt : 50);
     const int nck = (nt + K - 1) / K;
     const size_t fs = s->fstride;
@@ -805,6 +811,7 @@ void ews_destroy(ews_sim* s) {
     else cudaDeviceSynchronize();
     cudaFree(s->fields);
     cudaFree(s->medium);
+    cudaFree(s->cmed);
     cudaFree(s->prof);
     cudaFree(s->flags);
     cudaFree(s->err);
@@ -844,6 +851,64 @@ ews_status ews_set_model_vel(ews_sim* s, const float* vp, const float* vs, const
     return set_model(s, vp, vs, rho, on_device, 1);
 }
 
+ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float* a,
+                                const float* b, const float* rho, int from_velocities,
+                                int on_device) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (!a || !b || !rho) return fail(EWS_EINVAL, "null model array");
+    if (mx < 1 || my < 1 || mz < 1) return fail(EWS_EINVAL, "medium grid %d x %d x %d", mx, my, mz);
+    if (s->g.fs != kNoSurface)
+        return fail(EWS_EINVAL, "a coarse medium grid with a free surface is not built");
+    const size_t m = (size_t)mx * my * mz;
+    s->model_set = false;
+    for (int q = 0; q < 3; ++q) s->g.cm[q] = nullptr;
+    cudaFree(s->cmed);
+    s->cmed = nullptr;
+    CK(cudaMalloc(&s->cmed, 3 * m * sizeof(float)));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(s->cmed, a, m * sizeof(float), kind, s->stream));
+    CK(cudaMemcpyAsync(s->cmed + m, b, m * sizeof(float), kind, s->stream));
+    CK(cudaMemcpyAsync(s->cmed + 2 * m, rho, m * sizeof(float), kind, s->stream));
+    // validation, velocity -> Lame conversion and the medium bounds on the
+    // medium grid's own cells (the interpolated values lie between them)
+    DevGrid gc{};
+    gc.nx = mx;
+    gc.ny = my;
+    gc.nz = mz;
+    gc.pitch = mx;
+    gc.plane = (long long)mx * my;
+    gc.fs = kNoSurface;
+    CK(cudaMemsetAsync(s->flags, 0, 5 * sizeof(unsigned), s->stream));
+    CK(cudaMemsetAsync(s->flags + 2, 0x7F, 2 * sizeof(unsigned), s->stream));
+    CK(launch_medium_setup(gc, s->cmed, s->cmed + m, s->cmed + 2 * m, from_velocities, s->flags,
+                           s->stream));
+    unsigned hf[5];
+    CK(cudaMemcpyAsync(hf, s->flags, sizeof(hf), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (hf[0] & 1u) return fail(EWS_ENONFINITE, "model contains NaN or Inf");
+    if (hf[0] & 2u) return fail(EWS_EINVAL, "model has rho <= 0");
+    if (hf[0] & 4u) return fail(EWS_EINVAL, "model has mu < 0 (vs^2 < 0)");
+    if (hf[0] & 8u) return fail(EWS_EINVAL, "model has lambda + 2 mu <= 0");
+    float bnd[4];
+    std::memcpy(bnd, &hf[1], sizeof(bnd));
+    s->vpmax = bnd[0];
+    s->rho_min = bnd[1];
+    s->zs_min = bnd[2];
+    s->zp_max = bnd[3];
+    s->has_fluid = (hf[0] & 16u) != 0;
+    for (int q = 0; q < 3; ++q) s->g.cm[q] = s->cmed + q * m;
+    s->g.mx = mx;
+    s->g.my = my;
+    s->g.mz = mz;
+    s->g.rx = (float)((double)mx / s->g.nx);
+    s->g.ry = (float)((double)my / s->g.ny);
+    s->g.rz = (float)((double)mz / s->g.nz);
+    s->model_set = true;
+    s->pml_dt = -1.0;
+    s->gen++;
+    return EWS_OK;
+}
+
 ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const double comp[6],
                           const float* wavelet, int nt) {
     if (!s) return fail(EWS_EINVAL, "null simulation");
@@ -880,6 +945,8 @@ ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const doubl
 
 ews_status ews_set_free_surface(ews_sim* s, int ks, double eps) {
     if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (ks >= 0 && s->g.cm[0])
+        return fail(EWS_EINVAL, "a free surface with a coarse medium grid is not built");
     if (ks >= s->g.nz) return fail(EWS_EINVAL, "surface plane %d outside the grid (nz = %d)", ks, s->g.nz);
     if (ks >= 0 && !(eps > 0.0 && eps <= 1.0))
         return fail(EWS_EINVAL, "vacuum fraction %g outside (0, 1]", eps);

@@ -40,12 +40,53 @@ struct DevGrid {
     int fs;
     float c1z2;
     float fs_eps;         // vacuum fraction above the surface
+    // coarse medium grid (Sec. 2.2.1: medium textures smaller than the
+    // wavefield textures, sampled by trilinear interpolation): lambda, mu,
+    // rho as dense [mz][my][mx] arrays (null: the medium has the wavefield
+    // grid's cells), and m / n per axis
+    const float* cm[3];
+    int mx, my, mz;
+    float rx, ry, rz;
 };
 constexpr int kNoSurface = -(1 << 28);
 
+// Trilinear sampling of a coarse medium array (reading of Sec. 2.2.1): a
+// wavefield-grid position x (cells) maps to the medium coordinate
+// c = (x + 1/2) m / n - 1/2, clamped to [0, m - 1]; i0 is the lower of the
+// two medium cells used and f the weight of the upper one.
+struct Ax {
+    int i0;
+    float f;
+};
+__device__ __forceinline__ Ax axis_at(float x, float r, int m) {
+    float c = fmaf(x + 0.5f, r, -0.5f);
+    c = fminf(fmaxf(c, 0.0f), (float)(m - 1));
+    const int i0 = min((int)c, max(m - 2, 0));
+    return Ax{i0, c - (float)i0};
+}
+__device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(t, b - a, a); }
+// q: 0 lambda, 1 mu, 2 rho.  Axes of extent 1 read the same cell twice.
+__device__ __forceinline__ float coarse_tri(const DevGrid& g, int q, Ax x, Ax y, Ax z) {
+    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mx : 0;
+    const long long oz = g.mz > 1 ? (long long)g.mx * g.my : 0;
+    const float* p = g.cm[q] + ((long long)z.i0 * g.my + y.i0) * g.mx + x.i0;
+    const float c00 = lerp1(__ldg(p), __ldg(p + ox), x.f);
+    const float c10 = lerp1(__ldg(p + oy), __ldg(p + oy + ox), x.f);
+    const float c01 = lerp1(__ldg(p + oz), __ldg(p + oz + ox), x.f);
+    const float c11 = lerp1(__ldg(p + oz + oy), __ldg(p + oz + oy + ox), x.f);
+    return lerp1(lerp1(c00, c10, y.f), lerp1(c01, c11, y.f), z.f);
+}
+// Coarse-medium value q at wavefield-grid position (x, y, z) in cells.
+__device__ __forceinline__ float coarse_at(const DevGrid& g, int q, float x, float y, float z) {
+    return coarse_tri(g, q, axis_at(x, g.rx, g.mx), axis_at(y, g.ry, g.my),
+                      axis_at(z, g.rz, g.mz));
+}
+
 // Forms of the passes' z-differences: no free surface; the forward form
 // with a surface; the transposed form of the reverse sweep with a surface.
-enum { ZS_NONE = 0, ZS_FWD = 1, ZS_ADJ = 2 };
+// A pass variant is one of these, or VAR_COARSE (no surface, the medium
+// sampled from a coarse grid instead of read as tiles).
+enum { ZS_NONE = 0, ZS_FWD = 1, ZS_ADJ = 2, VAR_COARSE = 4 };
 
 // z-difference weights at output plane k (free-surface reading): a
 // z-derivative whose Eq. 4 stencil would take samples on both sides of the

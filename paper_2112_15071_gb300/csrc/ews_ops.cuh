@@ -65,7 +65,15 @@ __device__ __forceinline__ void inject_tap(const DevGrid& g, const DevFields& F,
                                            int* err) {
     const Tap tp = S.tap[t];
     float amp = tp.w * __ldg(wavelet + n);
-    if (S.kind == 1) amp *= buoy(M, g, tp.q - VX, tp.i, tp.j, tp.k);
+    if (S.kind == 1) {
+        if (g.cm[2]) {           // coarse medium: 1 / rho sampled at the v point
+            const int c = tp.q - VX;
+            amp *= 1.0f / coarse_at(g, 2, tp.i + (c == 0 ? 0.5f : 0.0f), tp.j + (c == 1 ? 0.5f : 0.0f),
+                                    tp.k + (c == 2 ? 0.5f : 0.0f));
+        } else {
+            amp *= buoy(M, g, tp.q - VX, tp.i, tp.j, tp.k);
+        }
+    }
     amp *= gain(B, tp.i, tp.j, tp.k);
     T* f = reinterpret_cast<T*>(F.f[tp.q]) + cidx(g, tp.i, tp.j, tp.k);
     if constexpr (sizeof(T) == 4) {

@@ -44,6 +44,7 @@ struct ews_sim {
     int es = 4;                   // bytes per stored wavefield element
     float* fields = nullptr;      // 9 * fstride elements of the storage type
     float* medium = nullptr;      // 3 * fstride floats: lambda, mu, rho
+    float* cmed = nullptr;        // coarse medium grid: lambda, mu, rho, dense [mz][my][mx]
     bool model_set = false;
     float vpmax = 0.0f;
     float rho_min = 0.0f, zs_min = 0.0f, zp_max = 0.0f;   // medium bounds

@@ -222,14 +222,16 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
 static_assert(MAXH == kMapsHalo && MAXC == kMapsCore, "tensor-map counts of Maps");
 
 // Issue the TMA loads of z-plane `z` of tile (x0, y0) into `slot`.
-template <typename T, int MODE>
+// CM: the medium is sampled from a coarse grid, so its tiles are not loaded.
+template <typename T, int MODE, bool CM = false>
 __device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, uint64_t* bar,
                                           int x0, int y0, int z, int hslot) {
     using L = Lay<T>;
-    mbar_expect_tx(bar, (uint32_t)(L::V_BYTES + (MODE == M_GRAD ? 3 * L::HB : 0)));
+    mbar_expect_tx(bar, (uint32_t)(L::V_BYTES + (MODE == M_GRAD ? 3 * L::HB : 0) -
+                                   (CM ? L::FHB : 0)));
 #pragma unroll
     for (int h = 0; h < 5; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
-    tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0 - 2, z);
+    if constexpr (!CM) tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0 - 2, z);
 #pragma unroll
     for (int c = 0; c < 4; ++c) tma_load_3d(slot + L::V_CORE + c * L::CB, &m.core[c], bar, x0, y0, z);
     if constexpr (MODE == M_GRAD)
@@ -238,15 +240,17 @@ __device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, ui
             tma_load_4d(slot + L::V_BYTES + c * L::HB, &m.hist, bar, x0 - St<T>::HO, y0 - 2, z,
                         3 * hslot + c);
 }
-template <typename T>
+template <typename T, bool CM = false>
 __device__ __forceinline__ void issue_str(const Maps& m, unsigned char* slot, uint64_t* bar,
                                           int x0, int y0, int z) {
     using L = Lay<T>;
-    mbar_expect_tx(bar, (uint32_t)L::S_BYTES);
+    mbar_expect_tx(bar, (uint32_t)(L::S_BYTES - (CM ? L::FHB + L::FCB : 0)));
 #pragma unroll
     for (int h = 0; h < 3; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
-    tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0 - 2, z);
-    tma_load_3d(slot + L::S_LAM, &m.core[0], bar, x0, y0, z);
+    if constexpr (!CM) {
+        tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0 - 2, z);
+        tma_load_3d(slot + L::S_LAM, &m.core[0], bar, x0, y0, z);
+    }
 #pragma unroll
     for (int c = 0; c < 6; ++c) tma_load_3d(slot + L::S_CORE + c * L::CB, &m.core[1 + c], bar, x0, y0, z);
 }
@@ -436,8 +440,9 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         const float* hr1 = (const float*)(sl1 + L::V_RHO) + G.hf;   // plane k + 1
         const T* vc = (const T*)(sl2 + L::V_CORE) + G.cc;
         const bool ktop = k + 1 < g.nz;
-        const ZW zw = zweights<FS == ZS_NONE ? ZS_NONE : ZS_FWD>(g, k);   // surface forms only
-        const ZT zt = FS == ZS_ADJ ? ztransposed(g, k) : ZT{};
+        constexpr int ZF = FS & 3;                         // z-difference form
+        const ZW zw = zweights<ZF == ZS_NONE ? ZS_NONE : ZS_FWD>(g, k);   // surface forms only
+        const ZT zt = ZF == ZS_ADJ ? ztransposed(g, k) : ZT{};
         const long long o = (long long)k * g.plane + G.obase;
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
@@ -449,15 +454,15 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             // vx at (i+1/2, j, k)
             float dxx = g.c1x * (F(hxx, R + 1) - F(hxx, R)) + g.c2x * (F(hxx, R + 2) - F(hxx, R - 1));
             float dxy = g.c1y * (F(hxy, R) - F(hxy, R - HX)) + g.c2y * (F(hxy, R + HX) - F(hxy, R - 2 * HX));
-            float dxz = zdiff<FS, false>(g, zw, zt, qxz[A], qxz[B], qxz[C], qxz[D]);
+            float dxz = zdiff<ZF, false>(g, zw, zt, qxz[A], qxz[B], qxz[C], qxz[D]);
             // vy at (i, j+1/2, k)
             float dyx = g.c1x * (F(hxy, R) - F(hxy, R - 1)) + g.c2x * (F(hxy, R + 1) - F(hxy, R - 2));
             float dyy = g.c1y * (F(hyy, R + HX) - F(hyy, R)) + g.c2y * (F(hyy, R + 2 * HX) - F(hyy, R - HX));
-            float dyz = zdiff<FS, false>(g, zw, zt, qyz[A], qyz[B], qyz[C], qyz[D]);
+            float dyz = zdiff<ZF, false>(g, zw, zt, qyz[A], qyz[B], qyz[C], qyz[D]);
             // vz at (i, j, k+1/2)
             float dzx = g.c1x * (F(hxz, R) - F(hxz, R - 1)) + g.c2x * (F(hxz, R + 1) - F(hxz, R - 2));
             float dzy = g.c1y * (F(hyz, R) - F(hyz, R - HX)) + g.c2y * (F(hyz, R + HX) - F(hyz, R - 2 * HX));
-            float dzz = zdiff<FS, true>(g, zw, zt, qzz[A], qzz[B], qzz[C], qzz[D]);
+            float dzz = zdiff<ZF, true>(g, zw, zt, qzz[A], qzz[B], qzz[C], qzz[D]);
             if constexpr (kScaled<T>) {     // stored -> physical units
                 dxx *= P.inv[SXX]; dxy *= P.inv[SXY]; dxz *= P.inv[SXZ];
                 dyx *= P.inv[SXY]; dyy *= P.inv[SYY]; dyz *= P.inv[SYZ];
@@ -497,7 +502,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                 const float* qhz = Q.hz[rr];
                 const float exx = g.c1x * (F(vhx, R) - F(vhx, R - 1)) + g.c2x * (F(vhx, R + 1) - F(vhx, R - 2));
                 const float eyy = g.c1y * (F(vhy, R) - F(vhy, R - HX)) + g.c2y * (F(vhy, R + HX) - F(vhy, R - 2 * HX));
-                constexpr int FW = FS == ZS_NONE ? ZS_NONE : ZS_FWD;   // forward strain rates
+                constexpr int FW = ZF == ZS_NONE ? ZS_NONE : ZS_FWD;   // forward strain rates
                 const float ezz = zdiff<FW, false>(g, zw, zt, qhz[A], qhz[B], qhz[C], qhz[D]);
                 const float gxy = g.c1y * (F(vhx, R + HX) - F(vhx, R)) + g.c2y * (F(vhx, R + 2 * HX) - F(vhx, R - HX)) +
                                   g.c1x * (F(vhy, R + 1) - F(vhy, R)) + g.c2x * (F(vhy, R + 2) - F(vhy, R - 1));
@@ -523,10 +528,22 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                     P.X.acc[7][oo] = ga[rr][7] + (gv[rr][2] * iG - F(vhz, R)) * F(vc, VC_VZ * CORE + rr * TX);
                 }
             }
-            const float r0 = hr[RF];
-            const float bx = __fdividef(2.0f, r0 + hr[RF + G.cx]);
-            const float by = __fdividef(2.0f, r0 + hr[RF + G.cy[rr]]);
-            const float bz = __fdividef(2.0f, r0 + (ktop ? hr1[RF] : r0));
+            float bx, by, bz;
+            if constexpr ((FS & VAR_COARSE) != 0) {
+                // coarse medium: 1 / rho sampled at each v point
+                const float fi = (float)G.i, fj = (float)(G.j0 + rr), fk = (float)k;
+                const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
+                const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
+                const Ax zk = axis_at(fk, g.rz, g.mz), zh = axis_at(fk + 0.5f, g.rz, g.mz);
+                bx = __fdividef(1.0f, coarse_tri(g, 2, xh, yj, zk));
+                by = __fdividef(1.0f, coarse_tri(g, 2, xi, yh, zk));
+                bz = __fdividef(1.0f, coarse_tri(g, 2, xi, yj, zh));
+            } else {
+                const float r0 = hr[RF];
+                bx = __fdividef(2.0f, r0 + hr[RF + G.cx]);
+                by = __fdividef(2.0f, r0 + hr[RF + G.cy[rr]]);
+                bz = __fdividef(2.0f, r0 + (ktop ? hr1[RF] : r0));
+            }
             float vx = F(vc, VC_VX * CORE + rr * TX) + P.dto[VX] * bx * (dxx + dxy + dxz);
             float vy = F(vc, VC_VY * CORE + rr * TX) + P.dto[VY] * by * (dyx + dyy + dyz);
             float vz = F(vc, VC_VZ * CORE + rr * TX) + P.dto[VZ] * bz * (dzx + dzy + dzz);
@@ -562,7 +579,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     }
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_vel<T, MODE>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m, P.X.hslot);
+        issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m, P.X.hslot);
     return true;
 }
 
@@ -575,7 +592,7 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
     const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_vel<T, MODE>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot);
+            issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot);
     VelQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
@@ -653,8 +670,9 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
         const float* lc = (const float*)(sl2 + L::S_LAM) + G.cc;
         const T* cr = (const T*)(sl2 + L::S_CORE) + G.cc;
         const long long o = (long long)k * g.plane + G.obase;
-        const ZW zw = zweights<FS == ZS_NONE ? ZS_NONE : ZS_FWD>(g, k);   // surface forms only
-        const ZT zt = FS == ZS_ADJ ? ztransposed(g, k) : ZT{};
+        constexpr int ZF = FS & 3;                         // z-difference form
+        const ZW zw = zweights<ZF == ZS_NONE ? ZS_NONE : ZS_FWD>(g, k);   // surface forms only
+        const ZT zt = ZF == ZS_ADJ ? ztransposed(g, k) : ZT{};
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
             if (!G.own[rr]) continue;
@@ -665,13 +683,13 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
             // normal strain rates at (i, j, k)
             float exx = g.c1x * (F(hvx, R) - F(hvx, R - 1)) + g.c2x * (F(hvx, R + 1) - F(hvx, R - 2));
             float eyy = g.c1y * (F(hvy, R) - F(hvy, R - HX)) + g.c2y * (F(hvy, R + HX) - F(hvy, R - 2 * HX));
-            float ezz = zdiff<FS, false>(g, zw, zt, qvz[A], qvz[B], qvz[C], qvz[D]);
+            float ezz = zdiff<ZF, false>(g, zw, zt, qvz[A], qvz[B], qvz[C], qvz[D]);
             // shear terms at the shear points
             float vxy = g.c1y * (F(hvx, R + HX) - F(hvx, R)) + g.c2y * (F(hvx, R + 2 * HX) - F(hvx, R - HX));
             float vyx = g.c1x * (F(hvy, R + 1) - F(hvy, R)) + g.c2x * (F(hvy, R + 2) - F(hvy, R - 1));
-            float vxz = zdiff<FS, true>(g, zw, zt, qvx[A], qvx[B], qvx[C], qvx[D]);
+            float vxz = zdiff<ZF, true>(g, zw, zt, qvx[A], qvx[B], qvx[C], qvx[D]);
             float vzx = g.c1x * (F(hvz, R + 1) - F(hvz, R)) + g.c2x * (F(hvz, R + 2) - F(hvz, R - 1));
-            float vyz = zdiff<FS, true>(g, zw, zt, qvy[A], qvy[B], qvy[C], qvy[D]);
+            float vyz = zdiff<ZF, true>(g, zw, zt, qvy[A], qvy[B], qvy[C], qvy[D]);
             float vzy = g.c1y * (F(hvz, R + HX) - F(hvz, R)) + g.c2y * (F(hvz, R + 2 * HX) - F(hvz, R - HX));
             if constexpr (kScaled<T>) {     // stored -> physical units
                 exx *= P.inv[VX]; vxy *= P.inv[VX]; vxz *= P.inv[VX];
@@ -698,19 +716,34 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                 }
             }
             // medium: lambda, mu at the cell; mu means at the shear points
-            const int cyr = G.cy[rr];
-            const float lam = lc[rr * TX];
-            const float mu0 = hmu[RF], mxp = hmu[RF + G.cx], myp = hmu[RF + cyr];
-            const float mzp = hmu1[RF];
-            const float mxy = 0.25f * (mu0 + mxp + myp + hmu[RF + G.cx + cyr]);
-            float mxz = 0.25f * (mu0 + mxp + mzp + hmu1[RF + G.cx]);
-            float myz = 0.25f * (mu0 + myp + mzp + hmu1[RF + cyr]);
-            if constexpr (FS != ZS_NONE) {
-                // xz / yz shear points on the free-surface plane z = ks - 1/2:
-                // harmonic mean of the 4 cells (vacuum-formulation reading)
-                if (k == g.fs - 1) {
-                    mxz = 4.0f / (1.0f / mu0 + 1.0f / mxp + 1.0f / mzp + 1.0f / hmu1[RF + G.cx]);
-                    myz = 4.0f / (1.0f / mu0 + 1.0f / myp + 1.0f / mzp + 1.0f / hmu1[RF + cyr]);
+            float lam, mu0, mxy, mxz, myz;
+            if constexpr ((FS & VAR_COARSE) != 0) {
+                // coarse medium: lambda, mu at the cell, mu at each shear point
+                const float fi = (float)G.i, fj = (float)(G.j0 + rr), fk = (float)k;
+                const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
+                const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
+                const Ax zk = axis_at(fk, g.rz, g.mz), zh = axis_at(fk + 0.5f, g.rz, g.mz);
+                lam = coarse_tri(g, 0, xi, yj, zk);
+                mu0 = coarse_tri(g, 1, xi, yj, zk);
+                mxy = coarse_tri(g, 1, xh, yh, zk);
+                mxz = coarse_tri(g, 1, xh, yj, zh);
+                myz = coarse_tri(g, 1, xi, yh, zh);
+            } else {
+                const int cyr = G.cy[rr];
+                lam = lc[rr * TX];
+                mu0 = hmu[RF];
+                const float mxp = hmu[RF + G.cx], myp = hmu[RF + cyr];
+                const float mzp = hmu1[RF];
+                mxy = 0.25f * (mu0 + mxp + myp + hmu[RF + G.cx + cyr]);
+                mxz = 0.25f * (mu0 + mxp + mzp + hmu1[RF + G.cx]);
+                myz = 0.25f * (mu0 + myp + mzp + hmu1[RF + cyr]);
+                if constexpr (ZF != ZS_NONE) {
+                    // xz / yz shear points on the free-surface plane z = ks - 1/2:
+                    // harmonic mean of the 4 cells (vacuum-formulation reading)
+                    if (k == g.fs - 1) {
+                        mxz = 4.0f / (1.0f / mu0 + 1.0f / mxp + 1.0f / mzp + 1.0f / hmu1[RF + G.cx]);
+                        myz = 4.0f / (1.0f / mu0 + 1.0f / myp + 1.0f / mzp + 1.0f / hmu1[RF + cyr]);
+                    }
                 }
             }
             const float l2m = lam + 2.0f * mu0;
@@ -749,7 +782,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
         }
     }
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_str<T>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
+        issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
     return true;
 }
 
@@ -759,7 +792,7 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
     const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_str<T>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
+            issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
     StrQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
@@ -1125,6 +1158,9 @@ cudaError_t occupancy(int* occ) {
     // free-surface variants: same slots, occupancy taken from the plain ones
     if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, ZS_FWD>, smem_bytes<BND, T>(), &c);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_FWD>, smem_bytes<BND, T>(), &c);
+    // coarse-medium variants (the medium tiles' slot space stays unused)
+    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, VAR_COARSE>, smem_bytes<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_stress<BND, T, VAR_COARSE>, smem_bytes<BND, T>(), &c);
     if constexpr (std::is_same<T, float>::value) {     // history and reverse modes
         if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP>, smem_bytes<BND, T, M_CAP>(), &c);
         if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP, ZS_FWD>, smem_bytes<BND, T, M_CAP>(), &c);
@@ -1280,6 +1316,8 @@ void launch_v_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
 // z-weights, the others the forward ones.
 template <typename T, int MODE = M_FWD>
 void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
+    if constexpr (MODE == M_FWD)
+        if (P.g.cm[0]) return launch_v_fs<T, MODE, VAR_COARSE>(sp, P, st);
     if (P.g.fs != kNoSurface) {
         if constexpr (MODE == M_GRAD)
             return launch_v_fs<T, MODE, ZS_ADJ>(sp, P, st);
@@ -1309,6 +1347,7 @@ void launch_s_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
 // a free surface; FP32 storage only).
 template <typename T>
 void launch_s(const StencilPlan* sp, const PassParams& P, cudaStream_t st, bool reverse) {
+    if (P.g.cm[0]) return launch_s_fs<T, VAR_COARSE>(sp, P, st);
     if (P.g.fs != kNoSurface) {
         if constexpr (std::is_same<T, float>::value)
             if (reverse) return launch_s_fs<T, ZS_ADJ>(sp, P, st);

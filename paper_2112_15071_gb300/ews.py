@@ -81,6 +81,7 @@ SIGNATURES = [
     ("ews_set_source", _I, [_P, _I, _P, _P, _P, _I]),
     ("ews_set_receivers", _I, [_P, _I, _P]),
     ("ews_set_free_surface", _I, [_P, _I, _D]),
+    ("ews_set_model_coarse", _I, [_P, _I, _I, _I, _P, _P, _P, _I, _I]),
     ("ews_run", _I, [_P, _I, _D, _P, _I, _P]),
     ("ews_advance", _I, [_P, _I, _I, _D, _P, _I, _I]),
     ("ews_reset", _I, [_P]),
@@ -213,6 +214,17 @@ def ews_set_receivers(sim, pos):
     r = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
     _check(load().ews_set_receivers(sim, int(r.shape[0]),
                                     r.ctypes.data_as(C.c_void_p) if r.size else None))
+
+
+def ews_set_model_coarse(sim, a, b, rho, from_velocities: bool = False):
+    """Medium on its own grid; a, b, rho are [mz][my][mx] float32."""
+    shape = tuple(a.shape)
+    assert tuple(b.shape) == shape and tuple(rho.shape) == shape
+    (pa, d0), (pb, d1), (pr, d2) = _ptr(a), _ptr(b), _ptr(rho)
+    assert d0 == d1 == d2, "model arrays must share residency"
+    mz, my, mx = shape
+    _check(load().ews_set_model_coarse(sim, int(mx), int(my), int(mz), pa, pb, pr,
+                                       int(bool(from_velocities)), d0))
 
 
 def ews_set_free_surface(sim, ks: int, eps: float = 1e-3):
@@ -420,6 +432,10 @@ class Simulation:
         ews_set_source(self._h, SOURCE[kind] if isinstance(kind, str) else kind, pos, comp,
                        wavelet)
 
+    def set_model_coarse(self, a, b, rho, from_velocities=False):
+        """Medium on its own (coarser) grid, sampled trilinearly (Sec. 2.2.1)."""
+        ews_set_model_coarse(self._h, a, b, rho, from_velocities)
+
     def set_free_surface(self, ks, eps=1e-3):
         """Vacuum free surface above plane ks (set the model afterwards)."""
         ews_set_free_surface(self._h, ks, eps)
@@ -488,7 +504,10 @@ def simulation_for(prob, **kw) -> Simulation:
                      width=prob.width, f0=prob.f0, **kw)
     if prob.free_surface is not None:
         sim.set_free_surface(*prob.free_surface)
-    sim.set_model_vel(prob.vp, prob.vs, prob.rho)
+    if prob.coarse_medium is not None:
+        sim.set_model_coarse(*[np.ascontiguousarray(a, np.float32) for a in prob.coarse_medium])
+    else:
+        sim.set_model_vel(prob.vp, prob.vs, prob.rho)
     sim.set_source(prob.src_kind, prob.src_pos, prob.src_comp, prob.wavelet)
     sim.set_receivers(prob.rec_pos)
     return sim

@@ -249,6 +249,7 @@ class Problem:
     f0: float = 10.0
     extra: dict = field(default_factory=dict)
     free_surface: tuple | None = None   # (ks, eps): vacuum above plane ks
+    coarse_medium: tuple | None = None  # (lambda, mu, rho) on a medium grid [mz][my][mx]
 
     @property
     def ncell(self) -> int:
@@ -506,6 +507,24 @@ def small_problem(nx=40, ny=36, nz=28, nt=60, h=10.0, boundary="sponge",
     return Problem(f"small_{nx}x{ny}x{nz}_{boundary}_{kind}", nx, ny, nz, sp, dt, nt,
                    vp, vs, rho, kind, src, comp, _wavelet_for(kind, nt, dt, f0), rec,
                    boundary, width, float(f0))
+
+
+def with_coarse_medium(prob: Problem, m, seed: int = SEED, layer_vp=None) -> Problem:
+    """The problem with its medium given on a grid of m = (mx, my, mz) cells
+    over the same box (the paper's coarse medium textures, Sec. 2.2.1): the
+    layered-plus-random recipe drawn at that resolution (cell size n h / m
+    per axis), as Lame parameters and density.  The problem's own vp / vs /
+    rho stay as they were (the CFL step is kept: the coarse speeds come from
+    the same layer table)."""
+    mx, my, mz = (int(a) for a in m)
+    sp = tuple(prob.spacing[a] * (prob.nx, prob.ny, prob.nz)[a] / (mx, my, mz)[a] for a in range(3))
+    kw = {} if layer_vp is None else {"layer_vp": layer_vp}
+    vp, vs, rho = layered_random(mx, my, mz, sp, corr_len=4 * max(sp), seed=seed, **kw)
+    vp64, vs64, rho64 = (a.astype(np.float64) for a in (vp, vs, rho))
+    mu = rho64 * vs64 * vs64
+    lam = rho64 * vp64 * vp64 - 2.0 * mu
+    prob.coarse_medium = (lam.astype(np.float32), mu.astype(np.float32), rho.astype(np.float32))
+    return prob
 
 
 def random_state(nx: int, ny: int, nz: int, seed: int = SEED,
