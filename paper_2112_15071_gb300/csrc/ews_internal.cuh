@@ -88,24 +88,24 @@ __device__ __forceinline__ float coarse_at(const DevGrid& g, int q, float x, flo
 // sampled from a coarse grid instead of read as tiles).
 enum { ZS_NONE = 0, ZS_FWD = 1, ZS_ADJ = 2, VAR_COARSE = 4 };
 
-// z-difference weights at output plane k (free-surface reading): a
+// z-difference forms at output plane k (free-surface reading): a
 // z-derivative whose Eq. 4 stencil would take samples on both sides of the
 // surface plane z = (ks - 1/2) dz uses the 2nd-order difference: outputs at
-// integer z (planes ks-1, ks) and at half-integer z (planes ks-2 .. ks).
-// c1i, c2i: integer-z outputs; c1h, c2h: half-integer-z outputs.  Without a
-// surface (FS = ZS_NONE) callers use the DevGrid weights directly.
+// integer z (planes ks-1, ks: i2) and at half-integer z (planes ks-2 .. ks:
+// h2).  Without a surface (FS = ZS_NONE) both are false.
 struct ZW {
-    float c1i, c2i, c1h, c2h;
+    bool i2, h2;
+    __host__ __device__ float c1i(const DevGrid& g) const { return i2 ? g.c1z2 : g.c1z; }
+    __host__ __device__ float c2i(const DevGrid& g) const { return i2 ? 0.0f : g.c2z; }
+    __host__ __device__ float c1h(const DevGrid& g) const { return h2 ? g.c1z2 : g.c1z; }
+    __host__ __device__ float c2h(const DevGrid& g) const { return h2 ? 0.0f : g.c2z; }
 };
 template <int FS>
 __host__ __device__ __forceinline__ ZW zweights(const DevGrid& g, int k) {
-    if constexpr (FS != ZS_NONE) {
-        const bool i2 = (unsigned)(k - g.fs + 1) < 2u;
-        const bool h2 = (unsigned)(k - g.fs + 2) < 3u;
-        return ZW{i2 ? g.c1z2 : g.c1z, i2 ? 0.0f : g.c2z, h2 ? g.c1z2 : g.c1z, h2 ? 0.0f : g.c2z};
-    } else {
-        return ZW{0.0f, 0.0f, 0.0f, 0.0f};   // callers take the DevGrid weights
-    }
+    if constexpr (FS != ZS_NONE)
+        return ZW{(unsigned)(k - g.fs + 1) < 2u, (unsigned)(k - g.fs + 2) < 3u};
+    else
+        return ZW{false, false};
 }
 
 // Transposed z-weights at output plane k, per tap (A..D = the four samples
@@ -123,7 +123,8 @@ __host__ __device__ __forceinline__ ZT ztransposed(const DevGrid& g, int k) {
     const ZW m2 = zweights<ZS_FWD>(g, k - 2), m1 = zweights<ZS_FWD>(g, k - 1);
     const ZW z0 = zweights<ZS_FWD>(g, k), p1 = zweights<ZS_FWD>(g, k + 1);
     const ZW p2 = zweights<ZS_FWD>(g, k + 2);
-    return ZT{-m2.c2h, -m1.c1h, z0.c1h, p1.c2h, -m1.c2i, -z0.c1i, p1.c1i, p2.c2i};
+    return ZT{-m2.c2h(g), -m1.c1h(g), z0.c1h(g), p1.c2h(g),
+              -m1.c2i(g), -z0.c1i(g), p1.c1i(g), p2.c2i(g)};
 }
 
 // One z-difference from the four samples a..d (lowest plane first) of an
@@ -135,7 +136,8 @@ __device__ __forceinline__ float zdiff(const DevGrid& g, const ZW& zw, const ZT&
         return HALF ? zt.hA * a + zt.hB * b + zt.hC * c + zt.hD * d
                     : zt.iA * a + zt.iB * b + zt.iC * c + zt.iD * d;
     } else if constexpr (FS == ZS_FWD) {
-        return HALF ? zw.c1h * (c - b) + zw.c2h * (d - a) : zw.c1i * (c - b) + zw.c2i * (d - a);
+        // Eq. 4, or its inner pair alone on the switched planes
+        return (HALF ? zw.h2 : zw.i2) ? g.c1z2 * (c - b) : g.c1z * (c - b) + g.c2z * (d - a);
     } else {
         return g.c1z * (c - b) + g.c2z * (d - a);
     }

@@ -368,9 +368,29 @@ __device__ __forceinline__ bool over(float x) { return fabsf(x) > 65504.0f; }
 enum { VH_SXX, VH_SYY, VH_SXY, VH_SXZ, VH_SYZ };
 enum { VC_SZZ, VC_VX, VC_VY, VC_VZ };
 
+// Coarse medium grid: bilinear samples of the medium grid (at the thread's
+// x-y positions) on the two medium planes around the current output plane,
+// for the quantities sampled at integer z (zi) and at half-integer z (zh);
+// refreshed when the output plane crosses a medium plane, so each plane
+// costs one z-interpolation per quantity.
+template <int NQ>
+struct CoarseZ {
+    float lo[ROWS][NQ], hi[ROWS][NQ];
+    int lvl;
+};
+// Bilinear sample of medium array q on medium plane lvl.
+__device__ __forceinline__ float coarse_bilin(const DevGrid& g, int q, Ax x, Ax y, int lvl) {
+    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mx : 0;
+    const float* p = g.cm[q] + ((long long)lvl * g.my + y.i0) * g.mx + x.i0;
+    return lerp1(lerp1(__ldg(p), __ldg(p + ox), x.f), lerp1(__ldg(p + oy), __ldg(p + oy + ox), x.f),
+                 y.f);
+}
+
 struct VelQ {
     float zz[ROWS][4], xz[ROWS][4], yz[ROWS][4];   // sigma_zz k-1..k+2, sigma_xz/yz k-2..k+1
     float hx[ROWS][4], hy[ROWS][4], hz[ROWS][4];   // M_GRAD history: vx/vy k-1..k+2, vz k-2..k+1
+    CoarseZ<2> ci;    // rho at (i+1/2, j), (i, j+1/2), integer z
+    CoarseZ<1> ch;    // rho at (i, j), half-integer z
 };
 
 // One arrival of the z-loop, ring position PH = m mod 4.  Returns false if
@@ -531,13 +551,26 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             float bx, by, bz;
             if constexpr ((FS & VAR_COARSE) != 0) {
                 // coarse medium: 1 / rho sampled at each v point
-                const float fi = (float)G.i, fj = (float)(G.j0 + rr), fk = (float)k;
-                const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
-                const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
-                const Ax zk = axis_at(fk, g.rz, g.mz), zh = axis_at(fk + 0.5f, g.rz, g.mz);
-                bx = __fdividef(1.0f, coarse_tri(g, 2, xh, yj, zk));
-                by = __fdividef(1.0f, coarse_tri(g, 2, xi, yh, zk));
-                bz = __fdividef(1.0f, coarse_tri(g, 2, xi, yj, zh));
+                const Ax zk = axis_at((float)k, g.rz, g.mz), zh = axis_at(k + 0.5f, g.rz, g.mz);
+                const int up = g.mz > 1 ? 1 : 0;
+                if (zk.i0 != Q.ci.lvl || zh.i0 != Q.ch.lvl) {   // uniform across the CTA
+                    const float fi = (float)G.i, fj = (float)(G.j0 + rr);
+                    const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
+                    const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
+                    Q.ci.lo[rr][0] = coarse_bilin(g, 2, xh, yj, zk.i0);
+                    Q.ci.hi[rr][0] = coarse_bilin(g, 2, xh, yj, zk.i0 + up);
+                    Q.ci.lo[rr][1] = coarse_bilin(g, 2, xi, yh, zk.i0);
+                    Q.ci.hi[rr][1] = coarse_bilin(g, 2, xi, yh, zk.i0 + up);
+                    Q.ch.lo[rr][0] = coarse_bilin(g, 2, xi, yj, zh.i0);
+                    Q.ch.hi[rr][0] = coarse_bilin(g, 2, xi, yj, zh.i0 + up);
+                    if (rr == ROWS - 1) {
+                        Q.ci.lvl = zk.i0;
+                        Q.ch.lvl = zh.i0;
+                    }
+                }
+                bx = __fdividef(1.0f, lerp1(Q.ci.lo[rr][0], Q.ci.hi[rr][0], zk.f));
+                by = __fdividef(1.0f, lerp1(Q.ci.lo[rr][1], Q.ci.hi[rr][1], zk.f));
+                bz = __fdividef(1.0f, lerp1(Q.ch.lo[rr][0], Q.ch.hi[rr][0], zh.f));
             } else {
                 const float r0 = hr[RF];
                 bx = __fdividef(2.0f, r0 + hr[RF + G.cx]);
@@ -600,6 +633,8 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
         for (int q = 0; q < 4; ++q) {
             Q.zz[rr][q] = 0.f; Q.xz[rr][q] = 0.f; Q.yz[rr][q] = 0.f;
             Q.hx[rr][q] = 0.f; Q.hy[rr][q] = 0.f; Q.hz[rr][q] = 0.f;
+    Q.ci.lvl = -1;
+    Q.ch.lvl = -1;
         }
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
@@ -632,6 +667,8 @@ enum { SC_SXX, SC_SYY, SC_SZZ, SC_SXY, SC_SXZ, SC_SYZ };
 
 struct StrQ {
     float vx[ROWS][4], vy[ROWS][4], vz[ROWS][4];   // vx/vy k-1..k+2, vz k-2..k+1
+    CoarseZ<3> ci;    // lambda, mu at (i, j); mu at (i+1/2, j+1/2); integer z
+    CoarseZ<2> ch;    // mu at (i+1/2, j), (i, j+1/2); half-integer z
 };
 
 template <int BND, typename T, int PH, int FS>
@@ -719,15 +756,32 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
             float lam, mu0, mxy, mxz, myz;
             if constexpr ((FS & VAR_COARSE) != 0) {
                 // coarse medium: lambda, mu at the cell, mu at each shear point
-                const float fi = (float)G.i, fj = (float)(G.j0 + rr), fk = (float)k;
-                const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
-                const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
-                const Ax zk = axis_at(fk, g.rz, g.mz), zh = axis_at(fk + 0.5f, g.rz, g.mz);
-                lam = coarse_tri(g, 0, xi, yj, zk);
-                mu0 = coarse_tri(g, 1, xi, yj, zk);
-                mxy = coarse_tri(g, 1, xh, yh, zk);
-                mxz = coarse_tri(g, 1, xh, yj, zh);
-                myz = coarse_tri(g, 1, xi, yh, zh);
+                const Ax zk = axis_at((float)k, g.rz, g.mz), zh = axis_at(k + 0.5f, g.rz, g.mz);
+                const int up = g.mz > 1 ? 1 : 0;
+                if (zk.i0 != Q.ci.lvl || zh.i0 != Q.ch.lvl) {   // uniform across the CTA
+                    const float fi = (float)G.i, fj = (float)(G.j0 + rr);
+                    const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
+                    const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
+                    Q.ci.lo[rr][0] = coarse_bilin(g, 0, xi, yj, zk.i0);
+                    Q.ci.hi[rr][0] = coarse_bilin(g, 0, xi, yj, zk.i0 + up);
+                    Q.ci.lo[rr][1] = coarse_bilin(g, 1, xi, yj, zk.i0);
+                    Q.ci.hi[rr][1] = coarse_bilin(g, 1, xi, yj, zk.i0 + up);
+                    Q.ci.lo[rr][2] = coarse_bilin(g, 1, xh, yh, zk.i0);
+                    Q.ci.hi[rr][2] = coarse_bilin(g, 1, xh, yh, zk.i0 + up);
+                    Q.ch.lo[rr][0] = coarse_bilin(g, 1, xh, yj, zh.i0);
+                    Q.ch.hi[rr][0] = coarse_bilin(g, 1, xh, yj, zh.i0 + up);
+                    Q.ch.lo[rr][1] = coarse_bilin(g, 1, xi, yh, zh.i0);
+                    Q.ch.hi[rr][1] = coarse_bilin(g, 1, xi, yh, zh.i0 + up);
+                    if (rr == ROWS - 1) {
+                        Q.ci.lvl = zk.i0;
+                        Q.ch.lvl = zh.i0;
+                    }
+                }
+                lam = lerp1(Q.ci.lo[rr][0], Q.ci.hi[rr][0], zk.f);
+                mu0 = lerp1(Q.ci.lo[rr][1], Q.ci.hi[rr][1], zk.f);
+                mxy = lerp1(Q.ci.lo[rr][2], Q.ci.hi[rr][2], zk.f);
+                mxz = lerp1(Q.ch.lo[rr][0], Q.ch.hi[rr][0], zh.f);
+                myz = lerp1(Q.ch.lo[rr][1], Q.ch.hi[rr][1], zh.f);
             } else {
                 const int cyr = G.cy[rr];
                 lam = lc[rr * TX];
@@ -798,6 +852,8 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
     for (int rr = 0; rr < ROWS; ++rr)
 #pragma unroll
         for (int q = 0; q < 4; ++q) { Q.vx[rr][q] = 0.f; Q.vy[rr][q] = 0.f; Q.vz[rr][q] = 0.f; }
+    Q.ci.lvl = -1;
+    Q.ch.lvl = -1;
     uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
