@@ -385,6 +385,15 @@ __device__ __forceinline__ float coarse_bilin(const DevGrid& g, int q, Ax x, Ax 
     return lerp1(lerp1(__ldg(p), __ldg(p + ox), x.f), lerp1(__ldg(p + oy), __ldg(p + oy + ox), x.f),
                  y.f);
 }
+// Bring the 4 cells of such a sample into L1 ahead of use (no registers held).
+__device__ __forceinline__ void coarse_prefetch(const DevGrid& g, int q, Ax x, Ax y, int lvl) {
+    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mx : 0;
+    const float* p = g.cm[q] + ((long long)lvl * g.my + y.i0) * g.mx + x.i0;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + ox));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + oy));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + oy + ox));
+}
 
 struct VelQ {
     float zz[ROWS][4], xz[ROWS][4], yz[ROWS][4];   // sigma_zz k-1..k+2, sigma_xz/yz k-2..k+1
@@ -568,6 +577,19 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                         Q.ch.lvl = zh.i0;
                     }
                 }
+                {   // the next plane crosses a medium plane: prefetch its samples
+                    const Ax zk1 = axis_at(k + 1.0f, g.rz, g.mz), zh1 = axis_at(k + 1.5f, g.rz, g.mz);
+                    if (zk1.i0 != zk.i0 || zh1.i0 != zh.i0) {
+                        const float fi = (float)G.i, fj = (float)(G.j0 + rr);
+                        const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
+                        const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
+                        for (int u = 0; u <= up; ++u) {
+                            coarse_prefetch(g, 2, xh, yj, zk1.i0 + u);
+                            coarse_prefetch(g, 2, xi, yh, zk1.i0 + u);
+                            coarse_prefetch(g, 2, xi, yj, zh1.i0 + u);
+                        }
+                    }
+                }
                 bx = __fdividef(1.0f, lerp1(Q.ci.lo[rr][0], Q.ci.hi[rr][0], zk.f));
                 by = __fdividef(1.0f, lerp1(Q.ci.lo[rr][1], Q.ci.hi[rr][1], zk.f));
                 bz = __fdividef(1.0f, lerp1(Q.ch.lo[rr][0], Q.ch.hi[rr][0], zh.f));
@@ -649,8 +671,15 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
     return true;
 }
 
+// The coarse-medium forms keep their medium samples in registers: at most 3
+// CTAs per SM (85 registers a thread) for them.
+template <int BND, typename T, int MODE, int FS>
+constexpr int var_blocks() {
+    return (FS & VAR_COARSE) && min_blocks<BND, T, MODE>() > 3 ? 3 : min_blocks<BND, T, MODE>();
+}
+
 template <int BND, typename T, int MODE, int FS = ZS_NONE>
-__global__ void __launch_bounds__(NTH, (min_blocks<BND, T, MODE>())) k_velocity(
+__global__ void __launch_bounds__(NTH, (var_blocks<BND, T, MODE, FS>())) k_velocity(
     const __grid_constant__ Maps maps, const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int SB = slot_bytes<T, MODE>();
@@ -777,6 +806,21 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                         Q.ch.lvl = zh.i0;
                     }
                 }
+                {   // the next plane crosses a medium plane: prefetch its samples
+                    const Ax zk1 = axis_at(k + 1.0f, g.rz, g.mz), zh1 = axis_at(k + 1.5f, g.rz, g.mz);
+                    if (zk1.i0 != zk.i0 || zh1.i0 != zh.i0) {
+                        const float fi = (float)G.i, fj = (float)(G.j0 + rr);
+                        const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
+                        const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
+                        for (int u = 0; u <= up; ++u) {
+                            coarse_prefetch(g, 0, xi, yj, zk1.i0 + u);
+                            coarse_prefetch(g, 1, xi, yj, zk1.i0 + u);
+                            coarse_prefetch(g, 1, xh, yh, zk1.i0 + u);
+                            coarse_prefetch(g, 1, xh, yj, zh1.i0 + u);
+                            coarse_prefetch(g, 1, xi, yh, zh1.i0 + u);
+                        }
+                    }
+                }
                 lam = lerp1(Q.ci.lo[rr][0], Q.ci.hi[rr][0], zk.f);
                 mu0 = lerp1(Q.ci.lo[rr][1], Q.ci.hi[rr][1], zk.f);
                 mxy = lerp1(Q.ci.lo[rr][2], Q.ci.hi[rr][2], zk.f);
@@ -868,7 +912,7 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
 }
 
 template <int BND, typename T, int FS = ZS_NONE>
-__global__ void __launch_bounds__(NTH, min_blocks<BND, T>()) k_stress(const __grid_constant__ Maps maps,
+__global__ void __launch_bounds__(NTH, (var_blocks<BND, T, M_FWD, FS>())) k_stress(const __grid_constant__ Maps maps,
                                                                       const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(
