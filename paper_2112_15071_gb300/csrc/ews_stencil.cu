@@ -385,15 +385,6 @@ __device__ __forceinline__ float coarse_bilin(const DevGrid& g, int q, Ax x, Ax 
     return lerp1(lerp1(__ldg(p), __ldg(p + ox), x.f), lerp1(__ldg(p + oy), __ldg(p + oy + ox), x.f),
                  y.f);
 }
-// Bring the 4 cells of such a sample into L1 ahead of use (no registers held).
-__device__ __forceinline__ void coarse_prefetch(const DevGrid& g, int q, Ax x, Ax y, int lvl) {
-    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mx : 0;
-    const float* p = g.cm[q] + ((long long)lvl * g.my + y.i0) * g.mx + x.i0;
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + ox));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + oy));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + oy + ox));
-}
 
 struct VelQ {
     float zz[ROWS][4], xz[ROWS][4], yz[ROWS][4];   // sigma_zz k-1..k+2, sigma_xz/yz k-2..k+1
@@ -575,19 +566,6 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                     if (rr == ROWS - 1) {
                         Q.ci.lvl = zk.i0;
                         Q.ch.lvl = zh.i0;
-                    }
-                }
-                {   // the next plane crosses a medium plane: prefetch its samples
-                    const Ax zk1 = axis_at(k + 1.0f, g.rz, g.mz), zh1 = axis_at(k + 1.5f, g.rz, g.mz);
-                    if (zk1.i0 != zk.i0 || zh1.i0 != zh.i0) {
-                        const float fi = (float)G.i, fj = (float)(G.j0 + rr);
-                        const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
-                        const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
-                        for (int u = 0; u <= up; ++u) {
-                            coarse_prefetch(g, 2, xh, yj, zk1.i0 + u);
-                            coarse_prefetch(g, 2, xi, yh, zk1.i0 + u);
-                            coarse_prefetch(g, 2, xi, yj, zh1.i0 + u);
-                        }
                     }
                 }
                 bx = __fdividef(1.0f, lerp1(Q.ci.lo[rr][0], Q.ci.hi[rr][0], zk.f));
@@ -804,21 +782,6 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                     if (rr == ROWS - 1) {
                         Q.ci.lvl = zk.i0;
                         Q.ch.lvl = zh.i0;
-                    }
-                }
-                {   // the next plane crosses a medium plane: prefetch its samples
-                    const Ax zk1 = axis_at(k + 1.0f, g.rz, g.mz), zh1 = axis_at(k + 1.5f, g.rz, g.mz);
-                    if (zk1.i0 != zk.i0 || zh1.i0 != zh.i0) {
-                        const float fi = (float)G.i, fj = (float)(G.j0 + rr);
-                        const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
-                        const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
-                        for (int u = 0; u <= up; ++u) {
-                            coarse_prefetch(g, 0, xi, yj, zk1.i0 + u);
-                            coarse_prefetch(g, 1, xi, yj, zk1.i0 + u);
-                            coarse_prefetch(g, 1, xh, yh, zk1.i0 + u);
-                            coarse_prefetch(g, 1, xh, yj, zh1.i0 + u);
-                            coarse_prefetch(g, 1, xi, yh, zh1.i0 + u);
-                        }
                     }
                 }
                 lam = lerp1(Q.ci.lo[rr][0], Q.ci.hi[rr][0], zk.f);
