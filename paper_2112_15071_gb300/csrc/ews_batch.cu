@@ -65,15 +65,26 @@ void gradient_forward_program(std::vector<Stage>& P, const BatchShot& B, int nt,
     P.push_back({BK_RESID, 0, 0, 0, 1});
 }
 
-void gradient_reverse_program(std::vector<Stage>& P, const BatchShot& B, int nt, int K, int c_res) {
-    P.push_back({BK_ZERO_A, 0, 0, 0, B.items_elem});
+// The reverse part as segments, last first: per segment a recompute phase
+// (restore the checkpoint and rerun the segment with history capture; empty
+// for the resident range) and a reverse phase (reverse steps, buoyancy
+// term, flushes).  The first reverse phase also zeroes the adjoint state,
+// the last one finalises the gradients.  Recompute phases run in the lean
+// executor (3 CTAs per SM), reverse phases in the one with the reverse
+// velocity pass (2 per SM).
+struct Phases {
+    std::vector<std::vector<Stage>> rec, rev;
+};
+void gradient_reverse_phases(Phases& F, const BatchShot& B, int nt, int K, int c_res) {
     for (int c = c_res; c >= 0; --c) {
+        std::vector<Stage> R, P;
         const int n0 = c * K, n1 = c == c_res ? nt : n0 + K;
         if (c < c_res) {
-            P.push_back({BK_LOAD, 0, c, 0, B.items_elem});
-            P.push_back({BK_HIST0, 0, 0, 0, B.items_elem});
-            for (int n = n0; n < n1; ++n) push_step(P, B, n, n - n0 + 1, false);
+            R.push_back({BK_LOAD, 0, c, 0, B.items_elem});
+            R.push_back({BK_HIST0, 0, 0, 0, B.items_elem});
+            for (int n = n0; n < n1; ++n) push_step(R, B, n, n - n0 + 1, false);
         }
+        if (c == c_res) P.push_back({BK_ZERO_A, 0, 0, 0, B.items_elem});
         for (int m = n1 - 1; m >= n0; --m) {
             P.push_back({BK_VEL_GRAD, m, m - n0 + 1, m + 1 < n1 ? 1 : 0, B.items_pass});
             P.push_back({BK_STR_ADJ, m, 0, 0, B.items_pass});
@@ -81,8 +92,10 @@ void gradient_reverse_program(std::vector<Stage>& P, const BatchShot& B, int nt,
         }
         P.push_back({BK_RHO, 0, 0, 0, B.items_elem});
         P.push_back({BK_FLUSH, 0, 0, 0, B.items_elem});
+        if (c == 0) P.push_back({BK_FINAL, 0, 0, 0, B.items_elem});
+        F.rec.push_back(std::move(R));
+        F.rev.push_back(std::move(P));
     }
-    P.push_back({BK_FINAL, 0, 0, 0, B.items_elem});
 }
 
 // First resident segment of the history budget (as in the adjoint of
@@ -373,7 +386,8 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
 
     int* d_err = shots[0].sim->err;            // any of the shots' error flags
     std::vector<BatchShot> bs(nshots);
-    std::vector<std::vector<Stage>> progs(nshots), rprogs(nshots);
+    std::vector<std::vector<Stage>> progs(nshots);
+    std::vector<Phases> phases(nshots);
     for (int i = 0; i < nshots; ++i) {
         ews_batch_shot& b = shots[i];
         ews_sim* s = b.sim;
@@ -396,18 +410,37 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         if (r != EWS_OK) return r;
         if (b.observed) {
             gradient_forward_program(progs[i], bs[i], b.nt, K, c_res);
-            gradient_reverse_program(rprogs[i], bs[i], b.nt, K, c_res);
+            gradient_reverse_phases(phases[i], bs[i], b.nt, K, c_res);
         } else {
             forward_program(progs[i], bs[i], b.nt);
         }
     }
     const unsigned long long wait = (unsigned long long)o.dep_wait_ms * 1000000ull;
-    ews_status r = run_persistent(bs, progs, bnd, any_fs ? BX_LEAN_FS : BX_LEAN, o.ctas_per_sm,
-                                  d_err, st, nullptr, wait, o.test_unsatisfiable != 0);
-    if (r == EWS_OK && grad)
-        r = run_persistent(bs, rprogs, bnd, any_fs ? BX_GRAD_FS : BX_GRAD, o.ctas_per_sm, d_err,
-                           st, nullptr, wait, false);
+    const int lean = any_fs ? BX_LEAN_FS : BX_LEAN, rev = any_fs ? BX_GRAD_FS : BX_GRAD;
+    ews_status r = run_persistent(bs, progs, bnd, lean, o.ctas_per_sm, d_err, st, nullptr, wait,
+                                  o.test_unsatisfiable != 0);
     if (r != EWS_OK) return r;
+    // Reverse parts, segment phase by segment phase: shots with fewer
+    // segments join for the last phases, so all finish in the last one.
+    size_t nph = 0;
+    for (const auto& f : phases) nph = std::max(nph, f.rev.size());
+    for (size_t ph = 0; ph < nph && grad; ++ph) {
+        std::vector<std::vector<Stage>> rec(nshots), rv(nshots);
+        bool any_rec = false;
+        for (int i = 0; i < nshots; ++i) {
+            const size_t n = phases[i].rev.size(), off = nph - n;
+            if (ph < off) continue;
+            rec[i] = phases[i].rec[ph - off];
+            rv[i] = phases[i].rev[ph - off];
+            any_rec |= !rec[i].empty();
+        }
+        if (any_rec && (r = run_persistent(bs, rec, bnd, lean, o.ctas_per_sm, d_err, st, nullptr,
+                                           wait, false)) != EWS_OK)
+            return r;
+        if ((r = run_persistent(bs, rv, bnd, rev, o.ctas_per_sm, d_err, st, nullptr, wait,
+                                false)) != EWS_OK)
+            return r;
+    }
     for (int i = 0; i < nshots; ++i) {
         ews_sim* s = shots[i].sim;
         s->fresh = false;
