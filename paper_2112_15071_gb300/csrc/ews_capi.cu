@@ -861,28 +861,24 @@ ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float*
     if (mx < 1 || my < 1 || mz < 1) return fail(EWS_EINVAL, "medium grid %d x %d x %d", mx, my, mz);
     if (s->g.fs != kNoSurface)
         return fail(EWS_EINVAL, "a coarse medium grid with a free surface is not built");
-    // rows padded to 16 bytes and arrays to 128 bytes (TMA strides and bases)
-    const int mpx = (mx + 3) / 4 * 4;
-    const size_t m = ((size_t)mpx * my * mz + 31) / 32 * 32;
+    const size_t m = (size_t)mx * my * mz;
     s->model_set = false;
     for (int q = 0; q < 3; ++q) s->g.cm[q] = nullptr;
     cudaFree(s->cmed);
     s->cmed = nullptr;
     CK(cudaMalloc(&s->cmed, 3 * m * sizeof(float)));
-    CK(cudaMemsetAsync(s->cmed, 0, 3 * m * sizeof(float), s->stream));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const float* src[3] = {a, b, rho};
-    for (int q = 0; q < 3; ++q)
-        CK(cudaMemcpy2DAsync(s->cmed + q * m, mpx * sizeof(float), src[q], mx * sizeof(float),
-                             mx * sizeof(float), (size_t)my * mz, kind, s->stream));
+    CK(cudaMemcpyAsync(s->cmed, a, m * sizeof(float), kind, s->stream));
+    CK(cudaMemcpyAsync(s->cmed + m, b, m * sizeof(float), kind, s->stream));
+    CK(cudaMemcpyAsync(s->cmed + 2 * m, rho, m * sizeof(float), kind, s->stream));
     // validation, velocity -> Lame conversion and the medium bounds on the
     // medium grid's own cells (the interpolated values lie between them)
     DevGrid gc{};
     gc.nx = mx;
     gc.ny = my;
     gc.nz = mz;
-    gc.pitch = mpx;
-    gc.plane = (long long)mpx * my;
+    gc.pitch = mx;
+    gc.plane = (long long)mx * my;
     gc.fs = kNoSurface;
     CK(cudaMemsetAsync(s->flags, 0, 5 * sizeof(unsigned), s->stream));
     CK(cudaMemsetAsync(s->flags + 2, 0x7F, 2 * sizeof(unsigned), s->stream));
@@ -906,7 +902,6 @@ ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float*
     s->g.mx = mx;
     s->g.my = my;
     s->g.mz = mz;
-    s->g.mpx = mpx;
     s->g.rx = (float)((double)mx / s->g.nx);
     s->g.ry = (float)((double)my / s->g.ny);
     s->g.rz = (float)((double)mz / s->g.nz);

@@ -46,7 +46,6 @@ struct DevGrid {
     // grid's cells), and m / n per axis
     const float* cm[3];
     int mx, my, mz;
-    int mpx;              // row pitch of the medium-grid arrays (mx rounded up to 4)
     float rx, ry, rz;
     // staged coarse medium: the medium cells a tile needs arrive with the
     // fields in the TMA ring as boxes of cbx x cby x 3 cells (0: sampled
@@ -79,9 +78,9 @@ __device__ __forceinline__ Ax axis_at(float x, float r, int m) {
 __device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(t, b - a, a); }
 // q: 0 lambda, 1 mu, 2 rho.  Axes of extent 1 read the same cell twice.
 __device__ __forceinline__ float coarse_tri(const DevGrid& g, int q, Ax x, Ax y, Ax z) {
-    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mpx : 0;
-    const long long oz = g.mz > 1 ? (long long)g.mpx * g.my : 0;
-    const float* p = g.cm[q] + ((long long)z.i0 * g.my + y.i0) * g.mpx + x.i0;
+    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mx : 0;
+    const long long oz = g.mz > 1 ? (long long)g.mx * g.my : 0;
+    const float* p = g.cm[q] + ((long long)z.i0 * g.my + y.i0) * g.mx + x.i0;
     const float c00 = lerp1(__ldg(p), __ldg(p + ox), x.f);
     const float c10 = lerp1(__ldg(p + oy), __ldg(p + oy + ox), x.f);
     const float c01 = lerp1(__ldg(p + oz), __ldg(p + oz + ox), x.f);

@@ -396,8 +396,8 @@ struct CoarseZ {
 };
 // Bilinear sample of medium array q on medium plane lvl.
 __device__ __forceinline__ float coarse_bilin(const DevGrid& g, int q, Ax x, Ax y, int lvl) {
-    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mpx : 0;
-    const float* p = g.cm[q] + ((long long)lvl * g.my + y.i0) * g.mpx + x.i0;
+    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.mx : 0;
+    const float* p = g.cm[q] + ((long long)lvl * g.my + y.i0) * g.mx + x.i0;
     return lerp1(lerp1(__ldg(p), __ldg(p + ox), x.f), lerp1(__ldg(p + oy), __ldg(p + oy + ox), x.f),
                  y.f);
 }
@@ -1567,7 +1567,7 @@ cudaError_t stencil_plan_set_medium(StencilPlan* p, const DevGrid& g, const DevM
     // medium boxes of cbx x cby x 3 cells over the dense medium grid
     auto box_map = [&](CUtensorMap* map, const float* base) {
         cuuint64_t dims[3] = {(cuuint64_t)g.mx, (cuuint64_t)g.my, (cuuint64_t)g.mz};
-        cuuint64_t strides[2] = {(cuuint64_t)g.mpx * 4, (cuuint64_t)g.mpx * g.my * 4};
+        cuuint64_t strides[2] = {(cuuint64_t)g.mx * 4, (cuuint64_t)g.mx * g.my * 4};
         cuuint32_t box[3] = {(cuuint32_t)g.cbx, (cuuint32_t)g.cby, 3};
         cuuint32_t es[3] = {1, 1, 1};
         return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides,
