@@ -207,8 +207,6 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
     if (!a || !b || !rho) return fail(EWS_EINVAL, "null model array");
     if (s->g.cm[0]) {                          // back from a coarse medium grid
         for (int q = 0; q < 3; ++q) s->g.cm[q] = nullptr;
-        s->g.cbx = s->g.cby = 0;
-        CK(stencil_plan_set_medium(s->plan, s->g, s->M()));
         s->gen++;
     }
     DevMedium M = s->M();
@@ -905,22 +903,6 @@ ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float*
     s->g.rx = (float)((double)mx / s->g.nx);
     s->g.ry = (float)((double)my / s->g.ny);
     s->g.rz = (float)((double)mz / s->g.nz);
-    // Stage the medium cells of each tile in the TMA ring when the boxes fit
-    // the slot space of the medium tiles they replace (FP32 fields, medium
-    // grid no finer than the wavefield grid): a 32 x 8 tile needs at most
-    // ceil(32 m/n) + 2 cells in x (plus 3 for the 16-byte aligned origin)
-    // and ceil(8 m/n) + 2 in y, 3 medium planes per output plane.
-    s->g.cbx = s->g.cby = 0;
-    if (s->opt.storage == EWS_STORAGE_F32 && mx <= s->g.nx && my <= s->g.ny && mz <= s->g.nz) {
-        const int bx = ((int)std::ceil(32.0 * mx / s->g.nx) + 6 + 3) / 4 * 4;
-        const int by = (int)std::ceil(8.0 * my / s->g.ny) + 3;
-        const int b = bx * by * 3 * 4;
-        if (b <= 1920 && (b + 127) / 128 * 128 + b <= 2944) {
-            s->g.cbx = bx;
-            s->g.cby = by;
-        }
-    }
-    CK(stencil_plan_set_medium(s->plan, s->g, s->M()));
     s->model_set = true;
     s->pml_dt = -1.0;
     s->gen++;

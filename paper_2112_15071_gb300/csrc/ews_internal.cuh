@@ -47,10 +47,6 @@ struct DevGrid {
     const float* cm[3];
     int mx, my, mz;
     float rx, ry, rz;
-    // staged coarse medium: the medium cells a tile needs arrive with the
-    // fields in the TMA ring as boxes of cbx x cby x 3 cells (0: sampled
-    // from global memory instead)
-    int cbx, cby;
 };
 constexpr int kNoSurface = -(1 << 28);
 
@@ -62,17 +58,10 @@ struct Ax {
     int i0;
     float f;
 };
-__host__ __device__ __forceinline__ float coarse_coord(float x, float r, int m) {
-    const float c = fmaf(x + 0.5f, r, -0.5f);
-    return c < 0.0f ? 0.0f : (c > (float)(m - 1) ? (float)(m - 1) : c);
-}
-__host__ __device__ __forceinline__ int coarse_lower(float c, int m) {
-    const int i0 = (int)c, top = m - 2 > 0 ? m - 2 : 0;
-    return i0 < top ? i0 : top;
-}
 __device__ __forceinline__ Ax axis_at(float x, float r, int m) {
-    const float c = coarse_coord(x, r, m);
-    const int i0 = coarse_lower(c, m);
+    float c = fmaf(x + 0.5f, r, -0.5f);
+    c = fminf(fmaxf(c, 0.0f), (float)(m - 1));
+    const int i0 = min((int)c, max(m - 2, 0));
     return Ax{i0, c - (float)i0};
 }
 __device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(t, b - a, a); }
@@ -97,14 +86,7 @@ __device__ __forceinline__ float coarse_at(const DevGrid& g, int q, float x, flo
 // with a surface; the transposed form of the reverse sweep with a surface.
 // A pass variant is one of these, or VAR_COARSE (no surface, the medium
 // sampled from a coarse grid instead of read as tiles).
-enum { ZS_NONE = 0, ZS_FWD = 1, ZS_ADJ = 2, VAR_COARSE = 4, VAR_COARSE_SM = 8 };
-
-// Lower medium-grid index of the box a tile (or a plane) needs: that of
-// position x (as in axis_at), rounded down to `align` (TMA needs the x
-// origin of a box on a 16-byte boundary).
-__host__ __device__ __forceinline__ int coarse_box0(float x, float r, int m, int align) {
-    return coarse_lower(coarse_coord(x, r, m), m) / align * align;
-}
+enum { ZS_NONE = 0, ZS_FWD = 1, ZS_ADJ = 2, VAR_COARSE = 4 };
 
 // z-difference forms at output plane k (free-surface reading): a
 // z-derivative whose Eq. 4 stencil would take samples on both sides of the
@@ -394,9 +376,6 @@ cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const 
                                  int* err, cudaStream_t st);
 // History buffer of the reverse pass: nslot slots of 3 fields, slot s field c
 // at hist + (3 s + c) * fstride, pitched like the wavefields.
-// Point the plan's medium tensor maps at the coarse medium boxes of g
-// (g.cbx > 0), or back at the wavefield-grid medium M.
-cudaError_t stencil_plan_set_medium(StencilPlan* p, const DevGrid& g, const DevMedium& M);
 cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const float* hist,
                                      long long fstride, int nslot);
 

@@ -223,22 +223,15 @@ static_assert(MAXH == kMapsHalo && MAXC == kMapsCore, "tensor-map counts of Maps
 
 // Issue the TMA loads of z-plane `z` of tile (x0, y0) into `slot`.
 // CM: the medium is sampled from a coarse grid, so its tiles are not loaded.
-// CS: the medium boxes of a staged coarse medium replace them (g gives the
-// box sizes and origins).
-template <typename T, int MODE, bool CM = false, bool CS = false>
+template <typename T, int MODE, bool CM = false>
 __device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, uint64_t* bar,
-                                          int x0, int y0, int z, int hslot, const DevGrid& g) {
+                                          int x0, int y0, int z, int hslot) {
     using L = Lay<T>;
-    const uint32_t cb = CS ? (uint32_t)(g.cbx * g.cby * 3 * 4) : 0u;
     mbar_expect_tx(bar, (uint32_t)(L::V_BYTES + (MODE == M_GRAD ? 3 * L::HB : 0) -
-                                   (CM ? L::FHB : 0)) + cb);
+                                   (CM ? L::FHB : 0)));
 #pragma unroll
     for (int h = 0; h < 5; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
-    if constexpr (CS)
-        tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, coarse_box0(x0, g.rx, g.mx, 4),
-                    coarse_box0(y0, g.ry, g.my, 1), coarse_box0(z, g.rz, g.mz, 1));
-    else if constexpr (!CM)
-        tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0 - 2, z);
+    if constexpr (!CM) tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0 - 2, z);
 #pragma unroll
     for (int c = 0; c < 4; ++c) tma_load_3d(slot + L::V_CORE + c * L::CB, &m.core[c], bar, x0, y0, z);
     if constexpr (MODE == M_GRAD)
@@ -247,23 +240,14 @@ __device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, ui
             tma_load_4d(slot + L::V_BYTES + c * L::HB, &m.hist, bar, x0 - St<T>::HO, y0 - 2, z,
                         3 * hslot + c);
 }
-// Byte offset of the second staged medium box (mu) after the first (lambda).
-__device__ __forceinline__ int coarse_box2(const DevGrid& g) { return (g.cbx * g.cby * 3 * 4 + 127) / 128 * 128; }
-
-template <typename T, bool CM = false, bool CS = false>
+template <typename T, bool CM = false>
 __device__ __forceinline__ void issue_str(const Maps& m, unsigned char* slot, uint64_t* bar,
-                                          int x0, int y0, int z, const DevGrid& g) {
+                                          int x0, int y0, int z) {
     using L = Lay<T>;
-    const uint32_t cb = CS ? (uint32_t)(2 * g.cbx * g.cby * 3 * 4) : 0u;
-    mbar_expect_tx(bar, (uint32_t)(L::S_BYTES - (CM ? L::FHB + L::FCB : 0)) + cb);
+    mbar_expect_tx(bar, (uint32_t)(L::S_BYTES - (CM ? L::FHB + L::FCB : 0)));
 #pragma unroll
     for (int h = 0; h < 3; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
-    if constexpr (CS) {
-        const int cx = coarse_box0(x0, g.rx, g.mx, 4), cy = coarse_box0(y0, g.ry, g.my, 1);
-        const int cz = coarse_box0(z, g.rz, g.mz, 1);
-        tma_load_3d(slot + L::S_MU, &m.core[0], bar, cx, cy, cz);                       // lambda
-        tma_load_3d(slot + L::S_MU + coarse_box2(g), &m.halo[3], bar, cx, cy, cz);      // mu
-    } else if constexpr (!CM) {
+    if constexpr (!CM) {
         tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0 - 2, z);
         tma_load_3d(slot + L::S_LAM, &m.core[0], bar, x0, y0, z);
     }
@@ -400,17 +384,6 @@ __device__ __forceinline__ float coarse_bilin(const DevGrid& g, int q, Ax x, Ax 
     const float* p = g.cm[q] + ((long long)lvl * g.my + y.i0) * g.mx + x.i0;
     return lerp1(lerp1(__ldg(p), __ldg(p + ox), x.f), lerp1(__ldg(p + oy), __ldg(p + oy + ox), x.f),
                  y.f);
-}
-
-// Trilinear sample from a staged medium box (cbx x cby x 3 cells whose
-// lowest cell is (cx0, cy0, cz0) of the medium grid).
-__device__ __forceinline__ float coarse_box_tri(const float* box, const DevGrid& g, Ax x, Ax y,
-                                                Ax z, int cx0, int cy0, int cz0) {
-    const int ox = g.mx > 1 ? 1 : 0, oy = g.my > 1 ? g.cbx : 0, oz = g.mz > 1 ? g.cbx * g.cby : 0;
-    const float* p = box + ((z.i0 - cz0) * g.cby + (y.i0 - cy0)) * g.cbx + (x.i0 - cx0);
-    const float c00 = lerp1(p[0], p[ox], x.f), c10 = lerp1(p[oy], p[oy + ox], x.f);
-    const float c01 = lerp1(p[oz], p[oz + ox], x.f), c11 = lerp1(p[oz + oy], p[oz + oy + ox], x.f);
-    return lerp1(lerp1(c00, c10, y.f), lerp1(c01, c11, y.f), z.f);
 }
 
 struct VelQ {
@@ -598,19 +571,6 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                 bx = __fdividef(1.0f, lerp1(Q.ci.lo[rr][0], Q.ci.hi[rr][0], zk.f));
                 by = __fdividef(1.0f, lerp1(Q.ci.lo[rr][1], Q.ci.hi[rr][1], zk.f));
                 bz = __fdividef(1.0f, lerp1(Q.ch.lo[rr][0], Q.ch.hi[rr][0], zh.f));
-            } else if constexpr ((FS & VAR_COARSE_SM) != 0) {
-                // staged coarse medium: rho box of plane k in the slot
-                const float* box = (const float*)(sl2 + L::V_RHO);
-                const int cx0 = coarse_box0((float)G.x0, g.rx, g.mx, 4);
-                const int cy0 = coarse_box0((float)G.y0, g.ry, g.my, 1);
-                const int cz0 = coarse_box0((float)k, g.rz, g.mz, 1);
-                const float fi = (float)G.i, fj = (float)(G.j0 + rr), fk = (float)k;
-                const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
-                const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
-                const Ax zk = axis_at(fk, g.rz, g.mz), zh = axis_at(fk + 0.5f, g.rz, g.mz);
-                bx = __fdividef(1.0f, coarse_box_tri(box, g, xh, yj, zk, cx0, cy0, cz0));
-                by = __fdividef(1.0f, coarse_box_tri(box, g, xi, yh, zk, cx0, cy0, cz0));
-                bz = __fdividef(1.0f, coarse_box_tri(box, g, xi, yj, zh, cx0, cy0, cz0));
             } else {
                 const float r0 = hr[RF];
                 bx = __fdividef(2.0f, r0 + hr[RF + G.cx]);
@@ -652,7 +612,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     }
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_vel<T, MODE, (FS & (VAR_COARSE | VAR_COARSE_SM)) != 0, (FS & VAR_COARSE_SM) != 0>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m, P.X.hslot, P.g);
+        issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m, P.X.hslot);
     return true;
 }
 
@@ -665,7 +625,7 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
     const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_vel<T, MODE, (FS & (VAR_COARSE | VAR_COARSE_SM)) != 0, (FS & VAR_COARSE_SM) != 0>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot, P.g);
+            issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot);
     VelQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
@@ -693,7 +653,7 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
 // CTAs per SM (85 registers a thread) for them.
 template <int BND, typename T, int MODE, int FS>
 constexpr int var_blocks() {
-    return (FS & (VAR_COARSE | VAR_COARSE_SM)) && min_blocks<BND, T, MODE>() > 3 ? 3 : min_blocks<BND, T, MODE>();
+    return (FS & VAR_COARSE) && min_blocks<BND, T, MODE>() > 3 ? 3 : min_blocks<BND, T, MODE>();
 }
 
 template <int BND, typename T, int MODE, int FS = ZS_NONE>
@@ -829,22 +789,6 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                 mxy = lerp1(Q.ci.lo[rr][2], Q.ci.hi[rr][2], zk.f);
                 mxz = lerp1(Q.ch.lo[rr][0], Q.ch.hi[rr][0], zh.f);
                 myz = lerp1(Q.ch.lo[rr][1], Q.ch.hi[rr][1], zh.f);
-            } else if constexpr ((FS & VAR_COARSE_SM) != 0) {
-                // staged coarse medium: lambda and mu boxes of plane k in the slot
-                const float* lbox = (const float*)(sl2 + L::S_MU);
-                const float* mbox = (const float*)(sl2 + L::S_MU + coarse_box2(g));
-                const int cx0 = coarse_box0((float)G.x0, g.rx, g.mx, 4);
-                const int cy0 = coarse_box0((float)G.y0, g.ry, g.my, 1);
-                const int cz0 = coarse_box0((float)k, g.rz, g.mz, 1);
-                const float fi = (float)G.i, fj = (float)(G.j0 + rr), fk = (float)k;
-                const Ax xi = axis_at(fi, g.rx, g.mx), xh = axis_at(fi + 0.5f, g.rx, g.mx);
-                const Ax yj = axis_at(fj, g.ry, g.my), yh = axis_at(fj + 0.5f, g.ry, g.my);
-                const Ax zk = axis_at(fk, g.rz, g.mz), zh = axis_at(fk + 0.5f, g.rz, g.mz);
-                lam = coarse_box_tri(lbox, g, xi, yj, zk, cx0, cy0, cz0);
-                mu0 = coarse_box_tri(mbox, g, xi, yj, zk, cx0, cy0, cz0);
-                mxy = coarse_box_tri(mbox, g, xh, yh, zk, cx0, cy0, cz0);
-                mxz = coarse_box_tri(mbox, g, xh, yj, zh, cx0, cy0, cz0);
-                myz = coarse_box_tri(mbox, g, xi, yh, zh, cx0, cy0, cz0);
             } else {
                 const int cyr = G.cy[rr];
                 lam = lc[rr * TX];
@@ -899,7 +843,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
         }
     }
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_str<T, (FS & (VAR_COARSE | VAR_COARSE_SM)) != 0, (FS & VAR_COARSE_SM) != 0>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m, P.g);
+        issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
     return true;
 }
 
@@ -909,7 +853,7 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
     const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_str<T, (FS & (VAR_COARSE | VAR_COARSE_SM)) != 0, (FS & VAR_COARSE_SM) != 0>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.g);
+            issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
     StrQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
@@ -1277,14 +1221,9 @@ cudaError_t occupancy(int* occ) {
     // free-surface variants: same slots, occupancy taken from the plain ones
     if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, ZS_FWD>, smem_bytes<BND, T>(), &c);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_FWD>, smem_bytes<BND, T>(), &c);
-    // coarse-medium variants (the medium tiles' slot space stays unused, or
-    // holds the staged medium boxes)
+    // coarse-medium variants (the medium tiles' slot space stays unused)
     if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, VAR_COARSE>, smem_bytes<BND, T>(), &c);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T, VAR_COARSE>, smem_bytes<BND, T>(), &c);
-    if constexpr (std::is_same<T, float>::value) {
-        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, VAR_COARSE_SM>, smem_bytes<BND, T>(), &c);
-        if (e == cudaSuccess) e = prepare(k_stress<BND, T, VAR_COARSE_SM>, smem_bytes<BND, T>(), &c);
-    }
     if constexpr (std::is_same<T, float>::value) {     // history and reverse modes
         if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP>, smem_bytes<BND, T, M_CAP>(), &c);
         if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP, ZS_FWD>, smem_bytes<BND, T, M_CAP>(), &c);
@@ -1441,11 +1380,7 @@ void launch_v_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
 template <typename T, int MODE = M_FWD>
 void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     if constexpr (MODE == M_FWD)
-        if (P.g.cm[0]) {
-            if constexpr (std::is_same<T, float>::value)
-                if (P.g.cbx) return launch_v_fs<T, MODE, VAR_COARSE_SM>(sp, P, st);
-            return launch_v_fs<T, MODE, VAR_COARSE>(sp, P, st);
-        }
+        if (P.g.cm[0]) return launch_v_fs<T, MODE, VAR_COARSE>(sp, P, st);
     if (P.g.fs != kNoSurface) {
         if constexpr (MODE == M_GRAD)
             return launch_v_fs<T, MODE, ZS_ADJ>(sp, P, st);
@@ -1475,11 +1410,7 @@ void launch_s_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
 // a free surface; FP32 storage only).
 template <typename T>
 void launch_s(const StencilPlan* sp, const PassParams& P, cudaStream_t st, bool reverse) {
-    if (P.g.cm[0]) {
-        if constexpr (std::is_same<T, float>::value)
-            if (P.g.cbx) return launch_s_fs<T, VAR_COARSE_SM>(sp, P, st);
-        return launch_s_fs<T, VAR_COARSE>(sp, P, st);
-    }
+    if (P.g.cm[0]) return launch_s_fs<T, VAR_COARSE>(sp, P, st);
     if (P.g.fs != kNoSurface) {
         if constexpr (std::is_same<T, float>::value)
             if (reverse) return launch_s_fs<T, ZS_ADJ>(sp, P, st);
@@ -1552,32 +1483,6 @@ cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const 
     P.X = X;
     launch_v<float, M_GRAD>(sp, P, st);
     return cudaGetLastError();
-}
-
-cudaError_t stencil_plan_set_medium(StencilPlan* p, const DevGrid& g, const DevMedium& M) {
-    if (p->storage != EWS_STORAGE_F32) return cudaSuccess;      // staged boxes: FP32 fields only
-    auto fn = encoder();
-    if (!fn) return cudaErrorInvalidValue;
-    if (!g.cm[0] || g.cbx <= 0) {                                // the wavefield-grid medium
-        bool ok = encode(&p->vmaps.halo[5], g, M.rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, HXF, HY);
-        ok &= encode(&p->smaps.halo[3], g, M.mu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, HXF, HY);
-        ok &= encode(&p->smaps.core[0], g, M.lam, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, TX, TY);
-        return ok ? cudaSuccess : cudaErrorInvalidValue;
-    }
-    // medium boxes of cbx x cby x 3 cells over the dense medium grid
-    auto box_map = [&](CUtensorMap* map, const float* base) {
-        cuuint64_t dims[3] = {(cuuint64_t)g.mx, (cuuint64_t)g.my, (cuuint64_t)g.mz};
-        cuuint64_t strides[2] = {(cuuint64_t)g.mx * 4, (cuuint64_t)g.mx * g.my * 4};
-        cuuint32_t box[3] = {(cuuint32_t)g.cbx, (cuuint32_t)g.cby, 3};
-        cuuint32_t es[3] = {1, 1, 1};
-        return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides,
-                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, EWS_L2PROMO,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-    };
-    bool ok = box_map(&p->vmaps.halo[5], g.cm[2]);
-    ok &= box_map(&p->smaps.core[0], g.cm[0]);
-    ok &= box_map(&p->smaps.halo[3], g.cm[1]);
-    return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const float* hist,
