@@ -209,6 +209,16 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
         for (int q = 0; q < 3; ++q) s->g.cm[q] = nullptr;
         s->gen++;
     }
+    if (!s->medium) {                          // released while a coarse grid was in use
+        s->model_set = false;
+        CK(cudaMalloc(&s->medium, 3 * s->fstride * sizeof(float)));
+        CK(cudaMemsetAsync(s->medium, 0, 3 * s->fstride * sizeof(float), s->stream));
+        StencilPlan* np = nullptr;
+        CK(stencil_plan_create(s->g, s->F(), s->M(), s->B, s->opt.storage, &np));
+        stencil_plan_destroy(s->plan);
+        s->plan = np;
+        s->gen++;
+    }
     DevMedium M = s->M();
     ews_status st;
     if ((st = copy_field_in(s, (float*)M.lam, a, on_device)) != EWS_OK) return st;
@@ -906,6 +916,20 @@ ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float*
     s->model_set = true;
     s->pml_dt = -1.0;
     s->gen++;
+    // The medium arrays of the wavefield grid are not read with a coarse
+    // grid: release them (3 floats per cell; allocated again by a later
+    // ews_set_model_lame / _vel).  Plans and graphs that point at them go.
+    if (s->medium) {
+        CK(cudaStreamSynchronize(s->stream));
+        for (GraphEntry& ge : s->graphs) cudaGraphExecDestroy(ge.exec);
+        s->graphs.clear();
+        stencil_plan_destroy(s->adj_plan);
+        s->adj_plan = nullptr;
+        s->adj_hist = nullptr;
+        s->adj_hist_slots = 0;
+        cudaFree(s->medium);
+        s->medium = nullptr;
+    }
     return EWS_OK;
 }
 

@@ -111,11 +111,11 @@ struct ews_sim {
         return f;
     }
     bool wide() const { return opt.storage == EWS_STORAGE_F32; }
-    DevMedium M() const {
+    DevMedium M() const {          // null while a coarse medium grid replaces it
         DevMedium m;
         m.lam = medium;
-        m.mu = medium + fstride;
-        m.rho = medium + 2 * fstride;
+        m.mu = medium ? medium + fstride : nullptr;
+        m.rho = medium ? medium + 2 * fstride : nullptr;
         return m;
     }
     long long ncell() const { return (long long)grid.nx * grid.ny * grid.nz; }

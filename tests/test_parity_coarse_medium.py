@@ -107,3 +107,23 @@ def test_coarse_validation(ews):
     # back to the wavefield-grid medium
     sim.set_model_vel(p.vp, p.vs, p.rho)
     sim.run(p.nt, p.dt)
+
+
+def test_coarse_grid_releases_the_cell_medium(ews):
+    """With a coarse grid the wavefield grid's medium arrays (3 floats per
+    cell) are released, and allocated again for a wavefield-grid medium."""
+    import torch
+    p = synth.config2(n=192, nt=4)
+    sim = ews.simulation_for(p)
+    sim.run(p.nt, p.dt)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    synth.with_coarse_medium(p, (48, 48, 48))
+    sim.set_model_coarse(*p.coarse_medium)
+    sim.run(p.nt, p.dt)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    cells = p.nx * p.ny * p.nz
+    assert free1 - free0 >= 0.9 * 3 * 4 * cells, (free1 - free0) / (12 * cells)
+    sim.set_model_vel(p.vp, p.vs, p.rho)
+    sim.run(p.nt, p.dt)
