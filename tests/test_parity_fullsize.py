@@ -94,3 +94,55 @@ def test_bf16_step_at_full_size(big, orc):
     assert np.all(rel[:, :3] <= 2.0 ** -8 * 1.01), rel[:, :3].max()
     scale = sb.abs().amax(dim=(1, 2, 3)).double().cpu().numpy()
     assert (np.abs(g - want) / scale)[:, 3:].max() <= 2.0 ** -8 * 4
+
+
+def test_free_surface_step_at_bench_size(orc):
+    """The free-surface forms of the passes at the size and boundary the
+    benchmark times them (256^3, C-PML 20, surface at ks = 20 below the top
+    slab): one step from a seeded random state; at sampled cells two to four
+    planes below the surface (outside every C-PML slab, but fed by the
+    switched planes), the oracle's step on the 9^3 block around each cell,
+    with the surface at the same place in the block, matches the GPU."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_15071_gb300 import ews
+    ews.load()
+    dev = torch.device("cuda")
+    p = synth.config2(n=256, nt=4)
+    ks, eps = p.width, 1e-3
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(73)
+    st = torch.randn((9, p.nz, p.ny, p.nx), generator=gen, device=dev)
+    st[:3] *= 1e-3
+    st[3:] *= 1e6
+    st[:, :ks] = 0.0                      # nothing above the surface
+    sim = ews.Simulation(p.nx, p.ny, p.nz, p.spacing, boundary="cpml", width=p.width, f0=p.f0)
+    sim.set_free_surface(ks, eps)
+    sim.set_model_vel(p.vp, p.vs, p.rho)
+    sim.set_state(st)
+    sim.advance(0, 1, p.dt, None, 1)
+    got = torch.empty_like(st)
+    ews.ews_get_state(sim.handle, got)
+    torch.cuda.synchronize()
+    sim.close()
+    rng = np.random.default_rng(6)
+    lo, hi = p.width + R, p.nx - p.width - R
+    cells = np.stack([rng.integers(ks + 2, ks + 5, 24), rng.integers(lo, hi, 24),
+                      rng.integers(lo, hi, 24)], axis=1)
+    want = np.zeros((len(cells), 9))
+    for n, (k, j, i) in enumerate(cells):
+        sl = (slice(k - R, k + R + 1), slice(j - R, j + R + 1), slice(i - R, i + R + 1))
+        vp, vs, rho = (a[sl].astype(np.float64) for a in (p.vp, p.vs, p.rho))
+        o = orc.OracleSim(2 * R + 1, 2 * R + 1, 2 * R + 1, p.spacing)
+        o.set_free_surface(ks - (k - R), eps)
+        o.set_medium_vel(vp, vs, rho)
+        o.set_boundary("none")
+        o.set_state(st[(slice(None),) + sl].double().cpu().numpy())
+        o.step_velocity(p.dt)
+        o.step_stress(p.dt)
+        want[n] = o.get_state()[:, R, R, R]
+    scale = st.abs().amax(dim=(1, 2, 3)).double().cpu().numpy()
+    g = got[:, cells[:, 0], cells[:, 1], cells[:, 2]].double().cpu().numpy().T
+    err = np.abs(g - want) / scale
+    assert err.max() <= 1e-5, err.max(axis=0)
