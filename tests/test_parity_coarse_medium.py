@@ -42,7 +42,8 @@ def coarse_problem(dims, m, boundary, kind, nt=90, seed=81):
 
 @pytest.mark.parametrize("boundary", ["none", "sponge", "cpml"])
 @pytest.mark.parametrize("kind", ["moment", "force"])
-@pytest.mark.parametrize("dims,m", [((70, 45, 37), (9, 7, 5)), ((33, 65, 40), (33, 13, 16))])
+@pytest.mark.parametrize("dims,m", [((70, 45, 37), (9, 7, 5)), ((33, 65, 40), (33, 13, 16)),
+                                    ((40, 36, 28), (1, 5, 1))])
 def test_coarse_forward_matches_oracle(ews, orc, boundary, kind, dims, m):
     p = coarse_problem(dims, m, boundary, kind)
     want, osim = orc.run_problem(p, return_sim=True)

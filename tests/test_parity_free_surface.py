@@ -68,6 +68,23 @@ def test_surface_forward_matches_oracle(ews, orc, boundary, kind, dims):
             assert rel(st[q], ost[q]) <= TOL, (q, rel(st[q], ost[q]))
 
 
+@pytest.mark.parametrize("ks", [0, 1, 35])
+def test_surface_at_the_grid_edges(ews, orc, ks):
+    """Degenerate surface planes: at the top face (no vacuum cells, the
+    switch on planes 0 and below), one plane down, and near the bottom."""
+    p = synth.small_problem(40, 36, 38, nt=80, boundary="none", width=1, kind="moment", nrec=4,
+                            seed=44)
+    p.free_surface = (ks, 1e-3)
+    want, osim = orc.run_problem(p, return_sim=True)
+    sim = ews.simulation_for(p)
+    got = sim.run(p.nt, p.dt)
+    assert rel(got, want) <= TOL, rel(got, want)
+    st, ost = sim.get_state(), osim.get_state()
+    for q in range(9):
+        if np.linalg.norm(ost[q]) > 0:
+            assert rel(st[q], ost[q]) <= TOL, (q, rel(st[q], ost[q]))
+
+
 def test_surface_changes_the_result(ews, orc):
     """The surface is not a no-op: without it the receivers record a
     clearly different wavefield, far beyond FP32 rounding (guards against a
