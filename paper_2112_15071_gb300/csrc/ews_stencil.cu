@@ -64,7 +64,6 @@ constexpr int HXF = TX + 8;                       // FP32 halo box: x0-4 .. x0+T
 constexpr int HALOF = HXF * HY;                   // floats per FP32 halo tile
 constexpr int CORE = TX * TY;                     // elements per core tile
 constexpr int NSLOT = 4;                          // ring depth (planes) = unroll
-constexpr int NBAR = NSLOT + 3;                   // ring + 3 memory-variable buffers
 constexpr int MAXH = 6, MAXC = 7;
 constexpr int ROWS = EWS_ROWS;                    // cells per thread (adjacent y rows)
 constexpr int RY = TY / ROWS;                     // thread rows
@@ -140,7 +139,7 @@ __host__ __device__ constexpr int slot_bytes() {
 constexpr int PSI_BYTES = 9 * CORE * 4;
 template <int BND, typename T, int MODE = M_FWD>
 constexpr size_t smem_bytes() {
-    return (size_t)NSLOT * slot_bytes<T, MODE>() + (BND == BND_CPML ? PSI_BYTES : 0) + 8 * NBAR;
+    return (size_t)NSLOT * slot_bytes<T, MODE>() + (BND == BND_CPML ? PSI_BYTES : 0) + 8 * (NSLOT + 1);
 }
 // CTAs per SM that the shared-memory footprint allows; the register budget of
 // the kernels is sized for exactly that many.
@@ -269,31 +268,11 @@ __device__ __forceinline__ void issue_psi(const Maps& m, float* buf, uint64_t* b
                 tma_load_3d(buf + (3 * d + q) * CORE, &m.psi[3 * d + q], bar, x0, y0, z);
 }
 
-// The 3 memory-variable tiles of direction d of plane z into `buf`.
-__device__ __forceinline__ void issue_psi_one(const Maps& m, float* buf, uint64_t* bar, int x0,
-                                              int y0, int z, int d) {
-    mbar_expect_tx(bar, 3 * CORE * (uint32_t)sizeof(float));
-#pragma unroll
-    for (int q = 0; q < 3; ++q) tma_load_3d(buf + q * CORE, &m.psi[3 * d + q], bar, x0, y0, z);
-}
-
-// Memory-variable buffer of one (tile, z-chunk).  A tile that needs at most
-// one damped direction at every output plane of its chunk uses the 9-tile
-// buffer as a ring of three planes of 3 tiles (bars[NSLOT + i % 3]), filled
-// up to three planes ahead like the field ring; the others keep one plane
-// with all its directions (bars[NSLOT]), refilled as soon as it is used.
-// `used` advances on every thread; `issued` and `last` (the last plane
-// issued) only on the issuing thread.
-struct PsiRing {
-    int issued, used, last;
-    bool ring;
-};
-
 __device__ __forceinline__ bool in_slab(int i, int n, int W) { return i < W || i >= n - W; }
 
 __device__ __forceinline__ void ring_init(uint64_t* bars, int tid) {
     if (tid == 0) {
-        for (int s = 0; s < NBAR; ++s) mbar_init(&bars[s], 1);   // ring + psi buffers
+        for (int s = 0; s <= NSLOT; ++s) mbar_init(&bars[s], 1);   // ring + psi buffer
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -303,12 +282,9 @@ __device__ __forceinline__ void ring_init(uint64_t* bars, int tid) {
 // Bounded-failure exit: record, wait for the loads still in flight
 // (planes m .. issued - 1 of the chunk), leave.
 __device__ __noinline__ void fail_exit(int* err, int bit, uint64_t* bars, int m, int issued,
-                                       PsiRing R) {
+                                       bool psi_pending, uint32_t psi_parity) {
     atomicOr(err, bit);
-    for (int i = R.used; i < R.issued; ++i)      // memory-variable loads in flight
-        if (!mbar_wait(&bars[NSLOT + (R.ring ? i % 3 : 0)],
-                       (uint32_t)(R.ring ? (i / 3) & 1 : i & 1)))
-            return;
+    if (psi_pending && !mbar_wait(&bars[NSLOT], psi_parity)) return;
     for (int q = m; q < issued; ++q)
         if (!mbar_wait(&bars[q & (NSLOT - 1)], (uint32_t)((q >> 2) & 1))) return;
 }
@@ -368,40 +344,6 @@ struct Geo {
     __device__ __forceinline__ unsigned dirs(int z, int nz) const {
         return tdirs | ((z >= 0 && z < nz && (z < W || z >= nz - W)) ? 4u : 0u);
     }
-    // next output plane after k in this chunk with memory variables (-1: none)
-    __device__ __forceinline__ int psi_next(int k, int nz) const {
-        const int z1 = z0 + P4 - 4;
-        for (int kk = k + 1; kk < z1; ++kk)
-            if (dirs(kk, nz)) return kk;
-        return -1;
-    }
-    // the buffer mode and the first fills of a chunk (fills on thread 0)
-    __device__ __forceinline__ PsiRing psi_start(const Maps& maps, float* buf, uint64_t* bars,
-                                                 int nz) const {
-        PsiRing R{0, 0, z0 - 1, false};
-        const int z1 = z0 + P4 - 4;
-        const bool zs = z0 < W || z1 > nz - W;           // the chunk meets a z slab
-        R.ring = __popc(tdirs) + (zs ? 1 : 0) <= 1;
-        if (threadIdx.x == 0 && threadIdx.y == 0) psi_fill(maps, buf, bars, nz, R);
-        return R;
-    }
-    // issue fills while there is room: 3 planes ahead in ring mode, 1 else
-    __device__ __forceinline__ void psi_fill(const Maps& maps, float* buf, uint64_t* bars, int nz,
-                                             PsiRing& R) const {
-        while (R.issued - R.used < (R.ring ? 3 : 1)) {
-            const int k = psi_next(R.last, nz);
-            if (k < 0) return;
-            const unsigned d = dirs(k, nz);
-            if (R.ring) {
-                const int sub = R.issued % 3;
-                issue_psi_one(maps, buf + sub * 3 * CORE, &bars[NSLOT + sub], x0, y0, k, __ffs(d) - 1);
-            } else {
-                issue_psi(maps, buf, &bars[NSLOT], x0, y0, k, d);
-            }
-            ++R.issued;
-            R.last = k;
-        }
-    }
 };
 
 // psi = b psi + a d; d += psi for the three terms of one damped direction.
@@ -456,7 +398,7 @@ struct VelQ {
 template <int BND, typename T, int MODE, int PH, int FS>
 __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, VelQ& Q, unsigned char* sm,
-                                         uint64_t* bars, int m, PsiRing& PR, bool& ovf) {
+                                         uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
     using L = Lay<T>;
     constexpr int HX = L::HX;
     constexpr int SB = slot_bytes<T, MODE>();
@@ -489,9 +431,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         }
     }
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
-    if (BND == BND_CPML && kd)
-        ok = mbar_wait(&bars[NSLOT + (PR.ring ? PR.used % 3 : 0)],
-                       (uint32_t)(PR.ring ? (PR.used / 3) & 1 : PR.used & 1)) && ok;
+    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
     const unsigned char* sl0 = sm + S0 * SB;
     const unsigned char* sl1 = sm + S1 * SB;
     const unsigned char* sl2 = sm + S2 * SB;
@@ -550,10 +490,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             }
             if (BND == BND_CPML) {
                 // memory variables of plane k from the psi buffer, updated, stored
-                // ring mode: the plane's single direction in its 3-tile entry
-                const float* ps = (const float*)(sm + NSLOT * SB) +
-                                  (PR.ring ? (PR.used % 3) * 3 * CORE : 0) + G.cc + rr * TX;
-                const int py = PR.ring ? 0 : 3 * CORE, pz = PR.ring ? 0 : 6 * CORE;
+                const float* ps = (const float*)(sm + NSLOT * SB) + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
@@ -561,12 +498,12 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                     P.B.psi[0][oo] = p0; P.B.psi[1][oo] = p1; P.B.psi[2][oo] = p2;
                 }
                 if (G.sy[rr]) {
-                    float p0 = ps[py], p1 = ps[py + CORE], p2 = ps[py + 2 * CORE];
+                    float p0 = ps[3 * CORE], p1 = ps[4 * CORE], p2 = ps[5 * CORE];
                     pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr], dxy, dyy, dzy);
                     P.B.psi[6][oo] = p0; P.B.psi[7][oo] = p1; P.B.psi[8][oo] = p2;
                 }
                 if (sz) {
-                    float p0 = ps[pz], p1 = ps[pz + CORE], p2 = ps[pz + 2 * CORE];
+                    float p0 = ps[6 * CORE], p1 = ps[7 * CORE], p2 = ps[8 * CORE];
                     pml_upd(p0, p1, p2, paz, pbz, dxz, dyz, dzz);
                     P.B.psi[12][oo] = p0; P.B.psi[13][oo] = p1; P.B.psi[14][oo] = p2;
                 }
@@ -661,14 +598,17 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     }
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && threadIdx.y == 0)
-            fail_exit(P.err, 1, bars, m, min(G.P4, max(NSLOT, m + 2)), PR);
+            fail_exit(P.err, 1, bars, m, min(G.P4, max(NSLOT, m + 2)), kd != 0u, psi_n & 1u);
         return false;
     }
     if (BND == BND_CPML) {
-        if (kd) ++PR.used;
-        // a psi entry is free: fetch the memory variables of the next planes
-        if (kd && threadIdx.x == 0 && threadIdx.y == 0)
-            G.psi_fill(maps, (float*)(sm + NSLOT * SB), bars, g.nz, PR);
+        if (kd) ++psi_n;
+        // the psi buffer is free: fetch the memory variables of the next output plane
+        const int kn = k + 1;
+        if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
+            const unsigned dn = G.dirs(kn, g.nz);
+            if (dn) issue_psi(maps, (float*)(sm + NSLOT * SB), &bars[NSLOT], G.x0, G.y0, kn, dn);
+        }
     }
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
@@ -696,14 +636,13 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
     Q.ci.lvl = -1;
     Q.ch.lvl = -1;
         }
-    PsiRing PR{0, 0, 0, false};                    // memory-variable buffer (C-PML)
-    if constexpr (BND == BND_CPML) PR = G.psi_start(maps, (float*)(sm + NSLOT * SB), bars, P.g.nz);
+    uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!vel_step<BND, T, MODE, 0, FS>(maps, P, G, Q, sm, bars, m, PR, ovf)) return false;
-        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1, FS>(maps, P, G, Q, sm, bars, m + 1, PR, ovf)) return false;
-        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2, FS>(maps, P, G, Q, sm, bars, m + 2, PR, ovf)) return false;
-        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3, FS>(maps, P, G, Q, sm, bars, m + 3, PR, ovf)) return false;
+        if (!vel_step<BND, T, MODE, 0, FS>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
+        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1, FS>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
+        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2, FS>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
+        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3, FS>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
@@ -742,7 +681,7 @@ struct StrQ {
 template <int BND, typename T, int PH, int FS>
 __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, StrQ& Q, unsigned char* sm,
-                                         uint64_t* bars, int m, PsiRing& PR, bool& ovf) {
+                                         uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
     using L = Lay<T>;
     constexpr int HX = L::HX;
     const DevGrid& g = P.g;
@@ -754,9 +693,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
     const float G3 = (BND == BND_SPONGE && out) ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
     const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
-    if (BND == BND_CPML && kd)
-        ok = mbar_wait(&bars[NSLOT + (PR.ring ? PR.used % 3 : 0)],
-                       (uint32_t)(PR.ring ? (PR.used / 3) & 1 : PR.used & 1)) && ok;
+    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
     const unsigned char* sl0 = sm + S0 * L::SLOT;
     const unsigned char* sl1 = sm + S1 * L::SLOT;
     const unsigned char* sl2 = sm + S2 * L::SLOT;
@@ -804,9 +741,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                 ezz *= P.inv[VZ]; vzx *= P.inv[VZ]; vzy *= P.inv[VZ];
             }
             if (BND == BND_CPML) {
-                const float* ps = (const float*)(sm + NSLOT * L::SLOT) +
-                                  (PR.ring ? (PR.used % 3) * 3 * CORE : 0) + G.cc + rr * TX;
-                const int py = PR.ring ? 0 : 3 * CORE, pz = PR.ring ? 0 : 6 * CORE;
+                const float* ps = (const float*)(sm + NSLOT * L::SLOT) + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
@@ -814,12 +749,12 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                     P.B.psi[3][oo] = p0; P.B.psi[4][oo] = p1; P.B.psi[5][oo] = p2;
                 }
                 if (G.sy[rr]) {
-                    float p0 = ps[py], p1 = ps[py + CORE], p2 = ps[py + 2 * CORE];
+                    float p0 = ps[3 * CORE], p1 = ps[4 * CORE], p2 = ps[5 * CORE];
                     pml_upd(p0, p1, p2, G.pay[rr], G.pby[rr], eyy, vxy, vzy);
                     P.B.psi[9][oo] = p0; P.B.psi[10][oo] = p1; P.B.psi[11][oo] = p2;
                 }
                 if (sz) {
-                    float p0 = ps[pz], p1 = ps[pz + CORE], p2 = ps[pz + 2 * CORE];
+                    float p0 = ps[6 * CORE], p1 = ps[7 * CORE], p2 = ps[8 * CORE];
                     pml_upd(p0, p1, p2, paz, pbz, ezz, vxz, vyz);
                     P.B.psi[15][oo] = p0; P.B.psi[16][oo] = p1; P.B.psi[17][oo] = p2;
                 }
@@ -896,13 +831,16 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
     }
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && threadIdx.y == 0)
-            fail_exit(P.err, 2, bars, m, min(G.P4, max(NSLOT, m + 2)), PR);
+            fail_exit(P.err, 2, bars, m, min(G.P4, max(NSLOT, m + 2)), kd != 0u, psi_n & 1u);
         return false;
     }
     if (BND == BND_CPML) {
-        if (kd) ++PR.used;
-        if (kd && threadIdx.x == 0 && threadIdx.y == 0)
-            G.psi_fill(maps, (float*)(sm + NSLOT * L::SLOT), bars, g.nz, PR);
+        if (kd) ++psi_n;
+        const int kn = k + 1;
+        if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
+            const unsigned dn = G.dirs(kn, g.nz);
+            if (dn) issue_psi(maps, (float*)(sm + NSLOT * L::SLOT), &bars[NSLOT], G.x0, G.y0, kn, dn);
+        }
     }
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
         issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
@@ -923,15 +861,13 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
         for (int q = 0; q < 4; ++q) { Q.vx[rr][q] = 0.f; Q.vy[rr][q] = 0.f; Q.vz[rr][q] = 0.f; }
     Q.ci.lvl = -1;
     Q.ch.lvl = -1;
-    PsiRing PR{0, 0, 0, false};                    // memory-variable buffer (C-PML)
-    if constexpr (BND == BND_CPML)
-        PR = G.psi_start(maps, (float*)(sm + NSLOT * Lay<T>::SLOT), bars, P.g.nz);
+    uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!str_step<BND, T, 0, FS>(maps, P, G, Q, sm, bars, m, PR, ovf)) return false;
-        if (m + 1 < G.P4 && !str_step<BND, T, 1, FS>(maps, P, G, Q, sm, bars, m + 1, PR, ovf)) return false;
-        if (m + 2 < G.P4 && !str_step<BND, T, 2, FS>(maps, P, G, Q, sm, bars, m + 2, PR, ovf)) return false;
-        if (m + 3 < G.P4 && !str_step<BND, T, 3, FS>(maps, P, G, Q, sm, bars, m + 3, PR, ovf)) return false;
+        if (!str_step<BND, T, 0, FS>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
+        if (m + 1 < G.P4 && !str_step<BND, T, 1, FS>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
+        if (m + 2 < G.P4 && !str_step<BND, T, 2, FS>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
+        if (m + 3 < G.P4 && !str_step<BND, T, 3, FS>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
@@ -1569,7 +1505,7 @@ cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const flo
 template <int BND, bool GRAD>
 constexpr size_t batch_smem() {
     return (size_t)NSLOT * (GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>()) +
-           8 * NBAR;
+           8 * (NSLOT + 1);
 }
 
 template <int BND, bool GRAD, bool FS>
