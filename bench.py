@@ -426,6 +426,17 @@ def adjoint_ratio(args, local):
     free_gb = torch.cuda.mem_get_info(dev)[0] / 1e9
     sim.set_history_budget(0)                # every segment recomputed from its checkpoint
     grad_rec_ms = timed(grad)
+    g32 = g.clone()
+    ck = {}
+    for stor in ("bf16", "f16"):             # 16-bit checkpoints, same recomputation
+        sim.set_checkpoint_storage(stor)
+        ms = timed(grad)
+        err = [float(torch.linalg.vector_norm(g[q] - g32[q]) / torch.linalg.vector_norm(g32[q]))
+               for q in range(3)]
+        ck[stor] = {"gradient_ms": round(ms, 2), "ratio": round(ms / fwd_ms, 3),
+                    "rel_l2_vs_f32_checkpoints": [float(f"{e:.3g}") for e in err]}
+    sim.set_checkpoint_storage("f32")
+    ck_gb = (start.nt // 50) * 9 * 4 * start.ncell / 1e9
     sim.set_history_budget(-1)
     sim.close()
     torch.cuda.empty_cache()
@@ -441,7 +452,9 @@ def adjoint_ratio(args, local):
             "recompute_all": {"gradient_ms": round(grad_rec_ms, 2),
                               "ratio": round(grad_rec_ms / fwd_ms, 3),
                               "history": "one 50-step segment; every earlier segment "
-                                         "recomputed from its checkpoint"}}
+                                         "recomputed from its checkpoint",
+                              "checkpoints_gb_f32": round(ck_gb, 2),
+                              "checkpoints_16bit": ck}}
 
 
 def storage_report(args, local, with_oracle: bool):

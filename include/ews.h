@@ -211,6 +211,17 @@ ews_status ews_adjoint(ews_sim* sim, int nt, double dt, const float* seis_adj,
                        int adj_on_device, float* g_lam, float* g_mu, float* g_rho,
                        int g_on_device, int ckpt_every);
 
+/* Element type of the wavefield checkpoints of ews_adjoint / ews_gradient:
+ * EWS_STORAGE_F32 (default), EWS_STORAGE_BF16 or EWS_STORAGE_F16 (half the
+ * memory).  A 16-bit checkpoint holds s_q times field q, s_q = 2^(14 - e)
+ * per field and checkpoint with max |f_q| = m 2^e, m in [0.5, 1) (s_q = 1
+ * for a zero field), so FP16 cannot overflow; segments recomputed from a
+ * 16-bit checkpoint start from the rounded state, so the gradient differs
+ * from the FP32-checkpoint one by about the storage precision.  Resident
+ * history (ews_set_history_budget) needs no checkpoints.  Batched shots
+ * (ews_batch) keep FP32 checkpoints.  Not in the paper. */
+ews_status ews_set_checkpoint_storage(ews_sim* sim, int storage);
+
 /* Device memory the adjoint may use for resident velocity history, in
  * bytes.  Each resident time step costs 3 fields (12 bytes per cell); with a
  * budget covering all nt steps the gradient needs no recomputation.  0: one

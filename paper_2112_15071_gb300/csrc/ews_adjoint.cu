@@ -317,6 +317,78 @@ dim3 plane_grid(const DevGrid& g) { return dim3((g.nx + 31) / 32, (g.ny + 7) / 8
 
 }  // namespace
 
+namespace {
+
+// 16-bit checkpoints (storage BF16 / FP16): per field q the state is stored
+// as s_q times its value, s_q = 2^(14 - e) with max |f_q| = m 2^e (m in
+// [0.5, 1)), so the largest stored magnitude is below 2^14 (FP16 holds up
+// to 65504); s_q = 1 for an all-zero field.  The maxima are gathered on the
+// device (float bits of non-negative values order like unsigned ints).
+__global__ void k_state_absmax(const float* __restrict__ f, long long fs, unsigned* amax) {
+    const int q = blockIdx.y;
+    float m = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < fs;
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(f[q * fs + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax + q, __float_as_uint(m));
+}
+
+__device__ __forceinline__ float ckpt_scale_of(unsigned amax_bits) {
+    const float m = __uint_as_float(amax_bits);
+    if (!(m > 0.0f) || !isfinite(m)) return 1.0f;
+    int e;
+    frexpf(m, &e);
+    return ldexpf(1.0f, 14 - e);
+}
+
+template <typename H>
+__global__ void k_ckpt_store(const float* __restrict__ f, long long fs, const unsigned* amax,
+                             float* scales, H* dst) {
+    const int q = blockIdx.y;
+    const float s = ckpt_scale_of(amax[q]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) scales[q] = s;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < fs;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[q * fs + i] = ops::Io<H>::put(f[q * fs + i] * s);
+}
+
+template <typename H>
+__global__ void k_ckpt_load(const H* __restrict__ src, long long fs, const float* scales, float* f) {
+    const int q = blockIdx.y;
+    const float inv = 1.0f / scales[q];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < fs;
+         i += (long long)gridDim.x * blockDim.x)
+        f[q * fs + i] = ops::Io<H>::get(src + q * fs + i) * inv;
+}
+
+}  // namespace
+
+cudaError_t launch_ckpt_store(const float* fields, long long fs, int storage, unsigned* amax,
+                              float* scales, void* dst, cudaStream_t st) {
+    const dim3 grid(1024, NFIELD);
+    cudaError_t e = cudaMemsetAsync(amax, 0, NFIELD * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    k_state_absmax<<<grid, 256, 0, st>>>(fields, fs, amax);
+    if (storage == EWS_STORAGE_BF16)
+        k_ckpt_store<__nv_bfloat16><<<grid, 256, 0, st>>>(fields, fs, amax, scales,
+                                                          static_cast<__nv_bfloat16*>(dst));
+    else
+        k_ckpt_store<__half><<<grid, 256, 0, st>>>(fields, fs, amax, scales, static_cast<__half*>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ckpt_load(const void* src, long long fs, int storage, const float* scales,
+                             float* fields, cudaStream_t st) {
+    const dim3 grid(1024, NFIELD);
+    if (storage == EWS_STORAGE_BF16)
+        k_ckpt_load<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(src), fs,
+                                                         scales, fields);
+    else
+        k_ckpt_load<__half><<<grid, 256, 0, st>>>(static_cast<const __half*>(src), fs, scales, fields);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_residual(const float* seis, const float* obs, float* sadj, long long n,
                             float dt, double* misfit, cudaStream_t st) {
     const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);

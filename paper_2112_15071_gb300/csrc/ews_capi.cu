@@ -491,6 +491,34 @@ ews_status ensure_buf(T** buf, size_t* cap, size_t need, const char* what) {
 
 // Reverse sweep for dL/dseis = sadj (device, [3][nrec][nt]); or, when obs is
 // given, first the L2 misfit residual of a recorded forward run.
+// Checkpoint c of the current state (FP32 copy, or 16-bit with per-field
+// scales), and its restore.
+ews_status ckpt_save(ews_sim* s, int c) {
+    const size_t fs = s->fstride;
+    if (s->ckpt_storage == EWS_STORAGE_F32) {
+        CK(cudaMemcpyAsync(s->ckpt + (size_t)c * 9 * fs, s->fields, 9 * fs * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s->stream));
+        return EWS_OK;
+    }
+    uint16_t* base = reinterpret_cast<uint16_t*>(s->ckpt) + (size_t)c * 9 * fs;
+    CK(launch_ckpt_store(s->fields, (long long)fs, s->ckpt_storage, s->ckpt_amax,
+                         s->ckpt_scale + 9 * c, base, s->stream));
+    return EWS_OK;
+}
+
+ews_status ckpt_load(ews_sim* s, int c) {
+    const size_t fs = s->fstride;
+    if (s->ckpt_storage == EWS_STORAGE_F32) {
+        CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s->stream));
+        return EWS_OK;
+    }
+    const uint16_t* base = reinterpret_cast<const uint16_t*>(s->ckpt) + (size_t)c * 9 * fs;
+    CK(launch_ckpt_load(base, (long long)fs, s->ckpt_storage, s->ckpt_scale + 9 * c, s->fields,
+                        s->stream));
+    return EWS_OK;
+}
+
 ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const float* sadj_dev,
                         const float* obs_dev, double* misfit, float* g_lam, float* g_mu,
                         float* g_rho, int g_on_device) {
@@ -520,7 +548,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     const int hslots = std::max(K, nt - n_res) + 1;
     // checkpoints only for the segments that will be recomputed
     if ((st = sim_adjoint_buffers(s, nt, transformed ? c_res : nck, transformed ? hslots : K + 1,
-                                  obs_dev != nullptr)) != EWS_OK)
+                                  obs_dev != nullptr, s->ckpt_pref)) != EWS_OK)
         return st;
     const size_t nseis = (size_t)3 * s->nrec * nt;
     AdjFields A;
@@ -533,9 +561,9 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     float* dseis = obs_dev ? s->aux : nullptr;
     for (int c = 0; c < nck; ++c) {
         const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
-        if (!transformed || c < c_res)   // resident segments are never restored
-            CK(cudaMemcpyAsync(s->ckpt + (size_t)c * 9 * fs, s->fields, 9 * fs * sizeof(float),
-                               cudaMemcpyDeviceToDevice, s->stream));
+        if ((!transformed || c < c_res) &&   // resident segments are never restored
+            (st = ckpt_save(s, c)) != EWS_OK)
+            return st;
         if (transformed && c >= c_res) {
             if (c == c_res)
                 CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float),
@@ -573,8 +601,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         for (int c = c_res; c >= 0; --c) {
             const int n0 = c * K, n1 = c == c_res ? nt : n0 + K;
             if (c < c_res) {
-                CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
-                                   cudaMemcpyDeviceToDevice, s->stream));
+                if ((st = ckpt_load(s, c)) != EWS_OK) return st;
                 CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float),
                                    cudaMemcpyDeviceToDevice, s->stream));
                 if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK)
@@ -600,8 +627,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     }
     for (int c = transformed ? -1 : nck - 1; c >= 0; --c) {
         const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
-        CK(cudaMemcpyAsync(s->fields, s->ckpt + (size_t)c * 9 * fs, 9 * fs * sizeof(float),
-                           cudaMemcpyDeviceToDevice, s->stream));
+        if ((st = ckpt_load(s, c)) != EWS_OK) return st;
         CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float), cudaMemcpyDeviceToDevice,
                            s->stream));
         if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK) return st;
@@ -660,9 +686,23 @@ ews_status sim_ready(ews_sim* s, int n_end, double dt) { return ensure_ready(s, 
 
 DevSource sim_source(const ews_sim* s, double dt) { return source_taps(s, s->src, dt); }
 
-ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool with_obs) {
+ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool with_obs,
+                               int ckpt_storage) {
     const size_t fs = s->fstride;
     const int nck = nckpt > 0 ? nckpt : 1;
+    s->ckpt_storage = ckpt_storage;
+    if (ckpt_storage != EWS_STORAGE_F32 && nck > s->ckpt_scale_cap) {
+        cudaFree(s->ckpt_scale);
+        s->ckpt_scale = nullptr;
+        s->ckpt_scale_cap = 0;
+        cudaError_t e = cudaMalloc(&s->ckpt_scale, (size_t)nck * 9 * sizeof(float));
+        if (e != cudaSuccess) return fail(EWS_ENOMEM, "checkpoint scales: %s", cudaGetErrorString(e));
+        s->ckpt_scale_cap = nck;
+        if (!s->ckpt_amax) {
+            e = cudaMalloc(&s->ckpt_amax, 9 * sizeof(unsigned));
+            if (e != cudaSuccess) return fail(EWS_ENOMEM, "checkpoint maxima: %s", cudaGetErrorString(e));
+        }
+    }
     if (!s->adj) {
         cudaError_t e = cudaMalloc(&s->adj, 17 * fs * sizeof(float));
         if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint state: %s", cudaGetErrorString(e));
@@ -672,7 +712,9 @@ ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool w
         if (e != cudaSuccess) return fail(EWS_ENOMEM, "misfit: %s", cudaGetErrorString(e));
     }
     ews_status st;
-    if ((st = ensure_buf(&s->ckpt, &s->ckpt_cap, (size_t)nck * 9 * fs, "checkpoints")) != EWS_OK) return st;
+    const size_t ck_floats = ckpt_storage == EWS_STORAGE_F32 ? (size_t)nck * 9 * fs
+                                                              : ((size_t)nck * 9 * fs + 1) / 2;
+    if ((st = ensure_buf(&s->ckpt, &s->ckpt_cap, ck_floats, "checkpoints")) != EWS_OK) return st;
     if ((st = ensure_buf(&s->vhist, &s->vhist_cap, (size_t)hslots * 3 * fs, "velocity history")) != EWS_OK)
         return st;
     const size_t nseis = (size_t)3 * s->nrec * nt;
@@ -834,6 +876,8 @@ void ews_destroy(ews_sim* s) {
     cudaFree(s->adj);
     cudaFree(s->acc64);
     cudaFree(s->ckpt);
+    cudaFree(s->ckpt_scale);
+    cudaFree(s->ckpt_amax);
     cudaFree(s->vhist);
     cudaFree(s->aux);
     cudaFree(s->gout);
@@ -964,6 +1008,14 @@ ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const doubl
     for (int a = 0; a < 3; ++a) sp.pos[a] = pos[a];
     for (int c = 0; c < 6; ++c) sp.comp[c] = c < nc ? comp[c] : 0.0;
     s->S.kind = kind;
+    return EWS_OK;
+}
+
+ews_status ews_set_checkpoint_storage(ews_sim* s, int storage) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (storage != EWS_STORAGE_F32 && storage != EWS_STORAGE_BF16 && storage != EWS_STORAGE_F16)
+        return fail(EWS_EINVAL, "unknown checkpoint storage %d", storage);
+    s->ckpt_pref = storage;
     return EWS_OK;
 }
 

@@ -205,6 +205,13 @@ cudaError_t launch_grad_finalize(const DevGrid& g, const AdjFields& A, const Dev
                                  float* glam, float* gmu, float* grho, cudaStream_t st);
 cudaError_t launch_residual(const float* seis, const float* obs, float* sadj, long long n,
                             float dt, double* misfit, cudaStream_t st);
+// 16-bit checkpoint of the 9 fields (each fs floats) into dst (storage
+// BF16 / FP16, 9 * fs elements), with per-field power-of-two scales written
+// to scales[9] (amax: 9 unsigned of scratch); and its restore.
+cudaError_t launch_ckpt_store(const float* fields, long long fs, int storage, unsigned* amax,
+                              float* scales, void* dst, cudaStream_t st);
+cudaError_t launch_ckpt_load(const void* src, long long fs, int storage, const float* scales,
+                             float* fields, cudaStream_t st);
 // Transformed formulation (p = alpha, q = tau; see ews_adjoint.cu).
 cudaError_t launch_adj_inject(const DevGrid& g, const AdjFields& A, const DevMedium& M,
                               const DevBoundary& B, const Tap* taps, int nrec, const float* sadj,

@@ -87,8 +87,13 @@ struct ews_sim {
     // adjoint buffers (allocated on first use)
     float* adj = nullptr;                 // P (3), Q (6), FP32 accumulators (8)
     double* acc64 = nullptr;              // FP64 accumulators (8)
-    float* ckpt = nullptr;                // checkpoints, nck x 9 fields
+    float* ckpt = nullptr;                // checkpoints, nck x 9 fields (FP32 or 16-bit)
     size_t ckpt_cap = 0;                  // fields' worth of floats
+    int ckpt_storage = EWS_STORAGE_F32;   // element type of the checkpoints held now
+    int ckpt_pref = EWS_STORAGE_F32;      // type ews_adjoint / ews_gradient use
+    float* ckpt_scale = nullptr;          // 16-bit checkpoints: [nck][9] field scales
+    unsigned* ckpt_amax = nullptr;        // [9] absolute maxima of the state being saved
+    int ckpt_scale_cap = 0;
     float* vhist = nullptr;               // velocity history, (K + 1) x 3 fields
     size_t vhist_cap = 0;
     float* aux = nullptr;                 // seismogram-sized adjoint source + observed
@@ -130,7 +135,8 @@ ews_status sim_ready(ews_sim* s, int n_end, double dt);        // model, dt, bou
 DevSource sim_source(const ews_sim* s, double dt);             // source taps for this dt
 // Adjoint buffers for nt steps with `nckpt` checkpoints and `hslots`
 // history slots (allocated once, grown when needed).
-ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool with_obs);
+ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool with_obs,
+                               int ckpt_storage = EWS_STORAGE_F32);
 // Stencil plan of the adjoint fields with its history map on s->vhist.
 ews_status sim_adjoint_plan(ews_sim* s);
 // History budget in bytes: the set value, or (automatic) `share` of the

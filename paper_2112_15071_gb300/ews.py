@@ -89,6 +89,7 @@ SIGNATURES = [
     ("ews_set_state", _I, [_P, _P, _I]),
     ("ews_set_field_scales", _I, [_P, _P]),
     ("ews_set_history_budget", _I, [_P, _D]),
+    ("ews_set_checkpoint_storage", _I, [_P, _I]),
     ("ews_release_workspace", _I, [_P]),
     ("ews_get_field_scales", _I, [_P, _P]),
     ("ews_adjoint", _I, [_P, _I, _D, _P, _I, _P, _P, _P, _I, _I]),
@@ -277,6 +278,11 @@ def ews_set_history_budget(sim, nbytes: float):
     _check(load().ews_set_history_budget(sim, float(nbytes)))
 
 
+def ews_set_checkpoint_storage(sim, storage):
+    storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    _check(load().ews_set_checkpoint_storage(sim, storage))
+
+
 def ews_release_workspace(sim):
     _check(load().ews_release_workspace(sim))
 
@@ -431,6 +437,10 @@ class Simulation:
     def set_source(self, kind, pos, comp, wavelet):
         ews_set_source(self._h, SOURCE[kind] if isinstance(kind, str) else kind, pos, comp,
                        wavelet)
+
+    def set_checkpoint_storage(self, storage):
+        """Element type of the adjoint's checkpoints: "f32", "bf16" or "f16"."""
+        ews_set_checkpoint_storage(self._h, storage)
 
     def set_model_coarse(self, a, b, rho, from_velocities=False):
         """Medium on its own (coarser) grid, sampled trilinearly (Sec. 2.2.1)."""

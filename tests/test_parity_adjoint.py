@@ -194,3 +194,28 @@ def test_release_workspace_and_run_again(ews):
     g2 = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
     s2 = sim.run(p.nt, p.dt)
     assert np.array_equal(g1, g2) and np.array_equal(s1, s2)
+
+
+@pytest.mark.parametrize("storage,cap", [("bf16", 3e-2), ("f16", 5e-3)])
+def test_16bit_checkpoints(ews, orc, storage, cap):
+    """Checkpoints stored in 16 bits with per-field scales: with every
+    segment recomputed from its checkpoint the gradient stays within the
+    storage precision of the FP32-checkpoint gradient (and of the FP64
+    adjoint); the field scales keep FP16 from overflowing."""
+    p = problem((40, 36, 28), "sponge", "moment", nt=150, seed=12)
+    A = np.random.default_rng(8).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    lame = [a.astype(np.float64) for a in p.lame()]
+    want = orc.gradient(p, A.astype(np.float64), ckpt_every=25, medium=lame)
+    sim = ews.simulation_for(p)
+    sim.set_history_budget(0)
+    g32 = sim.adjoint(p.nt, p.dt, A, ckpt_every=25).copy()
+    sim.set_checkpoint_storage(storage)
+    g16 = sim.adjoint(p.nt, p.dt, A, ckpt_every=25)
+    for q in range(3):
+        e = rel(g16[q], g32[q])
+        print(f"\n{storage} checkpoints, gradient {q}: rel L2 vs FP32 checkpoints {e:.2e}, "
+              f"vs FP64 adjoint {rel(g16[q], want[q]):.2e}")
+        assert 0 < e <= cap, e
+        assert rel(g16[q], want[q]) <= cap + TOL_ORACLE
+    with pytest.raises(ews.EwsError):
+        sim.set_checkpoint_storage(7)
