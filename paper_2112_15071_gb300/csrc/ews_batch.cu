@@ -263,6 +263,86 @@ ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector
     return EWS_OK;
 }
 
+// ---- a sequence of persistent launches under one CUDA graph ----
+
+// Device tables of one persistent launch (entries and counters).
+struct Prepared {
+    BatchEntry* ent = nullptr;
+    unsigned* cnt = nullptr;
+    unsigned long long* done = nullptr;
+    int nent = 0, exec = 0, grid = 0;
+};
+
+void release(std::vector<Prepared>& v) {
+    for (Prepared& p : v) {
+        cudaFree(p.ent);
+        cudaFree(p.cnt);
+        cudaFree(p.done);
+    }
+    v.clear();
+}
+
+// Merge the programs into one entry list (as run_persistent) and upload it.
+ews_status prepare_launch(const std::vector<std::vector<Stage>>& progs, int exec, int bnd,
+                          int ctas_per_sm, bool stall, cudaStream_t st, Prepared* out) {
+    const int ns = (int)progs.size();
+    std::vector<Entry> all;
+    for (int sh = 0; sh < ns; ++sh) {
+        long long need = 0;
+        const double R = (double)progs[sh].size();
+        for (size_t r = 0; r < progs[sh].size(); ++r) {
+            const Stage& g = progs[sh][r];
+            BatchEntry e{};
+            e.shot = sh;
+            e.kind = g.kind;
+            e.n = g.n;
+            e.slot = g.slot;
+            e.flag = g.flag;
+            e.need = need;
+            e.nitems = g.nitems;
+            all.push_back({(r + 0.5) / R, e});
+            need += g.nitems;
+        }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const Entry& a, const Entry& b) {
+        return a.key < b.key || (a.key == b.key && a.e.shot < b.e.shot);
+    });
+    std::vector<BatchEntry> ent(all.size());
+    for (size_t i = 0; i < all.size(); ++i) ent[i] = all[i].e;
+    if (stall && !ent.empty()) ent.back().need += 1;   // waits for an item that never exists
+    int dev = 0, sms = 0, per_sm = 0;
+    BCK(cudaGetDevice(&dev));
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BCK(batch_occupancy(bnd, exec, &per_sm));
+    if (per_sm < 1) return report(EWS_ECUDA, "batched executor does not fit on an SM");
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+    Prepared p;
+    p.nent = (int)ent.size();
+    p.exec = exec;
+    p.grid = sms * per_sm;
+    cudaError_t e = cudaMalloc(&p.ent, sizeof(BatchEntry) * std::max(p.nent, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p.cnt, sizeof(unsigned) * (p.nent + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p.done, sizeof(unsigned long long) * ns);
+    if (e == cudaSuccess && p.nent)
+        e = cudaMemcpyAsync(p.ent, ent.data(), sizeof(BatchEntry) * p.nent, cudaMemcpyHostToDevice, st);
+    *out = p;
+    if (e != cudaSuccess)
+        return report(e == cudaErrorMemoryAllocation ? EWS_ENOMEM : EWS_ECUDA, "batched tables: %s",
+                      cudaGetErrorString(e));
+    return EWS_OK;
+}
+
+// Counter resets and the launch of a prepared table, on `st` (capturable).
+cudaError_t enqueue(const Prepared& p, int bnd, int nshots, const BatchShot* d_shots, int* d_err,
+                    unsigned long long wait_ns, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(p.cnt, 0, sizeof(unsigned) * (p.nent + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.done, 0, sizeof(unsigned long long) * nshots, st);
+    if (e == cudaSuccess)
+        e = launch_batch(bnd, p.exec, p.grid, d_shots, p.ent, p.nent, p.cnt, p.cnt + 1, p.done, d_err,
+                         wait_ns, st);
+    return e;
+}
+
 // ---- autotuner: planes per tile in z, per grid size ----
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
@@ -415,13 +495,33 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
             forward_program(progs[i], bs[i], b.nt);
         }
     }
-    const unsigned long long wait = (unsigned long long)o.dep_wait_ms * 1000000ull;
+    const unsigned long long wait =
+        o.dep_wait_ms ? (unsigned long long)o.dep_wait_ms * 1000000ull : 4000000000ull;
     const int lean = any_fs ? BX_LEAN_FS : BX_LEAN, rev = any_fs ? BX_GRAD_FS : BX_GRAD;
-    ews_status r = run_persistent(bs, progs, bnd, lean, o.ctas_per_sm, d_err, st, nullptr, wait,
-                                  o.test_unsatisfiable != 0);
-    if (r != EWS_OK) return r;
-    // Reverse parts, segment phase by segment phase: shots with fewer
-    // segments join for the last phases, so all finish in the last one.
+    // The launches: the forward part of every shot, then the reverse parts
+    // segment phase by segment phase (a recomputation launch and a reverse
+    // launch per phase; shots with fewer segments join for the last phases,
+    // so all finish in the last one).  They are prepared up front and run as
+    // one captured CUDA graph, with one synchronisation at the end.
+    std::vector<Prepared> launches;
+    BatchShot* d_shots = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cs = nullptr;
+    auto cleanup = [&]() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        release(launches);
+        cudaFree(d_shots);
+    };
+    ews_status r = EWS_OK;
+    auto add = [&](const std::vector<std::vector<Stage>>& pr, int exec, bool stall) {
+        Prepared p;
+        if (r == EWS_OK) r = prepare_launch(pr, exec, bnd, o.ctas_per_sm, stall, st, &p);
+        launches.push_back(p);
+    };
+    add(progs, lean, o.test_unsatisfiable != 0);
     size_t nph = 0;
     for (const auto& f : phases) nph = std::max(nph, f.rev.size());
     for (size_t ph = 0; ph < nph && grad; ++ph) {
@@ -434,13 +534,40 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
             rv[i] = phases[i].rev[ph - off];
             any_rec |= !rec[i].empty();
         }
-        if (any_rec && (r = run_persistent(bs, rec, bnd, lean, o.ctas_per_sm, d_err, st, nullptr,
-                                           wait, false)) != EWS_OK)
-            return r;
-        if ((r = run_persistent(bs, rv, bnd, rev, o.ctas_per_sm, d_err, st, nullptr, wait,
-                                false)) != EWS_OK)
-            return r;
+        if (any_rec) add(rec, lean, false);
+        add(rv, rev, false);
     }
+    if (r != EWS_OK) {
+        cleanup();
+        return r;
+    }
+    cudaError_t e = cudaMalloc(&d_shots, sizeof(BatchShot) * nshots);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_shots, bs.data(), sizeof(BatchShot) * nshots, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);        // tables in place
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaSuccess;
+        for (const Prepared& p : launches)
+            if (le == cudaSuccess) le = enqueue(p, bnd, nshots, d_shots, d_err, wait, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gexec, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess)
+        return report(e == cudaErrorMemoryAllocation ? EWS_ENOMEM : EWS_ECUDA, "batched launches: %s",
+                      cudaGetErrorString(e));
+    if (herr & 11)
+        return report(EWS_ETIMEOUT, "batched executor: a %s wait gave up (flags %d)",
+                      (herr & 8) ? "dependency" : "pipeline", herr);
+    if (herr & 16) return report(EWS_ENONFINITE, "batched executor: a receiver recorded NaN or Inf");
     for (int i = 0; i < nshots; ++i) {
         ews_sim* s = shots[i].sim;
         s->fresh = false;
