@@ -531,7 +531,7 @@ def batch_report(args, local):
     own layered + random model each, sponge 16, explosion at nz/3, 8 x 8
     receivers): the forward of the first --batch-shots shots, and forward plus
     L2 gradient (data from a +5 % sphere variant) of the first
-    --batch-grad-shots, each as one persistent launch and as one shot after
+    --batch-grad-shots, each as persistent launches in one graph and as one shot after
     another.  Aggregate Gcell-updates/s counts cells x steps of every shot
     over the wall time of the whole job."""
     import torch
