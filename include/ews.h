@@ -274,6 +274,7 @@ enum {
     EWS_KERNEL_STRESS = 1,     /* stress pass, Eq. 2 (+ absorbing edge)        */
     EWS_KERNEL_INJECT = 2,     /* point-source injection                       */
     EWS_KERNEL_RECORD = 3,     /* receiver sampling, Sec. 2.4                  */
+    EWS_KERNEL_POINTS = 4,     /* moment injection + receivers in one launch   */
     EWS_NKERNEL = 8
 };
 

@@ -393,13 +393,21 @@ ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, d
                 CK(launch_inject(s->g, H, M, s->B, S, s->wavelet, n, stor, s->err, s->stream));
             }
         }
-        if (s->nrec > 0 && dseis) {
+        // receivers sample v^{n+1/2}: before the stress pass, or after it
+        // together with the moment source (the stress pass leaves v alone)
+        const bool rec = s->nrec > 0 && dseis;
+        const bool fuse = rec && S.kind == EWS_SOURCE_MOMENT;
+        if (rec && !fuse) {
             CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, stor, inv, s->err, s->stream));
             if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
         }
         CK(launch_stress(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
         if ((st = mark(s, EWS_KERNEL_STRESS)) != EWS_OK) return st;
-        if (S.kind == EWS_SOURCE_MOMENT) {
+        if (fuse) {
+            CK(launch_post_stress(s->g, F, M, s->B, S, s->wavelet, s->rtaps, s->nrec, dseis, ld, n,
+                                  stor, inv, s->err, s->stream));
+            if ((st = mark(s, EWS_KERNEL_POINTS)) != EWS_OK) return st;
+        } else if (S.kind == EWS_SOURCE_MOMENT) {
             CK(launch_inject(s->g, F, M, s->B, S, s->wavelet, n, stor, s->err, s->stream));
             if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
         }

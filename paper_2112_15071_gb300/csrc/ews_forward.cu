@@ -43,6 +43,28 @@ __global__ void k_record(DevGrid g, DevFields F, const Tap* __restrict__ taps, i
     seis[(long long)t * ld + n] = acc;
 }
 
+// The point terms that follow the stress pass, in one launch: block 0
+// injects the moment-rate source (one thread per tap; S.kind < 0: none),
+// blocks 1.. sample the receivers from v^{n+1/2}, which the stress pass
+// leaves unchanged (as k_record).
+template <typename T>
+__global__ void k_post_stress(DevGrid g, DevFields F, DevMedium M, DevBoundary B, DevSource S,
+                              const float* __restrict__ wavelet, const Tap* __restrict__ taps,
+                              int nrec, float* __restrict__ seis, int ld, int n, float i0, float i1,
+                              float i2, int* err) {
+    if (blockIdx.x == 0) {
+        if (S.kind >= 0 && (int)threadIdx.x < S.ntap)
+            ops::inject_tap<T>(g, F, M, B, S, wavelet, n, threadIdx.x, err);
+        return;
+    }
+    const int t = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
+    if (t >= 3 * nrec) return;
+    float acc = ops::record_one<T>(g, F, taps, t);
+    if constexpr (sizeof(T) == 2) acc *= (t < nrec ? i0 : t < 2 * nrec ? i1 : i2);
+    if (!isfinite(acc)) atomicOr(err, 16);
+    seis[(long long)t * ld + n] = acc;
+}
+
 // Stored field -> dense float32 (out = stored * inv_s) and back.
 template <typename T>
 __global__ void k_field_out(DevGrid g, const T* __restrict__ f, float inv_s, float* __restrict__ d) {
@@ -190,6 +212,26 @@ cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps,
             break;
         default:
             k_record<float><<<grid, 128, 0, st>>>(g, F, taps, nrec, seis, ld, n, 1.f, 1.f, 1.f, err);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_post_stress(const DevGrid& g, const DevFields& F, const DevMedium& M,
+                               const DevBoundary& B, const DevSource& S, const float* wavelet,
+                               const Tap* taps, int nrec, float* seis, int ld, int n, int storage,
+                               const float inv[3], int* err, cudaStream_t st) {
+    static_assert(kMaxSrcTaps <= 128, "source taps of one block");
+    const dim3 grid(1 + (3 * nrec + 127) / 128);
+    switch (storage) {
+        case EWS_STORAGE_BF16:
+            k_post_stress<__nv_bfloat16><<<grid, 128, 0, st>>>(g, F, M, B, S, wavelet, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2], err);
+            break;
+        case EWS_STORAGE_F16:
+            k_post_stress<__half><<<grid, 128, 0, st>>>(g, F, M, B, S, wavelet, taps, nrec, seis, ld, n, inv[0], inv[1], inv[2], err);
+            break;
+        default:
+            k_post_stress<float><<<grid, 128, 0, st>>>(g, F, M, B, S, wavelet, taps, nrec, seis, ld, n, 1.f, 1.f, 1.f, err);
             break;
     }
     return cudaGetLastError();

@@ -396,6 +396,12 @@ cudaError_t launch_inject(const DevGrid& g, const DevFields& F, const DevMedium&
 cudaError_t launch_record(const DevGrid& g, const DevFields& F, const Tap* taps, int nrec,
                           float* seis, int ld, int n, int storage, const float inv[3], int* err,
                           cudaStream_t st);
+// Moment-source injection (S.kind MOMENT, else none) and receiver sampling
+// of step n in one launch, after the stress pass.
+cudaError_t launch_post_stress(const DevGrid& g, const DevFields& F, const DevMedium& M,
+                               const DevBoundary& B, const DevSource& S, const float* wavelet,
+                               const Tap* taps, int nrec, float* seis, int ld, int n, int storage,
+                               const float inv[3], int* err, cudaStream_t st);
 // flags[0]: validity bits (bit4: some mu == 0); flags[1..4]: float bits of max vp, min rho,
 // min sqrt(rho mu) over cells with mu > 0 (else FLT_MAX), max sqrt(rho (lambda + 2 mu));
 // the two minima only over cells below a free surface.

@@ -28,8 +28,9 @@ EWS_STORAGE_F32, EWS_STORAGE_BF16, EWS_STORAGE_F16 = 0, 1, 2
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 EWS_SOURCE_MOMENT, EWS_SOURCE_FORCE = 0, 1
 EWS_KERNEL_VELOCITY, EWS_KERNEL_STRESS, EWS_KERNEL_INJECT, EWS_KERNEL_RECORD = 0, 1, 2, 3
+EWS_KERNEL_POINTS = 4
 EWS_NKERNEL = 8
-KERNEL_NAMES = ("velocity", "stress", "inject", "record")
+KERNEL_NAMES = ("velocity", "stress", "inject", "record", "points")
 BOUNDARY = {"none": 0, "sponge": 1, "cpml": 2}
 SOURCE = {"moment": 0, "force": 1}
 FIELDS = ("vx", "vy", "vz", "sxx", "syy", "szz", "sxy", "sxz", "syz")

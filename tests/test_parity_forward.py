@@ -193,16 +193,28 @@ def test_device_buffers_match_host_buffers(ews):
 
 
 def test_launch_accounting_and_profiling(ews):
+    """Per step: the two passes and the point terms (a moment source and the
+    receivers share one launch after the stress pass; a force source is
+    injected after the velocity pass and the receivers sampled before the
+    stress pass)."""
     p = synth.small_problem(40, 36, 28, nt=50, boundary="cpml", width=6)
     sim = ews.simulation_for(p)
     sim.set_profiling(True)
     sim.run(p.nt, p.dt)
     ms, n = sim.profile(reset=True)
     assert n[ews.EWS_KERNEL_VELOCITY] == 50 and n[ews.EWS_KERNEL_STRESS] == 50
-    assert n[ews.EWS_KERNEL_RECORD] == 50 and n[ews.EWS_KERNEL_INJECT] == 50
+    assert n[ews.EWS_KERNEL_POINTS] == 50
+    assert n[ews.EWS_KERNEL_RECORD] == 0 and n[ews.EWS_KERNEL_INJECT] == 0
     assert ms[ews.EWS_KERNEL_STRESS] > 0 and ms[ews.EWS_KERNEL_VELOCITY] > 0
     ms2, n2 = sim.profile()
     assert n2.sum() == 0 and ms2.sum() == 0
+    q = synth.small_problem(40, 36, 28, nt=50, boundary="cpml", width=6, kind="force")
+    sim = ews.simulation_for(q)
+    sim.set_profiling(True)
+    sim.run(q.nt, q.dt)
+    ms, n = sim.profile(reset=True)
+    assert n[ews.EWS_KERNEL_INJECT] == 50 and n[ews.EWS_KERNEL_RECORD] == 50
+    assert n[ews.EWS_KERNEL_POINTS] == 0
 
 
 def test_errors_are_reported(ews):
