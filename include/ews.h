@@ -219,7 +219,9 @@ ews_status ews_adjoint(ews_sim* sim, int nt, double dt, const float* seis_adj,
  * 16-bit checkpoint start from the rounded state, so the gradient differs
  * from the FP32-checkpoint one by about the storage precision.  Resident
  * history (ews_set_history_budget) needs no checkpoints.  Batched shots
- * (ews_batch) keep FP32 checkpoints.  Not in the paper. */
+ * (ews_batch) take BF16 checkpoints as asked for (without scale: BF16 has
+ * FP32's exponent range, and a power-of-two scale does not change its
+ * rounding) and keep FP16 ones in FP32.  Not in the paper. */
 ews_status ews_set_checkpoint_storage(ews_sim* sim, int storage);
 
 /* Device memory the adjoint may use for resident velocity history, in

@@ -161,6 +161,7 @@ ews_status fill_shot(BatchShot& B, ews_sim* s, const ews_batch_shot& in, int zch
     Q.X.gdt = (float)in.dt;
     B.vhist = s->vhist;
     B.ckpt = s->ckpt;
+    B.ck16 = s->ckpt_storage == EWS_STORAGE_BF16 ? 1 : 0;
     B.obs = in.observed;
     const size_t nseis = (size_t)3 * s->nrec * in.nt;
     if (!B.seis) B.seis = s->aux;                 // forward seismograms for the residual
@@ -476,7 +477,10 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         if (b.observed) {
             c_res = resident_from(s, b.nt, K, nshots);
             const int hslots = std::max(K, b.nt - c_res * K) + 1;
-            ews_status r = sim_adjoint_buffers(s, b.nt, c_res, hslots, true);
+            // BF16 checkpoints as asked for (FP16 ones are kept in FP32 here:
+            // their scales would need a reduction over the state first)
+            const int ck = s->ckpt_pref == EWS_STORAGE_BF16 ? EWS_STORAGE_BF16 : EWS_STORAGE_F32;
+            ews_status r = sim_adjoint_buffers(s, b.nt, c_res, hslots, true, ck);
             if (r == EWS_OK) r = sim_adjoint_plan(s);
             if (r != EWS_OK) return r;
         }

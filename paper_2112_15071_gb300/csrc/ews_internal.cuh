@@ -329,7 +329,7 @@ struct alignas(64) BatchShot {
     int items_pass;       // tiles x z-chunks of one pass
     int items_elem;       // cell chunks of one elementwise stage
     float dt;
-    int pad;
+    int ck16;             // checkpoints stored as BF16 (1) or FP32 (0)
 };
 static constexpr int kBatchElem = 8192;   // cells per elementwise work item
 

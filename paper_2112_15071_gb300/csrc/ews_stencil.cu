@@ -1124,13 +1124,21 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                 const DevFields& F = B.pf.F;
                 for (long long o = o0 + tid; o < o1; o += NTH) {
                     switch (E.kind) {
-                        case BK_SAVE:
-                            for (int q = 0; q < NFIELD; ++q)
-                                B.ckpt[((long long)E.slot * NFIELD + q) * fs + o] = F.f[q][o];
+                        case BK_SAVE:          // BF16 keeps FP32's range: no scale needed
+                            for (int q = 0; q < NFIELD; ++q) {
+                                const long long c = ((long long)E.slot * NFIELD + q) * fs + o;
+                                if (B.ck16)
+                                    reinterpret_cast<__nv_bfloat16*>(B.ckpt)[c] = __float2bfloat16_rn(F.f[q][o]);
+                                else
+                                    B.ckpt[c] = F.f[q][o];
+                            }
                             break;
                         case BK_LOAD:
-                            for (int q = 0; q < NFIELD; ++q)
-                                F.f[q][o] = B.ckpt[((long long)E.slot * NFIELD + q) * fs + o];
+                            for (int q = 0; q < NFIELD; ++q) {
+                                const long long c = ((long long)E.slot * NFIELD + q) * fs + o;
+                                F.f[q][o] = B.ck16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(B.ckpt)[c])
+                                                   : B.ckpt[c];
+                            }
                             break;
                         case BK_HIST0:
                             for (int q = 0; q < 3; ++q) B.vhist[q * fs + o] = F.f[q][o];

@@ -141,3 +141,35 @@ def test_unsatisfiable_dependency_times_out(ews):
     torch.cuda.synchronize()
     want = ews.simulation_for(probs[0]).run(probs[0].nt, probs[0].dt)
     assert rel(shots[0]["seis"].cpu().numpy(), want) <= 1e-6
+
+
+def test_batched_gradient_with_bf16_checkpoints(ews):
+    """BF16 checkpoints in the batched executor (every segment recomputed)
+    give the one-by-one BF16-checkpoint gradient: a power-of-two scale does
+    not change BF16 rounding, so the unscaled batched form and the scaled
+    single-shot form store the same values."""
+    import torch
+    probs = problems(nts=(60, 45, 70))
+    rng = np.random.default_rng(9)
+    obs = [rng.standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32) * 1e-3
+           for p in probs]
+    runs = []
+    for mode in (ews.EWS_BATCH_PERSISTENT, ews.EWS_BATCH_SEQUENTIAL):
+        shots = shots_for(ews, probs, grad=True, obs=obs)
+        for d in shots:
+            d["sim"].set_checkpoint_storage("bf16")
+            d["sim"].set_history_budget(0)
+        ews.ews_batch(shots, ckpt_every=15, mode=mode)
+        torch.cuda.synchronize()
+        runs.append(shots)
+    f32 = shots_for(ews, probs, grad=True, obs=obs)
+    for d in f32:
+        d["sim"].set_history_budget(0)
+    ews.ews_batch(f32, ckpt_every=15)
+    torch.cuda.synchronize()
+    a, b = runs
+    for i in range(len(probs)):
+        for k in ("g_lam", "g_mu", "g_rho"):
+            assert rel(a[i][k].cpu().numpy(), b[i][k].cpu().numpy()) <= 1e-5, (i, k)
+            e = rel(a[i][k].cpu().numpy(), f32[i][k].cpu().numpy())
+            assert 0 < e <= 3e-2, (i, k, e)
