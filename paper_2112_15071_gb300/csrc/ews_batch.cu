@@ -427,7 +427,8 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         for (int j = 0; j < i; ++j)
             if (shots[j].sim == s) return report(EWS_EINVAL, "shot %d: simulation used twice", i);
         if (s->opt.boundary != bnd) return report(EWS_EINVAL, "shot %d: boundary differs", i);
-        if (bnd == EWS_BOUNDARY_CPML) return report(EWS_EINVAL, "batched shots take NONE or SPONGE");
+        if (bnd == EWS_BOUNDARY_CPML && b.observed)
+            return report(EWS_EINVAL, "shot %d: gradients take the none or sponge boundary", i);
         if (s->opt.storage != EWS_STORAGE_F32) return report(EWS_EINVAL, "shot %d: F32 storage only", i);
         if (b.nt <= 0) return report(EWS_EINVAL, "shot %d: nt must be positive", i);
         if (b.observed) {

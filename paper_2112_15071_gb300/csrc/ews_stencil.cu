@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
             unsigned long long wait_ns) {
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int SB = GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB + (BND == BND_CPML ? PSI_BYTES : 0));
     __shared__ PassParams sP;
     __shared__ int s_e, s_it, s_stop, s_key;
     __shared__ unsigned long long s_fenced[4];   // map sets acquired, bit per shot < 64
@@ -1145,6 +1145,8 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                             break;
                         case BK_ZERO_F:
                             for (int q = 0; q < NFIELD; ++q) F.f[q][o] = 0.0f;
+                            if constexpr (BND == BND_CPML)   // C-PML memory variables from rest
+                                for (int t = 0; t < 18; ++t) B.pf.B.psi[t][o] = 0.0f;
                             break;
                         case BK_ZERO_A:
                             for (int q = 0; q < 3; ++q) B.A.p[q][o] = 0.0f;
@@ -1513,7 +1515,7 @@ cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const flo
 template <int BND, bool GRAD>
 constexpr size_t batch_smem() {
     return (size_t)NSLOT * (GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>()) +
-           8 * (NSLOT + 1);
+           (BND == BND_CPML ? PSI_BYTES : 0) + 8 * (NSLOT + 1);
 }
 
 template <int BND, bool GRAD, bool FS>
@@ -1521,20 +1523,25 @@ cudaError_t batch_prepare(int* per_sm) {
     return prepare(k_batch<BND, GRAD, FS>, batch_smem<BND, GRAD>(), per_sm);
 }
 
+// C-PML shots have no reverse executor (no C-PML adjoint).
 template <int BND>
 cudaError_t batch_occupancy_b(int exec, int* per_sm) {
     switch (exec) {
         case BX_LEAN: return batch_prepare<BND, false, false>(per_sm);
-        case BX_GRAD: return batch_prepare<BND, true, false>(per_sm);
         case BX_LEAN_FS: return batch_prepare<BND, false, true>(per_sm);
-        case BX_GRAD_FS: return batch_prepare<BND, true, true>(per_sm);
-        default: return cudaErrorInvalidValue;
+        default: break;
     }
+    if constexpr (BND != BND_CPML) {
+        if (exec == BX_GRAD) return batch_prepare<BND, true, false>(per_sm);
+        if (exec == BX_GRAD_FS) return batch_prepare<BND, true, true>(per_sm);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t batch_occupancy(int bnd, int exec, int* per_sm) {
     if (bnd == BND_SPONGE) return batch_occupancy_b<BND_SPONGE>(exec, per_sm);
     if (bnd == BND_NONE) return batch_occupancy_b<BND_NONE>(exec, per_sm);
+    if (bnd == BND_CPML) return batch_occupancy_b<BND_CPML>(exec, per_sm);
     return cudaErrorInvalidValue;
 }
 
@@ -1553,9 +1560,17 @@ cudaError_t launch_batch_b(int exec, int grid, const BatchShot* shots, const Bat
                            cudaStream_t st) {
     switch (exec) {
         case BX_LEAN: batch_go<BND, false, false>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
-        case BX_GRAD: batch_go<BND, true, false>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
         case BX_LEAN_FS: batch_go<BND, false, true>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
-        case BX_GRAD_FS: batch_go<BND, true, true>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st); break;
+        case BX_GRAD:
+        case BX_GRAD_FS:
+            if constexpr (BND != BND_CPML) {
+                if (exec == BX_GRAD)
+                    batch_go<BND, true, false>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st);
+                else
+                    batch_go<BND, true, true>(grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st);
+                break;
+            }
+            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -1569,6 +1584,8 @@ cudaError_t launch_batch(int bnd, int exec, int grid, const BatchShot* shots,
         return launch_batch_b<BND_SPONGE>(exec, grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st);
     if (bnd == BND_NONE)
         return launch_batch_b<BND_NONE>(exec, grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st);
+    if (bnd == BND_CPML)
+        return launch_batch_b<BND_CPML>(exec, grid, shots, entries, nentries, cur, taken, done, err, wait_ns, st);
     return cudaErrorInvalidValue;
 }
 
