@@ -328,14 +328,17 @@ ews_status ews_forward_noalloc(const ews_grid* grid, const ews_options* opt,
 
 /* ---- Batched shots (not in the paper, which runs one model at a time) ----
  * Many independent shots, each a configured simulation (model, source and
- * receivers set; F32 storage; boundary NONE or SPONGE, the same for all
- * shots), run forward - and, when observed data are given, through the L2
- * misfit gradient of ews_gradient - in ONE persistent kernel launch.  The
- * launch takes work items (a 32 x 8 x zchunk tile of a pass, a chunk of
- * cells, or a source/receiver step) of all shots from a device queue; an
- * item waits (bounded, EWS_ETIMEOUT) until its shot's earlier stages are
- * done, so shots of uneven size and step count share the GPU without a
- * grid-wide barrier.  Results equal those of ews_run / ews_gradient on each
+ * receivers set; F32 storage; the same boundary for all shots; C-PML for
+ * forward shots only), run forward - and, when observed data are given,
+ * through the L2 misfit gradient of ews_gradient - in persistent kernel
+ * launches replayed as one CUDA graph: one launch for the forward shots
+ * and the forward part of the gradient shots, then per segment of the
+ * reverse sweep a recomputation launch and a reverse launch.  A launch
+ * takes work items (a 32 x 8 x zchunk tile of a pass, a chunk of cells, or
+ * a source/receiver step) of all shots from a device queue; an item waits
+ * (bounded, EWS_ETIMEOUT) until its shot's earlier stages are done, so
+ * shots of uneven size and step count share the GPU without a grid-wide
+ * barrier.  Results equal those of ews_run / ews_gradient on each
  * simulation alone (bitwise for the forward, to accumulation order for the
  * gradient). */
 typedef struct {
@@ -367,9 +370,10 @@ typedef struct {
 
 /* Run nshots shots; opt may be NULL (persistent, autotuned).  All device
  * work runs on cuda_stream (NULL: default stream), which is synchronised
- * before return.  Errors: EWS_EINVAL (mixed boundaries, C-PML, 16-bit
- * storage, fluid cells for gradients, missing outputs), EWS_ECFL, EWS_ENOMEM,
- * EWS_ETIMEOUT (a dependency or pipeline wait gave up), EWS_ECUDA. */
+ * before return.  Errors: EWS_EINVAL (mixed boundaries, C-PML gradient
+ * shots, 16-bit storage, coarse medium grids, fluid cells for gradients,
+ * missing outputs), EWS_ECFL, EWS_ENOMEM, EWS_ETIMEOUT (a dependency or
+ * pipeline wait gave up), EWS_ECUDA. */
 ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
                      void* cuda_stream);
 
