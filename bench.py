@@ -197,12 +197,15 @@ def algorithmic_bytes(prob, es: int = 4):
 
 
 def kernel_source_sha() -> str:
-    """Hash of the stencil kernels' source (the kernels the traffic figure
-    belongs to); any edit there voids the committed figure."""
+    """Hash of the stencil kernels' source, the headers it includes and the
+    build flags (everything the traffic figure's kernels are compiled from);
+    any edit there voids the committed figure."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2112_15071_gb300", "csrc")
-    for f in ("ews_stencil.cu",):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    pkg = os.path.join(ROOT, "paper_2112_15071_gb300")
+    for f in (os.path.join(pkg, "csrc", "ews_stencil.cu"), os.path.join(pkg, "csrc", "ews_internal.cuh"),
+              os.path.join(pkg, "csrc", "ews_ops.cuh"), os.path.join(ROOT, "include", "ews.h"),
+              os.path.join(pkg, "_build.py")):
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -327,6 +330,13 @@ def run_ours(args, world, rank, local):
     whole_gbs = alg["step_min"] * prob.nt / (step_ms / 1e3) / 1e9
     whole = {"algorithmic_bytes_per_time_step": alg["step_min"],
              "achieved_gbs": round(whole_gbs, 1), "frac": round(whole_gbs / peak, 4)}
+    # the same without the C-PML terms: Gcell/s x (9 fields read + written
+    # + 3 medium arrays read) / peak
+    es = 4 if args.storage == "f32" else 2
+    min_cell = 18 * es + 12
+    gcells_dev = prob.nx * prob.ny * prob.nz * prob.nt / (step_ms / 1e3) / 1e9
+    whole["bytes_per_cell_fields_medium"] = min_cell
+    whole["frac_fields_medium"] = round(gcells_dev * min_cell / peak, 4)
     kernel_share = {names[k]: round(kms[k] / max(kms.sum(), 1e-12), 4)
                     for k in range(len(names)) if kl_prof[k]}
 
