@@ -361,7 +361,7 @@ typedef struct {
                                * one-by-one reference)                                 */
     int ckpt_every;           /* gradient checkpoint interval (0: 50)                 */
     int zchunk;               /* planes per tile in z; 0: picked per grid size by the
-                               * autotuner (timed trial launches, cached per process) */
+                               * autotuner (timed trial launches; see the table below) */
     int ctas_per_sm;          /* resident CTAs per SM to launch (0: as many as fit)   */
     int dep_wait_ms;          /* give-up time of one dependency wait (0: 4000 ms)     */
     int test_unsatisfiable;   /* testing only: the last item waits for an item that
@@ -397,8 +397,37 @@ ews_status ews_fwi_iteration(int nshots, ews_batch_shot* shots, float* lam, floa
                              float* rho, double max_rel_step, int ckpt_every, double* misfit0,
                              double* misfit1, double* step, void* cuda_stream);
 
-/* zchunk the autotuner picked for a grid (0 if not tuned yet). */
-int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int gradient);
+/* Autotuner table.  ews_batch with zchunk = 0 picks the planes per tile in
+ * z for each grid from timed trial launches of the forward executor (the
+ * choice serves forward and gradient shots of that grid) and keeps it for
+ * the life of the process, one entry per grid size, boundary kind and
+ * surface form (shots with a free surface run other kernel forms).  The
+ * table can be exported and imported, so that a tuning persists across
+ * processes (the Python binding stores it as JSON); entries are specific
+ * to the GPU they were timed on.  All four calls touch host memory only. */
+typedef struct {
+    int nx, ny, nz;           /* wavefield grid                                      */
+    int boundary;             /* EWS_BOUNDARY_*                                      */
+    int free_surface;         /* 1: entry of shots with a free surface, else 0       */
+    int zchunk;               /* planes per tile in z, 1 .. nz                       */
+} ews_tuned_zchunk;
+
+/* zchunk of the table entry for a grid (0 if not tuned yet). */
+int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int free_surface);
+
+/* Copy up to cap entries into out (ordered by nx, ny, nz, boundary,
+ * surface form); returns the number of entries in the table (out may be
+ * NULL to count them). */
+int ews_batch_tuning_export(ews_tuned_zchunk* out, int cap);
+
+/* Add n entries to the table, replacing entries with the same key.  All
+ * entries are checked first (sizes >= 1, a known boundary, free_surface 0
+ * or 1, 1 <= zchunk <= nz); any invalid one gives EWS_EINVAL and nothing is
+ * imported. */
+ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n);
+
+/* Empty the table (the next ews_batch with zchunk = 0 tunes again). */
+void ews_batch_tuning_clear(void);
 
 /* Time-step rule of Sec. 2.1.3, Eq. 5: 0.495 min(dx, dy, dz) / vmax. */
 double ews_cfl_dt(const ews_grid* grid, double vmax);

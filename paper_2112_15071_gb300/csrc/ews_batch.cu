@@ -396,15 +396,61 @@ ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, int exec, 
 
 extern "C" {
 
-int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int gradient) {
+int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int free_surface) {
     if (!grid) return 0;
     std::lock_guard<std::mutex> lk(ews::g_tune_mu);
     auto it = ews::g_tuned.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary,
-                                                gradient ? (int)ews::BX_GRAD : (int)ews::BX_LEAN));
-    if (it == ews::g_tuned.end() && !gradient)      // grids with a free surface
-        it = ews::g_tuned.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary,
-                                               (int)ews::BX_LEAN_FS));
+                                                free_surface ? (int)ews::BX_LEAN_FS
+                                                             : (int)ews::BX_LEAN));
     return it == ews::g_tuned.end() ? 0 : it->second;
+}
+
+// The autotuner times trial launches of the forward executor only (its
+// result serves forward and gradient shots alike), so the table has one
+// entry per grid, boundary and surface form.
+int ews_batch_tuning_export(ews_tuned_zchunk* out, int cap) {
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    int n = 0;
+    for (const auto& kv : ews::g_tuned) {
+        if (out && n < cap) {
+            ews_tuned_zchunk& e = out[n];
+            e.nx = std::get<0>(kv.first);
+            e.ny = std::get<1>(kv.first);
+            e.nz = std::get<2>(kv.first);
+            e.boundary = std::get<3>(kv.first);
+            e.free_surface = std::get<4>(kv.first) == ews::BX_LEAN_FS ? 1 : 0;
+            e.zchunk = kv.second;
+        }
+        ++n;
+    }
+    return n;
+}
+
+ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n) {
+    if (n < 0 || (n > 0 && !in)) return ews::report(EWS_EINVAL, "ews_batch_tuning_import: no entries");
+    for (int k = 0; k < n; ++k) {
+        const ews_tuned_zchunk& e = in[k];
+        if (e.nx < 1 || e.ny < 1 || e.nz < 1 || e.boundary < EWS_BOUNDARY_NONE ||
+            e.boundary > EWS_BOUNDARY_CPML || (e.free_surface != 0 && e.free_surface != 1) ||
+            e.zchunk < 1 || e.zchunk > e.nz)
+            return ews::report(EWS_EINVAL,
+                               "ews_batch_tuning_import: entry %d (%d x %d x %d, boundary %d, "
+                               "surface %d, zchunk %d) is invalid; nothing imported",
+                               k, e.nx, e.ny, e.nz, e.boundary, e.free_surface, e.zchunk);
+    }
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    for (int k = 0; k < n; ++k) {
+        const ews_tuned_zchunk& e = in[k];
+        ews::g_tuned[std::make_tuple(e.nx, e.ny, e.nz, e.boundary,
+                                     e.free_surface ? (int)ews::BX_LEAN_FS : (int)ews::BX_LEAN)] =
+            e.zchunk;
+    }
+    return EWS_OK;
+}
+
+void ews_batch_tuning_clear(void) {
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    ews::g_tuned.clear();
 }
 
 ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,

@@ -66,6 +66,11 @@ class ews_batch_options(C.Structure):
                 ("test_unsatisfiable", C.c_int)]
 
 
+class ews_tuned_zchunk(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("boundary", C.c_int),
+                ("free_surface", C.c_int), ("zchunk", C.c_int)]
+
+
 EWS_BATCH_PERSISTENT, EWS_BATCH_SEQUENTIAL = 0, 1
 
 _lock = threading.Lock()
@@ -101,6 +106,9 @@ SIGNATURES = [
                              _P, _P, _P, _I, _P, _I, _D, _P, _P]),
     ("ews_batch", _I, [_I, C.POINTER(ews_batch_shot), C.POINTER(ews_batch_options), _P]),
     ("ews_batch_tuned_zchunk", _I, [C.POINTER(ews_grid), _I, _I]),
+    ("ews_batch_tuning_export", _I, [C.POINTER(ews_tuned_zchunk), _I]),
+    ("ews_batch_tuning_import", _I, [C.POINTER(ews_tuned_zchunk), _I]),
+    ("ews_batch_tuning_clear", None, []),
     ("ews_fwi_iteration", _I, [_I, C.POINTER(ews_batch_shot), _P, _P, _P, _D, _I, _P, _P, _P,
                                _P]),
     ("ews_cfl_dt", _D, [C.POINTER(ews_grid), _D]),
@@ -355,8 +363,75 @@ def ews_fwi_iteration(shots, lam, mu, rho, max_rel_step: float = 0.02, ckpt_ever
     return j0.value, j1.value, a.value
 
 
-def ews_batch_tuned_zchunk(grid: ews_grid, boundary: int, gradient: bool) -> int:
-    return load().ews_batch_tuned_zchunk(C.byref(grid), int(boundary), int(bool(gradient)))
+def ews_batch_tuned_zchunk(grid: ews_grid, boundary: int, free_surface: bool) -> int:
+    return load().ews_batch_tuned_zchunk(C.byref(grid), int(boundary), int(bool(free_surface)))
+
+
+_BOUNDARY_NAMES = {v: k for k, v in BOUNDARY.items()}
+TUNING_FORMAT = "ews-batch-tuning/1"
+
+
+def ews_batch_tuning_export() -> list:
+    """The autotuner table as a list of dicts (nx, ny, nz, boundary name,
+    free_surface, zchunk)."""
+    lib = load()
+    n = lib.ews_batch_tuning_export(None, 0)
+    arr = (ews_tuned_zchunk * max(n, 1))()
+    n = min(n, lib.ews_batch_tuning_export(arr, n))
+    return [{"nx": e.nx, "ny": e.ny, "nz": e.nz, "boundary": _BOUNDARY_NAMES.get(e.boundary, e.boundary),
+             "free_surface": bool(e.free_surface), "zchunk": e.zchunk} for e in arr[:n]]
+
+
+def ews_batch_tuning_import(entries) -> None:
+    """Add entries (dicts as ews_batch_tuning_export returns) to the table."""
+    entries = list(entries)
+    arr = (ews_tuned_zchunk * max(len(entries), 1))()
+    for k, e in enumerate(entries):
+        b = e["boundary"]
+        arr[k] = ews_tuned_zchunk(int(e["nx"]), int(e["ny"]), int(e["nz"]),
+                                  BOUNDARY[b] if isinstance(b, str) else int(b),
+                                  int(bool(e["free_surface"])), int(e["zchunk"]))
+    _check(load().ews_batch_tuning_import(arr, len(entries)))
+
+
+def ews_batch_tuning_clear() -> None:
+    load().ews_batch_tuning_clear()
+
+
+def _device_name():
+    try:
+        import torch
+        return torch.cuda.get_device_name() if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
+def save_batch_tuning(path: str, device: str | None = None) -> int:
+    """Write the autotuner table to a JSON file, tagged with the GPU it was
+    timed on (default: the current CUDA device).  Returns the entry count."""
+    import json
+    entries = ews_batch_tuning_export()
+    doc = {"format": TUNING_FORMAT, "device": device if device is not None else _device_name(),
+           "entries": entries}
+    with open(path, "w") as f:
+        json.dump(doc, f, indent=1)
+    return len(entries)
+
+
+def load_batch_tuning(path: str, device: str | None = None) -> int:
+    """Import a table written by save_batch_tuning.  Entries timed on another
+    GPU are not imported (returns 0); device defaults to the current CUDA
+    device.  Returns the number of entries imported."""
+    import json
+    with open(path) as f:
+        doc = json.load(f)
+    if doc.get("format") != TUNING_FORMAT:
+        raise ValueError(f"{path}: not an autotuner table ({doc.get('format')!r})")
+    here = device if device is not None else _device_name()
+    if doc.get("device") is not None and here is not None and doc["device"] != here:
+        return 0
+    ews_batch_tuning_import(doc["entries"])
+    return len(doc["entries"])
 
 
 def ews_set_profiling(sim, on: bool):

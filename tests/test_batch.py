@@ -200,3 +200,31 @@ def test_cpml_forward_batch_matches_run(ews, zchunk):
     torch.cuda.synchronize()
     for d, e in zip(shots, shots2):
         assert rel(e["seis"].cpu().numpy(), d["seis"].cpu().numpy()) <= 1e-7
+
+
+def test_imported_tuning_is_used_without_retuning(ews, tmp_path):
+    """A table written by save_batch_tuning and read back by
+    load_batch_tuning serves ews_batch with zchunk = 0: no grid is tuned
+    again (the table is unchanged afterwards) and the results still match
+    the one-by-one path."""
+    import torch
+    probs = problems()[:2]
+    forced = [{"nx": p.nx, "ny": p.ny, "nz": p.nz, "boundary": "sponge", "free_surface": False,
+               "zchunk": 12} for p in probs]
+    path = str(tmp_path / "tuning.json")
+    ews.ews_batch_tuning_clear()
+    ews.ews_batch_tuning_import(forced)
+    assert ews.save_batch_tuning(path) == 2
+    ews.ews_batch_tuning_clear()
+    try:
+        assert ews.load_batch_tuning(path) == 2
+        shots = shots_for(ews, probs)
+        ews.ews_batch(shots)
+        torch.cuda.synchronize()
+        key = lambda e: (e["nx"], e["ny"], e["nz"])
+        assert sorted(ews.ews_batch_tuning_export(), key=key) == sorted(forced, key=key)
+        for p, d in zip(probs, shots):
+            want = ews.simulation_for(p).run(p.nt, p.dt)
+            assert rel(d["seis"].cpu().numpy(), want) <= 1e-6
+    finally:
+        ews.ews_batch_tuning_clear()
