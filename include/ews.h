@@ -401,10 +401,14 @@ ews_status ews_fwi_iteration(int nshots, ews_batch_shot* shots, float* lam, floa
  * z for each grid from timed trial launches of the forward executor (the
  * choice serves forward and gradient shots of that grid) and keeps it for
  * the life of the process, one entry per grid size, boundary kind and
- * surface form (shots with a free surface run other kernel forms).  The
- * table can be exported and imported, so that a tuning persists across
- * processes (the Python binding stores it as JSON); entries are specific
- * to the GPU they were timed on.  All four calls touch host memory only. */
+ * surface form (shots with a free surface run other kernel forms).  A
+ * batch of several forward shots then also times its first steps with
+ * whole tile columns (one z-chunk per column) against the table's values
+ * and keeps the faster, cached per batch composition (not part of the
+ * table; cleared with it).  The table can be exported and imported, so
+ * that a tuning persists across processes (the Python binding stores it
+ * as JSON); entries are specific to the GPU they were timed on.  All four
+ * calls touch host memory only. */
 typedef struct {
     int nx, ny, nz;           /* wavefield grid                                      */
     int boundary;             /* EWS_BOUNDARY_*                                      */

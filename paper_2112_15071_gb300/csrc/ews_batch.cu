@@ -391,6 +391,59 @@ ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, int exec, 
     return EWS_OK;
 }
 
+// ---- batch level: the per-size table or whole tile columns ----
+// The table comes from trials of one shot alone, where short z-chunks buy
+// parallelism.  A batch of many forward shots has that parallelism already,
+// and whole tile columns (one chunk per column: fewer halo planes, items
+// and dependency waits) can be faster: the 48-shot forward batch of cubes
+// 96..224 ran at 41.5 Gcell/s with the table and 43.2 with 128-plane
+// chunks.  So such a batch times its first steps both ways and keeps the
+// faster; the choice is cached per batch composition.
+std::map<std::vector<std::tuple<int, int, int, int, int>>, bool> g_whole;   // under g_tune_mu
+
+ews_status choose_whole_columns(const ews_batch_shot* shots, int nshots, const std::vector<int>& zc,
+                                int bnd, int exec, int ctas, int* d_err, cudaStream_t st,
+                                bool* whole) {
+    std::vector<std::tuple<int, int, int, int, int>> key;
+    for (int i = 0; i < nshots; ++i) {
+        const ews_sim* s = shots[i].sim;
+        key.emplace_back(s->g.nx, s->g.ny, s->g.nz, bnd, exec);
+    }
+    std::sort(key.begin(), key.end());
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_whole.find(key);
+        if (it != g_whole.end()) {
+            *whole = it->second;
+            return EWS_OK;
+        }
+    }
+    int T = 6;                                        // trial: the first few forward steps
+    for (int i = 0; i < nshots; ++i) T = std::min(T, shots[i].nt);
+    float best[2] = {0, 0};
+    for (int w = 0; w < 2; ++w) {
+        std::vector<BatchShot> bs(nshots);
+        std::vector<std::vector<Stage>> progs(nshots);
+        for (int i = 0; i < nshots; ++i) {
+            ews_batch_shot probe = shots[i];
+            probe.seis = nullptr;
+            probe.nt = T;
+            ews_status r = fill_shot(bs[i], probe.sim, probe, w ? probe.sim->g.nz : zc[i], d_err, false);
+            if (r != EWS_OK) return r;
+            for (int n = 0; n < T; ++n) push_step(progs[i], bs[i], n, -1, false);
+        }
+        float ms = 0, ms2 = 0;
+        ews_status r;
+        if ((r = run_persistent(bs, progs, bnd, exec, ctas, d_err, st, &ms)) != EWS_OK) return r;
+        if ((r = run_persistent(bs, progs, bnd, exec, ctas, d_err, st, &ms2)) != EWS_OK) return r;
+        best[w] = std::min(ms, ms2);
+    }
+    *whole = best[1] < best[0];
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_whole[key] = *whole;
+    return EWS_OK;
+}
+
 }  // namespace
 }  // namespace ews
 
@@ -439,6 +492,7 @@ ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n) {
                                k, e.nx, e.ny, e.nz, e.boundary, e.free_surface, e.zchunk);
     }
     std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    ews::g_whole.clear();                       // batch-level choices were made against the old entries
     for (int k = 0; k < n; ++k) {
         const ews_tuned_zchunk& e = in[k];
         ews::g_tuned[std::make_tuple(e.nx, e.ny, e.nz, e.boundary,
@@ -451,6 +505,7 @@ ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n) {
 void ews_batch_tuning_clear(void) {
     std::lock_guard<std::mutex> lk(ews::g_tune_mu);
     ews::g_tuned.clear();
+    ews::g_whole.clear();
 }
 
 ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
@@ -516,6 +571,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
     std::vector<BatchShot> bs(nshots);
     std::vector<std::vector<Stage>> progs(nshots);
     std::vector<Phases> phases(nshots);
+    std::vector<int> zcs(nshots, 0), cres(nshots, 0);
     for (int i = 0; i < nshots; ++i) {
         ews_batch_shot& b = shots[i];
         ews_sim* s = b.sim;
@@ -531,24 +587,36 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
             if (r == EWS_OK) r = sim_adjoint_plan(s);
             if (r != EWS_OK) return r;
         }
-        int zc = o.zchunk;
-        if (zc == 0) {
+        zcs[i] = o.zchunk;
+        cres[i] = c_res;
+        if (zcs[i] == 0) {
             ews_status r = tune_zchunk(s, b, bnd, s->g.fs != kNoSurface ? BX_LEAN_FS : BX_LEAN,
-                                       o.ctas_per_sm, d_err, st, &zc);
+                                       o.ctas_per_sm, d_err, st, &zcs[i]);
             if (r != EWS_OK) return r;
         }
-        ews_status r = fill_shot(bs[i], s, b, zc, d_err, b.observed != nullptr);
+    }
+    const int lean = any_fs ? BX_LEAN_FS : BX_LEAN, rev = any_fs ? BX_GRAD_FS : BX_GRAD;
+    bool whole = false;
+    if (o.zchunk == 0 && !grad && nshots > 1) {
+        ews_status r = choose_whole_columns(shots, nshots, zcs, bnd, lean, o.ctas_per_sm, d_err, st,
+                                            &whole);
+        if (r != EWS_OK) return r;
+    }
+    for (int i = 0; i < nshots; ++i) {
+        ews_batch_shot& b = shots[i];
+        ews_sim* s = b.sim;
+        const int K = std::min(K0, b.nt);
+        ews_status r = fill_shot(bs[i], s, b, whole ? s->g.nz : zcs[i], d_err, b.observed != nullptr);
         if (r != EWS_OK) return r;
         if (b.observed) {
-            gradient_forward_program(progs[i], bs[i], b.nt, K, c_res);
-            gradient_reverse_phases(phases[i], bs[i], b.nt, K, c_res);
+            gradient_forward_program(progs[i], bs[i], b.nt, K, cres[i]);
+            gradient_reverse_phases(phases[i], bs[i], b.nt, K, cres[i]);
         } else {
             forward_program(progs[i], bs[i], b.nt);
         }
     }
     const unsigned long long wait =
         o.dep_wait_ms ? (unsigned long long)o.dep_wait_ms * 1000000ull : 4000000000ull;
-    const int lean = any_fs ? BX_LEAN_FS : BX_LEAN, rev = any_fs ? BX_GRAD_FS : BX_GRAD;
     // The launches: the forward part of every shot, then the reverse parts
     // segment phase by segment phase (a recomputation launch and a reverse
     // launch per phase; shots with fewer segments join for the last phases,

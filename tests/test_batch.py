@@ -54,7 +54,7 @@ def problems(kinds=("moment", "force", "moment"), nts=(70, 45, 90)):
                                 nrec=6, seed=30 + i) for i in range(len(kinds))]
 
 
-@pytest.mark.parametrize("zchunk,ctas", [(0, 0), (8, 1), (13, 2)])
+@pytest.mark.parametrize("zchunk,ctas", [(0, 0), (8, 1), (13, 2), (64, 0)])   # 64: whole columns
 def test_forward_batch_matches_run(ews, zchunk, ctas):
     import torch
     probs = problems()
