@@ -391,19 +391,25 @@ ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, int exec, 
     return EWS_OK;
 }
 
-// ---- batch level: the per-size table or whole tile columns ----
+// ---- batch level: the per-size table or longer z-chunks ----
 // The table comes from trials of one shot alone, where short z-chunks buy
 // parallelism.  A batch of many forward shots has that parallelism already,
-// and whole tile columns (one chunk per column: fewer halo planes, items
-// and dependency waits) can be faster: the 48-shot forward batch of cubes
-// 96..224 ran at 41.5 Gcell/s with the table and 43.2 with 128-plane
-// chunks.  So such a batch times its first steps both ways and keeps the
-// faster; the choice is cached per batch composition.
-std::map<std::vector<std::tuple<int, int, int, int, int>>, bool> g_whole;   // under g_tune_mu
+// and longer chunks (fewer halo planes, items and dependency waits) can be
+// faster: the 48-shot forward batch of cubes 96..224 ran at 41.5 Gcell/s
+// with the table, 42.4 with 64-plane chunks, 43.2 with 128-plane chunks.
+// So such a batch times its first steps with each candidate (the table;
+// 64 and 128 planes; whole tile columns) and keeps the fastest; the choice
+// is cached per batch composition.
+constexpr int kBatchChunks[] = {0, 64, 128, 1 << 30};            // 0: the table
+std::map<std::vector<std::tuple<int, int, int, int, int>>, int> g_choice;   // under g_tune_mu
 
-ews_status choose_whole_columns(const ews_batch_shot* shots, int nshots, const std::vector<int>& zc,
-                                int bnd, int exec, int ctas, int* d_err, cudaStream_t st,
-                                bool* whole) {
+int chunk_for(int choice, int table_zc, int nz) {
+    return choice == 0 ? table_zc : std::min(kBatchChunks[choice], nz);
+}
+
+ews_status choose_batch_chunks(const ews_batch_shot* shots, int nshots, const std::vector<int>& zc,
+                               int bnd, int exec, int ctas, int* d_err, cudaStream_t st,
+                               int* choice) {
     std::vector<std::tuple<int, int, int, int, int>> key;
     for (int i = 0; i < nshots; ++i) {
         const ews_sim* s = shots[i].sim;
@@ -412,23 +418,30 @@ ews_status choose_whole_columns(const ews_batch_shot* shots, int nshots, const s
     std::sort(key.begin(), key.end());
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_whole.find(key);
-        if (it != g_whole.end()) {
-            *whole = it->second;
+        auto it = g_choice.find(key);
+        if (it != g_choice.end()) {
+            *choice = it->second;
             return EWS_OK;
         }
     }
     int T = 6;                                        // trial: the first few forward steps
     for (int i = 0; i < nshots; ++i) T = std::min(T, shots[i].nt);
-    float best[2] = {0, 0};
-    for (int w = 0; w < 2; ++w) {
+    const int ncand = (int)(sizeof(kBatchChunks) / sizeof(kBatchChunks[0]));
+    std::vector<std::vector<int>> tried;
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int c = 0; c < ncand; ++c) {
+        std::vector<int> z(nshots);
+        for (int i = 0; i < nshots; ++i) z[i] = chunk_for(c, zc[i], shots[i].sim->g.nz);
+        if (std::find(tried.begin(), tried.end(), z) != tried.end()) continue;   // same launch
+        tried.push_back(z);
         std::vector<BatchShot> bs(nshots);
         std::vector<std::vector<Stage>> progs(nshots);
         for (int i = 0; i < nshots; ++i) {
             ews_batch_shot probe = shots[i];
             probe.seis = nullptr;
             probe.nt = T;
-            ews_status r = fill_shot(bs[i], probe.sim, probe, w ? probe.sim->g.nz : zc[i], d_err, false);
+            ews_status r = fill_shot(bs[i], probe.sim, probe, z[i], d_err, false);
             if (r != EWS_OK) return r;
             for (int n = 0; n < T; ++n) push_step(progs[i], bs[i], n, -1, false);
         }
@@ -436,11 +449,15 @@ ews_status choose_whole_columns(const ews_batch_shot* shots, int nshots, const s
         ews_status r;
         if ((r = run_persistent(bs, progs, bnd, exec, ctas, d_err, st, &ms)) != EWS_OK) return r;
         if ((r = run_persistent(bs, progs, bnd, exec, ctas, d_err, st, &ms2)) != EWS_OK) return r;
-        best[w] = std::min(ms, ms2);
+        ms = std::min(ms, ms2);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
     }
-    *whole = best[1] < best[0];
+    *choice = best;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_whole[key] = *whole;
+    g_choice[key] = best;
     return EWS_OK;
 }
 
@@ -492,7 +509,7 @@ ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n) {
                                k, e.nx, e.ny, e.nz, e.boundary, e.free_surface, e.zchunk);
     }
     std::lock_guard<std::mutex> lk(ews::g_tune_mu);
-    ews::g_whole.clear();                       // batch-level choices were made against the old entries
+    ews::g_choice.clear();                      // batch-level choices were made against the old entries
     for (int k = 0; k < n; ++k) {
         const ews_tuned_zchunk& e = in[k];
         ews::g_tuned[std::make_tuple(e.nx, e.ny, e.nz, e.boundary,
@@ -505,7 +522,7 @@ ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n) {
 void ews_batch_tuning_clear(void) {
     std::lock_guard<std::mutex> lk(ews::g_tune_mu);
     ews::g_tuned.clear();
-    ews::g_whole.clear();
+    ews::g_choice.clear();
 }
 
 ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
@@ -596,17 +613,18 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         }
     }
     const int lean = any_fs ? BX_LEAN_FS : BX_LEAN, rev = any_fs ? BX_GRAD_FS : BX_GRAD;
-    bool whole = false;
+    int choice = 0;                            // the per-size table
     if (o.zchunk == 0 && !grad && nshots > 1) {
-        ews_status r = choose_whole_columns(shots, nshots, zcs, bnd, lean, o.ctas_per_sm, d_err, st,
-                                            &whole);
+        ews_status r = choose_batch_chunks(shots, nshots, zcs, bnd, lean, o.ctas_per_sm, d_err, st,
+                                           &choice);
         if (r != EWS_OK) return r;
     }
     for (int i = 0; i < nshots; ++i) {
         ews_batch_shot& b = shots[i];
         ews_sim* s = b.sim;
         const int K = std::min(K0, b.nt);
-        ews_status r = fill_shot(bs[i], s, b, whole ? s->g.nz : zcs[i], d_err, b.observed != nullptr);
+        ews_status r = fill_shot(bs[i], s, b, chunk_for(choice, zcs[i], s->g.nz), d_err,
+                                 b.observed != nullptr);
         if (r != EWS_OK) return r;
         if (b.observed) {
             gradient_forward_program(progs[i], bs[i], b.nt, K, cres[i]);
