@@ -34,7 +34,7 @@ def ricker(nt: int, dt: float, f0: float, t0: float | None = None,
     """Ricker wavelet sampled at t = (n + shift) * dt, n = 0..nt-1 (float32).
 
     The paper does not state its source time function; a Ricker with
-    t0 = 1.5 / f0 starts at ~2e-10 of its peak, so there is no step at t = 0.
+    t0 = 1.5 / f0 starts at ~1e-8 of its peak, so there is no step at t = 0.
     ``shift = 0.5`` gives the half-step samples a moment-rate source needs,
     ``shift = 0`` the integer-step samples of a force source.
     """
