@@ -1,7 +1,8 @@
 // ews_batch.cu -- host side of the batched executor (ews_batch in
 // include/ews.h): per-shot programs of stages, their merge into one entry
-// list, the z-chunk autotuner, and the one-by-one reference mode.  The
-// executor kernel itself is k_batch in ews_stencil.cu.
+// list, the z-chunk autotuner (per-size table, its export / import, and the
+// batch-level choice of longer chunks), and the one-by-one reference mode.
+// The executor kernel itself is k_batch in ews_stencil.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
