@@ -74,6 +74,9 @@ def parse_args():
                     help="time steps timed with and without the free surface")
     ap.add_argument("--no-coarse", action="store_true",
                     help="skip the coarse-medium-grid timing")
+    ap.add_argument("--no-fwi", action="store_true",
+                    help="skip the multi-shot inversion-iteration timing")
+    ap.add_argument("--fwi-shots", type=int, default=8)
     ap.add_argument("--no-storage", action="store_true",
                     help="skip the FP32 / BF16 / FP16 storage comparison")
     ap.add_argument("--storage-nt", type=int, default=40,
@@ -388,6 +391,8 @@ def run_ours(args, world, rank, local):
         out["free_surface"] = free_surface_report(args, local)
     if not args.no_coarse:
         out["coarse_medium"] = coarse_report(args, local)
+    if not args.no_fwi:
+        out["fwi_iteration"] = fwi_report(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
     sim.close()
@@ -726,6 +731,73 @@ def coarse_report(args, local):
     rows["workload"] = (f"{args.n}^3 C-PML workload, {args.fs_nt} timed steps; medium on a "
                         f"{m}^3 grid (same recipe) sampled trilinearly at the staggered points")
     return rows
+
+
+def fwi_report(args, local):
+    """One multi-shot inversion iteration (ews_fwi_iteration) on the adjoint
+    case's recipe at 128^3 (layers + random + 10 % sphere as the true model,
+    smoothed layers as the start), --fwi-shots explosions on a grid at
+    k = W + 10, 600 steps: batched gradients, their sum, the scaled
+    direction and the parabolic line search.  Reported: the iteration's
+    time, that time in units of one batched forward of all shots, and the
+    misfit before and after."""
+    import numpy as np
+    import torch
+    from paper_2112_15071_gb300 import ews, synth
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    true, start = synth.config4(n=128, nt=600)
+    ns = args.fwi_shots
+    h = start.spacing[0]
+    w = start.width
+    xs = np.linspace(w + 8, start.nx - w - 8, 4) * h
+    ys = np.linspace(w + 8, start.ny - w - 8, max(1, (ns + 3) // 4)) * h
+    srcs = [np.array([x, y, (w + 10) * h]) for y in ys for x in xs][:ns]
+
+    def sims_for(p):
+        out = []
+        for s in srcs:
+            sim = ews.Simulation(p.nx, p.ny, p.nz, p.spacing, boundary=p.boundary, width=p.width)
+            sim.set_model_vel(p.vp, p.vs, p.rho)
+            sim.set_source(p.src_kind, s, p.src_comp, p.wavelet)
+            sim.set_receivers(p.rec_pos)
+            out.append(sim)
+        return out
+
+    tsims = sims_for(true)
+    obs = [torch.zeros((3, start.rec_pos.shape[0], start.nt), device=dev) for _ in srcs]
+    ews.ews_batch([{"sim": t, "nt": start.nt, "dt": start.dt, "seis": o}
+                   for t, o in zip(tsims, obs)], stream_handle=stream.cuda_stream)
+    for t in tsims:
+        t.close()
+    sims = sims_for(start)
+    seis = [torch.zeros_like(o) for o in obs]
+    fwd = [{"sim": s, "nt": start.nt, "dt": start.dt, "seis": x} for s, x in zip(sims, seis)]
+    ews.ews_batch(fwd, stream_handle=stream.cuda_stream)           # warm-up, tuning
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ews.ews_batch(fwd, stream_handle=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    lam, mu, rho = (torch.from_numpy(a).to(dev) for a in start.lame())
+    shots = [{"sim": s, "nt": start.nt, "dt": start.dt, "observed": o} for s, o in zip(sims, obs)]
+    # warm-up on a copy of the model (every shot's gradient state gets allocated)
+    ews.ews_fwi_iteration(shots, lam.clone(), mu.clone(), rho.clone(), max_rel_step=0.02,
+                          ckpt_every=50, stream_handle=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    j0, j1, a = ews.ews_fwi_iteration(shots, lam, mu, rho, max_rel_step=0.02, ckpt_every=50,
+                                      stream_handle=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_it = time.perf_counter() - t0
+    for s in sims:
+        s.close()
+    torch.cuda.empty_cache()
+    return {"workload": f"{ns} explosions on the adjoint recipe at 128^3 (dx {h} m), {start.nt} "
+                        "steps, sponge, 10 % sphere hidden in layers + random; start = smoothed layers",
+            "iteration_s": round(t_it, 3), "batched_forward_s": round(t_fwd, 3),
+            "forward_equivalents": round(t_it / t_fwd, 2), "misfit_before": j0,
+            "misfit_after": j1, "accepted_step": a}
 
 
 # --- reference arm: the FP64 oracle on the host cores -------------------------
