@@ -10,7 +10,7 @@ printed values; the adjoint-vs-forward consistency tests are left out)
 against that copy.  Every mistake must fail at least one pin.  The oracle
 itself is never modified.
 
-    python oracle/mutation_study.py [name ...]
+    python tests/oracle_mutation_study.py [name ...]
 """
 import os
 import shutil
