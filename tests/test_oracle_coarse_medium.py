@@ -92,3 +92,35 @@ def test_separable_restatement(orc):
                   (med[7][k, j, i], sample(mu, *pos(0, 0.5, 0.5)))]
         for got, want in checks:
             assert abs(got - want) <= 1e-13 * abs(want), (i, j, k, got, want)
+
+
+def test_wavefield_grid_medium_is_linear_filtering(orc):
+    """Reading R4 against the paper's own statement (Sec. 2.2.1: the medium
+    is read with linear texture filtering at the staggered points, clamped
+    at the edges): numpy.interp along each axis over the cell centres of the
+    wavefield-grid medium, evaluated at the staggered points, gives the
+    oracle's 2- and 4-cell means; rho is interpolated, then inverted."""
+    rng = np.random.default_rng(8)
+    n = (7, 6, 5)
+    lam, mu, rho = (rng.uniform(1.0, 2.0, (n[2], n[1], n[0])) * s for s in (1e10, 1e10, 2e3))
+    med = medium_of(orc, n, fine=(lam, mu, rho))
+    cen = [np.arange(nn, dtype=np.float64) for nn in n]
+
+    def sample(a, x, y, z):
+        t = np.array([[np.interp(x, cen[0], a[kk, jj, :]) for jj in range(n[1])]
+                      for kk in range(n[2])])
+        t = np.array([np.interp(y, cen[1], t[kk, :]) for kk in range(n[2])])
+        return np.interp(z, cen[2], t)
+
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                checks = [(1.0 / med[0][k, j, i], sample(rho, i + 0.5, j, k)),
+                          (1.0 / med[1][k, j, i], sample(rho, i, j + 0.5, k)),
+                          (1.0 / med[2][k, j, i], sample(rho, i, j, k + 0.5)),
+                          (med[3][k, j, i], sample(lam, i, j, k)),
+                          (med[5][k, j, i], sample(mu, i + 0.5, j + 0.5, k)),
+                          (med[6][k, j, i], sample(mu, i + 0.5, j, k + 0.5)),
+                          (med[7][k, j, i], sample(mu, i, j + 0.5, k + 0.5))]
+                for got, want in checks:
+                    assert abs(got - want) <= 1e-13 * abs(want), (i, j, k, got, want)
