@@ -105,3 +105,22 @@ def test_oracle_and_product_share_no_code():
             txt = open(os.path.join(orc, f)).read()
             assert not re.search(r"^\s*(from|import)\s+paper_2112_15071_gb300", txt, re.M), f
             assert not re.search(r"#\s*include\s*[<\"].*(ews|csrc)", txt), f
+
+
+def test_every_entry_point_is_documented():
+    """Each declaration in include/ews.h follows a comment (its contract),
+    or directly follows a sibling declaration that shares it."""
+    lines = open(os.path.join(ROOT, "include", "ews.h")).read().split("\n")
+    decl = re.compile(r"^(ews_status|int|double|void|const char\*)\s+\**\s*(ews_[a-z_0-9]+)\s*\(")
+    seen = 0
+    for n, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        seen += 1
+        k = n - 1
+        while k >= 0 and not lines[k].strip():
+            k -= 1
+        prev = lines[k].strip()
+        assert prev.endswith("*/") or prev.endswith(");"), m.group(2)
+    assert seen == len(declared_symbols())
