@@ -373,3 +373,27 @@ def test_double_couple_tensor():
     assert abs(np.trace(M)) < 1e-12
     ev = np.sort(np.linalg.eigvalsh(M))
     assert np.allclose(ev, [-1.0, 0.0, 1.0], atol=1e-12)
+
+
+def test_sponge_is_cerjans_profile(orc):
+    """Reading R6 against the published Cerjan et al. (1985) damping strip:
+    20 cells with G = exp(-(0.015 (20 - d))^2) at distance d from the outer
+    face (0.914 at the outer cell), product over the axes, applied to every
+    field after its update.  Observed through one velocity pass of a state
+    with v = 1 and sigma = 0 (no stress gradient, so the pass only damps)."""
+    n, W = 48, 20
+    s = orc.OracleSim(n, n, n, (10.0, 10.0, 10.0))
+    vp, vs, rho = synth.homogeneous(n, n, n)
+    s.set_medium_vel(vp, vs, rho)
+    s.set_boundary("sponge", W)
+    st = np.zeros((9, n, n, n))
+    st[:3] = 1.0
+    s.set_state(st)
+    s.step_velocity(1e-3)
+    v = s.get_state()[:3]
+    d = np.minimum(np.arange(n), n - 1 - np.arange(n))
+    g = np.where(d < W, np.exp(-(0.015 * (W - d)) ** 2), 1.0)
+    want = g[:, None, None] * g[None, :, None] * g[None, None, :]
+    for q in range(3):
+        assert np.max(np.abs(v[q] - want)) <= 1e-15
+    assert g[0] == pytest.approx(0.91393, abs=1e-5)
