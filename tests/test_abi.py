@@ -124,3 +124,45 @@ def test_every_entry_point_is_documented():
         prev = lines[k].strip()
         assert prev.endswith("*/") or prev.endswith(");"), m.group(2)
     assert seen == len(declared_symbols())
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("big_side", "above the no-allocation limit"),
+    ("big_cells", "padded cells"),
+    ("cpml", "C-PML needs memory variables"),
+    ("bf16", "only F32 storage"),
+    ("nt0", "nt must be positive"),
+    ("many_receivers", "no-allocation limit is 64"),
+    ("source_out", "source outside"),
+    ("receiver_out", "receiver 1 outside"),
+    ("bad_dt", "dt must be positive"),
+])
+def test_noalloc_validates_on_the_host(case, msg):
+    """ews_forward_noalloc checks every argument before any device work, so
+    its limits and errors hold on a machine without a GPU.  The device
+    pointers are placeholders: nothing reads them before the checks."""
+    import ctypes as C
+    lib = ews.load()
+    n = {"big_side": (1100, 8, 8), "big_cells": (512, 512, 8)}.get(case, (40, 36, 28))
+    g = ews.ews_grid(*n, 10.0, 10.0, 10.0)
+    opt = ews.ews_options(ews.EWS_BOUNDARY_SPONGE, 4, 0, 0, 0, 0.0, 0.0, 0.0)
+    if case == "cpml":
+        opt.boundary = ews.EWS_BOUNDARY_CPML
+    if case == "bf16":
+        opt.storage = ews.EWS_STORAGE_BF16
+    fake = C.c_void_p(0x1000)
+    pos = np.array([200.0, 180.0, 140.0])
+    if case == "source_out":
+        pos = np.array([1.0, 180.0, 140.0])
+    nrec = 70 if case == "many_receivers" else 2
+    rec = np.tile(np.array([150.0, 150.0, 100.0]), (nrec, 1))
+    if case == "receiver_out":
+        rec[1, 2] = 1e6
+    comp = np.zeros(6)
+    nt = 0 if case == "nt0" else 10
+    dt = -1.0 if case == "bad_dt" else 1e-3
+    st = lib.ews_forward_noalloc(C.byref(g), C.byref(opt), fake, fake, fake, ews.EWS_SOURCE_MOMENT,
+                                 pos.ctypes.data_as(C.c_void_p), comp.ctypes.data_as(C.c_void_p),
+                                 fake, nrec, rec.ctypes.data_as(C.c_void_p), nt, dt, fake, None)
+    assert st == ews.EWS_EINVAL
+    assert msg in ews.ews_last_error()
