@@ -166,3 +166,23 @@ def test_noalloc_validates_on_the_host(case, msg):
                                  fake, nrec, rec.ctypes.data_as(C.c_void_p), nt, dt, fake, None)
     assert st == ews.EWS_EINVAL
     assert msg in ews.ews_last_error()
+
+
+def test_batch_validates_on_the_host():
+    """ews_batch rejects empty batches, unknown modes, negative options and
+    missing simulations before any device work."""
+    import ctypes as C
+    lib = ews.load()
+    shots = (ews.ews_batch_shot * 1)()
+    shots[0].nt = 10
+    shots[0].dt = 1e-3
+    assert lib.ews_batch(0, shots, None, None) == ews.EWS_EINVAL
+    assert "no shots" in ews.ews_last_error()
+    o = ews.ews_batch_options(5, 0, 0, 0, 0, 0)
+    assert lib.ews_batch(1, shots, C.byref(o), None) == ews.EWS_EINVAL
+    assert "unknown batch mode" in ews.ews_last_error()
+    o = ews.ews_batch_options(0, 0, -8, 0, 0, 0)
+    assert lib.ews_batch(1, shots, C.byref(o), None) == ews.EWS_EINVAL
+    assert "negative" in ews.ews_last_error()
+    assert lib.ews_batch(1, shots, None, None) == ews.EWS_EINVAL
+    assert "null simulation" in ews.ews_last_error()
