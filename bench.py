@@ -181,6 +181,18 @@ class ClockSampler:
                 "reasons": reasons}
 
 
+def section(fn, *a):
+    """Run one of the secondary sections after the headline measurement; if
+    it raises, record the error in its place (and on stderr) so that the
+    JSON line with the headline number is still printed."""
+    try:
+        return fn(*a)
+    except Exception as e:                       # noqa: BLE001 -- reported, not hidden
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"[:400]}
+
+
 # --- roofline bookkeeping ----------------------------------------------------
 
 def algorithmic_bytes(prob, es: int = 4):
@@ -380,21 +392,21 @@ def run_ours(args, world, rank, local):
         "e2e": e2e, "clocks": clk,
     }
     if not args.no_adjoint:
-        out["adjoint"] = adjoint_ratio(args, local)
+        out["adjoint"] = section(adjoint_ratio, args, local)
     if not args.no_storage:
-        out["storage"] = storage_report(args, local, rank == 0 and world == 1)
+        out["storage"] = section(storage_report, args, local, rank == 0 and world == 1)
     if not args.no_batch:
-        out["batch"] = batch_report(args, local)
+        out["batch"] = section(batch_report, args, local)
     if not args.no_sweep:
-        out["paper_sweep"] = paper_sweep(args, local)
+        out["paper_sweep"] = section(paper_sweep, args, local)
     if not args.no_free_surface:
-        out["free_surface"] = free_surface_report(args, local)
+        out["free_surface"] = section(free_surface_report, args, local)
     if not args.no_coarse:
-        out["coarse_medium"] = coarse_report(args, local)
+        out["coarse_medium"] = section(coarse_report, args, local)
     if not args.no_fwi:
-        out["fwi_iteration"] = fwi_report(args, local)
+        out["fwi_iteration"] = section(fwi_report, args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_oracle_rate(prob, args.cpu_seconds)
+        out["cpu_baseline"] = section(cpu_oracle_rate, prob, args.cpu_seconds)
     sim.close()
     return out
 

@@ -57,3 +57,12 @@ def test_committed_traffic_lines_parse():
             found += 1
             assert int(m.group(4)) > 0
     assert found >= 2
+
+
+def test_a_failing_section_keeps_the_headline_line(capsys):
+    def boom(x):
+        raise RuntimeError(f"no memory for {x}")
+    assert bench.section(lambda a, b: a + b, 2, 3) == 5
+    r = bench.section(boom, "the sweep")
+    assert r == {"error": "RuntimeError: no memory for the sweep"}
+    assert "RuntimeError" in capsys.readouterr().err
