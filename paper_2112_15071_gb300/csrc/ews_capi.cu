@@ -26,6 +26,10 @@ ews_status fail(ews_status s, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+    // A failed device allocation leaves its (non-sticky) error for
+    // cudaGetLastError; take it here so that a later call's error check
+    // does not report it as its own.
+    if (s == EWS_ENOMEM) (void)cudaGetLastError();
     return s;
 }
 
@@ -53,6 +57,7 @@ ews_status report(ews_status s, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+    if (s == EWS_ENOMEM) (void)cudaGetLastError();     // as in fail()
     return s;
 }
 }  // namespace ews
