@@ -152,8 +152,11 @@ ews_status ews_set_model_coarse(ews_sim* sim, int mx, int my, int mz, const floa
  * (0, 1] (1e-3 is a usual value).  The damping of the top face still
  * applies, so the surface is normally placed at or below it (ks >= width).
  * The medium must be set (again) after this call: until then runs return
- * EWS_ESTATE.  Forward runs and batched forward shots support the surface;
- * gradients return EWS_EINVAL. */
+ * EWS_ESTATE.  Forward runs, gradients (ews_adjoint / ews_gradient: the
+ * reverse sweep takes the transposed z-differences and the chain rule of the
+ * harmonic means; model values above the surface get a zero gradient) and
+ * batched forward and gradient shots support the surface; a fluid cell (mu
+ * = 0) below the surface makes the gradient return EWS_EINVAL. */
 ews_status ews_set_free_surface(ews_sim* sim, int ks, double eps);
 
 /* Point source.  kind MOMENT: comp = (Mxx, Myy, Mzz, Mxy, Mxz, Myz) in N m
@@ -319,7 +322,11 @@ ews_status ews_get_profile(ews_sim* sim, double* ms, long long* launches, int re
  * Every call shares the one array and starts by clearing the wavefields, so
  * results do not depend on earlier calls, but calls that overlap on the GPU
  * (other streams or host threads) race on it.  The call synchronises
- * `cuda_stream` (NULL = default stream) before returning. */
+ * `cuda_stream` (NULL = default stream) before returning, on success and on
+ * every error found after its first device operation, so no work of a
+ * failed call is left writing the shared array.  Host threads may make
+ * their first calls concurrently; the host-side staging is a few KB of
+ * stack plus thread-local storage. */
 ews_status ews_forward_noalloc(const ews_grid* grid, const ews_options* opt,
                                const float* lam, const float* mu, const float* rho,
                                int src_kind, const double pos[3], const double comp[6],
@@ -432,6 +439,24 @@ ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n);
 
 /* Empty the table (the next ews_batch with zchunk = 0 tunes again). */
 void ews_batch_tuning_clear(void);
+
+/* ---- Device memory held by the library (not in the paper) ----
+ * Every device allocation libews makes (simulations, adjoint state,
+ * checkpoints, velocity history, batch and inversion buffers) is counted.
+ * ews_set_memory_limit caps the total, process-wide and over all devices:
+ * an allocation that would take the count above `bytes` fails before CUDA
+ * is asked, exactly as when the device is full -- the call returns
+ * EWS_ENOMEM, releases what it had set up and leaves the simulation (and the
+ * CUDA context) usable, and ews_last_error names the limit.  The automatic
+ * history budget of the adjoint stays within the room the limit leaves.
+ * bytes < 0 removes the limit (the default); a limit below the current use
+ * only refuses later allocations.  NaN gives EWS_EINVAL.  Host-only calls.
+ * (ews_forward_noalloc allocates nothing and is not counted.) */
+ews_status ews_set_memory_limit(double bytes);
+/* The limit in force (< 0: none). */
+double ews_memory_limit(void);
+/* Bytes of device memory the library holds now. */
+double ews_memory_in_use(void);
 
 /* Time-step rule of Sec. 2.1.3, Eq. 5: 0.495 min(dx, dy, dz) / vmax. */
 double ews_cfl_dt(const ews_grid* grid, double vmax);
