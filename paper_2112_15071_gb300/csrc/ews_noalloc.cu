@@ -14,13 +14,18 @@
 // it (about 12 MiB) until the process exits.  Host code cannot pass the
 // array's name to a kernel (on the host it is only a stand-in symbol), so the
 // first call on each device looks up its device address with
-// cudaGetSymbolAddress while that device is current and caches it.  Make that
-// first call before capturing any stream on the device.  All calls share the
-// one array and it keeps the previous call's contents: this entry point
-// clears what must start at zero, and calls that overlap on the GPU (other
-// streams, other host threads) race on it.
+// cudaGetSymbolAddress while that device is current and caches it (one
+// atomic slot per device, so host threads making their first calls at the
+// same time are safe).  Make that first call before capturing any stream on
+// the device.  All calls share the one array and it keeps the previous
+// call's contents: this entry point clears what must start at zero, and
+// calls that overlap on the GPU (other streams, other host threads) race on
+// it.  Host-side staging is small (a few KB of stack; the stencil plan's
+// tensor maps in thread-local storage), so the call also suits service
+// threads with small stacks.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -46,21 +51,24 @@ constexpr size_t kScratchFloats = kOffFlags + 64;                  // flags, vp_
 static __device__ __align__(256) float g_scratch[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
-float* g_scratch_dev[kMaxDevices] = {};   // device address of g_scratch, per device
+std::atomic<float*> g_scratch_dev[kMaxDevices];   // device address of g_scratch, per device
 
 ews_status scratch_address(float** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return report(EWS_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return report(EWS_ECUDA, "device index %d unsupported", dev);
-    if (!g_scratch_dev[dev]) {
+    float* a = g_scratch_dev[dev].load(std::memory_order_acquire);
+    if (!a) {
+        // Two threads may both look it up; they store the same address.
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p)
             return report(EWS_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_scratch_dev[dev] = static_cast<float*>(p);
+        a = static_cast<float*>(p);
+        g_scratch_dev[dev].store(a, std::memory_order_release);
     }
-    *out = g_scratch_dev[dev];
+    *out = a;
     return EWS_OK;
 }
 
@@ -101,11 +109,16 @@ bool position_ok(const ews_grid& gr, const double p[3]) {
     return true;
 }
 
+// On failure after device work was queued, wait for the work already on
+// the stream (its kernels may still be writing the shared array) before
+// returning, so the next call, on any stream, does not race with it.
 #define NA_CK(call)                                                                    \
     do {                                                                               \
         cudaError_t e_ = (call);                                                       \
-        if (e_ != cudaSuccess)                                                         \
+        if (e_ != cudaSuccess) {                                                       \
+            (void)cudaStreamSynchronize(stream);                                       \
             return report(EWS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
+        }                                                                              \
     } while (0)
 
 }  // namespace
@@ -154,6 +167,8 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
         if (!position_ok(gr, rec_pos + 3 * r))
             return report(EWS_EINVAL, "receiver %d outside the valid range", r);
     if (!(dt > 0) || !std::isfinite(dt)) return report(EWS_EINVAL, "dt must be positive");
+    for (int c = 0; c < (src_kind == EWS_SOURCE_MOMENT ? 6 : 3); ++c)
+        if (!std::isfinite(comp[c])) return report(EWS_ENONFINITE, "source component not finite");
 
     float* base = nullptr;
     ews_status st = scratch_address(&base);
@@ -207,27 +222,37 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
         return report(EWS_ECFL, "dt exceeds the stability bound");
 
     // ---- sponge profiles and receiver taps, computed here, copied in ----
-    float prof[9 * kMaxDim];
+    // One axis (and a chunk of receivers) at a time through small host
+    // buffers: an asynchronous copy from pageable memory has staged its
+    // source when it returns, so the buffer can be refilled at once.  The
+    // C-PML rows (pa, pb) are unused by these passes and are zeroed.
+    float prof[kMaxDim];
     const int n3[3] = {gr.nx, gr.ny, gr.nz};
     const double alpha = (opt && opt->sponge_alpha > 0) ? opt->sponge_alpha : 0.3;
-    for (int a = 0; a < 3; ++a)
-        for (int i = 0; i < kMaxDim; ++i) {
+    for (int a = 0; a < 3; ++a) {
+        for (int i = 0; i < n3[a]; ++i) {
             float gval = 1.0f;
             const int d = i < n3[a] - 1 - i ? i : n3[a] - 1 - i;
-            if (bnd == EWS_BOUNDARY_SPONGE && i < n3[a] && d < W) {
+            if (bnd == EWS_BOUNDARY_SPONGE && d < W) {
                 const double x = alpha * (W - d) / W;
                 gval = (float)std::exp(-x * x);
             }
-            prof[a * kMaxDim + i] = gval;
-            prof[(3 + a) * kMaxDim + i] = 0.0f;
-            prof[(6 + a) * kMaxDim + i] = 0.0f;
+            prof[i] = gval;
         }
-    NA_CK(cudaMemcpyAsync(base + kOffProf, prof, sizeof(prof), cudaMemcpyHostToDevice, stream));
-    Tap taps[24 * kMaxRec];
+        NA_CK(cudaMemcpyAsync(base + kOffProf + a * kMaxDim, prof, n3[a] * sizeof(float),
+                              cudaMemcpyHostToDevice, stream));
+    }
+    NA_CK(cudaMemsetAsync(base + kOffProf + 3 * kMaxDim, 0, 6 * kMaxDim * sizeof(float), stream));
+    constexpr int kRecChunk = 16;
+    Tap taps[8 * kRecChunk];
     for (int c = 0; c < 3; ++c)
-        for (int r = 0; r < nrec; ++r) point_taps(gr, VX + c, rec_pos + 3 * r, 1.0, &taps[8 * (c * nrec + r)]);
-    if (nrec > 0)
-        NA_CK(cudaMemcpyAsync(rtaps, taps, sizeof(Tap) * 24 * nrec, cudaMemcpyHostToDevice, stream));
+        for (int r0 = 0; r0 < nrec; r0 += kRecChunk) {
+            const int nr = nrec - r0 < kRecChunk ? nrec - r0 : kRecChunk;
+            for (int r = 0; r < nr; ++r)
+                point_taps(gr, VX + c, rec_pos + 3 * (r0 + r), 1.0, &taps[8 * r]);
+            NA_CK(cudaMemcpyAsync(rtaps + 8 * (c * nrec + r0), taps, sizeof(Tap) * 8 * nr,
+                                  cudaMemcpyHostToDevice, stream));
+        }
     DevBoundary B{};
     B.kind = bnd == EWS_BOUNDARY_SPONGE ? BND_SPONGE : BND_NONE;
     B.W = W;
@@ -242,7 +267,6 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
     const double vol = gr.dx * gr.dy * gr.dz;
     const int nc = src_kind == EWS_SOURCE_MOMENT ? 6 : 3;
     for (int c = 0; c < nc; ++c) {
-        if (!std::isfinite(comp[c])) return report(EWS_ENONFINITE, "source component not finite");
         if (comp[c] == 0.0) continue;
         if (src_kind == EWS_SOURCE_MOMENT)
             point_taps(gr, SXX + c, pos, -dt * comp[c] / vol, &S.tap[S.ntap]);
@@ -251,11 +275,16 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
         S.ntap += 8;
     }
 
-    // ---- state starts at zero; the plan is built in host stack storage ----
+    // ---- state starts at zero; the plan is built in thread-local storage ----
     NA_CK(cudaMemsetAsync(F.f[0], 0, 9 * (size_t)kMaxCells * sizeof(float), stream));
     NA_CK(cudaMemsetAsync(err, 0, sizeof(int), stream));
-    alignas(64) unsigned char plan_buf[16384];
-    if (stencil_plan_bytes() > sizeof(plan_buf)) return report(EWS_ECUDA, "plan storage too small");
+    // The plan (tensor maps, launch geometry) only has to live until the
+    // launches below have taken their parameters: thread-local host storage.
+    alignas(64) static thread_local unsigned char plan_buf[16384];
+    if (stencil_plan_bytes() > sizeof(plan_buf)) {
+        (void)cudaStreamSynchronize(stream);
+        return report(EWS_ECUDA, "plan storage too small");
+    }
     StencilPlan* plan = nullptr;
     NA_CK(stencil_plan_fill(plan_buf, g, F, M, B, &plan));
 
