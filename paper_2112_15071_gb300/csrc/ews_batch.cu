@@ -226,15 +226,15 @@ ews_status run_persistent(std::vector<BatchShot>& shots, std::vector<std::vector
     unsigned* d_cnt = nullptr;       // cur, taken[nent]
     unsigned long long* d_done = nullptr;
     auto cleanup = [&]() {
-        cudaFree(d_shots);
-        cudaFree(d_ent);
-        cudaFree(d_cnt);
-        cudaFree(d_done);
+        dev_free(d_shots);
+        dev_free(d_ent);
+        dev_free(d_cnt);
+        dev_free(d_done);
     };
-    cudaError_t e = cudaMalloc(&d_shots, sizeof(BatchShot) * ns);
-    if (e == cudaSuccess) e = cudaMalloc(&d_ent, sizeof(BatchEntry) * nent);
-    if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(unsigned) * (nent + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&d_done, sizeof(unsigned long long) * ns);
+    cudaError_t e = dev_malloc((void**)&d_shots, sizeof(BatchShot) * ns);
+    if (e == cudaSuccess) e = dev_malloc((void**)&d_ent, sizeof(BatchEntry) * nent);
+    if (e == cudaSuccess) e = dev_malloc((void**)&d_cnt, sizeof(unsigned) * (nent + 1));
+    if (e == cudaSuccess) e = dev_malloc((void**)&d_done, sizeof(unsigned long long) * ns);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_shots, shots.data(), sizeof(BatchShot) * ns, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(BatchEntry) * nent, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * (nent + 1), st);
@@ -277,9 +277,9 @@ struct Prepared {
 
 void release(std::vector<Prepared>& v) {
     for (Prepared& p : v) {
-        cudaFree(p.ent);
-        cudaFree(p.cnt);
-        cudaFree(p.done);
+        dev_free(p.ent);
+        dev_free(p.cnt);
+        dev_free(p.done);
     }
     v.clear();
 }
@@ -322,9 +322,9 @@ ews_status prepare_launch(const std::vector<std::vector<Stage>>& progs, int exec
     p.nent = (int)ent.size();
     p.exec = exec;
     p.grid = sms * per_sm;
-    cudaError_t e = cudaMalloc(&p.ent, sizeof(BatchEntry) * std::max(p.nent, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p.cnt, sizeof(unsigned) * (p.nent + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p.done, sizeof(unsigned long long) * ns);
+    cudaError_t e = dev_malloc((void**)&p.ent, sizeof(BatchEntry) * std::max(p.nent, 1));
+    if (e == cudaSuccess) e = dev_malloc((void**)&p.cnt, sizeof(unsigned) * (p.nent + 1));
+    if (e == cudaSuccess) e = dev_malloc((void**)&p.done, sizeof(unsigned long long) * ns);
     if (e == cudaSuccess && p.nent)
         e = cudaMemcpyAsync(p.ent, ent.data(), sizeof(BatchEntry) * p.nent, cudaMemcpyHostToDevice, st);
     *out = p;
@@ -651,7 +651,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         if (graph) cudaGraphDestroy(graph);
         if (cs) cudaStreamDestroy(cs);
         release(launches);
-        cudaFree(d_shots);
+        dev_free(d_shots);
     };
     ews_status r = EWS_OK;
     auto add = [&](const std::vector<std::vector<Stage>>& pr, int exec, bool stall) {
@@ -679,7 +679,7 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
         cleanup();
         return r;
     }
-    cudaError_t e = cudaMalloc(&d_shots, sizeof(BatchShot) * nshots);
+    cudaError_t e = dev_malloc((void**)&d_shots, sizeof(BatchShot) * nshots);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_shots, bs.data(), sizeof(BatchShot) * nshots, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);

@@ -21,15 +21,28 @@ namespace {
 
 thread_local char g_err[512] = "";
 
+// A failed device allocation leaves its (non-sticky) error for
+// cudaGetLastError; take it so that a later call's error check does not
+// report it as its own (a refusal by the library's memory limit leaves
+// none, and an unrelated pending error is left alone).  With a limit set,
+// the message says so.
+void enomem_tail(ews_status s) {
+    if (s != EWS_ENOMEM) return;
+    if (cudaPeekAtLastError() == cudaErrorMemoryAllocation) (void)cudaGetLastError();
+    const double lim = ews_memory_limit();
+    if (lim >= 0) {
+        const size_t n = strlen(g_err);
+        snprintf(g_err + n, sizeof(g_err) - n, " [libews memory limit %.0f bytes, %.0f in use]",
+                 lim, ews_memory_in_use());
+    }
+}
+
 ews_status fail(ews_status s, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
-    // A failed device allocation leaves its (non-sticky) error for
-    // cudaGetLastError; take it here so that a later call's error check
-    // does not report it as its own.
-    if (s == EWS_ENOMEM) (void)cudaGetLastError();
+    enomem_tail(s);
     return s;
 }
 
@@ -57,7 +70,7 @@ ews_status report(ews_status s, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
-    if (s == EWS_ENOMEM) (void)cudaGetLastError();     // as in fail()
+    enomem_tail(s);                                    // as in fail()
     return s;
 }
 }  // namespace ews
@@ -216,7 +229,7 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
     }
     if (!s->medium) {                          // released while a coarse grid was in use
         s->model_set = false;
-        CK(cudaMalloc(&s->medium, 3 * s->fstride * sizeof(float)));
+        CK(dev_malloc((void**)&s->medium, 3 * s->fstride * sizeof(float)));
         CK(cudaMemsetAsync(s->medium, 0, 3 * s->fstride * sizeof(float), s->stream));
         StencilPlan* np = nullptr;
         CK(stencil_plan_create(s->g, s->F(), s->M(), s->B, s->opt.storage, &np));
@@ -492,10 +505,10 @@ ews_status collect_profile(ews_sim* s) {
 template <typename T>
 ews_status ensure_buf(T** buf, size_t* cap, size_t need, const char* what) {
     if (*buf && *cap >= need) return EWS_OK;
-    cudaFree(*buf);
+    dev_free(*buf);
     *buf = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(buf, need * sizeof(T));
+    cudaError_t e = dev_malloc((void**)buf, need * sizeof(T));
     if (e != cudaSuccess) return fail(EWS_ENOMEM, "%s (%zu bytes): %s", what, need * sizeof(T),
                                       cudaGetErrorString(e));
     *cap = need;
@@ -705,24 +718,38 @@ ews_status sim_adjoint_buffers(ews_sim* s, int nt, int nckpt, int hslots, bool w
     const int nck = nckpt > 0 ? nckpt : 1;
     s->ckpt_storage = ckpt_storage;
     if (ckpt_storage != EWS_STORAGE_F32 && nck > s->ckpt_scale_cap) {
-        cudaFree(s->ckpt_scale);
+        dev_free(s->ckpt_scale);
         s->ckpt_scale = nullptr;
         s->ckpt_scale_cap = 0;
-        cudaError_t e = cudaMalloc(&s->ckpt_scale, (size_t)nck * 9 * sizeof(float));
+        cudaError_t e = dev_malloc((void**)&s->ckpt_scale, (size_t)nck * 9 * sizeof(float));
         if (e != cudaSuccess) return fail(EWS_ENOMEM, "checkpoint scales: %s", cudaGetErrorString(e));
         s->ckpt_scale_cap = nck;
         if (!s->ckpt_amax) {
-            e = cudaMalloc(&s->ckpt_amax, 9 * sizeof(unsigned));
+            e = dev_malloc((void**)&s->ckpt_amax, 9 * sizeof(unsigned));
             if (e != cudaSuccess) return fail(EWS_ENOMEM, "checkpoint maxima: %s", cudaGetErrorString(e));
         }
     }
     if (!s->adj) {
-        cudaError_t e = cudaMalloc(&s->adj, 17 * fs * sizeof(float));
-        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint state: %s", cudaGetErrorString(e));
-        e = cudaMalloc(&s->acc64, 8 * fs * sizeof(double));
-        if (e != cudaSuccess) return fail(EWS_ENOMEM, "adjoint accumulators: %s", cudaGetErrorString(e));
-        e = cudaMalloc(&s->dmisfit, sizeof(double));
-        if (e != cudaSuccess) return fail(EWS_ENOMEM, "misfit: %s", cudaGetErrorString(e));
+        // all three or none: a later call tests s->adj alone
+        const char* what = "adjoint state";
+        cudaError_t e = dev_malloc((void**)&s->adj, 17 * fs * sizeof(float));
+        if (e == cudaSuccess) {
+            what = "adjoint accumulators";
+            e = dev_malloc((void**)&s->acc64, 8 * fs * sizeof(double));
+        }
+        if (e == cudaSuccess) {
+            what = "misfit";
+            e = dev_malloc((void**)&s->dmisfit, sizeof(double));
+        }
+        if (e != cudaSuccess) {
+            dev_free(s->adj);
+            dev_free(s->acc64);
+            dev_free(s->dmisfit);
+            s->adj = nullptr;
+            s->acc64 = nullptr;
+            s->dmisfit = nullptr;
+            return fail(EWS_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+        }
     }
     ews_status st;
     const size_t ck_floats = ckpt_storage == EWS_STORAGE_F32 ? (size_t)nck * 9 * fs
@@ -740,7 +767,10 @@ double sim_history_budget(const ews_sim* s, double share) {
     if (s->hist_budget >= 0) return s->hist_budget;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0.0;
-    return share * ((double)free_b + (double)s->vhist_cap * sizeof(float));
+    const double held = (double)s->vhist_cap * sizeof(float);
+    const double room = dev_headroom();          // under the library's memory limit
+    const double avail = (double)free_b < room ? (double)free_b : room;
+    return share * (avail + held);
 }
 
 ews_status sim_adjoint_plan(ews_sim* s) {
@@ -839,20 +869,20 @@ ews_status ews_create(const ews_grid* grid, const ews_options* opt, ews_sim** ou
         ews_destroy(s);
         return st;
     };
-    e = cudaMalloc(&s->fields, NFIELD * s->fstride * s->es);
+    e = dev_malloc((void**)&s->fields, NFIELD * s->fstride * s->es);
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "wavefields: %s", cudaGetErrorString(e)));
-    e = cudaMalloc(&s->medium, 3 * s->fstride * sizeof(float));
+    e = dev_malloc((void**)&s->medium, 3 * s->fstride * sizeof(float));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "medium: %s", cudaGetErrorString(e)));
     const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
-    e = cudaMalloc(&s->prof, 9 * (size_t)nmax * sizeof(float));
+    e = dev_malloc((void**)&s->prof, 9 * (size_t)nmax * sizeof(float));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "profiles: %s", cudaGetErrorString(e)));
-    e = cudaMalloc(&s->flags, 5 * sizeof(unsigned));
+    e = dev_malloc((void**)&s->flags, 5 * sizeof(unsigned));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "flags: %s", cudaGetErrorString(e)));
-    e = cudaMalloc(&s->err, sizeof(int));
+    e = dev_malloc((void**)&s->err, sizeof(int));
     if (e != cudaSuccess) return cleanup(fail(EWS_ENOMEM, "err: %s", cudaGetErrorString(e)));
     if (o.boundary == EWS_BOUNDARY_CPML) {
         s->psi_floats = 18 * s->fstride;
-        e = cudaMalloc(&s->psi, s->psi_floats * sizeof(float));
+        e = dev_malloc((void**)&s->psi, s->psi_floats * sizeof(float));
         if (e != cudaSuccess)
             return cleanup(fail(EWS_ENOMEM, "C-PML memory: %s", cudaGetErrorString(e)));
         for (int t = 0; t < 18; ++t) s->B.psi[t] = s->psi + t * s->fstride;
@@ -874,28 +904,28 @@ void ews_destroy(ews_sim* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
-    cudaFree(s->fields);
-    cudaFree(s->medium);
-    cudaFree(s->cmed);
-    cudaFree(s->prof);
-    cudaFree(s->flags);
-    cudaFree(s->err);
+    dev_free(s->fields);
+    dev_free(s->medium);
+    dev_free(s->cmed);
+    dev_free(s->prof);
+    dev_free(s->flags);
+    dev_free(s->err);
     stencil_plan_destroy(s->plan);
     stencil_plan_destroy(s->adj_plan);
-    cudaFree(s->psi);
-    cudaFree(s->wavelet);
-    cudaFree(s->rtaps);
-    cudaFree(s->seis_buf);
-    cudaFree(s->adj);
-    cudaFree(s->acc64);
-    cudaFree(s->ckpt);
-    cudaFree(s->ckpt_scale);
-    cudaFree(s->ckpt_amax);
-    cudaFree(s->vhist);
-    cudaFree(s->aux);
-    cudaFree(s->gout);
-    cudaFree(s->dmisfit);
-    cudaFree(s->stage);
+    dev_free(s->psi);
+    dev_free(s->wavelet);
+    dev_free(s->rtaps);
+    dev_free(s->seis_buf);
+    dev_free(s->adj);
+    dev_free(s->acc64);
+    dev_free(s->ckpt);
+    dev_free(s->ckpt_scale);
+    dev_free(s->ckpt_amax);
+    dev_free(s->vhist);
+    dev_free(s->aux);
+    dev_free(s->gout);
+    dev_free(s->dmisfit);
+    dev_free(s->stage);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     for (GraphEntry& ge : s->graphs) cudaGraphExecDestroy(ge.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -929,9 +959,9 @@ ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float*
     const size_t m = (size_t)mx * my * mz;
     s->model_set = false;
     for (int q = 0; q < 3; ++q) s->g.cm[q] = nullptr;
-    cudaFree(s->cmed);
+    dev_free(s->cmed);
     s->cmed = nullptr;
-    CK(cudaMalloc(&s->cmed, 3 * m * sizeof(float)));
+    CK(dev_malloc((void**)&s->cmed, 3 * m * sizeof(float)));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(s->cmed, a, m * sizeof(float), kind, s->stream));
     CK(cudaMemcpyAsync(s->cmed + m, b, m * sizeof(float), kind, s->stream));
@@ -984,7 +1014,7 @@ ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float*
         s->adj_plan = nullptr;
         s->adj_hist = nullptr;
         s->adj_hist_slots = 0;
-        cudaFree(s->medium);
+        dev_free(s->medium);
         s->medium = nullptr;
     }
     return EWS_OK;
@@ -1004,10 +1034,10 @@ ews_status ews_set_source(ews_sim* s, int kind, const double pos[3], const doubl
     for (int n = 0; n < nt; ++n)
         if (!std::isfinite(wavelet[n])) return fail(EWS_ENONFINITE, "wavelet not finite");
     if (nt > s->wavelet_nt) {
-        cudaFree(s->wavelet);
+        dev_free(s->wavelet);
         s->wavelet = nullptr;
         s->wavelet_nt = 0;
-        CK(cudaMalloc(&s->wavelet, nt * sizeof(float)));
+        CK(dev_malloc((void**)&s->wavelet, nt * sizeof(float)));
     }
     CK(cudaMemcpyAsync(s->wavelet, wavelet, nt * sizeof(float), cudaMemcpyHostToDevice,
                        s->stream));
@@ -1057,11 +1087,11 @@ ews_status ews_set_receivers(ews_sim* s, int nrec, const double* pos) {
     std::vector<Tap> taps((size_t)24 * nrec);
     for (int c = 0; c < 3; ++c)
         for (int r = 0; r < nrec; ++r) taps_for(s, VX + c, pos + 3 * r, 1.0, &taps[(size_t)8 * (c * nrec + r)]);
-    cudaFree(s->rtaps);
+    dev_free(s->rtaps);
     s->rtaps = nullptr;
     s->nrec = 0;
     if (nrec > 0) {
-        CK(cudaMalloc(&s->rtaps, taps.size() * sizeof(Tap)));
+        CK(dev_malloc((void**)&s->rtaps, taps.size() * sizeof(Tap)));
         CK(cudaMemcpyAsync(s->rtaps, taps.data(), taps.size() * sizeof(Tap),
                            cudaMemcpyHostToDevice, s->stream));
         CK(cudaStreamSynchronize(s->stream));
@@ -1094,10 +1124,10 @@ ews_status ews_advance(ews_sim* s, int n0, int nsteps, double dt, float* seis, i
         } else {
             size_t need = (size_t)3 * s->nrec * ld;
             if (need > s->seis_cap) {
-                cudaFree(s->seis_buf);
+                dev_free(s->seis_buf);
                 s->seis_buf = nullptr;
                 s->seis_cap = 0;
-                CK(cudaMalloc(&s->seis_buf, need * sizeof(float)));
+                CK(dev_malloc((void**)&s->seis_buf, need * sizeof(float)));
                 s->seis_cap = need;
             }
             dseis = s->seis_buf;
@@ -1223,12 +1253,12 @@ ews_status ews_release_workspace(ews_sim* s) {
     s->adj_hist_slots = 0;
     float** fbufs[] = {&s->adj, &s->ckpt, &s->vhist, &s->aux, &s->gout, &s->stage, &s->seis_buf};
     for (float** b : fbufs) {
-        cudaFree(*b);
+        dev_free(*b);
         *b = nullptr;
     }
-    cudaFree(s->acc64);
+    dev_free(s->acc64);
     s->acc64 = nullptr;
-    cudaFree(s->dmisfit);
+    dev_free(s->dmisfit);
     s->dmisfit = nullptr;
     s->ckpt_cap = s->vhist_cap = s->aux_cap = s->stage_cap = s->seis_cap = 0;
     return EWS_OK;

@@ -112,26 +112,26 @@ extern "C" ews_status ews_fwi_iteration(int nshots, ews_batch_shot* shots, float
     unsigned* d_max = nullptr;
     double* d_mis = nullptr;
     auto cleanup = [&]() {
-        for (float* p : gs) cudaFree(p);
-        for (float* p : seis) cudaFree(p);
-        cudaFree(gt);
-        cudaFree(trial);
-        cudaFree(d_gl);
-        cudaFree(d_max);
-        cudaFree(d_mis);
+        for (float* p : gs) dev_free(p);
+        for (float* p : seis) dev_free(p);
+        dev_free(gt);
+        dev_free(trial);
+        dev_free(d_gl);
+        dev_free(d_max);
+        dev_free(d_mis);
     };
     ews_status result = EWS_OK;
     auto run = [&]() -> ews_status {
-        for (auto& p : gs) FCK(cudaMalloc(&p, n * sizeof(float)));
+        for (auto& p : gs) FCK(dev_malloc((void**)&p, n * sizeof(float)));
         for (int i = 0; i < nshots; ++i) {
             const ews_sim* s = shots[i].sim;
-            FCK(cudaMalloc(&seis[i], sizeof(float) * 3 * std::max(1, s->nrec) * shots[i].nt));
+            FCK(dev_malloc((void**)&seis[i], sizeof(float) * 3 * std::max(1, s->nrec) * shots[i].nt));
         }
-        FCK(cudaMalloc(&gt, 3 * n * sizeof(float)));
-        FCK(cudaMalloc(&trial, 3 * n * sizeof(float)));
-        FCK(cudaMalloc(&d_gl, 3 * nshots * sizeof(float*)));
-        FCK(cudaMalloc(&d_max, 6 * sizeof(unsigned)));
-        FCK(cudaMalloc(&d_mis, sizeof(double)));
+        FCK(dev_malloc((void**)&gt, 3 * n * sizeof(float)));
+        FCK(dev_malloc((void**)&trial, 3 * n * sizeof(float)));
+        FCK(dev_malloc((void**)&d_gl, 3 * nshots * sizeof(float*)));
+        FCK(dev_malloc((void**)&d_max, 6 * sizeof(unsigned)));
+        FCK(dev_malloc((void**)&d_mis, sizeof(double)));
         // misfit and gradient of every shot at the current model, one launch
         std::vector<ews_batch_shot> b(shots, shots + nshots);
         for (int i = 0; i < nshots; ++i) {

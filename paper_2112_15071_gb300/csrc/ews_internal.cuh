@@ -224,6 +224,14 @@ cudaError_t launch_grad_finalize_t(const DevGrid& g, const AdjFields& A, const D
 // Thread-local error message for ews_last_error() (ews_capi.cu).
 ews_status report(ews_status s, const char* fmt, ...);
 
+// Device allocations of the library (ews_mem.cu): counted against the
+// optional process-wide limit of ews_set_memory_limit.  dev_malloc returns
+// cudaErrorMemoryAllocation, without calling CUDA, for a request above the
+// limit; dev_headroom is the room left under it (INFINITY without a limit).
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+double dev_headroom();
+
 // Stencil passes (ews_stencil.cu): TMA tensor maps and launch geometry are
 // built once per simulation (the field and medium addresses never change).
 // Extra operands of the velocity pass when it captures the velocity history

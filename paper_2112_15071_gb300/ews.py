@@ -111,6 +111,9 @@ SIGNATURES = [
     ("ews_batch_tuning_clear", None, []),
     ("ews_fwi_iteration", _I, [_I, C.POINTER(ews_batch_shot), _P, _P, _P, _D, _I, _P, _P, _P,
                                _P]),
+    ("ews_set_memory_limit", _I, [_D]),
+    ("ews_memory_limit", _D, []),
+    ("ews_memory_in_use", _D, []),
     ("ews_cfl_dt", _D, [C.POINTER(ews_grid), _D]),
     ("ews_max_freq", _D, [C.POINTER(ews_grid), _D]),
     ("ews_last_error", C.c_char_p, []),
@@ -171,6 +174,18 @@ def ews_version() -> int:
 def ews_last_error() -> str:
     m = load().ews_last_error()
     return m.decode() if m else ""
+
+
+def ews_set_memory_limit(nbytes: float):
+    _check(load().ews_set_memory_limit(float(nbytes)))
+
+
+def ews_memory_limit() -> float:
+    return load().ews_memory_limit()
+
+
+def ews_memory_in_use() -> float:
+    return load().ews_memory_in_use()
 
 
 def ews_cfl_dt(grid: ews_grid, vmax: float) -> float:

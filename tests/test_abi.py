@@ -186,3 +186,20 @@ def test_batch_validates_on_the_host():
     assert "negative" in ews.ews_last_error()
     assert lib.ews_batch(1, shots, None, None) == ews.EWS_EINVAL
     assert "null simulation" in ews.ews_last_error()
+
+
+def test_memory_limit_calls_are_host_only():
+    """ews_set_memory_limit / ews_memory_limit / ews_memory_in_use touch host
+    state only: without a device nothing is held, a limit can be set and
+    read back, a negative value removes it and NaN is refused."""
+    assert ews.ews_memory_in_use() == 0.0
+    try:
+        ews.ews_set_memory_limit(123456789.0)
+        assert ews.ews_memory_limit() == 123456789.0
+        ews.ews_set_memory_limit(-5.0)
+        assert ews.ews_memory_limit() < 0
+        with pytest.raises(ews.EwsError) as e:
+            ews.ews_set_memory_limit(float("nan"))
+        assert e.value.status == ews.EWS_EINVAL
+    finally:
+        ews.ews_set_memory_limit(-1.0)
