@@ -249,13 +249,16 @@ struct VelExtra {
 struct StencilPlan;
 
 // Tensor maps of one pass (ews_stencil.cu), in the order of its shared-memory
-// slot layout: halo tiles, core tiles, C-PML terms [3 * direction + term],
-// and the velocity-history map of the reverse pass.
-static constexpr int kMapsHalo = 6, kMapsCore = 7;
+// slot layout: halo tiles, core tiles (fields that lie next to each other in
+// the field allocation go through one 4D map over [field][nz][ny][pitch], so
+// one copy brings several tiles), the C-PML memory variables (one 4D map over
+// the 18 arrays: one copy brings the 3 terms of a damped direction), and the
+// velocity-history map of the reverse pass.
+static constexpr int kMapsHalo = 6, kMapsCore = 2;
 struct Maps {
     CUtensorMap halo[kMapsHalo];
     CUtensorMap core[kMapsCore];
-    CUtensorMap psi[9];
+    CUtensorMap psi;      // C-PML memory variables [term][nz][ny][pitch] (4D)
     CUtensorMap hist;     // velocity history [slot * 3 + component][nz][ny][pitch] (4D)
 };
 

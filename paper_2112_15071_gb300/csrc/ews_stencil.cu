@@ -5,9 +5,13 @@
 // adjacent cells of it) and marches through z.  For every z-plane p one
 // thread issues TMA tile loads of all fields the pass reads into one slot of
 // a 4-slot shared-memory ring:
-//   * "halo" boxes of 40 x (TY + 4) cells (x from x0-4, y from y0-2) for
-//     fields whose x or y derivative is taken, so every Eq. 4 tap (+-3/2
-//     around a staggered point) of the tile sits in shared memory;
+//   * halo boxes for fields whose x or y derivative is taken, each only as
+//     wide as its derivatives need, so every Eq. 4 tap (+-3/2 around a
+//     staggered point) of the tile sits in shared memory: 40 x TY cells (x
+//     from x0-4) for x-derivatives only, 32 x (TY + 4) (y from y0-2) for
+//     y-derivatives only, 40 x (TY + 4) for both;
+//   * medium boxes of 40 x (TY + 1) cells (x from x0-4, y from y0): the cell
+//     and its +x / +y neighbours for the staggered means;
 //   * "core" boxes of 32 x TY cells for fields read only at the cell itself.
 // The 9 wavefields are stored as FP32, BF16 or FP16 (the medium always as
 // FP32); arithmetic is FP32.  A 16-bit field f holds s_f times its value, a
@@ -15,6 +19,9 @@
 // multiplied by 1/s_f, updates by dt s_f of the output field.  16-bit halo
 // boxes are 48 cells wide (x from x0-8) so that every copy starts on a
 // 16-byte boundary.
+// With C-PML, the memory variables of the output plane come through a
+// separate two-entry buffer, filled two planes ahead (so their load latency
+// overlaps two planes of work, like the field ring's).
 // TMA writes zeros outside the grid, which is exactly the zero exterior of
 // the wavefields (Sec. 2.2.2 reading), so there are no edge branches.
 // z-derivatives come from per-thread register queues of 4 planes.  Output
@@ -61,10 +68,9 @@ namespace {
 constexpr int TX = 32, TY = EWS_TILE_Y;
 constexpr int HY = TY + 4;                        // halo rows: y0-2 .. y0+TY+1
 constexpr int HXF = TX + 8;                       // FP32 halo box: x0-4 .. x0+TX+3
-constexpr int HALOF = HXF * HY;                   // floats per FP32 halo tile
 constexpr int CORE = TX * TY;                     // elements per core tile
 constexpr int NSLOT = 4;                          // ring depth (planes) = unroll
-constexpr int MAXH = 6, MAXC = 7;
+constexpr int MAXH = 6, MAXC = 2;
 constexpr int ROWS = EWS_ROWS;                    // cells per thread (adjacent y rows)
 constexpr int RY = TY / ROWS;                     // thread rows
 constexpr int NTH = TX * RY;                      // threads per CTA
@@ -94,30 +100,46 @@ template <> struct St<__half> {
     __device__ static __half put(float x) { return __float2half_rn(x); }
 };
 
+constexpr int r128(int b) { return (b + 127) / 128 * 128; }
+
 // Slot layout of one plane, in bytes (every tile 128-byte aligned):
-//   velocity pass: 5 field halo tiles (sxx syy sxy sxz syz), the rho halo
-//   tile, 4 field core tiles (szz vx vy vz);
-//   stress pass: 3 field halo tiles (vx vy vz), the mu halo tile, the
+//   velocity pass: sxx (x halo), syy (y halo), sxy (x and y halo), sxz (x
+//   halo), syz (y halo), the rho medium box, 4 field core tiles (szz vx vy
+//   vz);
+//   stress pass: vx, vy, vz (x and y halo each), the mu medium box, the
 //   lambda core tile, 6 field core tiles.
+// *_TX are the bytes the TMA copies of one plane deliver (the mbarrier's
+// transaction count); the slot offsets round each tile up to 128 bytes.
 template <typename T>
 struct Lay {
-    static constexpr int HX = TX + 2 * St<T>::HO;             // field halo box width
-    static constexpr int HALO = HX * HY;                       // elements per field halo tile
-    static constexpr int HB = HALO * (int)sizeof(T);           // bytes per field halo tile
-    static constexpr int CB = CORE * (int)sizeof(T);           // bytes per field core tile
-    static constexpr int FHB = HALOF * 4, FCB = CORE * 4;      // FP32 halo / core tile bytes
+    static constexpr int ES = (int)sizeof(T);
+    static constexpr int HX = TX + 2 * St<T>::HO;             // field x-halo box width
+    static constexpr int XB = HX * TY * ES;                    // x-halo tile bytes
+    static constexpr int YB = TX * HY * ES;                    // y-halo tile bytes
+    static constexpr int HB = HX * HY * ES;                    // x- and y-halo tile bytes
+    static constexpr int CB = CORE * ES;                       // core tile bytes
+    static constexpr int MB = HXF * (TY + 1) * 4;              // FP32 medium box bytes
+    static constexpr int FCB = CORE * 4;                       // FP32 core tile bytes
+    static constexpr int HBF = HXF * HY * 4;                   // FP32 x- and y-halo tile bytes
     // velocity pass
-    static constexpr int V_RHO = 5 * HB;
-    static constexpr int V_CORE = V_RHO + FHB;
-    static constexpr int V_BYTES = V_CORE + 4 * CB;
+    static constexpr int V_SXX = 0;
+    static constexpr int V_SYY = V_SXX + r128(XB);
+    static constexpr int V_SXY = V_SYY + r128(YB);
+    static constexpr int V_SXZ = V_SXY + r128(HB);
+    static constexpr int V_SYZ = V_SXZ + r128(XB);
+    static constexpr int V_RHO = V_SYZ + r128(YB);
+    static constexpr int V_CORE = V_RHO + r128(MB);
+    static constexpr int V_BYTES = V_CORE + 4 * r128(CB);
+    static constexpr int V_TX = 2 * XB + 2 * YB + HB + MB + 4 * CB;
     // stress pass
-    static constexpr int S_MU = 3 * HB;
-    static constexpr int S_LAM = S_MU + FHB;
-    static constexpr int S_CORE = S_LAM + FCB;
-    static constexpr int S_BYTES = S_CORE + 6 * CB;
-    static constexpr int SLOT = ((V_BYTES > S_BYTES ? V_BYTES : S_BYTES) + 127) / 128 * 128;
-    static_assert(HB % 128 == 0 && CB % 128 == 0 && FHB % 128 == 0 && FCB % 128 == 0,
-                  "TMA destinations must stay 128-byte aligned");
+    static constexpr int S_MU = 3 * r128(HB);
+    static constexpr int S_LAM = S_MU + r128(MB);
+    static constexpr int S_CORE = S_LAM + r128(FCB);
+    static constexpr int S_BYTES = S_CORE + 6 * r128(CB);
+    static constexpr int S_TX = 3 * HB + MB + FCB + 6 * CB;
+    static constexpr int VSLOT = r128(V_BYTES), SSLOT = r128(S_BYTES);
+    static constexpr int SLOT = VSLOT > SSLOT ? VSLOT : SSLOT;
+    static_assert(CB % 128 == 0 && FCB % 128 == 0, "core tiles keep 128-byte alignment");
 };
 
 // Kernel modes of the velocity pass: plain forward; forward that also
@@ -125,29 +147,44 @@ struct Lay {
 // (adjoint) pass that also accumulates the gradient products, for which each
 // slot carries the three velocity-history halo tiles of the same plane.
 enum { M_FWD = 0, M_CAP = 1, M_GRAD = 2 };
+// Velocity-pass slot (the reverse mode adds the three FP32 history tiles).
 template <typename T, int MODE>
-__host__ __device__ constexpr int slot_bytes() {
-    return MODE == M_GRAD ? ((Lay<T>::V_BYTES + 3 * Lay<T>::HB > Lay<T>::SLOT
-                                  ? Lay<T>::V_BYTES + 3 * Lay<T>::HB
-                                  : Lay<T>::SLOT) + 127) / 128 * 128
-                          : Lay<T>::SLOT;
+__host__ __device__ constexpr int vslot_bytes() {
+    return MODE == M_GRAD ? r128(Lay<T>::V_BYTES + 3 * Lay<T>::HBF) : Lay<T>::VSLOT;
 }
 
-// C-PML memory variables of the output plane live in one extra buffer of 9
-// FP32 core tiles (3 terms for each damped direction), refilled for the next
-// output plane as soon as the current one has been consumed.
+// C-PML memory variables: a two-entry buffer of 9 FP32 core tiles each (3
+// terms for each damped direction).  Output plane k uses entry (k - z0) & 1,
+// which is refilled with plane k + 2 as soon as plane k has been consumed.
 constexpr int PSI_BYTES = 9 * CORE * 4;
-template <int BND, typename T, int MODE = M_FWD>
-constexpr size_t smem_bytes() {
-    return (size_t)NSLOT * slot_bytes<T, MODE>() + (BND == BND_CPML ? PSI_BYTES : 0) + 8 * (NSLOT + 1);
+constexpr int NPSI = 2;
+// Dynamic shared memory of a pass kernel: [psi buffer (C-PML only)] [ring of
+// NSLOT plane slots] [barriers].  The psi buffer sits just below the ring.
+__device__ __forceinline__ float* psi_base(unsigned char* ring) {
+    return reinterpret_cast<float*>(ring - NPSI * PSI_BYTES);
 }
-// CTAs per SM that the shared-memory footprint allows; the register budget of
-// the kernels is sized for exactly that many.
+constexpr int NBAR = NSLOT + NPSI;                // ring barriers, then psi-buffer barriers
+template <int BND>
+constexpr size_t tail_bytes() {
+    return (BND == BND_CPML ? (size_t)NPSI * PSI_BYTES : 0) + 8 * NBAR;
+}
 template <int BND, typename T, int MODE = M_FWD>
-constexpr int min_blocks() {
-    return (227 * 1024) / (int)(smem_bytes<BND, T, MODE>() + 1024) < 1   ? 1
-           : (227 * 1024) / (int)(smem_bytes<BND, T, MODE>() + 1024) > 4 ? 4
-                                                                         : (227 * 1024) / (int)(smem_bytes<BND, T, MODE>() + 1024);
+constexpr size_t smem_v() {
+    return (size_t)NSLOT * vslot_bytes<T, MODE>() + tail_bytes<BND>();
+}
+template <int BND, typename T>
+constexpr size_t smem_s() {
+    return (size_t)NSLOT * Lay<T>::SSLOT + tail_bytes<BND>();
+}
+// CTAs per SM that a shared-memory footprint allows (at most 4, and at most
+// 3 for FP32 storage, whose passes need more than 64 registers); the register
+// budget of the kernels is sized for exactly that many.
+template <typename T>
+constexpr int blocks_for(size_t smem) {
+    return (227 * 1024) / (int)(smem + 1024) < 1 ? 1
+           : (227 * 1024) / (int)(smem + 1024) > (sizeof(T) == 4 ? 3 : 4)
+               ? (sizeof(T) == 4 ? 3 : 4)
+               : (227 * 1024) / (int)(smem + 1024);
 }
 
 // --- PTX wrappers -------------------------------------------------------------
@@ -227,52 +264,53 @@ template <typename T, int MODE, bool CM = false>
 __device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, uint64_t* bar,
                                           int x0, int y0, int z, int hslot) {
     using L = Lay<T>;
-    mbar_expect_tx(bar, (uint32_t)(L::V_BYTES + (MODE == M_GRAD ? 3 * L::HB : 0) -
-                                   (CM ? L::FHB : 0)));
-#pragma unroll
-    for (int h = 0; h < 5; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
-    if constexpr (!CM) tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0 - 2, z);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) tma_load_3d(slot + L::V_CORE + c * L::CB, &m.core[c], bar, x0, y0, z);
+    constexpr int HO = St<T>::HO;
+    mbar_expect_tx(bar, (uint32_t)(L::V_TX + (MODE == M_GRAD ? 3 * L::HBF : 0) - (CM ? L::MB : 0)));
+    tma_load_3d(slot + L::V_SXX, &m.halo[0], bar, x0 - HO, y0, z);        // x halo
+    tma_load_3d(slot + L::V_SYY, &m.halo[1], bar, x0, y0 - 2, z);         // y halo
+    tma_load_3d(slot + L::V_SXY, &m.halo[2], bar, x0 - HO, y0 - 2, z);    // x and y halo
+    tma_load_3d(slot + L::V_SXZ, &m.halo[3], bar, x0 - HO, y0, z);        // x halo
+    tma_load_3d(slot + L::V_SYZ, &m.halo[4], bar, x0, y0 - 2, z);         // y halo
+    if constexpr (!CM) tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0, z);
+    tma_load_3d(slot + L::V_CORE, &m.core[0], bar, x0, y0, z);                   // szz
+    tma_load_4d(slot + L::V_CORE + L::CB, &m.core[1], bar, x0, y0, z, VX);      // vx vy vz
     if constexpr (MODE == M_GRAD)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            tma_load_4d(slot + L::V_BYTES + c * L::HB, &m.hist, bar, x0 - St<T>::HO, y0 - 2, z,
+            tma_load_4d(slot + L::V_BYTES + c * L::HBF, &m.hist, bar, x0 - 4, y0 - 2, z,
                         3 * hslot + c);
 }
 template <typename T, bool CM = false>
 __device__ __forceinline__ void issue_str(const Maps& m, unsigned char* slot, uint64_t* bar,
                                           int x0, int y0, int z) {
     using L = Lay<T>;
-    mbar_expect_tx(bar, (uint32_t)(L::S_BYTES - (CM ? L::FHB + L::FCB : 0)));
-#pragma unroll
-    for (int h = 0; h < 3; ++h) tma_load_3d(slot + h * L::HB, &m.halo[h], bar, x0 - St<T>::HO, y0 - 2, z);
+    static_assert(L::HB % 128 == 0, "the three velocity halo tiles are contiguous");
+    mbar_expect_tx(bar, (uint32_t)(L::S_TX - (CM ? L::MB + L::FCB : 0)));
+    tma_load_4d(slot, &m.halo[0], bar, x0 - St<T>::HO, y0 - 2, z, VX);          // vx vy vz
     if constexpr (!CM) {
-        tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0 - 2, z);
+        tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0, z);
         tma_load_3d(slot + L::S_LAM, &m.core[0], bar, x0, y0, z);
     }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) tma_load_3d(slot + L::S_CORE + c * L::CB, &m.core[1 + c], bar, x0, y0, z);
+    tma_load_4d(slot + L::S_CORE, &m.core[1], bar, x0, y0, z, SXX);             // 6 stresses
 }
 
 // Issue the TMA loads of the C-PML memory variables of plane `z` for the
-// damped directions in `dirs` (bit d = direction d) into `buf`.
+// damped directions in `dirs` (bit d = direction d) into `buf`: one copy of
+// the 3 terms of each direction (arrays 6 d + t0 .. 6 d + t0 + 2; t0 = 0 for
+// the velocity pass, 3 for the stress pass).
 __device__ __forceinline__ void issue_psi(const Maps& m, float* buf, uint64_t* bar, int x0, int y0,
-                                          int z, unsigned dirs) {
+                                          int z, unsigned dirs, int t0) {
     mbar_expect_tx(bar, __popc(dirs) * 3 * CORE * (uint32_t)sizeof(float));
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-        if ((dirs >> d) & 1u)
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                tma_load_3d(buf + (3 * d + q) * CORE, &m.psi[3 * d + q], bar, x0, y0, z);
+        if ((dirs >> d) & 1u) tma_load_4d(buf + 3 * d * CORE, &m.psi, bar, x0, y0, z, 6 * d + t0);
 }
 
 __device__ __forceinline__ bool in_slab(int i, int n, int W) { return i < W || i >= n - W; }
 
 __device__ __forceinline__ void ring_init(uint64_t* bars, int tid) {
     if (tid == 0) {
-        for (int s = 0; s <= NSLOT; ++s) mbar_init(&bars[s], 1);   // ring + psi buffer
+        for (int s = 0; s < NBAR; ++s) mbar_init(&bars[s], 1);     // ring + psi buffers
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -280,11 +318,13 @@ __device__ __forceinline__ void ring_init(uint64_t* bars, int tid) {
 }
 
 // Bounded-failure exit: record, wait for the loads still in flight
-// (planes m .. issued - 1 of the chunk), leave.
+// (planes m .. issued - 1 of the chunk, and the psi-buffer entries whose bit
+// is set in psi_pend, each on the phase given by its bit of psi_par), leave.
 __device__ __noinline__ void fail_exit(int* err, int bit, uint64_t* bars, int m, int issued,
-                                       bool psi_pending, uint32_t psi_parity) {
+                                       unsigned psi_pend, unsigned psi_par) {
     atomicOr(err, bit);
-    if (psi_pending && !mbar_wait(&bars[NSLOT], psi_parity)) return;
+    for (int b = 0; b < NPSI; ++b)
+        if (((psi_pend >> b) & 1u) && !mbar_wait(&bars[NSLOT + b], (psi_par >> b) & 1u)) return;
     for (int q = m; q < issued; ++q)
         if (!mbar_wait(&bars[q & (NSLOT - 1)], (uint32_t)((q >> 2) & 1))) return;
 }
@@ -292,7 +332,7 @@ __device__ __noinline__ void fail_exit(int* err, int bit, uint64_t* bars, int m,
 // Per-thread geometry shared by both passes.
 template <int BND, typename T>
 struct Geo {
-    int x0, y0, z0, P4, i, j0, hc, hf, cc, cx, W;
+    int x0, y0, z0, P4, i, j0, hc, hf16, cc, cx, W;
     unsigned tdirs;                                   // tile inside the x / y slabs
     bool own[ROWS], sy[ROWS], sx;
     int cy[ROWS];                                     // medium y+1 offset (clamped) in FP32 tiles
@@ -314,8 +354,8 @@ struct Geo {
         y0 = (t / P.ntx) * TY;
         i = x0 + tx;
         j0 = y0 + ROWS * ty;
-        hc = (ROWS * ty + 2) * Lay<T>::HX + tx + St<T>::HO;   // row 0 cell, field halo tile
-        hf = (ROWS * ty + 2) * HXF + tx + 4;                  // row 0 cell, FP32 halo tile
+        hc = (ROWS * ty + 2) * Lay<T>::HX + tx + St<T>::HO;   // row 0 cell, x- and y-halo tile
+        hf16 = ROWS * ty * HXF + tx + 4;                      // row 0 cell, FP32 medium box
         cc = ROWS * ty * TX + tx;                             // row 0 cell, core tile
         cx = (i + 1 < g.nx) ? 1 : 0;                  // medium clamp at the top edges
         W = P.B.W;
@@ -340,11 +380,56 @@ struct Geo {
             pby[rr] = sy[rr] ? __ldg(P.B.pb[1] + j) : 0.f;
         }
     }
+    // row 0 cell in an x-halo tile (no halo rows) and in a y-halo tile (the
+    // core tile's row stride, two halo rows above)
+    __device__ __forceinline__ int hcx() const { return hc - 2 * Lay<T>::HX; }
+    __device__ __forceinline__ int hcy() const { return cc + 2 * TX; }
+    // row 0 cell in an FP32 medium box (x from x0-4, no halo rows above);
+    // with FP32 fields it is the x-halo tile's offset
+    __device__ __forceinline__ int hf() const { return sizeof(T) == 4 ? hcx() : hf16; }
     // damped directions whose memory variables plane z needs
     __device__ __forceinline__ unsigned dirs(int z, int nz) const {
         return tdirs | ((z >= 0 && z < nz && (z < W || z >= nz - W)) ? 4u : 0u);
     }
 };
+
+// C-PML psi buffer, entry b = (k - z0) & 1 for output plane k.  The first
+// two output planes are fetched up front; after plane k has been consumed by
+// every thread its entry is refilled with plane k + 2 (one thread issues the
+// copies).  psi_pend (bit b): a fill of entry b is in flight (tracked by the
+// issuing thread, for the failure exit); psi_par (bit b): the phase the next
+// wait on entry b expects (toggled by every thread at each consumed fill).
+template <int BND, typename T>
+__device__ __forceinline__ void psi_prologue(const Maps& maps, const Geo<BND, T>& G, float* psib,
+                                             uint64_t* bars, int nz, int t0, unsigned& psi_pend) {
+    const int z1 = G.z0 + G.P4 - 4;
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int b = 0; b < NPSI; ++b) {
+            const int kq = G.z0 + b;
+            const unsigned dn = kq < z1 ? G.dirs(kq, nz) : 0u;
+            if (dn) {
+                issue_psi(maps, psib + b * 9 * CORE, &bars[NSLOT + b], G.x0, G.y0, kq, dn, t0);
+                psi_pend |= 1u << b;
+            }
+        }
+}
+template <int BND, typename T>
+__device__ __forceinline__ void psi_refill(const Maps& maps, const Geo<BND, T>& G, float* psib,
+                                           uint64_t* bars, int b, int k, unsigned kd, int nz, int t0,
+                                           unsigned& psi_pend, unsigned& psi_par) {
+    if (kd) {
+        psi_pend &= ~(1u << b);
+        psi_par ^= 1u << b;
+    }
+    const int kn = k + 2;
+    if (k >= G.z0 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned dn = G.dirs(kn, nz);
+        if (dn) {
+            issue_psi(maps, psib + b * 9 * CORE, &bars[NSLOT + b], G.x0, G.y0, kn, dn, t0);
+            psi_pend |= 1u << b;
+        }
+    }
+}
 
 // psi = b psi + a d; d += psi for the three terms of one damped direction.
 __device__ __forceinline__ void pml_upd(float& p0, float& p1, float& p2, float a, float b,
@@ -395,13 +480,17 @@ struct VelQ {
 
 // One arrival of the z-loop, ring position PH = m mod 4.  Returns false if
 // the CTA must stop (a wait gave up).
-template <int BND, typename T, int MODE, int PH, int FS>
+// RS: slot stride of the ring (0: the pass's own slot size).
+template <int BND, typename T, int MODE, int PH, int FS, int RS>
 __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, VelQ& Q, unsigned char* sm,
-                                         uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
+                                         uint64_t* bars, int m, unsigned& psi_pend,
+                                         unsigned& psi_par, bool& ovf) {
+    float* psib = psi_base(sm);
     using L = Lay<T>;
     constexpr int HX = L::HX;
-    constexpr int SB = slot_bytes<T, MODE>();
+    constexpr int SB = RS ? RS : vslot_bytes<T, MODE>();
+    constexpr int PB = PH & 1;                                     // psi entry of plane k
     const DevGrid& g = P.g;
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
     const int k = G.z0 - 4 + m;                                    // output plane
@@ -431,7 +520,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         }
     }
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
-    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
+    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT + PB], (psi_par >> PB) & 1u) && ok;
     const unsigned char* sl0 = sm + S0 * SB;
     const unsigned char* sl1 = sm + S1 * SB;
     const unsigned char* sl2 = sm + S2 * SB;
@@ -440,24 +529,24 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     for (int rr = 0; rr < ROWS; ++rr) {
         Q.zz[rr][PH] = F((const T*)(sl0 + L::V_CORE + VC_SZZ * L::CB), G.cc + rr * TX);
         if (m > 0) {
-            Q.xz[rr][PH] = F((const T*)(sl1 + VH_SXZ * L::HB), G.hc + rr * HX);
-            Q.yz[rr][PH] = F((const T*)(sl1 + VH_SYZ * L::HB), G.hc + rr * HX);
+            Q.xz[rr][PH] = F((const T*)(sl1 + L::V_SXZ), G.hcx() + rr * HX);
+            Q.yz[rr][PH] = F((const T*)(sl1 + L::V_SYZ), G.hcy() + rr * TX);
         }
         if constexpr (MODE == M_GRAD) {   // history: vx, vy of plane p; vz of plane p - 1
-            Q.hx[rr][PH] = F((const T*)(sl0 + L::V_BYTES + 0 * L::HB), G.hc + rr * HX);
-            Q.hy[rr][PH] = F((const T*)(sl0 + L::V_BYTES + 1 * L::HB), G.hc + rr * HX);
-            if (m > 0) Q.hz[rr][PH] = F((const T*)(sl1 + L::V_BYTES + 2 * L::HB), G.hc + rr * HX);
+            Q.hx[rr][PH] = F((const T*)(sl0 + L::V_BYTES + 0 * L::HBF), G.hc + rr * HX);
+            Q.hy[rr][PH] = F((const T*)(sl0 + L::V_BYTES + 1 * L::HBF), G.hc + rr * HX);
+            if (m > 0) Q.hz[rr][PH] = F((const T*)(sl1 + L::V_BYTES + 2 * L::HBF), G.hc + rr * HX);
         }
     }
     if (out && ok) {
         constexpr int A = (PH + 1) & 3, B = (PH + 2) & 3, C = (PH + 3) & 3, D = PH;  // oldest..newest
-        const T* hxx = (const T*)(sl2 + VH_SXX * L::HB) + G.hc;      // plane k, own cell
-        const T* hyy = (const T*)(sl2 + VH_SYY * L::HB) + G.hc;
-        const T* hxy = (const T*)(sl2 + VH_SXY * L::HB) + G.hc;
-        const T* hxz = (const T*)(sl2 + VH_SXZ * L::HB) + G.hc;
-        const T* hyz = (const T*)(sl2 + VH_SYZ * L::HB) + G.hc;
-        const float* hr = (const float*)(sl2 + L::V_RHO) + G.hf;
-        const float* hr1 = (const float*)(sl1 + L::V_RHO) + G.hf;   // plane k + 1
+        const T* hxx = (const T*)(sl2 + L::V_SXX) + G.hcx();     // plane k, own cell (x halo)
+        const T* hyy = (const T*)(sl2 + L::V_SYY) + G.hcy();     // (y halo)
+        const T* hxy = (const T*)(sl2 + L::V_SXY) + G.hc;      // (x and y halo)
+        const T* hxz = (const T*)(sl2 + L::V_SXZ) + G.hcx();
+        const T* hyz = (const T*)(sl2 + L::V_SYZ) + G.hcy();
+        const float* hr = (const float*)(sl2 + L::V_RHO) + G.hf();
+        const float* hr1 = (const float*)(sl1 + L::V_RHO) + G.hf();   // plane k + 1
         const T* vc = (const T*)(sl2 + L::V_CORE) + G.cc;
         const bool ktop = k + 1 < g.nz;
         constexpr int ZF = FS & 3;                         // z-difference form
@@ -467,7 +556,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
 #pragma unroll
         for (int rr = 0; rr < ROWS; ++rr) {
             if (!G.own[rr]) continue;
-            const int R = rr * HX, RF = rr * HXF;
+            const int R = rr * HX, RY = rr * TX, RF = rr * HXF;
             const float* qxz = Q.xz[rr];
             const float* qyz = Q.yz[rr];
             const float* qzz = Q.zz[rr];
@@ -477,11 +566,11 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             float dxz = zdiff<ZF, false>(g, zw, zt, qxz[A], qxz[B], qxz[C], qxz[D]);
             // vy at (i, j+1/2, k)
             float dyx = g.c1x * (F(hxy, R) - F(hxy, R - 1)) + g.c2x * (F(hxy, R + 1) - F(hxy, R - 2));
-            float dyy = g.c1y * (F(hyy, R + HX) - F(hyy, R)) + g.c2y * (F(hyy, R + 2 * HX) - F(hyy, R - HX));
+            float dyy = g.c1y * (F(hyy, RY + TX) - F(hyy, RY)) + g.c2y * (F(hyy, RY + 2 * TX) - F(hyy, RY - TX));
             float dyz = zdiff<ZF, false>(g, zw, zt, qyz[A], qyz[B], qyz[C], qyz[D]);
             // vz at (i, j, k+1/2)
             float dzx = g.c1x * (F(hxz, R) - F(hxz, R - 1)) + g.c2x * (F(hxz, R + 1) - F(hxz, R - 2));
-            float dzy = g.c1y * (F(hyz, R) - F(hyz, R - HX)) + g.c2y * (F(hyz, R + HX) - F(hyz, R - 2 * HX));
+            float dzy = g.c1y * (F(hyz, RY) - F(hyz, RY - TX)) + g.c2y * (F(hyz, RY + TX) - F(hyz, RY - 2 * TX));
             float dzz = zdiff<ZF, true>(g, zw, zt, qzz[A], qzz[B], qzz[C], qzz[D]);
             if constexpr (kScaled<T>) {     // stored -> physical units
                 dxx *= P.inv[SXX]; dxy *= P.inv[SXY]; dxz *= P.inv[SXZ];
@@ -490,7 +579,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
             }
             if (BND == BND_CPML) {
                 // memory variables of plane k from the psi buffer, updated, stored
-                const float* ps = (const float*)(sm + NSLOT * SB) + G.cc + rr * TX;
+                const float* ps = psib + PB * 9 * CORE + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
@@ -514,9 +603,9 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                 // the cell; the medium enters at the end): strain rates E of
                 // the forward v^{m+1/2} (Eq. 2/3 operators) against u, the
                 // adjoint stress variable before this pass.
-                const T* vhx = (const T*)(sl2 + L::V_BYTES + 0 * L::HB) + G.hc;
-                const T* vhy = (const T*)(sl2 + L::V_BYTES + 1 * L::HB) + G.hc;
-                const T* vhz = (const T*)(sl2 + L::V_BYTES + 2 * L::HB) + G.hc;
+                const T* vhx = (const T*)(sl2 + L::V_BYTES + 0 * L::HBF) + G.hc;
+                const T* vhy = (const T*)(sl2 + L::V_BYTES + 1 * L::HBF) + G.hc;
+                const T* vhz = (const T*)(sl2 + L::V_BYTES + 2 * L::HBF) + G.hc;
                 const float* qhx = Q.hx[rr];
                 const float* qhy = Q.hy[rr];
                 const float* qhz = Q.hz[rr];
@@ -530,14 +619,14 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
                                   g.c1x * (F(vhz, R + 1) - F(vhz, R)) + g.c2x * (F(vhz, R + 2) - F(vhz, R - 1));
                 const float gyz = zdiff<FW, true>(g, zw, zt, qhy[A], qhy[B], qhy[C], qhy[D]) +
                                   g.c1y * (F(vhz, R + HX) - F(vhz, R)) + g.c2y * (F(vhz, R + 2 * HX) - F(vhz, R - HX));
-                const float uxx = F(hxx, R), uyy = F(hyy, R), uzz = F(vc, VC_SZZ * CORE + rr * TX);
+                const float uxx = F(hxx, R), uyy = F(hyy, RY), uzz = F(vc, VC_SZZ * CORE + rr * TX);
                 const float gdt = P.X.gdt;
                 const long long oo = o + rr * g.pitch;
                 P.X.acc[0][oo] = ga[rr][0] + gdt * (exx + eyy + ezz) * (uxx + uyy + uzz);
                 P.X.acc[1][oo] = ga[rr][1] + gdt * (exx * uxx + eyy * uyy + ezz * uzz);
                 P.X.acc[2][oo] = ga[rr][2] + gdt * gxy * F(hxy, R);
                 P.X.acc[3][oo] = ga[rr][3] + gdt * gxz * F(hxz, R);
-                P.X.acc[4][oo] = ga[rr][4] + gdt * gyz * F(hyz, R);
+                P.X.acc[4][oo] = ga[rr][4] + gdt * gyz * F(hyz, RY);
                 if (P.X.vnext) {
                     // buoyancy term of step m + 1: (v^{m+3/2} / G - v^{m+1/2}) times
                     // the adjoint velocity variable before this pass
@@ -598,18 +687,10 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     }
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && threadIdx.y == 0)
-            fail_exit(P.err, 1, bars, m, min(G.P4, max(NSLOT, m + 2)), kd != 0u, psi_n & 1u);
+            fail_exit(P.err, 1, bars, m, min(G.P4, max(NSLOT, m + 2)), psi_pend, psi_par);
         return false;
     }
-    if (BND == BND_CPML) {
-        if (kd) ++psi_n;
-        // the psi buffer is free: fetch the memory variables of the next output plane
-        const int kn = k + 1;
-        if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
-            const unsigned dn = G.dirs(kn, g.nz);
-            if (dn) issue_psi(maps, (float*)(sm + NSLOT * SB), &bars[NSLOT], G.x0, G.y0, kn, dn);
-        }
-    }
+    if (BND == BND_CPML) psi_refill(maps, G, psib, bars, PB, k, kd, g.nz, 0, psi_pend, psi_par);
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
         issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m, P.X.hslot);
@@ -618,14 +699,16 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
 
 // One (tile, z-chunk) of the velocity pass; the ring barriers must be freshly
 // initialised.  Returns false if a wait gave up (the error is recorded).
-template <int BND, typename T, int MODE, int FS = ZS_NONE>
+template <int BND, typename T, int MODE, int FS = ZS_NONE, int RS = 0>
 __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, int item,
                                          unsigned char* sm, uint64_t* bars) {
-    constexpr int SB = slot_bytes<T, MODE>();
+    constexpr int SB = RS ? RS : vslot_bytes<T, MODE>();
     const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
             issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot);
+    unsigned psi_pend = 0, psi_par = 0;            // psi-buffer entries in flight / phases
+    if (BND == BND_CPML) psi_prologue(maps, G, psi_base(sm), bars, P.g.nz, 0, psi_pend);
     VelQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
@@ -636,34 +719,43 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
     Q.ci.lvl = -1;
     Q.ch.lvl = -1;
         }
-    uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!vel_step<BND, T, MODE, 0, FS>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
-        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1, FS>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
-        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2, FS>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
-        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3, FS>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
+        if (!vel_step<BND, T, MODE, 0, FS, RS>(maps, P, G, Q, sm, bars, m, psi_pend, psi_par, ovf)) return false;
+        if (m + 1 < G.P4 && !vel_step<BND, T, MODE, 1, FS, RS>(maps, P, G, Q, sm, bars, m + 1, psi_pend, psi_par, ovf)) return false;
+        if (m + 2 < G.P4 && !vel_step<BND, T, MODE, 2, FS, RS>(maps, P, G, Q, sm, bars, m + 2, psi_pend, psi_par, ovf)) return false;
+        if (m + 3 < G.P4 && !vel_step<BND, T, MODE, 3, FS, RS>(maps, P, G, Q, sm, bars, m + 3, psi_pend, psi_par, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
     return true;
 }
 
-// The coarse-medium forms keep their medium samples in registers: at most 3
-// CTAs per SM (85 registers a thread) for them.
+// CTAs per SM of a pass form.  The coarse-medium forms keep their medium
+// samples in registers (at most 3 CTAs per SM, 85 registers a thread); the
+// reverse form with its fused gradient products needs about 100 (2 per SM).
 template <int BND, typename T, int MODE, int FS>
 constexpr int var_blocks() {
-    return (FS & VAR_COARSE) && min_blocks<BND, T, MODE>() > 3 ? 3 : min_blocks<BND, T, MODE>();
+    return MODE == M_GRAD ? 2
+           : (FS & VAR_COARSE) && blocks_for<T>(smem_v<BND, T, MODE>()) > 3
+               ? 3
+               : blocks_for<T>(smem_v<BND, T, MODE>());
+}
+template <int BND, typename T, int FS>
+constexpr int str_blocks() {
+    return (FS & VAR_COARSE) && blocks_for<T>(smem_s<BND, T>()) > 3 ? 3
+                                                                     : blocks_for<T>(smem_s<BND, T>());
 }
 
 template <int BND, typename T, int MODE, int FS = ZS_NONE>
 __global__ void __launch_bounds__(NTH, (var_blocks<BND, T, MODE, FS>())) k_velocity(
     const __grid_constant__ Maps maps, const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
-    constexpr int SB = slot_bytes<T, MODE>();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB + (BND == BND_CPML ? PSI_BYTES : 0));
+    constexpr int SB = vslot_bytes<T, MODE>();
+    unsigned char* ring = sm + (BND == BND_CPML ? NPSI * PSI_BYTES : 0);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NSLOT * SB);
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    vel_tile<BND, T, MODE, FS>(maps, P, (int)blockIdx.x, sm, bars);
+    vel_tile<BND, T, MODE, FS>(maps, P, (int)blockIdx.x, ring, bars);
 }
 
 // ------------------------------------------------------------------------------
@@ -678,12 +770,17 @@ struct StrQ {
     CoarseZ<2> ch;    // mu at (i+1/2, j), (i, j+1/2); half-integer z
 };
 
-template <int BND, typename T, int PH, int FS>
+template <int BND, typename T, int PH, int FS, int RS>
 __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                                          const Geo<BND, T>& G, StrQ& Q, unsigned char* sm,
-                                         uint64_t* bars, int m, uint32_t& psi_n, bool& ovf) {
+                                         uint64_t* bars, int m, unsigned& psi_pend,
+                                         unsigned& psi_par, bool& ovf) {
+    float* psib = psi_base(sm);
     using L = Lay<T>;
     constexpr int HX = L::HX;
+    constexpr int SB = RS ? RS : L::SSLOT;
+    constexpr int HS = r128(L::HB);                                // halo tile stride
+    constexpr int PB = PH & 1;                                     // psi entry of plane k
     const DevGrid& g = P.g;
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
     const int k = G.z0 - 4 + m;
@@ -693,24 +790,24 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
     const float G3 = (BND == BND_SPONGE && out) ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
     const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
-    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT], psi_n & 1u) && ok;
-    const unsigned char* sl0 = sm + S0 * L::SLOT;
-    const unsigned char* sl1 = sm + S1 * L::SLOT;
-    const unsigned char* sl2 = sm + S2 * L::SLOT;
+    if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT + PB], (psi_par >> PB) & 1u) && ok;
+    const unsigned char* sl0 = sm + S0 * SB;
+    const unsigned char* sl1 = sm + S1 * SB;
+    const unsigned char* sl2 = sm + S2 * SB;
     // push own-column values: vx, vy of plane p, vz of plane p - 1
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr) {
-        Q.vx[rr][PH] = F((const T*)(sl0 + SH_VX * L::HB), G.hc + rr * HX);
-        Q.vy[rr][PH] = F((const T*)(sl0 + SH_VY * L::HB), G.hc + rr * HX);
-        if (m > 0) Q.vz[rr][PH] = F((const T*)(sl1 + SH_VZ * L::HB), G.hc + rr * HX);
+        Q.vx[rr][PH] = F((const T*)(sl0 + SH_VX * HS), G.hc + rr * HX);
+        Q.vy[rr][PH] = F((const T*)(sl0 + SH_VY * HS), G.hc + rr * HX);
+        if (m > 0) Q.vz[rr][PH] = F((const T*)(sl1 + SH_VZ * HS), G.hc + rr * HX);
     }
     if (out && ok) {
         constexpr int A = (PH + 1) & 3, B = (PH + 2) & 3, C = (PH + 3) & 3, D = PH;
-        const T* hvx = (const T*)(sl2 + SH_VX * L::HB) + G.hc;       // plane k, own cell
-        const T* hvy = (const T*)(sl2 + SH_VY * L::HB) + G.hc;
-        const T* hvz = (const T*)(sl2 + SH_VZ * L::HB) + G.hc;
-        const float* hmu = (const float*)(sl2 + L::S_MU) + G.hf;
-        const float* hmu1 = (const float*)((k + 1 < g.nz ? sl1 : sl2) + L::S_MU) + G.hf;   // k + 1
+        const T* hvx = (const T*)(sl2 + SH_VX * HS) + G.hc;       // plane k, own cell
+        const T* hvy = (const T*)(sl2 + SH_VY * HS) + G.hc;
+        const T* hvz = (const T*)(sl2 + SH_VZ * HS) + G.hc;
+        const float* hmu = (const float*)(sl2 + L::S_MU) + G.hf();
+        const float* hmu1 = (const float*)((k + 1 < g.nz ? sl1 : sl2) + L::S_MU) + G.hf();   // k + 1
         const float* lc = (const float*)(sl2 + L::S_LAM) + G.cc;
         const T* cr = (const T*)(sl2 + L::S_CORE) + G.cc;
         const long long o = (long long)k * g.plane + G.obase;
@@ -741,7 +838,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
                 ezz *= P.inv[VZ]; vzx *= P.inv[VZ]; vzy *= P.inv[VZ];
             }
             if (BND == BND_CPML) {
-                const float* ps = (const float*)(sm + NSLOT * L::SLOT) + G.cc + rr * TX;
+                const float* ps = psib + PB * 9 * CORE + G.cc + rr * TX;
                 const long long oo = o + rr * g.pitch;
                 if (G.sx) {
                     float p0 = ps[0 * CORE], p1 = ps[1 * CORE], p2 = ps[2 * CORE];
@@ -831,29 +928,24 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
     }
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && threadIdx.y == 0)
-            fail_exit(P.err, 2, bars, m, min(G.P4, max(NSLOT, m + 2)), kd != 0u, psi_n & 1u);
+            fail_exit(P.err, 2, bars, m, min(G.P4, max(NSLOT, m + 2)), psi_pend, psi_par);
         return false;
     }
-    if (BND == BND_CPML) {
-        if (kd) ++psi_n;
-        const int kn = k + 1;
-        if (m >= 3 && kn < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0) {
-            const unsigned dn = G.dirs(kn, g.nz);
-            if (dn) issue_psi(maps, (float*)(sm + NSLOT * L::SLOT), &bars[NSLOT], G.x0, G.y0, kn, dn);
-        }
-    }
+    if (BND == BND_CPML) psi_refill(maps, G, psib, bars, PB, k, kd, g.nz, 3, psi_pend, psi_par);
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
-        issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + S2 * L::SLOT, &bars[S2], G.x0, G.y0, G.z0 + m);
+        issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m);
     return true;
 }
 
-template <int BND, typename T, int FS = ZS_NONE>
+template <int BND, typename T, int FS = ZS_NONE, int RS = 0>
 __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, int item,
                                          unsigned char* sm, uint64_t* bars) {
     const Geo<BND, T> G(P, item);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int s = 0; s < NSLOT && s < G.P4; ++s)
-            issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + s * Lay<T>::SLOT, &bars[s], G.x0, G.y0, G.z0 - 2 + s);
+            issue_str<T, (FS & VAR_COARSE) != 0>(maps, sm + s * (RS ? RS : Lay<T>::SSLOT), &bars[s], G.x0, G.y0, G.z0 - 2 + s);
+    unsigned psi_pend = 0, psi_par = 0;            // psi-buffer entries in flight / phases
+    if (BND == BND_CPML) psi_prologue(maps, G, psi_base(sm), bars, P.g.nz, 3, psi_pend);
     StrQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
@@ -861,13 +953,12 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
         for (int q = 0; q < 4; ++q) { Q.vx[rr][q] = 0.f; Q.vy[rr][q] = 0.f; Q.vz[rr][q] = 0.f; }
     Q.ci.lvl = -1;
     Q.ch.lvl = -1;
-    uint32_t psi_n = 0;                            // psi-buffer fills consumed
     bool ovf = false;                              // an FP16 value out of range
     for (int m = 0; m < G.P4; m += 4) {
-        if (!str_step<BND, T, 0, FS>(maps, P, G, Q, sm, bars, m, psi_n, ovf)) return false;
-        if (m + 1 < G.P4 && !str_step<BND, T, 1, FS>(maps, P, G, Q, sm, bars, m + 1, psi_n, ovf)) return false;
-        if (m + 2 < G.P4 && !str_step<BND, T, 2, FS>(maps, P, G, Q, sm, bars, m + 2, psi_n, ovf)) return false;
-        if (m + 3 < G.P4 && !str_step<BND, T, 3, FS>(maps, P, G, Q, sm, bars, m + 3, psi_n, ovf)) return false;
+        if (!str_step<BND, T, 0, FS, RS>(maps, P, G, Q, sm, bars, m, psi_pend, psi_par, ovf)) return false;
+        if (m + 1 < G.P4 && !str_step<BND, T, 1, FS, RS>(maps, P, G, Q, sm, bars, m + 1, psi_pend, psi_par, ovf)) return false;
+        if (m + 2 < G.P4 && !str_step<BND, T, 2, FS, RS>(maps, P, G, Q, sm, bars, m + 2, psi_pend, psi_par, ovf)) return false;
+        if (m + 3 < G.P4 && !str_step<BND, T, 3, FS, RS>(maps, P, G, Q, sm, bars, m + 3, psi_pend, psi_par, ovf)) return false;
     }
     if constexpr (kHalf<T>)
         if (__syncthreads_or(ovf) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(P.err, 4);
@@ -875,13 +966,13 @@ __device__ __forceinline__ bool str_tile(const Maps& maps, const PassParams& P, 
 }
 
 template <int BND, typename T, int FS = ZS_NONE>
-__global__ void __launch_bounds__(NTH, (var_blocks<BND, T, M_FWD, FS>())) k_stress(const __grid_constant__ Maps maps,
-                                                                      const PassParams P) {
+__global__ void __launch_bounds__(NTH, (str_blocks<BND, T, FS>())) k_stress(const __grid_constant__ Maps maps,
+                                                                            const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(
-        sm + NSLOT * Lay<T>::SLOT + (BND == BND_CPML ? PSI_BYTES : 0));
+    unsigned char* ring = sm + (BND == BND_CPML ? NPSI * PSI_BYTES : 0);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NSLOT * Lay<T>::SSLOT);
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
-    str_tile<BND, T, FS>(maps, P, (int)blockIdx.x, sm, bars);
+    str_tile<BND, T, FS>(maps, P, (int)blockIdx.x, ring, bars);
 }
 
 // ------------------------------------------------------------------------------
@@ -910,9 +1001,9 @@ __device__ __forceinline__ unsigned ld_relaxed_u(const unsigned* p) {
 __device__ __forceinline__ void ring_rearm(uint64_t* bars, int tid) {
     __syncthreads();
     if (tid == 0) {
-        for (int s = 0; s <= NSLOT; ++s)
+        for (int s = 0; s < NBAR; ++s)
             asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[s])) : "memory");
-        for (int s = 0; s <= NSLOT; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < NBAR; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -953,14 +1044,23 @@ struct ItemBox {
     }
 };
 
+// Ring slot of the batched executor: large enough for every pass it runs.
+template <bool GRAD>
+constexpr int batch_slot() {
+    constexpr int v = GRAD ? vslot_bytes<float, M_GRAD>() : vslot_bytes<float, M_FWD>();
+    return v > Lay<float>::SSLOT ? v : Lay<float>::SSLOT;
+}
+
 template <int BND, bool GRAD, bool FS = false>
 __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
     k_batch(const BatchShot* __restrict__ shots, const BatchEntry* __restrict__ entries,
             int nentries, unsigned* cur, unsigned* taken, unsigned long long* done, int* err,
             unsigned long long wait_ns) {
     extern __shared__ __align__(128) unsigned char sm[];
-    constexpr int SB = GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSLOT * SB + (BND == BND_CPML ? PSI_BYTES : 0));
+    // one ring for every item kind: slots as large as the largest pass's
+    constexpr int SB = batch_slot<GRAD>();
+    unsigned char* ring = sm + (BND == BND_CPML ? NPSI * PSI_BYTES : 0);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NSLOT * SB);
     __shared__ PassParams sP;
     __shared__ int s_e, s_it, s_stop, s_key;
     __shared__ unsigned long long s_fenced[4];   // map sets acquired, bit per shot < 64
@@ -1044,15 +1144,15 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
                 ring_rearm(bars, tid);
                 constexpr int ZF = FS ? ZS_FWD : ZS_NONE, ZA = FS ? ZS_ADJ : ZS_NONE;
                 if (E.kind == BK_VEL)
-                    ok = vel_tile<BND, float, M_FWD, ZF>(B.vf, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_FWD, ZF, SB>(B.vf, sP, it, ring, bars);
                 else if (E.kind == BK_VEL_CAP)
-                    ok = vel_tile<BND, float, M_CAP, ZF>(B.vf, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_CAP, ZF, SB>(B.vf, sP, it, ring, bars);
                 else if (E.kind == BK_STR)
-                    ok = str_tile<BND, float, ZF>(B.sf, sP, it, sm, bars);
+                    ok = str_tile<BND, float, ZF, SB>(B.sf, sP, it, ring, bars);
                 else if (E.kind == BK_STR_ADJ)
-                    ok = str_tile<BND, float, ZA>(B.sa, sP, it, sm, bars);
+                    ok = str_tile<BND, float, ZA, SB>(B.sa, sP, it, ring, bars);
                 else if constexpr (GRAD)
-                    ok = vel_tile<BND, float, M_GRAD, ZA>(B.va, sP, it, sm, bars);
+                    ok = vel_tile<BND, float, M_GRAD, ZA, SB>(B.va, sP, it, ring, bars);
                 if (!ok) break;
                 // Point terms of this step inside the item's cells, after its
                 // stores (the next pass starts only when every item is done):
@@ -1200,6 +1300,23 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
+// Tensor map of nt pitched [nz][ny][pitch] arrays lying tstride bytes apart,
+// as a 4D tensor [array][nz][ny][pitch], with a box of bw x bh x 1 x bt.
+bool encode4(CUtensorMap* map, const DevGrid& g, const void* base, CUtensorMapDataType dt,
+             int esize, long long tstride, int nt, int bw, int bh, int bt) {
+    auto fn = encoder();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)nt};
+    cuuint64_t strides[3] = {(cuuint64_t)g.pitch * esize, (cuuint64_t)g.plane * esize,
+                             (cuuint64_t)tstride};
+    cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)bh, 1, (cuuint32_t)bt};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, dt, 4, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, EWS_L2PROMO,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // Tensor map of one pitched [nz][ny][pitch] array with a box of bw x bh x 1.
 bool encode(CUtensorMap* map, const DevGrid& g, const void* base, CUtensorMapDataType dt,
             int esize, int bw, int bh) {
@@ -1226,23 +1343,23 @@ cudaError_t prepare(K kern, size_t smem, int* blocks_per_sm) {
 template <int BND, typename T>
 cudaError_t occupancy(int* occ) {
     int a = 0, b = 0, c = 0;
-    cudaError_t e = prepare(k_velocity<BND, T, M_FWD>, smem_bytes<BND, T>(), &a);
-    if (e == cudaSuccess) e = prepare(k_stress<BND, T>, smem_bytes<BND, T>(), &b);
+    cudaError_t e = prepare(k_velocity<BND, T, M_FWD>, smem_v<BND, T>(), &a);
+    if (e == cudaSuccess) e = prepare(k_stress<BND, T>, smem_s<BND, T>(), &b);
     // free-surface variants: same slots, occupancy taken from the plain ones
-    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, ZS_FWD>, smem_bytes<BND, T>(), &c);
-    if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_FWD>, smem_bytes<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, ZS_FWD>, smem_v<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_FWD>, smem_s<BND, T>(), &c);
     // coarse-medium variants (the medium tiles' slot space stays unused)
-    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, VAR_COARSE>, smem_bytes<BND, T>(), &c);
-    if (e == cudaSuccess) e = prepare(k_stress<BND, T, VAR_COARSE>, smem_bytes<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, VAR_COARSE>, smem_v<BND, T>(), &c);
+    if (e == cudaSuccess) e = prepare(k_stress<BND, T, VAR_COARSE>, smem_s<BND, T>(), &c);
     if constexpr (std::is_same<T, float>::value) {     // history and reverse modes
-        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP>, smem_bytes<BND, T, M_CAP>(), &c);
-        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP, ZS_FWD>, smem_bytes<BND, T, M_CAP>(), &c);
+        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP>, smem_v<BND, T, M_CAP>(), &c);
+        if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_CAP, ZS_FWD>, smem_v<BND, T, M_CAP>(), &c);
         if constexpr (BND != BND_CPML) {
             if (e == cudaSuccess)
-                e = prepare(k_velocity<BND, T, M_GRAD>, smem_bytes<BND, T, M_GRAD>(), &c);
+                e = prepare(k_velocity<BND, T, M_GRAD>, smem_v<BND, T, M_GRAD>(), &c);
             if (e == cudaSuccess)
-                e = prepare(k_velocity<BND, T, M_GRAD, ZS_ADJ>, smem_bytes<BND, T, M_GRAD>(), &c);
-            if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_ADJ>, smem_bytes<BND, T>(), &c);
+                e = prepare(k_velocity<BND, T, M_GRAD, ZS_ADJ>, smem_v<BND, T, M_GRAD>(), &c);
+            if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_ADJ>, smem_s<BND, T>(), &c);
         }
     }
     *occ = a < b ? a : b;
@@ -1266,26 +1383,34 @@ bool encode_maps(Maps* vm, Maps* smp, const DevGrid& g, const DevFields& F, cons
     constexpr int es = (int)sizeof(T), HX = Lay<T>::HX;
     const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     bool ok = true;
-    // velocity: field halos sxx syy sxy sxz syz, rho halo; cores szz vx vy vz
+    // The 9 fields lie fstride elements apart in one allocation (state
+    // order), so runs of neighbouring fields are one 4D tensor.
+    const long long fsb = (const char*)F.f[1] - (const char*)F.f[0];
+    for (int q = 1; q < NFIELD; ++q)
+        if ((const char*)F.f[q] - (const char*)F.f[0] != q * fsb) return false;
+    // velocity: sxx (x halo), syy (y halo), sxy (x and y), sxz (x), syz (y),
+    // rho medium box; cores szz, then vx vy vz in one copy
     const float* vh[5] = {F.f[SXX], F.f[SYY], F.f[SXY], F.f[SXZ], F.f[SYZ]};
-    const float* vc[4] = {F.f[SZZ], F.f[VX], F.f[VY], F.f[VZ]};
-    for (int h = 0; h < 5; ++h) ok &= encode(&vm->halo[h], g, vh[h], dt, es, HX, HY);
-    ok &= encode(&vm->halo[5], g, M.rho, f32, 4, HXF, HY);
-    for (int c = 0; c < 4; ++c) ok &= encode(&vm->core[c], g, vc[c], dt, es, TX, TY);
-    // stress: field halos vx vy vz, mu halo; lambda core, then the six stress cores
-    const float* sh[3] = {F.f[VX], F.f[VY], F.f[VZ]};
-    const float* sc[6] = {F.f[SXX], F.f[SYY], F.f[SZZ], F.f[SXY], F.f[SXZ], F.f[SYZ]};
-    for (int h = 0; h < 3; ++h) ok &= encode(&smp->halo[h], g, sh[h], dt, es, HX, HY);
-    ok &= encode(&smp->halo[3], g, M.mu, f32, 4, HXF, HY);
+    const int vw[5] = {HX, TX, HX, HX, TX}, vhh[5] = {TY, HY, HY, TY, HY};
+    for (int h = 0; h < 5; ++h) ok &= encode(&vm->halo[h], g, vh[h], dt, es, vw[h], vhh[h]);
+    ok &= encode(&vm->halo[5], g, M.rho, f32, 4, HXF, TY + 1);
+    ok &= encode(&vm->core[0], g, F.f[SZZ], dt, es, TX, TY);
+    ok &= encode4(&vm->core[1], g, F.f[0], dt, es, fsb, NFIELD, TX, TY, 3);
+    // stress: vx vy vz halos in one copy, mu medium box; lambda core, then the
+    // six stress cores in one copy
+    ok &= encode4(&smp->halo[0], g, F.f[0], dt, es, fsb, NFIELD, HX, HY, 3);
+    ok &= encode(&smp->halo[3], g, M.mu, f32, 4, HXF, TY + 1);
     ok &= encode(&smp->core[0], g, M.lam, f32, 4, TX, TY);
-    for (int c = 0; c < 6; ++c) ok &= encode(&smp->core[1 + c], g, sc[c], dt, es, TX, TY);
-    // C-PML memory variables (FP32): psi[6 d + t]; velocity pass t = 0..2, stress 3..5
-    if (B.kind == BND_CPML)
-        for (int d = 0; d < 3; ++d)
-            for (int q = 0; q < 3; ++q) {
-                ok &= encode(&vm->psi[3 * d + q], g, B.psi[6 * d + q], f32, 4, TX, TY);
-                ok &= encode(&smp->psi[3 * d + q], g, B.psi[6 * d + 3 + q], f32, 4, TX, TY);
-            }
+    ok &= encode4(&smp->core[1], g, F.f[0], dt, es, fsb, NFIELD, TX, TY, 6);
+    // C-PML memory variables (FP32, 18 arrays psi[6 d + t], velocity pass t =
+    // 0..2, stress 3..5): one copy per damped direction
+    if (B.kind == BND_CPML) {
+        const long long psb = (const char*)B.psi[1] - (const char*)B.psi[0];
+        for (int t = 1; t < 18; ++t)
+            if ((const char*)B.psi[t] - (const char*)B.psi[0] != t * psb) return false;
+        ok &= encode4(&vm->psi, g, B.psi[0], f32, 4, psb, 18, TX, TY, 3);
+        smp->psi = vm->psi;
+    }
     return ok;
 }
 
@@ -1373,14 +1498,14 @@ void launch_v_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     dim3 blk(TX, RY);
     switch (sp->kind) {
         case BND_SPONGE:
-            k_velocity<BND_SPONGE, T, MODE, FS><<<sp->grid, blk, smem_bytes<BND_SPONGE, T, MODE>(), st>>>(sp->vmaps, P);
+            k_velocity<BND_SPONGE, T, MODE, FS><<<sp->grid, blk, smem_v<BND_SPONGE, T, MODE>(), st>>>(sp->vmaps, P);
             break;
         case BND_CPML:
             if constexpr (MODE != M_GRAD)
-                k_velocity<BND_CPML, T, MODE, FS><<<sp->grid, blk, smem_bytes<BND_CPML, T, MODE>(), st>>>(sp->vmaps, P);
+                k_velocity<BND_CPML, T, MODE, FS><<<sp->grid, blk, smem_v<BND_CPML, T, MODE>(), st>>>(sp->vmaps, P);
             break;
         default:
-            k_velocity<BND_NONE, T, MODE, FS><<<sp->grid, blk, smem_bytes<BND_NONE, T, MODE>(), st>>>(sp->vmaps, P);
+            k_velocity<BND_NONE, T, MODE, FS><<<sp->grid, blk, smem_v<BND_NONE, T, MODE>(), st>>>(sp->vmaps, P);
             break;
     }
 }
@@ -1405,13 +1530,13 @@ void launch_s_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
     dim3 blk(TX, RY);
     switch (sp->kind) {
         case BND_SPONGE:
-            k_stress<BND_SPONGE, T, FS><<<sp->grid, blk, smem_bytes<BND_SPONGE, T>(), st>>>(sp->smaps, P);
+            k_stress<BND_SPONGE, T, FS><<<sp->grid, blk, smem_s<BND_SPONGE, T>(), st>>>(sp->smaps, P);
             break;
         case BND_CPML:
-            k_stress<BND_CPML, T, FS><<<sp->grid, blk, smem_bytes<BND_CPML, T>(), st>>>(sp->smaps, P);
+            k_stress<BND_CPML, T, FS><<<sp->grid, blk, smem_s<BND_CPML, T>(), st>>>(sp->smaps, P);
             break;
         default:
-            k_stress<BND_NONE, T, FS><<<sp->grid, blk, smem_bytes<BND_NONE, T>(), st>>>(sp->smaps, P);
+            k_stress<BND_NONE, T, FS><<<sp->grid, blk, smem_s<BND_NONE, T>(), st>>>(sp->smaps, P);
             break;
     }
 }
@@ -1514,8 +1639,7 @@ cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const flo
 
 template <int BND, bool GRAD>
 constexpr size_t batch_smem() {
-    return (size_t)NSLOT * (GRAD ? slot_bytes<float, M_GRAD>() : slot_bytes<float, M_FWD>()) +
-           (BND == BND_CPML ? PSI_BYTES : 0) + 8 * (NSLOT + 1);
+    return (size_t)NSLOT * batch_slot<GRAD>() + tail_bytes<BND>();
 }
 
 template <int BND, bool GRAD, bool FS>
