@@ -143,14 +143,15 @@ __device__ __forceinline__ void flush_cell(const AdjFields& A, long long o) {
 // occurs mult times among the 4 (top edge clamped): mult / 4 for the
 // arithmetic mean; mult mean^2 / (4 mu_cell^2) for the harmonic mean of the
 // xz / yz points on a free-surface plane (reading of Sec. 2.5).
-__device__ __forceinline__ double shear_d(double mean, double mu_cell, int mult, bool harmonic) {
-    return harmonic ? mult * mean * mean / (4.0 * mu_cell * mu_cell) : 0.25 * mult;
+__device__ __forceinline__ float shear_d(float mean, float mu_cell, int mult, bool harmonic) {
+    if (!harmonic) return 0.25f * mult;
+    const float r = mean / mu_cell;
+    return 0.25f * mult * r * r;
 }
 
 // 4-cell shear mean of mu, harmonic on a free-surface plane.
-__device__ __forceinline__ double shear_mean(double a, double b, double c, double d,
-                                             bool harmonic) {
-    return harmonic ? 4.0 / (1.0 / a + 1.0 / b + 1.0 / c + 1.0 / d) : 0.25 * (a + b + c + d);
+__device__ __forceinline__ float shear_mean(float a, float b, float c, float d, bool harmonic) {
+    return harmonic ? 4.0f / (1.0f / a + 1.0f / b + 1.0f / c + 1.0f / d) : 0.25f * (a + b + c + d);
 }
 
 struct Grad3 {
@@ -164,13 +165,18 @@ struct Grad3 {
 //          over the 4-cell means (each point / its mean times the mean's
 //          derivative, top edge clamped);
 // dJ/drho = -1/2 sum over the 2-cell v points of the cell of acc5..7.
+// The time sums arrive in FP64; the difference acc1 - lambda acc0 / kappa
+// (which can cancel) and the sums over points stay in FP64, while the
+// medium factors (reciprocals, means) are FP32: each carries a relative
+// error of ~1e-7, far below the gradient's FP32 accumulation error, and
+// FP64 division is a long instruction sequence at GB300's low FP64 rate.
 __device__ __forceinline__ Grad3 grad_t_cell(const DevGrid& g, const AdjFields& A,
                                              const DevMedium& M, int i, int j, int k) {
     const long long o = cidx(g, i, j, k);
-    const double lam = __ldg(M.lam + o), mu0 = __ldg(M.mu + o);
-    const double kap = 3.0 * lam + 2.0 * mu0;
+    const float lamf = __ldg(M.lam + o), mu0f = __ldg(M.mu + o);
+    const double rkap = (double)(1.0f / (3.0f * lamf + 2.0f * mu0f));
     const double a0 = A.acc64[0][o];
-    double mu = (A.acc64[1][o] - lam * a0 / kap) / mu0;
+    double mu = (A.acc64[1][o] - (double)lamf * a0 * rkap) * (double)(1.0f / mu0f);
     double rho = 0.0;
     for (int da = -1; da <= 0; ++da)
         for (int db = -1; db <= 0; ++db) {
@@ -179,9 +185,9 @@ __device__ __forceinline__ Grad3 grad_t_cell(const DevGrid& g, const AdjFields& 
                 const int ap = min(a + 1, g.nx - 1), bp = min(b + 1, g.ny - 1);
                 const int mult = (a == i && b == j) + (ap == i && b == j) + (a == i && bp == j) + (ap == i && bp == j);
                 if (mult) {
-                    const double mb = 0.25 * ((double)med(M.mu, g, a, b, k) + med(M.mu, g, ap, b, k) +
+                    const float mb = 0.25f * (med(M.mu, g, a, b, k) + med(M.mu, g, ap, b, k) +
                                               med(M.mu, g, a, bp, k) + med(M.mu, g, ap, bp, k));
-                    mu += 0.25 * mult * A.acc64[2][cidx(g, a, b, k)] / mb;
+                    mu += A.acc64[2][cidx(g, a, b, k)] * (double)(0.25f * mult / mb);
                 }
             }
             a = i + da; b = k + db;
@@ -190,9 +196,9 @@ __device__ __forceinline__ Grad3 grad_t_cell(const DevGrid& g, const AdjFields& 
                 const int mult = (a == i && b == k) + (ap == i && b == k) + (a == i && bp == k) + (ap == i && bp == k);
                 if (mult) {
                     const bool h = b == g.fs - 1;
-                    const double mb = shear_mean(med(M.mu, g, a, j, b), med(M.mu, g, ap, j, b),
-                                                 med(M.mu, g, a, j, bp), med(M.mu, g, ap, j, bp), h);
-                    mu += shear_d(mb, mu0, mult, h) * A.acc64[3][cidx(g, a, j, b)] / mb;
+                    const float mb = shear_mean(med(M.mu, g, a, j, b), med(M.mu, g, ap, j, b),
+                                                med(M.mu, g, a, j, bp), med(M.mu, g, ap, j, bp), h);
+                    mu += A.acc64[3][cidx(g, a, j, b)] * (double)(shear_d(mb, mu0f, mult, h) / mb);
                 }
             }
             a = j + da; b = k + db;
@@ -201,9 +207,9 @@ __device__ __forceinline__ Grad3 grad_t_cell(const DevGrid& g, const AdjFields& 
                 const int mult = (a == j && b == k) + (ap == j && b == k) + (a == j && bp == k) + (ap == j && bp == k);
                 if (mult) {
                     const bool h = b == g.fs - 1;
-                    const double mb = shear_mean(med(M.mu, g, i, a, b), med(M.mu, g, i, ap, b),
-                                                 med(M.mu, g, i, a, bp), med(M.mu, g, i, ap, bp), h);
-                    mu += shear_d(mb, mu0, mult, h) * A.acc64[4][cidx(g, i, a, b)] / mb;
+                    const float mb = shear_mean(med(M.mu, g, i, a, b), med(M.mu, g, i, ap, b),
+                                                med(M.mu, g, i, a, bp), med(M.mu, g, i, ap, bp), h);
+                    mu += A.acc64[4][cidx(g, i, a, b)] * (double)(shear_d(mb, mu0f, mult, h) / mb);
                 }
             }
         }
@@ -215,9 +221,9 @@ __device__ __forceinline__ Grad3 grad_t_cell(const DevGrid& g, const AdjFields& 
             const int n = c == 0 ? g.nx : (c == 1 ? g.ny : g.nz);
             const int self = c == 0 ? i : (c == 1 ? j : k);
             const int mult = (a == self) + (min(a + 1, n - 1) == self);
-            if (mult) rho += -0.5 * mult * A.acc64[5 + c][cidx(g, ii, jj, kk)];
+            if (mult) rho += (-0.5 * mult) * A.acc64[5 + c][cidx(g, ii, jj, kk)];
         }
-    return Grad3{a0 / kap, mu, rho};
+    return Grad3{a0 * rkap, mu, rho};
 }
 
 // Gradients of the input model at cell (i, j, k), dense [nz][ny][nx]

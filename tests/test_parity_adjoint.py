@@ -219,3 +219,45 @@ def test_16bit_checkpoints(ews, orc, storage, cap):
         assert rel(g16[q], want[q]) <= cap + TOL_ORACLE
     with pytest.raises(ews.EwsError):
         sim.set_checkpoint_storage(7)
+
+
+def test_config4_48cube_per_cell_finite_differences(ews, orc):
+    """The adjoint benchmark recipe at 48^3: the FP32 GPU gradient of J at
+    single cells against FP64 central finite differences of the oracle
+    forward, for lambda, mu and rho, on 20 seeded cells per parameter among
+    those whose gradient is at least a tenth of its largest (the stated
+    target: gradients within 1e-3 of finite differences)."""
+    true, start = synth.config4(n=48, nt=300, h=60.0, width=8)
+    obs = orc.run_problem(true).astype(np.float32)
+    lame32 = start.lame()
+    sim = ews.simulation_for(start)
+    sim.set_model_lame(*lame32)
+    _, g = sim.gradient(start.nt, start.dt, obs, ckpt_every=50)
+    m = [a.astype(np.float64) for a in lame32]
+
+    def J(l, mu, r):
+        s = orc.OracleSim(start.nx, start.ny, start.nz, start.spacing)
+        s.set_medium_lame(l, mu, r)
+        s.set_boundary(start.boundary, start.width, start.dt, start.f0)
+        x = s.forward(start.nt, start.dt, start.src_kind, start.src_pos, start.src_comp,
+                      start.wavelet, start.rec_pos)
+        return 0.5 * start.dt * float(np.sum((x - obs) ** 2))
+
+    rng = np.random.default_rng(20)
+    worst = 0.0
+    for q in range(3):
+        gq = g[q].astype(np.float64)
+        big = np.flatnonzero(np.abs(gq) >= 0.1 * np.abs(gq).max())
+        assert big.size >= 20
+        for c in rng.choice(big, size=20, replace=False):
+            cz, cy, cx = np.unravel_index(c, gq.shape)
+            h = 1e-4 * m[q][cz, cy, cx]
+            plus = [a.copy() for a in m]
+            minus = [a.copy() for a in m]
+            plus[q][cz, cy, cx] += h
+            minus[q][cz, cy, cx] -= h
+            fd = (J(*plus) - J(*minus)) / (2 * h)
+            err = abs(fd - gq[cz, cy, cx]) / abs(fd)
+            worst = max(worst, err)
+            assert err <= TOL_FD, (q, (cz, cy, cx), fd, gq[cz, cy, cx])
+    print(f"\nper-cell FD, 60 cells: worst relative error {worst:.2e}")
