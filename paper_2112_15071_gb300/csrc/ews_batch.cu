@@ -148,11 +148,11 @@ ews_status fill_shot(BatchShot& B, ews_sim* s, const ews_batch_shot& in, int zch
     PassParams& Q = B.pa;
     Q = P;
     for (int q = 0; q < NFIELD; ++q) {
-        Q.F.f[q] = s->adj + q * fs;
+        Q.F.f[q] = s->adj + fslot(q) * fs;
         Q.dto[q] = -(float)in.dt;
     }
-    for (int q = 0; q < 3; ++q) B.A.p[q] = s->adj + q * fs;
-    for (int q = 0; q < 6; ++q) B.A.q[q] = s->adj + (3 + q) * fs;
+    for (int q = 0; q < 3; ++q) B.A.p[q] = s->adj + fslot(VX + q) * fs;
+    for (int q = 0; q < 6; ++q) B.A.q[q] = s->adj + fslot(SXX + q) * fs;
     for (int q = 0; q < 8; ++q) {
         B.A.acc[q] = s->adj + (9 + q) * fs;
         B.A.acc64[q] = s->acc64 + q * fs;

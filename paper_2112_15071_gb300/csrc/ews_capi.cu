@@ -578,8 +578,8 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         return st;
     const size_t nseis = (size_t)3 * s->nrec * nt;
     AdjFields A;
-    for (int c = 0; c < 3; ++c) A.p[c] = s->adj + c * fs;
-    for (int c = 0; c < 6; ++c) A.q[c] = s->adj + (3 + c) * fs;
+    for (int c = 0; c < 3; ++c) A.p[c] = s->adj + fslot(VX + c) * fs;
+    for (int c = 0; c < 6; ++c) A.q[c] = s->adj + fslot(SXX + c) * fs;
     for (int c = 0; c < 8; ++c) { A.acc[c] = s->adj + (9 + c) * fs; A.acc64[c] = s->acc64 + c * fs; }
     // forward with checkpoints (and seismograms when a misfit is asked for);
     // the resident segments also write their velocity history
@@ -592,7 +592,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
             return st;
         if (transformed && c >= c_res) {
             if (c == c_res)
-                CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float),
+                CK(cudaMemcpyAsync(s->vhist, s->field(VX), 3 * fs * sizeof(float),
                                    cudaMemcpyDeviceToDevice, s->stream));
             // steps() puts v^{n+1/2} at slot n - n0 + 1 of the buffer it is given
             float* base = s->vhist + (size_t)(n0 - n_res) * 3 * fs;
@@ -615,7 +615,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
         // Reverse sweep in (alpha, tau): the forward passes with -dt on the
         // adjoint fields, gradient products fused into the velocity pass.
         DevFields AF;
-        for (int q = 0; q < NFIELD; ++q) AF.f[q] = s->adj + q * fs;
+        for (int q = 0; q < NFIELD; ++q) AF.f[q] = s->adj + fslot(q) * fs;
         if ((st = sim_adjoint_plan(s)) != EWS_OK) return st;
         float mdt[NFIELD], one[NFIELD];
         for (int q = 0; q < NFIELD; ++q) {
@@ -628,7 +628,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
             const int n0 = c * K, n1 = c == c_res ? nt : n0 + K;
             if (c < c_res) {
                 if ((st = ckpt_load(s, c)) != EWS_OK) return st;
-                CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float),
+                CK(cudaMemcpyAsync(s->vhist, s->field(VX), 3 * fs * sizeof(float),
                                    cudaMemcpyDeviceToDevice, s->stream));
                 if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK)
                     return st;
@@ -654,7 +654,7 @@ ews_status adjoint_core(ews_sim* s, int nt, double dt, int ckpt_every, const flo
     for (int c = transformed ? -1 : nck - 1; c >= 0; --c) {
         const int n0 = c * K, n1 = n0 + K < nt ? n0 + K : nt;
         if ((st = ckpt_load(s, c)) != EWS_OK) return st;
-        CK(cudaMemcpyAsync(s->vhist, s->fields, 3 * fs * sizeof(float), cudaMemcpyDeviceToDevice,
+        CK(cudaMemcpyAsync(s->vhist, s->field(VX), 3 * fs * sizeof(float), cudaMemcpyDeviceToDevice,
                            s->stream));
         if ((st = steps(s, s->src, n0, n1 - n0, dt, nullptr, nt, s->vhist)) != EWS_OK) return st;
         for (int n = n1 - 1; n >= n0; --n) {
@@ -776,7 +776,7 @@ double sim_history_budget(const ews_sim* s, double share) {
 ews_status sim_adjoint_plan(ews_sim* s) {
     const size_t fs = s->fstride;
     DevFields AF;
-    for (int q = 0; q < NFIELD; ++q) AF.f[q] = s->adj + q * fs;
+    for (int q = 0; q < NFIELD; ++q) AF.f[q] = s->adj + fslot(q) * fs;
     if (!s->adj_plan) {
         cudaError_t e = stencil_plan_create(s->g, AF, s->M(), s->B, EWS_STORAGE_F32, &s->adj_plan);
         if (e != cudaSuccess) return fail(EWS_ECUDA, "adjoint stencil plan: %s", cudaGetErrorString(e));

@@ -26,6 +26,19 @@
 namespace ews {
 
 enum { VX, VY, VZ, SXX, SYY, SZZ, SXY, SXZ, SYZ, NFIELD };
+
+// Physical slot fslot(q) of field q (state order above) in a 9-field allocation
+// (wavefields, adjoint fields, the no-allocation scratch): slots 0..8 hold
+// sxx sxz syy syz sxy szz vx vy vz.  Each pass's fields then sit next to
+// each other in the shapes it fetches them in (sxx/sxz with x halos, syy/syz
+// with y halos, szz vx vy vz as core tiles; vx vy vz with x and y halos, the
+// six stresses as core tiles), so one 4D TMA copy brings several tiles.
+// Checkpoints copy the whole allocation, and the velocity history copies
+// slots 6..8 (vx vy vz) as one block.
+__host__ __device__ constexpr int fslot(int q) {
+    return q == VX ? 6 : q == VY ? 7 : q == VZ ? 8 : q == SXX ? 0 : q == SYY ? 2 : q == SZZ ? 5
+         : q == SXY ? 4 : q == SXZ ? 1 : 3;
+}
 enum { BND_NONE = 0, BND_SPONGE = 1, BND_CPML = 2 };
 
 struct DevGrid {
@@ -254,7 +267,7 @@ struct StencilPlan;
 // one copy brings several tiles), the C-PML memory variables (one 4D map over
 // the 18 arrays: one copy brings the 3 terms of a damped direction), and the
 // velocity-history map of the reverse pass.
-static constexpr int kMapsHalo = 6, kMapsCore = 2;
+static constexpr int kMapsHalo = 6, kMapsCore = 1;
 struct Maps {
     CUtensorMap halo[kMapsHalo];
     CUtensorMap core[kMapsCore];

@@ -191,7 +191,7 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
     g.c1z2 = (float)(1.0 / gr.dz);
     g.fs_eps = 0.0f;
     DevFields F;
-    for (int q = 0; q < NFIELD; ++q) F.f[q] = base + kOffFields + q * (size_t)kMaxCells;
+    for (int q = 0; q < NFIELD; ++q) F.f[q] = base + kOffFields + fslot(q) * (size_t)kMaxCells;
     float* mlam = base + kOffMedium;
     float* mmu = mlam + kMaxCells;
     float* mrho = mmu + kMaxCells;
@@ -276,7 +276,7 @@ extern "C" ews_status ews_forward_noalloc(const ews_grid* grid, const ews_option
     }
 
     // ---- state starts at zero; the plan is built in thread-local storage ----
-    NA_CK(cudaMemsetAsync(F.f[0], 0, 9 * (size_t)kMaxCells * sizeof(float), stream));
+    NA_CK(cudaMemsetAsync(base + kOffFields, 0, 9 * (size_t)kMaxCells * sizeof(float), stream));
     NA_CK(cudaMemsetAsync(err, 0, sizeof(int), stream));
     // The plan (tensor maps, launch geometry) only has to live until the
     // launches below have taken their parameters: thread-local host storage.

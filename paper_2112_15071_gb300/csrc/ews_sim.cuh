@@ -109,7 +109,7 @@ struct ews_sim {
     const float* adj_hist = nullptr;      // history buffer the plan's map points at
     int adj_hist_slots = 0;
 
-    void* field(int q) const { return (char*)fields + (size_t)q * fstride * es; }
+    void* field(int q) const { return (char*)fields + (size_t)fslot(q) * fstride * es; }
     DevFields F() const {
         DevFields f;
         for (int q = 0; q < NFIELD; ++q) f.f[q] = (float*)field(q);

@@ -70,7 +70,7 @@ constexpr int HY = TY + 4;                        // halo rows: y0-2 .. y0+TY+1
 constexpr int HXF = TX + 8;                       // FP32 halo box: x0-4 .. x0+TX+3
 constexpr int CORE = TX * TY;                     // elements per core tile
 constexpr int NSLOT = 4;                          // ring depth (planes) = unroll
-constexpr int MAXH = 6, MAXC = 2;
+constexpr int MAXH = 6, MAXC = 1;
 constexpr int ROWS = EWS_ROWS;                    // cells per thread (adjacent y rows)
 constexpr int RY = TY / ROWS;                     // thread rows
 constexpr int NTH = TX * RY;                      // threads per CTA
@@ -102,14 +102,16 @@ template <> struct St<__half> {
 
 constexpr int r128(int b) { return (b + 127) / 128 * 128; }
 
-// Slot layout of one plane, in bytes (every tile 128-byte aligned):
-//   velocity pass: sxx (x halo), syy (y halo), sxy (x and y halo), sxz (x
-//   halo), syz (y halo), the rho medium box, 4 field core tiles (szz vx vy
-//   vz);
-//   stress pass: vx, vy, vz (x and y halo each), the mu medium box, the
-//   lambda core tile, 6 field core tiles.
+// Slot layout of one plane, in bytes, following the copies that fill it
+// (fields in their physical slot order, fslot):
+//   velocity pass: sxx, sxz (x halos, one copy), syy, syz (y halos, one
+//   copy), sxy (x and y halo), the rho medium box, and szz vx vy vz (core
+//   tiles, one copy);
+//   stress pass: vx vy vz (x and y halos, one copy), the lambda and mu medium
+//   boxes (one copy), and the six stress core tiles in slot order (one copy).
 // *_TX are the bytes the TMA copies of one plane deliver (the mbarrier's
-// transaction count); the slot offsets round each tile up to 128 bytes.
+// transaction count).  A copy's tiles lie back to back; each copy starts on
+// a 128-byte boundary.
 template <typename T>
 struct Lay {
     static constexpr int ES = (int)sizeof(T);
@@ -123,23 +125,24 @@ struct Lay {
     static constexpr int HBF = HXF * HY * 4;                   // FP32 x- and y-halo tile bytes
     // velocity pass
     static constexpr int V_SXX = 0;
-    static constexpr int V_SYY = V_SXX + r128(XB);
-    static constexpr int V_SXY = V_SYY + r128(YB);
-    static constexpr int V_SXZ = V_SXY + r128(HB);
-    static constexpr int V_SYZ = V_SXZ + r128(XB);
-    static constexpr int V_RHO = V_SYZ + r128(YB);
-    static constexpr int V_CORE = V_RHO + r128(MB);
-    static constexpr int V_BYTES = V_CORE + 4 * r128(CB);
+    static constexpr int V_SXZ = V_SXX + XB;
+    static constexpr int V_SYY = r128(V_SXZ + XB);
+    static constexpr int V_SYZ = V_SYY + YB;
+    static constexpr int V_SXY = r128(V_SYZ + YB);
+    static constexpr int V_RHO = r128(V_SXY + HB);
+    static constexpr int V_CORE = r128(V_RHO + MB);
+    static constexpr int V_BYTES = V_CORE + 4 * CB;
     static constexpr int V_TX = 2 * XB + 2 * YB + HB + MB + 4 * CB;
     // stress pass
-    static constexpr int S_MU = 3 * r128(HB);
-    static constexpr int S_LAM = S_MU + r128(MB);
-    static constexpr int S_CORE = S_LAM + r128(FCB);
-    static constexpr int S_BYTES = S_CORE + 6 * r128(CB);
+    static constexpr int S_MU = r128(3 * HB);
+    static constexpr int S_LAM = r128(S_MU + MB);
+    static constexpr int S_CORE = S_LAM + FCB;
+    static constexpr int S_BYTES = S_CORE + 6 * CB;
     static constexpr int S_TX = 3 * HB + MB + FCB + 6 * CB;
     static constexpr int VSLOT = r128(V_BYTES), SSLOT = r128(S_BYTES);
     static constexpr int SLOT = VSLOT > SSLOT ? VSLOT : SSLOT;
-    static_assert(CB % 128 == 0 && FCB % 128 == 0, "core tiles keep 128-byte alignment");
+    static_assert(CB % 16 == 0 && XB % 16 == 0 && YB % 16 == 0 && HB % 16 == 0,
+                  "tiles of one copy keep 16-byte alignment");
 };
 
 // Kernel modes of the velocity pass: plain forward; forward that also
@@ -266,32 +269,25 @@ __device__ __forceinline__ void issue_vel(const Maps& m, unsigned char* slot, ui
     using L = Lay<T>;
     constexpr int HO = St<T>::HO;
     mbar_expect_tx(bar, (uint32_t)(L::V_TX + (MODE == M_GRAD ? 3 * L::HBF : 0) - (CM ? L::MB : 0)));
-    tma_load_3d(slot + L::V_SXX, &m.halo[0], bar, x0 - HO, y0, z);        // x halo
-    tma_load_3d(slot + L::V_SYY, &m.halo[1], bar, x0, y0 - 2, z);         // y halo
-    tma_load_3d(slot + L::V_SXY, &m.halo[2], bar, x0 - HO, y0 - 2, z);    // x and y halo
-    tma_load_3d(slot + L::V_SXZ, &m.halo[3], bar, x0 - HO, y0, z);        // x halo
-    tma_load_3d(slot + L::V_SYZ, &m.halo[4], bar, x0, y0 - 2, z);         // y halo
+    tma_load_4d(slot + L::V_SXX, &m.halo[0], bar, x0 - HO, y0, z, fslot(SXX));      // sxx sxz
+    tma_load_4d(slot + L::V_SYY, &m.halo[1], bar, x0, y0 - 2, z, fslot(SYY));       // syy syz
+    tma_load_3d(slot + L::V_SXY, &m.halo[2], bar, x0 - HO, y0 - 2, z);                  // sxy
     if constexpr (!CM) tma_load_3d(slot + L::V_RHO, &m.halo[5], bar, x0 - 4, y0, z);
-    tma_load_3d(slot + L::V_CORE, &m.core[0], bar, x0, y0, z);                   // szz
-    tma_load_4d(slot + L::V_CORE + L::CB, &m.core[1], bar, x0, y0, z, VX);      // vx vy vz
-    if constexpr (MODE == M_GRAD)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            tma_load_4d(slot + L::V_BYTES + c * L::HBF, &m.hist, bar, x0 - 4, y0 - 2, z,
-                        3 * hslot + c);
+    tma_load_4d(slot + L::V_CORE, &m.core[0], bar, x0, y0, z, fslot(SZZ));          // szz vx vy vz
+    if constexpr (MODE == M_GRAD)      // vx vy vz of history slot hslot, one copy
+        tma_load_4d(slot + L::V_BYTES, &m.hist, bar, x0 - 4, y0 - 2, z, 3 * hslot);
 }
 template <typename T, bool CM = false>
 __device__ __forceinline__ void issue_str(const Maps& m, unsigned char* slot, uint64_t* bar,
                                           int x0, int y0, int z) {
     using L = Lay<T>;
-    static_assert(L::HB % 128 == 0, "the three velocity halo tiles are contiguous");
     mbar_expect_tx(bar, (uint32_t)(L::S_TX - (CM ? L::MB + L::FCB : 0)));
-    tma_load_4d(slot, &m.halo[0], bar, x0 - St<T>::HO, y0 - 2, z, VX);          // vx vy vz
+    tma_load_4d(slot, &m.halo[0], bar, x0 - St<T>::HO, y0 - 2, z, fslot(VX));   // vx vy vz
     if constexpr (!CM) {
-        tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0, z);
-        tma_load_3d(slot + L::S_LAM, &m.core[0], bar, x0, y0, z);
+        tma_load_3d(slot + L::S_MU, &m.halo[3], bar, x0 - 4, y0, z);                 // mu
+        tma_load_3d(slot + L::S_LAM, &m.halo[4], bar, x0, y0, z);                    // lambda
     }
-    tma_load_4d(slot + L::S_CORE, &m.core[1], bar, x0, y0, z, SXX);             // 6 stresses
+    tma_load_4d(slot + L::S_CORE, &m.core[0], bar, x0, y0, z, 0);                     // 6 stresses
 }
 
 // Issue the TMA loads of the C-PML memory variables of plane `z` for the
@@ -450,8 +446,12 @@ __device__ __forceinline__ bool over(float x) { return fabsf(x) > 65504.0f; }
 // ------------------------------------------------------------------------------
 // Velocity pass (Eq. 1 + Eq. 4).
 // ------------------------------------------------------------------------------
-enum { VH_SXX, VH_SYY, VH_SXY, VH_SXZ, VH_SYZ };
+// the four core tiles of a velocity-pass slot (physical slots 5..8)
 enum { VC_SZZ, VC_VX, VC_VY, VC_VZ };
+static_assert(fslot(SZZ) == 5 && fslot(VX) == 6 && fslot(VY) == 7 &&
+                  fslot(VZ) == 8 && fslot(SXZ) == fslot(SXX) + 1 &&
+                  fslot(SYZ) == fslot(SYY) + 1,
+              "the copies of the velocity pass follow the physical field order");
 
 // Coarse medium grid: bilinear samples of the medium grid (at the thread's
 // x-y positions) on the two medium planes around the current output plane,
@@ -762,7 +762,11 @@ __global__ void __launch_bounds__(NTH, (var_blocks<BND, T, MODE, FS>())) k_veloc
 // Stress pass (Eq. 2/3 + Eq. 4).
 // ------------------------------------------------------------------------------
 enum { SH_VX, SH_VY, SH_VZ };
-enum { SC_SXX, SC_SYY, SC_SZZ, SC_SXY, SC_SXZ, SC_SYZ };
+// the six stress core tiles of a stress-pass slot, in physical slot order
+enum {
+    SC_SXX = fslot(SXX), SC_SYY = fslot(SYY), SC_SZZ = fslot(SZZ),
+    SC_SXY = fslot(SXY), SC_SXZ = fslot(SXZ), SC_SYZ = fslot(SYZ)
+};
 
 struct StrQ {
     float vx[ROWS][4], vy[ROWS][4], vz[ROWS][4];   // vx/vy k-1..k+2, vz k-2..k+1
@@ -779,7 +783,7 @@ __device__ __forceinline__ bool str_step(const Maps& maps, const PassParams& P,
     using L = Lay<T>;
     constexpr int HX = L::HX;
     constexpr int SB = RS ? RS : L::SSLOT;
-    constexpr int HS = r128(L::HB);                                // halo tile stride
+    constexpr int HS = L::HB;                                      // halo tile stride
     constexpr int PB = PH & 1;                                     // psi entry of plane k
     const DevGrid& g = P.g;
     constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3;   // planes p, p-1, p-2
@@ -1383,25 +1387,31 @@ bool encode_maps(Maps* vm, Maps* smp, const DevGrid& g, const DevFields& F, cons
     constexpr int es = (int)sizeof(T), HX = Lay<T>::HX;
     const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     bool ok = true;
-    // The 9 fields lie fstride elements apart in one allocation (state
-    // order), so runs of neighbouring fields are one 4D tensor.
-    const long long fsb = (const char*)F.f[1] - (const char*)F.f[0];
-    for (int q = 1; q < NFIELD; ++q)
-        if ((const char*)F.f[q] - (const char*)F.f[0] != q * fsb) return false;
-    // velocity: sxx (x halo), syy (y halo), sxy (x and y), sxz (x), syz (y),
-    // rho medium box; cores szz, then vx vy vz in one copy
-    const float* vh[5] = {F.f[SXX], F.f[SYY], F.f[SXY], F.f[SXZ], F.f[SYZ]};
-    const int vw[5] = {HX, TX, HX, HX, TX}, vhh[5] = {TY, HY, HY, TY, HY};
-    for (int h = 0; h < 5; ++h) ok &= encode(&vm->halo[h], g, vh[h], dt, es, vw[h], vhh[h]);
-    ok &= encode(&vm->halo[5], g, M.rho, f32, 4, HXF, TY + 1);
-    ok &= encode(&vm->core[0], g, F.f[SZZ], dt, es, TX, TY);
-    ok &= encode4(&vm->core[1], g, F.f[0], dt, es, fsb, NFIELD, TX, TY, 3);
-    // stress: vx vy vz halos in one copy, mu medium box; lambda core, then the
-    // six stress cores in one copy
-    ok &= encode4(&smp->halo[0], g, F.f[0], dt, es, fsb, NFIELD, HX, HY, 3);
-    ok &= encode(&smp->halo[3], g, M.mu, f32, 4, HXF, TY + 1);
-    ok &= encode(&smp->core[0], g, M.lam, f32, 4, TX, TY);
-    ok &= encode4(&smp->core[1], g, F.f[0], dt, es, fsb, NFIELD, TX, TY, 6);
+    // The 9 fields lie in one allocation, field q in physical slot
+    // fslot(q), slots fsb bytes apart: runs of neighbouring slots are
+    // one 4D tensor [slot][nz][ny][pitch].
+    static_assert(fslot(SXX) == 0 && fslot(SXZ) == 1, "sxx, sxz in slots 0, 1");
+    const char* f0 = (const char*)F.f[SXX];                                    // slot 0
+    const long long fsb = (const char*)F.f[SXZ] - (const char*)F.f[SXX];
+    for (int q = 0; q < NFIELD; ++q)
+        if ((const char*)F.f[q] - f0 != fslot(q) * fsb) return false;
+    // velocity: sxx sxz (x halos), syy syz (y halos), sxy (x and y halo),
+    // rho medium box, szz vx vy vz (cores)
+    ok &= encode4(&vm->halo[0], g, f0, dt, es, fsb, NFIELD, HX, TY, 2);
+    ok &= encode4(&vm->halo[1], g, f0, dt, es, fsb, NFIELD, TX, HY, 2);
+    ok &= encode(&vm->halo[2], g, F.f[SXY], dt, es, HX, HY);
+    ok &= encode4(&vm->core[0], g, f0, dt, es, fsb, NFIELD, TX, TY, 4);
+    // stress: vx vy vz (x and y halos); lambda, mu (medium boxes); the six
+    // stresses (cores)
+    ok &= encode4(&smp->halo[0], g, f0, dt, es, fsb, NFIELD, HX, HY, 3);
+    ok &= encode4(&smp->core[0], g, f0, dt, es, fsb, NFIELD, TX, TY, 6);
+    // medium (without the wavefield-grid medium, i.e. with a coarse medium
+    // grid, these maps are unused): rho and mu boxes, the lambda core
+    if (M.lam) {
+        ok &= encode(&vm->halo[5], g, M.rho, f32, 4, HXF, TY + 1);
+        ok &= encode(&smp->halo[3], g, M.mu, f32, 4, HXF, TY + 1);
+        ok &= encode(&smp->halo[4], g, M.lam, f32, 4, TX, TY);
+    }
     // C-PML memory variables (FP32, 18 arrays psi[6 d + t], velocity pass t =
     // 0..2, stress 3..5): one copy per damped direction
     if (B.kind == BND_CPML) {
@@ -1628,7 +1638,7 @@ cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const flo
                           (cuuint64_t)(3 * nslot)};
     cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4,
                              (cuuint64_t)fstride * 4};
-    cuuint32_t box[4] = {(cuuint32_t)HXF, (cuuint32_t)HY, 1, 1};
+    cuuint32_t box[4] = {(cuuint32_t)HXF, (cuuint32_t)HY, 1, 3};   // the 3 components of a slot
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = fn(&p->vmaps.hist, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(hist),
                     dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
