@@ -783,7 +783,8 @@ ews_status sim_adjoint_plan(ews_sim* s) {
     }
     const int cap_slots = (int)(s->vhist_cap / (3 * fs));
     if (s->adj_hist != s->vhist || s->adj_hist_slots != cap_slots) {
-        CK(stencil_plan_set_history(s->adj_plan, s->g, s->vhist, (long long)fs, cap_slots));
+        CK(stencil_plan_set_history(s->adj_plan, s->g, s->vhist, (long long)fs, cap_slots,
+                                    s->adj + 9 * fs));
         s->adj_hist = s->vhist;
         s->adj_hist_slots = cap_slots;
     }

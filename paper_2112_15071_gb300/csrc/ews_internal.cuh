@@ -272,7 +272,10 @@ struct Maps {
     CUtensorMap halo[kMapsHalo];
     CUtensorMap core[kMapsCore];
     CUtensorMap psi;      // C-PML memory variables [term][nz][ny][pitch] (4D)
-    CUtensorMap hist;     // velocity history [slot * 3 + component][nz][ny][pitch] (4D)
+    CUtensorMap hist;     // velocity history [slot * 3 + component][nz][ny][pitch] (4D),
+                          // x and y halo boxes of the 3 components of a slot
+    CUtensorMap hcore;    // the same history, core boxes of the 3 components
+    CUtensorMap acc;      // the 8 FP32 gradient accumulators [q][nz][ny][pitch] (4D)
 };
 
 // Parameters of one pass launch (or one batched work item).
@@ -406,9 +409,10 @@ cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const 
                                  const DevBoundary& B, const float dto[9], const VelExtra& X,
                                  int* err, cudaStream_t st);
 // History buffer of the reverse pass: nslot slots of 3 fields, slot s field c
-// at hist + (3 s + c) * fstride, pitched like the wavefields.
+// at hist + (3 s + c) * fstride, pitched like the wavefields; and its 8 FP32
+// gradient accumulators, accumulator q at acc + q * fstride.
 cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const float* hist,
-                                     long long fstride, int nslot);
+                                     long long fstride, int nslot, const float* acc);
 
 // Sources, receivers, medium set-up and storage conversion (ews_forward.cu).
 // All run on `st`; `storage` is the EWS_STORAGE_* type of the wavefields.

@@ -62,9 +62,6 @@ namespace {
 #ifndef EWS_WAVES
 #define EWS_WAVES 4            // waves of (tile, z-chunk) CTAs per pass
 #endif
-#ifndef EWS_WAVES_CPML
-#define EWS_WAVES_CPML 8       // C-PML: tiles carry uneven work, finer chunks balance it
-#endif
 constexpr int TX = 32, TY = EWS_TILE_Y;
 constexpr int HY = TY + 4;                        // halo rows: y0-2 .. y0+TY+1
 constexpr int HXF = TX + 8;                       // FP32 halo box: x0-4 .. x0+TX+3
@@ -140,7 +137,6 @@ struct Lay {
     static constexpr int S_BYTES = S_CORE + 6 * CB;
     static constexpr int S_TX = 3 * HB + MB + FCB + 6 * CB;
     static constexpr int VSLOT = r128(V_BYTES), SSLOT = r128(S_BYTES);
-    static constexpr int SLOT = VSLOT > SSLOT ? VSLOT : SSLOT;
     static_assert(CB % 16 == 0 && XB % 16 == 0 && YB % 16 == 0 && HB % 16 == 0,
                   "tiles of one copy keep 16-byte alignment");
 };
@@ -161,23 +157,33 @@ __host__ __device__ constexpr int vslot_bytes() {
 // which is refilled with plane k + 2 as soon as plane k has been consumed.
 constexpr int PSI_BYTES = 9 * CORE * 4;
 constexpr int NPSI = 2;
-// Dynamic shared memory of a pass kernel: [psi buffer (C-PML only)] [ring of
-// NSLOT plane slots] [barriers].  The psi buffer sits just below the ring.
+// The reverse velocity pass reads, at its output cells only, the 8 FP32
+// gradient accumulators and v^{m+3/2} (3 components): a two-entry buffer of
+// 11 FP32 core tiles, used like the psi buffer (entry (k - z0) & 1, refilled
+// with plane k + 2 after plane k).  C-PML has no reverse pass, so the two
+// buffers never coexist and share the place below the ring.
+constexpr int AUX_TILES = 11;
+constexpr int AUX_BYTES = AUX_TILES * CORE * 4;
+// Dynamic shared memory of a pass kernel: [psi buffer (C-PML) or accumulator
+// buffer (reverse velocity pass)] [ring of NSLOT plane slots] [barriers].
 __device__ __forceinline__ float* psi_base(unsigned char* ring) {
     return reinterpret_cast<float*>(ring - NPSI * PSI_BYTES);
 }
-constexpr int NBAR = NSLOT + NPSI;                // ring barriers, then psi-buffer barriers
-template <int BND>
-constexpr size_t tail_bytes() {
-    return (BND == BND_CPML ? (size_t)NPSI * PSI_BYTES : 0) + 8 * NBAR;
+__device__ __forceinline__ float* aux_base(unsigned char* ring) {
+    return reinterpret_cast<float*>(ring - NPSI * AUX_BYTES);
 }
+template <int BND, bool GRAD>
+constexpr size_t pre_bytes() {
+    return BND == BND_CPML ? (size_t)NPSI * PSI_BYTES : GRAD ? (size_t)NPSI * AUX_BYTES : 0;
+}
+constexpr int NBAR = NSLOT + NPSI;                // ring barriers, then psi-buffer barriers
 template <int BND, typename T, int MODE = M_FWD>
 constexpr size_t smem_v() {
-    return (size_t)NSLOT * vslot_bytes<T, MODE>() + tail_bytes<BND>();
+    return pre_bytes<BND, MODE == M_GRAD>() + (size_t)NSLOT * vslot_bytes<T, MODE>() + 8 * NBAR;
 }
 template <int BND, typename T>
 constexpr size_t smem_s() {
-    return (size_t)NSLOT * Lay<T>::SSLOT + tail_bytes<BND>();
+    return pre_bytes<BND, false>() + (size_t)NSLOT * Lay<T>::SSLOT + 8 * NBAR;
 }
 // CTAs per SM that a shared-memory footprint allows (at most 4, and at most
 // 3 for FP32 storage, whose passes need more than 64 registers); the register
@@ -427,6 +433,39 @@ __device__ __forceinline__ void psi_refill(const Maps& maps, const Geo<BND, T>& 
     }
 }
 
+// Accumulator buffer of the reverse velocity pass (entry b for output plane
+// k): the 8 accumulators of plane k and, when the buoyancy term is due,
+// v^{m+3/2} (history slot hslot + 1) there.  Same bookkeeping as the psi
+// buffer (every output plane has a fill).
+template <int BND, typename T>
+__device__ __forceinline__ void aux_issue(const Maps& maps, const Geo<BND, T>& G, float* auxb,
+                                          uint64_t* bars, int b, int kq, const VelExtra& X,
+                                          unsigned& pend) {
+    float* buf = auxb + b * AUX_TILES * CORE;
+    const bool vn = X.vnext != nullptr;
+    mbar_expect_tx(&bars[NSLOT + b], (uint32_t)((vn ? AUX_TILES : 8) * CORE * 4));
+    tma_load_4d(buf, &maps.acc, &bars[NSLOT + b], G.x0, G.y0, kq, 0);
+    if (vn) tma_load_4d(buf + 8 * CORE, &maps.hcore, &bars[NSLOT + b], G.x0, G.y0, kq, 3 * (X.hslot + 1));
+    pend |= 1u << b;
+}
+template <int BND, typename T>
+__device__ __forceinline__ void aux_prologue(const Maps& maps, const Geo<BND, T>& G, float* auxb,
+                                             uint64_t* bars, const VelExtra& X, unsigned& pend) {
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int b = 0; b < NPSI; ++b)
+            if (G.z0 + b < G.z0 + G.P4 - 4) aux_issue(maps, G, auxb, bars, b, G.z0 + b, X, pend);
+}
+template <int BND, typename T>
+__device__ __forceinline__ void aux_refill(const Maps& maps, const Geo<BND, T>& G, float* auxb,
+                                           uint64_t* bars, int b, int k, const VelExtra& X,
+                                           unsigned& pend, unsigned& par) {
+    if (k < G.z0) return;
+    pend &= ~(1u << b);
+    par ^= 1u << b;
+    if (k + 2 < G.z0 + G.P4 - 4 && threadIdx.x == 0 && threadIdx.y == 0)
+        aux_issue(maps, G, auxb, bars, b, k + 2, X, pend);
+}
+
 // psi = b psi + a d; d += psi for the three terms of one damped direction.
 __device__ __forceinline__ void pml_upd(float& p0, float& p1, float& p2, float a, float b,
                                         float& d0, float& d1, float& d2) {
@@ -500,27 +539,22 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
     const float paz = sz ? __ldg(P.B.pa[2] + k) : 0.f, pbz = sz ? __ldg(P.B.pb[2] + k) : 0.f;
     const float G3 = (BND == BND_SPONGE && out) ? G.gx * __ldg(P.B.g[2] + k) : 1.0f;
     const unsigned kd = (BND == BND_CPML && out) ? G.dirs(k, g.nz) : 0u;   // damped dirs of k
-    // M_GRAD: gradient accumulators and v^{m+3/2} of the output cells, loaded
-    // before the wait so their latency overlaps it
-    float ga[ROWS][8], gv[ROWS][3];
-    if constexpr (MODE == M_GRAD) {
-#pragma unroll
-        for (int rr = 0; rr < ROWS; ++rr) {
-            const long long oo = (long long)k * g.plane + G.obase + rr * g.pitch;
-            const bool on = out && G.own[rr];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) ga[rr][q] = on ? P.X.acc[q][oo] : 0.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                ga[rr][5 + c] = (on && P.X.vnext) ? P.X.acc[5 + c][oo] : 0.f;
-                // plain (coherent) load: the batched executor rewrites the
-                // history within one launch
-                gv[rr][c] = (on && P.X.vnext) ? P.X.vnext[c * P.X.fstride + oo] : 0.f;
-            }
-        }
-    }
     bool ok = mbar_wait(&bars[S0], (uint32_t)((m >> 2) & 1));
     if (BND == BND_CPML && kd) ok = mbar_wait(&bars[NSLOT + PB], (psi_par >> PB) & 1u) && ok;
+    // M_GRAD: gradient accumulators and v^{m+3/2} of the output cells, from
+    // the accumulator buffer (fetched two planes ahead)
+    float ga[ROWS][8], gv[ROWS][3];
+    if constexpr (MODE == M_GRAD) {
+        if (out) ok = mbar_wait(&bars[NSLOT + PB], (psi_par >> PB) & 1u) && ok;
+        const float* ax = aux_base(sm) + PB * AUX_TILES * CORE + G.cc;
+#pragma unroll
+        for (int rr = 0; rr < ROWS; ++rr) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) ga[rr][q] = ax[q * CORE + rr * TX];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gv[rr][c] = P.X.vnext ? ax[(8 + c) * CORE + rr * TX] : 0.f;
+        }
+    }
     const unsigned char* sl0 = sm + S0 * SB;
     const unsigned char* sl1 = sm + S1 * SB;
     const unsigned char* sl2 = sm + S2 * SB;
@@ -691,6 +725,7 @@ __device__ __forceinline__ bool vel_step(const Maps& maps, const PassParams& P,
         return false;
     }
     if (BND == BND_CPML) psi_refill(maps, G, psib, bars, PB, k, kd, g.nz, 0, psi_pend, psi_par);
+    if constexpr (MODE == M_GRAD) aux_refill(maps, G, aux_base(sm), bars, PB, k, P.X, psi_pend, psi_par);
     // plane k's slot (S2) is free: refill it with plane z0 - 2 + (m + 2)
     if (m >= 2 && m + 2 < G.P4 && threadIdx.x == 0 && threadIdx.y == 0)
         issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + S2 * SB, &bars[S2], G.x0, G.y0, G.z0 + m, P.X.hslot);
@@ -709,6 +744,7 @@ __device__ __forceinline__ bool vel_tile(const Maps& maps, const PassParams& P, 
             issue_vel<T, MODE, (FS & VAR_COARSE) != 0>(maps, sm + s * SB, &bars[s], G.x0, G.y0, G.z0 - 2 + s, P.X.hslot);
     unsigned psi_pend = 0, psi_par = 0;            // psi-buffer entries in flight / phases
     if (BND == BND_CPML) psi_prologue(maps, G, psi_base(sm), bars, P.g.nz, 0, psi_pend);
+    if constexpr (MODE == M_GRAD) aux_prologue(maps, G, aux_base(sm), bars, P.X, psi_pend);
     VelQ Q;
 #pragma unroll
     for (int rr = 0; rr < ROWS; ++rr)
@@ -752,7 +788,7 @@ __global__ void __launch_bounds__(NTH, (var_blocks<BND, T, MODE, FS>())) k_veloc
     const __grid_constant__ Maps maps, const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int SB = vslot_bytes<T, MODE>();
-    unsigned char* ring = sm + (BND == BND_CPML ? NPSI * PSI_BYTES : 0);
+    unsigned char* ring = sm + pre_bytes<BND, MODE == M_GRAD>();
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NSLOT * SB);
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
     vel_tile<BND, T, MODE, FS>(maps, P, (int)blockIdx.x, ring, bars);
@@ -973,7 +1009,7 @@ template <int BND, typename T, int FS = ZS_NONE>
 __global__ void __launch_bounds__(NTH, (str_blocks<BND, T, FS>())) k_stress(const __grid_constant__ Maps maps,
                                                                             const PassParams P) {
     extern __shared__ __align__(128) unsigned char sm[];
-    unsigned char* ring = sm + (BND == BND_CPML ? NPSI * PSI_BYTES : 0);
+    unsigned char* ring = sm + pre_bytes<BND, false>();
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NSLOT * Lay<T>::SSLOT);
     ring_init(bars, threadIdx.y * TX + threadIdx.x);
     str_tile<BND, T, FS>(maps, P, (int)blockIdx.x, ring, bars);
@@ -1063,7 +1099,7 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
     extern __shared__ __align__(128) unsigned char sm[];
     // one ring for every item kind: slots as large as the largest pass's
     constexpr int SB = batch_slot<GRAD>();
-    unsigned char* ring = sm + (BND == BND_CPML ? NPSI * PSI_BYTES : 0);
+    unsigned char* ring = sm + pre_bytes<BND, GRAD>();
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NSLOT * SB);
     __shared__ PassParams sP;
     __shared__ int s_e, s_it, s_stop, s_key;
@@ -1466,18 +1502,15 @@ cudaError_t plan_build(StencilPlan* p, const DevGrid& g, const DevFields& F, con
     // chunk c of all tiles is resident at once, so neighbouring tiles march
     // through z together and the halo planes one CTA loads are still in L2
     // when its neighbours load them.  Use as many chunks as a few waves of
-    // the resident slots allow (at least 8 planes each).  With C-PML the
-    // slab tiles carry more work, so more, shorter chunks balance the SMs
-    // better (measured on 256^3: 8 waves 3 % faster than 4; without C-PML 4
-    // waves are 4 % faster than 8).  16-bit storage fits 4 CTAs per SM, so
-    // 4 waves already give chunks that short (measured: 8 waves 7 % slower).
+    // the resident slots allow (at least 8 planes each).  4 waves: on
+    // 256^3 C-PML, 3 / 4 / 6 / 8 / 12 waves gave 38.1 / 39.6 / 38.6 / 38.6 /
+    // 37.7 Gcell/s; without C-PML 4 waves were 4 % faster than 8; 16-bit
+    // storage (4 CTAs per SM) 8 waves 7 % slower than 4.
     p->ntx = (g.nx + TX - 1) / TX;
     p->nty = (g.ny + TY - 1) / TY;
     const long long ntile = (long long)p->ntx * p->nty;
     const long long slots = (long long)sms * occ;
-    const long long waves =
-        B.kind == BND_CPML && storage == EWS_STORAGE_F32 ? EWS_WAVES_CPML : EWS_WAVES;
-    long long nchunk = (slots * waves) / ntile;
+    long long nchunk = (slots * EWS_WAVES) / ntile;
     if (nchunk > g.nz / 8) nchunk = g.nz / 8;
     if (nchunk < 1) nchunk = 1;
     p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
@@ -1631,25 +1664,20 @@ cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const 
 }
 
 cudaError_t stencil_plan_set_history(StencilPlan* p, const DevGrid& g, const float* hist,
-                                     long long fstride, int nslot) {
-    auto fn = encoder();
-    if (!fn) return cudaErrorInvalidValue;
-    cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
-                          (cuuint64_t)(3 * nslot)};
-    cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4,
-                             (cuuint64_t)fstride * 4};
-    cuuint32_t box[4] = {(cuuint32_t)HXF, (cuuint32_t)HY, 1, 3};   // the 3 components of a slot
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = fn(&p->vmaps.hist, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(hist),
-                    dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, EWS_L2PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    p->has_hist = r == CUDA_SUCCESS;
+                                     long long fstride, int nslot, const float* acc) {
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const long long fsb = fstride * 4;
+    // history: the 3 components of a slot, x and y halos (strain rates) or
+    // core tiles (v^{m+3/2} of the buoyancy term); accumulators: all 8
+    p->has_hist = encode4(&p->vmaps.hist, g, hist, f32, 4, fsb, 3 * nslot, HXF, HY, 3) &&
+                  encode4(&p->vmaps.hcore, g, hist, f32, 4, fsb, 3 * nslot, TX, TY, 3) &&
+                  encode4(&p->vmaps.acc, g, acc, f32, 4, fsb, 8, TX, TY, 8);
     return p->has_hist ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <int BND, bool GRAD>
 constexpr size_t batch_smem() {
-    return (size_t)NSLOT * batch_slot<GRAD>() + tail_bytes<BND>();
+    return pre_bytes<BND, GRAD>() + (size_t)NSLOT * batch_slot<GRAD>() + 8 * NBAR;
 }
 
 template <int BND, bool GRAD, bool FS>
