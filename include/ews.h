@@ -273,6 +273,45 @@ ews_status ews_set_field_scales(ews_sim* sim, const float* scale);
 /* The scales in use (after a run: the ones that run used). */
 ews_status ews_get_field_scales(ews_sim* sim, float* scale);
 
+/* ---- Tile shape of the forward passes (not in the paper) ----
+ * The velocity and stress passes march tiles of cells through z; the tile
+ * shape that runs fastest depends on the grid, the boundary and the storage
+ * type (on a GB300 at 256^3: 32 x 8 with C-PML, 32 x 4 for FP32 with a
+ * sponge, 32 x 16 for BF16 with a sponge).  Every shape runs the same
+ * arithmetic per cell in the same order (separately compiled, so results
+ * agree to FP32 rounding).  With EWS_TILE_AUTO (the default), ews_run picks the shape for its
+ * grid size, boundary and storage type from a per-process table, filling a
+ * missing entry by timing a few steps with each shape before the run (the
+ * wavefields are reset afterwards); plain forward steps use it (runs with a
+ * free surface or a coarse medium grid, the adjoint's forward part and
+ * batched shots keep 32 x 8). */
+enum { EWS_TILE_AUTO = 0, EWS_TILE_32X8 = 1, EWS_TILE_32X4 = 2, EWS_TILE_32X16 = 3 };
+
+/* Use this shape for later runs (EWS_TILE_AUTO: the tuned one). */
+ews_status ews_set_tile_shape(ews_sim* sim, int shape);
+/* The shape the forward passes of the last run used (EWS_TILE_32X8 ..). */
+int ews_get_tile_shape(ews_sim* sim);
+
+/* Tile-shape table, one entry per grid size, boundary and storage type;
+ * can be exported and imported so that a tuning outlives the process (the
+ * Python binding stores it with the z-chunk table).  Host memory only. */
+typedef struct {
+    int nx, ny, nz;           /* wavefield grid                                      */
+    int boundary;             /* EWS_BOUNDARY_*                                      */
+    int storage;              /* EWS_STORAGE_*                                       */
+    int shape;                /* EWS_TILE_32X8 .. EWS_TILE_32X16                     */
+} ews_tuned_tile;
+
+/* Shape of the table entry for a grid (0 if not tuned yet). */
+int ews_tile_tuned(const ews_grid* grid, int boundary, int storage);
+/* Copy up to cap entries into out; returns the number of entries. */
+int ews_tile_tuning_export(ews_tuned_tile* out, int cap);
+/* Add entries (replacing entries with the same key); any invalid entry gives
+ * EWS_EINVAL and nothing is imported. */
+ews_status ews_tile_tuning_import(const ews_tuned_tile* in, int n);
+/* Empty the table. */
+void ews_tile_tuning_clear(void);
+
 /* Kernel classes for launch counting and timing. */
 enum {
     EWS_KERNEL_VELOCITY = 0,   /* velocity pass, Eq. 1 (+ absorbing edge)      */

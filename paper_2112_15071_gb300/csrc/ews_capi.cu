@@ -4,11 +4,15 @@
 // include/ews.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ews.h"
@@ -60,6 +64,32 @@ constexpr double kC1 = 9.0 / 8.0;
 constexpr double kC2 = -1.0 / 24.0;
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---- tile shapes of the forward passes ----
+// Plain forward steps (no free surface, no coarse medium grid, no history
+// capture) may run the passes of another tile shape; the others use 32 x 8.
+bool tile_eligible(const ews_sim* s) { return s->g.fs == kNoSurface && !s->g.cm[0]; }
+
+void drop_tile_plans(ews_sim* s) {
+    t32x4::stencil_plan_destroy(static_cast<t32x4::StencilPlan*>(s->tplan[EWS_TILE_32X4]));
+    t32x16::stencil_plan_destroy(static_cast<t32x16::StencilPlan*>(s->tplan[EWS_TILE_32X16]));
+    s->tplan[EWS_TILE_32X4] = s->tplan[EWS_TILE_32X16] = nullptr;
+}
+
+ews_status tile_plan(ews_sim* s, int shape) {
+    if (shape == EWS_TILE_32X8 || s->tplan[shape]) return EWS_OK;
+    if (shape == EWS_TILE_32X4) {
+        t32x4::StencilPlan* p = nullptr;
+        CK(t32x4::stencil_plan_create(s->g, s->F(), s->M(), s->B, s->opt.storage, &p));
+        s->tplan[shape] = p;
+    } else {
+        t32x16::StencilPlan* p = nullptr;
+        CK(t32x16::stencil_plan_create(s->g, s->F(), s->M(), s->B, s->opt.storage, &p));
+        s->tplan[shape] = p;
+    }
+    return EWS_OK;
+}
+
 
 }  // namespace
 
@@ -235,6 +265,7 @@ ews_status set_model(ews_sim* s, const float* a, const float* b, const float* rh
         CK(stencil_plan_create(s->g, s->F(), s->M(), s->B, s->opt.storage, &np));
         stencil_plan_destroy(s->plan);
         s->plan = np;
+        drop_tile_plans(s);
         s->gen++;
     }
     DevMedium M = s->M();
@@ -376,8 +407,39 @@ DevSource source_taps(const ews_sim* s, const SourceSpec& src, double dt) {
     return S;
 }
 
+cudaError_t vel_launch(ews_sim* s, int shape, const DevFields& F, const float dto[9],
+                       const float inv[9]) {
+    switch (shape) {
+        case EWS_TILE_32X4:
+            return t32x4::launch_velocity(static_cast<t32x4::StencilPlan*>(s->tplan[shape]), s->g, F,
+                                          s->B, dto, inv, s->err, s->stream);
+        case EWS_TILE_32X16:
+            return t32x16::launch_velocity(static_cast<t32x16::StencilPlan*>(s->tplan[shape]), s->g,
+                                           F, s->B, dto, inv, s->err, s->stream);
+        default:
+            return launch_velocity(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream);
+    }
+}
+
+cudaError_t str_launch(ews_sim* s, int shape, const DevFields& F, const float dto[9],
+                       const float inv[9]) {
+    switch (shape) {
+        case EWS_TILE_32X4:
+            return t32x4::launch_stress(static_cast<t32x4::StencilPlan*>(s->tplan[shape]), s->g, F,
+                                        s->B, dto, inv, s->err, s->stream);
+        case EWS_TILE_32X16:
+            return t32x16::launch_stress(static_cast<t32x16::StencilPlan*>(s->tplan[shape]), s->g,
+                                         F, s->B, dto, inv, s->err, s->stream);
+        default:
+            return launch_stress(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream);
+    }
+}
+
 ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
                         float* dseis, int ld, float* vcap) {
+    const int shape = (!vcap && tile_eligible(s)) ? s->tile_used : EWS_TILE_32X8;
+    ews_status st0 = tile_plan(s, shape);
+    if (st0 != EWS_OK) return st0;
     DevFields F = s->F();
     DevMedium M = s->M();
     const DevSource S = source_taps(s, src, dt);
@@ -398,7 +460,7 @@ ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, d
             X.fstride = (long long)s->fstride;
             CK(launch_velocity_cap(s->plan, s->g, F, s->B, dto, X, s->err, s->stream));
         } else {
-            CK(launch_velocity(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
+            CK(vel_launch(s, shape, F, dto, inv));
         }
         if ((st = mark(s, EWS_KERNEL_VELOCITY)) != EWS_OK) return st;
         if (S.kind == EWS_SOURCE_FORCE) {
@@ -419,7 +481,7 @@ ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, d
             CK(launch_record(s->g, F, s->rtaps, s->nrec, dseis, ld, n, stor, inv, s->err, s->stream));
             if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
         }
-        CK(launch_stress(s->plan, s->g, F, s->B, dto, inv, s->err, s->stream));
+        CK(str_launch(s, shape, F, dto, inv));
         if ((st = mark(s, EWS_KERNEL_STRESS)) != EWS_OK) return st;
         if (fuse) {
             CK(launch_post_stress(s->g, F, M, s->B, S, s->wavelet, s->rtaps, s->nrec, dseis, ld, n,
@@ -448,6 +510,9 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
             hit = &ge;
     if (!hit) {
         if (!s->cap_stream) CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+        // the tile shape's plan exists before the capture starts
+        ews_status sp = tile_plan(s, (!vcap && tile_eligible(s)) ? s->tile_used : EWS_TILE_32X8);
+        if (sp != EWS_OK) return sp;
         long long before[EWS_NKERNEL];
         std::memcpy(before, s->launches, sizeof(before));
         cudaStream_t user = s->stream;
@@ -485,6 +550,97 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
     CK(cudaGraphLaunch(hit->exec, s->stream));
     for (int k = 0; k < EWS_NKERNEL; ++k) s->launches[k] += hit->launches[k];
     s->fresh = false;
+    return EWS_OK;
+}
+
+// ---- tile-shape tuner ----
+// Per process: (nx, ny, nz, boundary, storage) -> EWS_TILE_* shape.
+std::mutex g_tile_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tile;
+
+std::tuple<int, int, int, int, int> tile_key(const ews_sim* s) {
+    return std::make_tuple(s->grid.nx, s->grid.ny, s->grid.nz, s->opt.boundary, s->opt.storage);
+}
+
+void set_tile_used(ews_sim* s, int shape) {
+    if (shape != s->tile_used) {
+        s->tile_used = shape;
+        s->gen++;                               // recapture the time loops
+    }
+}
+
+// Before a run from rest: the requested shape, else the table's entry for
+// this grid, else the fastest of a few timed steps with each shape (taken
+// from rest and thrown away: the caller resets the wavefields afterwards).
+// With per-launch profiling on, an untuned grid keeps 32 x 8 (the trial
+// launches would land in the profile).
+ews_status choose_tile(ews_sim* s, int nt, double dt) {
+    if (!tile_eligible(s)) {
+        set_tile_used(s, EWS_TILE_32X8);
+        return EWS_OK;
+    }
+    if (s->tile_req != EWS_TILE_AUTO) {
+        set_tile_used(s, s->tile_req);
+        return EWS_OK;
+    }
+    const auto key = tile_key(s);
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        auto it = g_tile.find(key);
+        if (it != g_tile.end()) {
+            set_tile_used(s, it->second);
+            return EWS_OK;
+        }
+    }
+    if (s->profiling) {
+        set_tile_used(s, EWS_TILE_32X8);
+        return EWS_OK;
+    }
+    const int T = std::min(nt, 6);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(EWS_ECUDA, "tile tuner: %s", cudaGetErrorString(ce));
+    }
+    int best = EWS_TILE_32X8;
+    float best_ms = 1e30f;
+    ews_status st = EWS_OK;
+    for (int shape : {EWS_TILE_32X8, EWS_TILE_32X4, EWS_TILE_32X16}) {
+        s->tile_used = shape;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && st == EWS_OK; ++rep) {   // the first is a warm-up
+            ce = cudaEventRecord(e0, s->stream);
+            if (ce == cudaSuccess && (st = steps_direct(s, s->src, 0, T, dt, nullptr, T, nullptr)) != EWS_OK)
+                break;
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s->stream);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            if (ce != cudaSuccess) break;
+            if (rep > 0) ms = std::min(ms, t);
+        }
+        if (st != EWS_OK || ce != cudaSuccess) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = shape;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->tile_used = EWS_TILE_32X8;
+    if (st != EWS_OK) return st;
+    if (ce != cudaSuccess) return fail(EWS_ECUDA, "tile tuner: %s", cudaGetErrorString(ce));
+    // the trial steps leave no trace: the error flag (an FP16 trial from
+    // unscaled fields may overflow) is cleared; the wavefields are reset by
+    // the caller
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        g_tile[key] = best;
+    }
+    set_tile_used(s, best);
     return EWS_OK;
 }
 
@@ -797,6 +953,67 @@ extern "C" {
 
 int ews_version(void) { return 100; }
 
+ews_status ews_set_tile_shape(ews_sim* s, int shape) {
+    if (!s) return fail(EWS_EINVAL, "null simulation");
+    if (shape < EWS_TILE_AUTO || shape > EWS_TILE_32X16)
+        return fail(EWS_EINVAL, "unknown tile shape %d", shape);
+    s->tile_req = shape;
+    if (shape != EWS_TILE_AUTO) set_tile_used(s, tile_eligible(s) ? shape : EWS_TILE_32X8);
+    return EWS_OK;
+}
+
+int ews_get_tile_shape(ews_sim* s) { return s ? s->tile_used : 0; }
+
+int ews_tile_tuned(const ews_grid* grid, int boundary, int storage) {
+    if (!grid) return 0;
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary, storage));
+    return it == g_tile.end() ? 0 : it->second;
+}
+
+int ews_tile_tuning_export(ews_tuned_tile* out, int cap) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    int n = 0;
+    for (const auto& kv : g_tile) {
+        if (out && n < cap) {
+            ews_tuned_tile& e = out[n];
+            e.nx = std::get<0>(kv.first);
+            e.ny = std::get<1>(kv.first);
+            e.nz = std::get<2>(kv.first);
+            e.boundary = std::get<3>(kv.first);
+            e.storage = std::get<4>(kv.first);
+            e.shape = kv.second;
+        }
+        ++n;
+    }
+    return n;
+}
+
+ews_status ews_tile_tuning_import(const ews_tuned_tile* in, int n) {
+    if (n < 0 || (n > 0 && !in)) return fail(EWS_EINVAL, "ews_tile_tuning_import: no entries");
+    for (int k = 0; k < n; ++k) {
+        const ews_tuned_tile& e = in[k];
+        if (e.nx < 4 || e.ny < 4 || e.nz < 4 || e.boundary < EWS_BOUNDARY_NONE ||
+            e.boundary > EWS_BOUNDARY_CPML || e.storage < EWS_STORAGE_F32 ||
+            e.storage > EWS_STORAGE_F16 || e.shape < EWS_TILE_32X8 || e.shape > EWS_TILE_32X16)
+            return fail(EWS_EINVAL,
+                        "ews_tile_tuning_import: entry %d (%d x %d x %d, boundary %d, storage %d, "
+                        "shape %d) is invalid; nothing imported",
+                        k, e.nx, e.ny, e.nz, e.boundary, e.storage, e.shape);
+    }
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    for (int k = 0; k < n; ++k) {
+        const ews_tuned_tile& e = in[k];
+        g_tile[std::make_tuple(e.nx, e.ny, e.nz, e.boundary, e.storage)] = e.shape;
+    }
+    return EWS_OK;
+}
+
+void ews_tile_tuning_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tile.clear();
+}
+
 const char* ews_last_error(void) { return g_err; }
 
 double ews_cfl_dt(const ews_grid* g, double vmax) {
@@ -913,6 +1130,7 @@ void ews_destroy(ews_sim* s) {
     dev_free(s->err);
     stencil_plan_destroy(s->plan);
     stencil_plan_destroy(s->adj_plan);
+    drop_tile_plans(s);
     dev_free(s->psi);
     dev_free(s->wavelet);
     dev_free(s->rtaps);
@@ -1015,6 +1233,7 @@ ews_status ews_set_model_coarse(ews_sim* s, int mx, int my, int mz, const float*
         s->adj_plan = nullptr;
         s->adj_hist = nullptr;
         s->adj_hist_slots = 0;
+        drop_tile_plans(s);
         dev_free(s->medium);
         s->medium = nullptr;
     }
@@ -1167,6 +1386,7 @@ ews_status ews_run(ews_sim* s, int nt, double dt, float* seis, int seis_on_devic
     if (s->nrec > 0 && !seis) return fail(EWS_EINVAL, "seis is NULL but receivers are set");
     ews_status st = ensure_ready(s, nt, dt);
     if (st != EWS_OK) return st;
+    if ((st = choose_tile(s, nt, dt)) != EWS_OK) return st;
     if ((st = ews_reset(s)) != EWS_OK) return st;
     const int every = s->opt.snapshot_every;
     const unsigned mask = s->opt.snapshot_mask;

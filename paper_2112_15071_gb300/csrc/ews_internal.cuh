@@ -408,6 +408,28 @@ cudaError_t launch_velocity_cap(const StencilPlan* sp, const DevGrid& g, const D
 cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                                  const DevBoundary& B, const float dto[9], const VelExtra& X,
                                  int* err, cudaStream_t st);
+// The plain forward passes built again with other tile shapes
+// (ews_stencil_t4.cu: 32 x 4 cells; ews_stencil_t16.cu: 32 x 16 cells, two
+// rows per thread), each in its own namespace.  Every cell runs the same
+// arithmetic in the same order as in the 32 x 8 passes (separately
+// compiled, so results agree to FP32 rounding).  No free surface, coarse medium grid or history capture: the
+// callers use these only for plain forward steps.
+#define EWS_SHAPE_DECLS(NS)                                                                  \
+    namespace NS {                                                                           \
+    struct StencilPlan;                                                                      \
+    cudaError_t stencil_plan_create(const DevGrid& g, const DevFields& F, const DevMedium& M, \
+                                    const DevBoundary& B, int storage, StencilPlan** out);   \
+    void stencil_plan_destroy(StencilPlan* p);                                               \
+    cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFields& F, \
+                                const DevBoundary& B, const float dto[9], const float inv[9], \
+                                int* err, cudaStream_t st);                                  \
+    cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,   \
+                              const DevBoundary& B, const float dto[9], const float inv[9],  \
+                              int* err, cudaStream_t st, bool reverse = false);              \
+    }
+EWS_SHAPE_DECLS(t32x4)
+EWS_SHAPE_DECLS(t32x16)
+
 // History buffer of the reverse pass: nslot slots of 3 fields, slot s field c
 // at hist + (3 s + c) * fstride, pitched like the wavefields; and its 8 FP32
 // gradient accumulators, accumulator q at acc + q * fstride.

@@ -76,6 +76,11 @@ struct ews_sim {
     unsigned* flags = nullptr;    // device scratch for medium checks
     int* err = nullptr;           // device flag: bounded waits that gave up
     StencilPlan* plan = nullptr;
+    // tile shape of the forward passes of plain steps (EWS_TILE_*): asked for,
+    // and in use; plans of the other shapes, created on first use
+    int tile_req = EWS_TILE_AUTO;
+    int tile_used = EWS_TILE_32X8;
+    void* tplan[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t stream = nullptr;
     // launch accounting and optional per-launch event timing
     long long launches[EWS_NKERNEL] = {};

@@ -49,7 +49,22 @@
 #define EWS_L2PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_256B
 #endif
 
+// This file is compiled once per tile shape.  The default build (32 x 8
+// tiles) has every pass form, the batched executor and the entry points of
+// ews_internal.cuh; a build with EWS_SHAPE_NS defined (ews_stencil_t4.cu,
+// ews_stencil_t16.cu) holds only the plain forward passes (no free
+// surface, no coarse medium grid, no history capture) with its own tile
+// shape, inside namespace ews::EWS_SHAPE_NS.
+#ifdef EWS_SHAPE_NS
+#define EWS_FULL 0
+#else
+#define EWS_FULL 1
+#endif
+
 namespace ews {
+#ifdef EWS_SHAPE_NS
+namespace EWS_SHAPE_NS {
+#endif
 
 namespace {
 
@@ -1015,6 +1030,7 @@ __global__ void __launch_bounds__(NTH, (str_blocks<BND, T, FS>())) k_stress(cons
     str_tile<BND, T, FS>(maps, P, (int)blockIdx.x, ring, bars);
 }
 
+#if EWS_FULL
 // ------------------------------------------------------------------------------
 // Batched executor: one persistent launch over the work items of many shots
 // (see BatchShot / BatchEntry).  Each CTA claims an item, waits (bounded) for
@@ -1326,6 +1342,7 @@ __global__ void __launch_bounds__(NTH, GRAD ? 2 : 3)
         }
     }
 }
+#endif  // EWS_FULL
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1385,6 +1402,7 @@ cudaError_t occupancy(int* occ) {
     int a = 0, b = 0, c = 0;
     cudaError_t e = prepare(k_velocity<BND, T, M_FWD>, smem_v<BND, T>(), &a);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T>, smem_s<BND, T>(), &b);
+#if EWS_FULL
     // free-surface variants: same slots, occupancy taken from the plain ones
     if (e == cudaSuccess) e = prepare(k_velocity<BND, T, M_FWD, ZS_FWD>, smem_v<BND, T>(), &c);
     if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_FWD>, smem_s<BND, T>(), &c);
@@ -1402,6 +1420,8 @@ cudaError_t occupancy(int* occ) {
             if (e == cudaSuccess) e = prepare(k_stress<BND, T, ZS_ADJ>, smem_s<BND, T>(), &c);
         }
     }
+#endif
+    (void)c;
     *occ = a < b ? a : b;
     return e;
 }
@@ -1557,6 +1577,7 @@ void launch_v_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
 // z-weights, the others the forward ones.
 template <typename T, int MODE = M_FWD>
 void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
+#if EWS_FULL
     if constexpr (MODE == M_FWD)
         if (P.g.cm[0]) return launch_v_fs<T, MODE, VAR_COARSE>(sp, P, st);
     if (P.g.fs != kNoSurface) {
@@ -1565,6 +1586,7 @@ void launch_v(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
         else
             return launch_v_fs<T, MODE, ZS_FWD>(sp, P, st);
     }
+#endif
     launch_v_fs<T, MODE, ZS_NONE>(sp, P, st);
 }
 
@@ -1588,12 +1610,16 @@ void launch_s_fs(const StencilPlan* sp, const PassParams& P, cudaStream_t st) {
 // a free surface; FP32 storage only).
 template <typename T>
 void launch_s(const StencilPlan* sp, const PassParams& P, cudaStream_t st, bool reverse) {
+#if EWS_FULL
     if (P.g.cm[0]) return launch_s_fs<T, VAR_COARSE>(sp, P, st);
     if (P.g.fs != kNoSurface) {
         if constexpr (std::is_same<T, float>::value)
             if (reverse) return launch_s_fs<T, ZS_ADJ>(sp, P, st);
         return launch_s_fs<T, ZS_FWD>(sp, P, st);
     }
+#else
+    (void)reverse;
+#endif
     launch_s_fs<T, ZS_NONE>(sp, P, st);
 }
 
@@ -1640,6 +1666,7 @@ cudaError_t launch_velocity(const StencilPlan* sp, const DevGrid& g, const DevFi
     return cudaGetLastError();
 }
 
+#if EWS_FULL
 cudaError_t launch_velocity_cap(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                                 const DevBoundary& B, const float dto[9], const VelExtra& X,
                                 int* err, cudaStream_t st) {
@@ -1760,6 +1787,7 @@ void stencil_plan_export(const StencilPlan* p, Maps* vmaps, Maps* smaps, int* nt
     *zchunk = p->zchunk;
     *items = p->grid;
 }
+#endif  // EWS_FULL
 
 cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFields& F,
                           const DevBoundary& B, const float dto[9], const float inv[9],
@@ -1773,4 +1801,7 @@ cudaError_t launch_stress(const StencilPlan* sp, const DevGrid& g, const DevFiel
     return cudaGetLastError();
 }
 
+#ifdef EWS_SHAPE_NS
+}  // namespace EWS_SHAPE_NS
+#endif
 }  // namespace ews

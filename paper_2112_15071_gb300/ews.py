@@ -71,7 +71,15 @@ class ews_tuned_zchunk(C.Structure):
                 ("free_surface", C.c_int), ("zchunk", C.c_int)]
 
 
+class ews_tuned_tile(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("boundary", C.c_int),
+                ("storage", C.c_int), ("shape", C.c_int)]
+
+
 EWS_BATCH_PERSISTENT, EWS_BATCH_SEQUENTIAL = 0, 1
+EWS_TILE_AUTO, EWS_TILE_32X8, EWS_TILE_32X4, EWS_TILE_32X16 = 0, 1, 2, 3
+TILE = {"auto": EWS_TILE_AUTO, "32x8": EWS_TILE_32X8, "32x4": EWS_TILE_32X4,
+        "32x16": EWS_TILE_32X16}
 
 _lock = threading.Lock()
 _lib = None
@@ -111,6 +119,12 @@ SIGNATURES = [
     ("ews_batch_tuning_clear", None, []),
     ("ews_fwi_iteration", _I, [_I, C.POINTER(ews_batch_shot), _P, _P, _P, _D, _I, _P, _P, _P,
                                _P]),
+    ("ews_set_tile_shape", _I, [_P, _I]),
+    ("ews_get_tile_shape", _I, [_P]),
+    ("ews_tile_tuned", _I, [C.POINTER(ews_grid), _I, _I]),
+    ("ews_tile_tuning_export", _I, [C.POINTER(ews_tuned_tile), _I]),
+    ("ews_tile_tuning_import", _I, [C.POINTER(ews_tuned_tile), _I]),
+    ("ews_tile_tuning_clear", None, []),
     ("ews_set_memory_limit", _I, [_D]),
     ("ews_memory_limit", _D, []),
     ("ews_memory_in_use", _D, []),
@@ -413,6 +427,54 @@ def ews_batch_tuning_clear() -> None:
     load().ews_batch_tuning_clear()
 
 
+_TILE_NAMES = {v: k for k, v in TILE.items()}
+_STORAGE_NAMES = {v: k for k, v in STORAGE.items()}
+
+
+def ews_set_tile_shape(sim, shape):
+    _check(load().ews_set_tile_shape(sim, TILE[shape] if isinstance(shape, str) else int(shape)))
+
+
+def ews_get_tile_shape(sim) -> int:
+    return load().ews_get_tile_shape(sim)
+
+
+def ews_tile_tuned(grid: ews_grid, boundary, storage) -> int:
+    b = BOUNDARY[boundary] if isinstance(boundary, str) else int(boundary)
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    return load().ews_tile_tuned(C.byref(grid), b, st)
+
+
+def ews_tile_tuning_export() -> list:
+    """The tile-shape table as a list of dicts (nx, ny, nz, boundary name,
+    storage name, shape name)."""
+    lib = load()
+    n = lib.ews_tile_tuning_export(None, 0)
+    arr = (ews_tuned_tile * max(n, 1))()
+    n = min(n, lib.ews_tile_tuning_export(arr, n))
+    return [{"nx": e.nx, "ny": e.ny, "nz": e.nz,
+             "boundary": _BOUNDARY_NAMES.get(e.boundary, e.boundary),
+             "storage": _STORAGE_NAMES.get(e.storage, e.storage),
+             "shape": _TILE_NAMES.get(e.shape, e.shape)} for e in arr[:n]]
+
+
+def ews_tile_tuning_import(entries) -> None:
+    """Add entries (dicts as ews_tile_tuning_export returns) to the table."""
+    entries = list(entries)
+    arr = (ews_tuned_tile * max(len(entries), 1))()
+    for k, e in enumerate(entries):
+        b, st, sh = e["boundary"], e["storage"], e["shape"]
+        arr[k] = ews_tuned_tile(int(e["nx"]), int(e["ny"]), int(e["nz"]),
+                                BOUNDARY[b] if isinstance(b, str) else int(b),
+                                STORAGE[st] if isinstance(st, str) else int(st),
+                                TILE[sh] if isinstance(sh, str) else int(sh))
+    _check(load().ews_tile_tuning_import(arr, len(entries)))
+
+
+def ews_tile_tuning_clear() -> None:
+    load().ews_tile_tuning_clear()
+
+
 def _device_name():
     try:
         import torch
@@ -422,12 +484,15 @@ def _device_name():
 
 
 def save_batch_tuning(path: str, device: str | None = None) -> int:
-    """Write the autotuner table to a JSON file, tagged with the GPU it was
-    timed on (default: the current CUDA device).  Returns the entry count."""
+    """Write the autotuner tables (batch z-chunks, and the tile shapes of the
+    forward passes under "tiles") to a JSON file, tagged with the GPU they
+    were timed on (default: the current CUDA device).  Returns the z-chunk
+    entry count."""
     import json
     entries = ews_batch_tuning_export()
+    tiles = ews_tile_tuning_export()
     doc = {"format": TUNING_FORMAT, "device": device if device is not None else _device_name(),
-           "entries": entries}
+           "entries": entries, "tiles": tiles}
     with open(path, "w") as f:
         json.dump(doc, f, indent=1)
     return len(entries)
@@ -446,6 +511,7 @@ def load_batch_tuning(path: str, device: str | None = None) -> int:
     if doc.get("device") is not None and here is not None and doc["device"] != here:
         return 0
     ews_batch_tuning_import(doc["entries"])
+    ews_tile_tuning_import(doc.get("tiles", []))
     return len(doc["entries"])
 
 
@@ -570,6 +636,13 @@ class Simulation:
             out = np.zeros((3, self.nz, self.ny, self.nx), np.float32)
         mis = ews_gradient(self._h, nt, dt, observed, out[0], out[1], out[2], ckpt_every)
         return mis, out
+
+    def set_tile_shape(self, shape):
+        ews_set_tile_shape(self._h, shape)
+
+    @property
+    def tile_shape(self) -> str:
+        return _TILE_NAMES.get(ews_get_tile_shape(self._h), "?")
 
     def set_profiling(self, on=True):
         ews_set_profiling(self._h, on)

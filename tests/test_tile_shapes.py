@@ -1,0 +1,114 @@
+"""The forward passes at every tile shape the tuner chooses from (32 x 8,
+32 x 4, 32 x 16 with two rows per thread).  Every shape runs the same
+arithmetic per cell in the same order, so seismograms and wavefields must
+equal the 32 x 8 passes to the rounding of separately compiled code (FP32
+1e-6; BF16 storage, where a rounding difference can move a stored value by
+one unit, 1e-3) -- on ragged grids with partial tiles, every boundary kind
+and FP32 / BF16 storage -- and match the FP64 oracle.
+The tuner fills its table from timed trials and leaves the results
+unchanged; an imported entry is used as it is; runs the other shapes do not
+cover (free surface, coarse medium grid) keep 32 x 8."""
+import numpy as np
+import pytest
+
+from paper_2112_15071_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = ["32x8", "32x4", "32x16"]
+
+
+@pytest.fixture(scope="module")
+def ews():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_15071_gb300 import ews as E
+    E.load()
+    yield E
+    E.ews_tile_tuning_clear()
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run(ews, p, shape, storage="f32"):
+    sim = ews.simulation_for(p, storage=storage)
+    sim.set_tile_shape(shape)
+    seis = sim.run(p.nt, p.dt)
+    assert sim.tile_shape == shape
+    return seis, sim.get_state()
+
+
+@pytest.mark.parametrize("boundary", ["none", "sponge", "cpml"])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("kind", ["moment", "force"])
+def test_every_shape_gives_the_same_results(ews, boundary, storage, kind):
+    p = synth.small_problem(70, 45, 37, nt=60, boundary=boundary, kind=kind, width=6,
+                            seed=101)
+    tol = 1e-6 if storage == "f32" else 1e-3
+    ref_seis, ref_state = run(ews, p, "32x8", storage)
+    assert np.abs(ref_seis).max() > 0
+    for shape in SHAPES[1:]:
+        seis, state = run(ews, p, shape, storage)
+        assert rel(seis, ref_seis) <= tol, (shape, rel(seis, ref_seis))
+        for q in range(9):
+            assert rel(state[q], ref_state[q]) <= tol, (shape, q)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_every_shape_matches_the_oracle(ews, orc, shape):
+    p = synth.small_problem(33, 65, 40, nt=120, boundary="cpml", kind="moment", width=6,
+                            seed=102, spacing=(10.0, 14.0, 7.0))
+    want, osim = orc.run_problem(p, return_sim=True)
+    got, state = run(ews, p, shape)
+    assert rel(got, want) <= 1e-5, (shape, rel(got, want))
+    ost = osim.get_state()
+    for q in range(9):
+        assert rel(state[q], ost[q]) <= 1e-5, (shape, q)
+
+
+def test_tuner_fills_the_table_without_changing_results(ews):
+    ews.ews_tile_tuning_clear()
+    p = synth.small_problem(64, 48, 40, nt=50, boundary="sponge", kind="moment", width=6,
+                            seed=103)
+    g = ews.ews_grid(p.nx, p.ny, p.nz, *p.spacing)
+    assert ews.ews_tile_tuned(g, "sponge", "f32") == 0
+    sim = ews.simulation_for(p)                          # automatic shape
+    got = sim.run(p.nt, p.dt)
+    tuned = ews.ews_tile_tuned(g, "sponge", "f32")
+    assert tuned in (ews.EWS_TILE_32X8, ews.EWS_TILE_32X4, ews.EWS_TILE_32X16)
+    assert ews.ews_get_tile_shape(sim.handle) == tuned
+    want, _ = run(ews, p, "32x8")
+    assert rel(got, want) <= 1e-6
+    # a second run takes the table's entry and gives the same result
+    assert np.array_equal(sim.run(p.nt, p.dt), got)
+
+
+def test_imported_entry_is_used(ews):
+    p = synth.small_problem(40, 36, 28, nt=30, boundary="cpml", kind="force", width=5, seed=104)
+    ews.ews_tile_tuning_import([{"nx": p.nx, "ny": p.ny, "nz": p.nz, "boundary": "cpml",
+                                 "storage": "f32", "shape": "32x16"}])
+    sim = ews.simulation_for(p)
+    sim.run(p.nt, p.dt)
+    assert sim.tile_shape == "32x16"
+
+
+def test_surface_and_coarse_medium_keep_32x8(ews):
+    p = synth.small_problem(40, 36, 30, nt=20, boundary="sponge", kind="moment", width=5,
+                            seed=105)
+    p.free_surface = (6, 1e-3)
+    sim = ews.simulation_for(p)
+    sim.set_tile_shape("32x4")
+    sim.run(p.nt, p.dt)
+    assert sim.tile_shape == "32x8"
+    q = synth.small_problem(40, 36, 30, nt=20, boundary="sponge", kind="moment", width=5,
+                            seed=106, layered=False)
+    synth.with_coarse_medium(q, (9, 7, 5), seed=106, layer_vp=(2400.0, 2700.0, 2950.0))
+    sim = ews.simulation_for(q)
+    sim.set_tile_shape("32x16")
+    sim.run(q.nt, q.dt)
+    assert sim.tile_shape == "32x8"
