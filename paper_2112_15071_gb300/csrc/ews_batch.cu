@@ -462,129 +462,10 @@ ews_status choose_batch_chunks(const ews_batch_shot* shots, int nshots, const st
     return EWS_OK;
 }
 
-}  // namespace
-}  // namespace ews
-
-extern "C" {
-
-int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int free_surface) {
-    if (!grid) return 0;
-    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
-    auto it = ews::g_tuned.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary,
-                                                free_surface ? (int)ews::BX_LEAN_FS
-                                                             : (int)ews::BX_LEAN));
-    return it == ews::g_tuned.end() ? 0 : it->second;
-}
-
-// The autotuner times trial launches of the forward executor only (its
-// result serves forward and gradient shots alike), so the table has one
-// entry per grid, boundary and surface form.
-int ews_batch_tuning_export(ews_tuned_zchunk* out, int cap) {
-    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
-    int n = 0;
-    for (const auto& kv : ews::g_tuned) {
-        if (out && n < cap) {
-            ews_tuned_zchunk& e = out[n];
-            e.nx = std::get<0>(kv.first);
-            e.ny = std::get<1>(kv.first);
-            e.nz = std::get<2>(kv.first);
-            e.boundary = std::get<3>(kv.first);
-            e.free_surface = std::get<4>(kv.first) == ews::BX_LEAN_FS ? 1 : 0;
-            e.zchunk = kv.second;
-        }
-        ++n;
-    }
-    return n;
-}
-
-ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n) {
-    if (n < 0 || (n > 0 && !in)) return ews::report(EWS_EINVAL, "ews_batch_tuning_import: no entries");
-    for (int k = 0; k < n; ++k) {
-        const ews_tuned_zchunk& e = in[k];
-        if (e.nx < 1 || e.ny < 1 || e.nz < 1 || e.boundary < EWS_BOUNDARY_NONE ||
-            e.boundary > EWS_BOUNDARY_CPML || (e.free_surface != 0 && e.free_surface != 1) ||
-            e.zchunk < 1 || e.zchunk > e.nz)
-            return ews::report(EWS_EINVAL,
-                               "ews_batch_tuning_import: entry %d (%d x %d x %d, boundary %d, "
-                               "surface %d, zchunk %d) is invalid; nothing imported",
-                               k, e.nx, e.ny, e.nz, e.boundary, e.free_surface, e.zchunk);
-    }
-    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
-    ews::g_choice.clear();                      // batch-level choices were made against the old entries
-    for (int k = 0; k < n; ++k) {
-        const ews_tuned_zchunk& e = in[k];
-        ews::g_tuned[std::make_tuple(e.nx, e.ny, e.nz, e.boundary,
-                                     e.free_surface ? (int)ews::BX_LEAN_FS : (int)ews::BX_LEAN)] =
-            e.zchunk;
-    }
-    return EWS_OK;
-}
-
-void ews_batch_tuning_clear(void) {
-    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
-    ews::g_tuned.clear();
-    ews::g_choice.clear();
-}
-
-ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
-                     void* cuda_stream) {
-    using namespace ews;
-    if (nshots <= 0 || !shots) return report(EWS_EINVAL, "no shots");
-    ews_batch_options o{};
-    if (opt) o = *opt;
-    if (o.mode != EWS_BATCH_PERSISTENT && o.mode != EWS_BATCH_SEQUENTIAL)
-        return report(EWS_EINVAL, "unknown batch mode %d", o.mode);
-    if (o.ckpt_every < 0 || o.zchunk < 0 || o.ctas_per_sm < 0 || o.dep_wait_ms < 0)
-        return report(EWS_EINVAL, "negative batch option");
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int bnd = shots[0].sim ? shots[0].sim->opt.boundary : -1;
-    bool grad = false, any_fs = false;
-    for (int i = 0; i < nshots; ++i) {
-        const ews_batch_shot& b = shots[i];
-        ews_sim* s = b.sim;
-        if (!s) return report(EWS_EINVAL, "shot %d: null simulation", i);
-        for (int j = 0; j < i; ++j)
-            if (shots[j].sim == s) return report(EWS_EINVAL, "shot %d: simulation used twice", i);
-        if (s->opt.boundary != bnd) return report(EWS_EINVAL, "shot %d: boundary differs", i);
-        if (bnd == EWS_BOUNDARY_CPML && b.observed)
-            return report(EWS_EINVAL, "shot %d: gradients take the none or sponge boundary", i);
-        if (s->opt.storage != EWS_STORAGE_F32) return report(EWS_EINVAL, "shot %d: F32 storage only", i);
-        if (b.nt <= 0) return report(EWS_EINVAL, "shot %d: nt must be positive", i);
-        if (b.observed) {
-            grad = true;
-            if (!b.g_lam || !b.g_mu || !b.g_rho)
-                return report(EWS_EINVAL, "shot %d: gradient outputs missing", i);
-        }
-        ews_status r = sim_ready(s, b.nt, b.dt);
-        if (r != EWS_OK) return r;
-        if (b.observed && s->has_fluid)
-            return report(EWS_EINVAL, "shot %d: fluid cells (mu = 0) are not batched", i);
-        if (s->g.fs != kNoSurface) any_fs = true;
-        if (s->g.cm[0]) return report(EWS_EINVAL, "shot %d: coarse medium grids are not batched", i);
-    }
+// The persistent executor over all the given shots in one captured graph.
+ews_status batch_persistent(int nshots, ews_batch_shot* shots, const ews_batch_options& o, int bnd,
+                            bool grad, bool any_fs, cudaStream_t st) {
     const int K0 = o.ckpt_every > 0 ? o.ckpt_every : 50;
-
-    if (o.mode == EWS_BATCH_SEQUENTIAL) {      // one shot after the other
-        for (int i = 0; i < nshots; ++i) {
-            ews_batch_shot& b = shots[i];
-            ews_sim* s = b.sim;
-            ews_status r = ews_set_stream(s, st);
-            if (r != EWS_OK) return r;
-            if (b.observed) {
-                r = ews_gradient(s, b.nt, b.dt, b.observed, 1, &b.misfit, b.g_lam, b.g_mu,
-                                 b.g_rho, 1, K0);
-                if (r == EWS_OK && b.seis && s->nrec > 0)
-                    BCK(cudaMemcpyAsync(b.seis, s->aux, (size_t)3 * s->nrec * b.nt * sizeof(float),
-                                        cudaMemcpyDeviceToDevice, st));
-            } else {
-                r = ews_run(s, b.nt, b.dt, b.seis, 1, nullptr);
-            }
-            if (r != EWS_OK) return r;
-        }
-        BCK(cudaStreamSynchronize(st));
-        return EWS_OK;
-    }
-
     int* d_err = shots[0].sim->err;            // any of the shots' error flags
     std::vector<BatchShot> bs(nshots);
     std::vector<std::vector<Stage>> progs(nshots);
@@ -713,6 +594,190 @@ ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options*
             BCK(cudaMemcpy(&shots[i].misfit, s->dmisfit, sizeof(double), cudaMemcpyDeviceToHost));
     }
     return EWS_OK;
+}
+
+// Gradient shots in waves.  The gradient state of a shot (adjoint fields,
+// accumulators, checkpoints and a segment of velocity history: about 1.2 to
+// 1.6 KB per cell) is set up for every shot of a launch at once; when that
+// does not fit the device (or the library's memory limit), the shots are
+// split in two halves run one after the other (the forward shots go with the
+// first), recursively, and each finished wave releases its shots' gradient
+// state (ews_release_workspace) for the next.
+ews_status batch_waves(ews_batch_shot* shots, const std::vector<int>& idx,
+                       const ews_batch_options& o, int bnd, bool any_fs, cudaStream_t st) {
+    std::vector<ews_batch_shot> sub(idx.size());
+    std::vector<int> grads;
+    bool grad = false;
+    for (size_t k = 0; k < idx.size(); ++k) {
+        sub[k] = shots[idx[k]];
+        if (sub[k].observed) {
+            grad = true;
+            grads.push_back((int)k);
+        }
+    }
+    ews_status r = batch_persistent((int)sub.size(), sub.data(), o, bnd, grad, any_fs, st);
+    if (r == EWS_OK) {
+        for (size_t k = 0; k < idx.size(); ++k) shots[idx[k]].misfit = sub[k].misfit;
+        return EWS_OK;
+    }
+    if (r != EWS_ENOMEM || grads.size() < 2) return r;
+    // too much gradient state at once: release what was set up, split, retry
+    for (int k : grads) {
+        const ews_status rr = ews_release_workspace(sub[k].sim);
+        if (rr != EWS_OK) return rr;
+    }
+    std::vector<int> first, second;
+    const size_t half = grads.size() / 2;
+    size_t g = 0;
+    for (size_t k = 0; k < idx.size(); ++k) {
+        if (sub[k].observed) {
+            (g++ < half ? first : second).push_back(idx[k]);
+        } else {
+            first.push_back(idx[k]);                 // forward shots go with the first wave
+        }
+    }
+    if ((r = batch_waves(shots, first, o, bnd, any_fs, st)) != EWS_OK) return r;
+    for (int i : first)
+        if (shots[i].observed && (r = ews_release_workspace(shots[i].sim)) != EWS_OK) return r;
+    return batch_waves(shots, second, o, bnd, any_fs, st);
+}
+
+}  // namespace
+}  // namespace ews
+
+extern "C" {
+
+int ews_batch_tuned_zchunk(const ews_grid* grid, int boundary, int free_surface) {
+    if (!grid) return 0;
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    auto it = ews::g_tuned.find(std::make_tuple(grid->nx, grid->ny, grid->nz, boundary,
+                                                free_surface ? (int)ews::BX_LEAN_FS
+                                                             : (int)ews::BX_LEAN));
+    return it == ews::g_tuned.end() ? 0 : it->second;
+}
+
+// The autotuner times trial launches of the forward executor only (its
+// result serves forward and gradient shots alike), so the table has one
+// entry per grid, boundary and surface form.
+int ews_batch_tuning_export(ews_tuned_zchunk* out, int cap) {
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    int n = 0;
+    for (const auto& kv : ews::g_tuned) {
+        if (out && n < cap) {
+            ews_tuned_zchunk& e = out[n];
+            e.nx = std::get<0>(kv.first);
+            e.ny = std::get<1>(kv.first);
+            e.nz = std::get<2>(kv.first);
+            e.boundary = std::get<3>(kv.first);
+            e.free_surface = std::get<4>(kv.first) == ews::BX_LEAN_FS ? 1 : 0;
+            e.zchunk = kv.second;
+        }
+        ++n;
+    }
+    return n;
+}
+
+ews_status ews_batch_tuning_import(const ews_tuned_zchunk* in, int n) {
+    if (n < 0 || (n > 0 && !in)) return ews::report(EWS_EINVAL, "ews_batch_tuning_import: no entries");
+    for (int k = 0; k < n; ++k) {
+        const ews_tuned_zchunk& e = in[k];
+        if (e.nx < 1 || e.ny < 1 || e.nz < 1 || e.boundary < EWS_BOUNDARY_NONE ||
+            e.boundary > EWS_BOUNDARY_CPML || (e.free_surface != 0 && e.free_surface != 1) ||
+            e.zchunk < 1 || e.zchunk > e.nz)
+            return ews::report(EWS_EINVAL,
+                               "ews_batch_tuning_import: entry %d (%d x %d x %d, boundary %d, "
+                               "surface %d, zchunk %d) is invalid; nothing imported",
+                               k, e.nx, e.ny, e.nz, e.boundary, e.free_surface, e.zchunk);
+    }
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    ews::g_choice.clear();                      // batch-level choices were made against the old entries
+    for (int k = 0; k < n; ++k) {
+        const ews_tuned_zchunk& e = in[k];
+        ews::g_tuned[std::make_tuple(e.nx, e.ny, e.nz, e.boundary,
+                                     e.free_surface ? (int)ews::BX_LEAN_FS : (int)ews::BX_LEAN)] =
+            e.zchunk;
+    }
+    return EWS_OK;
+}
+
+void ews_batch_tuning_clear(void) {
+    std::lock_guard<std::mutex> lk(ews::g_tune_mu);
+    ews::g_tuned.clear();
+    ews::g_choice.clear();
+}
+
+ews_status ews_batch(int nshots, ews_batch_shot* shots, const ews_batch_options* opt,
+                     void* cuda_stream) {
+    using namespace ews;
+    if (nshots <= 0 || !shots) return report(EWS_EINVAL, "no shots");
+    ews_batch_options o{};
+    if (opt) o = *opt;
+    if (o.mode != EWS_BATCH_PERSISTENT && o.mode != EWS_BATCH_SEQUENTIAL)
+        return report(EWS_EINVAL, "unknown batch mode %d", o.mode);
+    if (o.ckpt_every < 0 || o.zchunk < 0 || o.ctas_per_sm < 0 || o.dep_wait_ms < 0)
+        return report(EWS_EINVAL, "negative batch option");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int bnd = shots[0].sim ? shots[0].sim->opt.boundary : -1;
+    bool grad = false, any_fs = false;
+    for (int i = 0; i < nshots; ++i) {
+        const ews_batch_shot& b = shots[i];
+        ews_sim* s = b.sim;
+        if (!s) return report(EWS_EINVAL, "shot %d: null simulation", i);
+        for (int j = 0; j < i; ++j)
+            if (shots[j].sim == s) return report(EWS_EINVAL, "shot %d: simulation used twice", i);
+        if (s->opt.boundary != bnd) return report(EWS_EINVAL, "shot %d: boundary differs", i);
+        if (bnd == EWS_BOUNDARY_CPML && b.observed)
+            return report(EWS_EINVAL, "shot %d: gradients take the none or sponge boundary", i);
+        if (s->opt.storage != EWS_STORAGE_F32) return report(EWS_EINVAL, "shot %d: F32 storage only", i);
+        if (b.nt <= 0) return report(EWS_EINVAL, "shot %d: nt must be positive", i);
+        if (b.observed) {
+            grad = true;
+            if (!b.g_lam || !b.g_mu || !b.g_rho)
+                return report(EWS_EINVAL, "shot %d: gradient outputs missing", i);
+        }
+        ews_status r = sim_ready(s, b.nt, b.dt);
+        if (r != EWS_OK) return r;
+        if (b.observed && s->has_fluid)
+            return report(EWS_EINVAL, "shot %d: fluid cells (mu = 0) are not batched", i);
+        if (s->g.fs != kNoSurface) any_fs = true;
+        if (s->g.cm[0]) return report(EWS_EINVAL, "shot %d: coarse medium grids are not batched", i);
+    }
+    const int K0 = o.ckpt_every > 0 ? o.ckpt_every : 50;
+
+    if (o.mode == EWS_BATCH_SEQUENTIAL) {      // one shot after the other
+        for (int i = 0; i < nshots; ++i) {
+            ews_batch_shot& b = shots[i];
+            ews_sim* s = b.sim;
+            ews_status r = ews_set_stream(s, st);
+            if (r != EWS_OK) return r;
+            if (b.observed) {
+                r = ews_gradient(s, b.nt, b.dt, b.observed, 1, &b.misfit, b.g_lam, b.g_mu,
+                                 b.g_rho, 1, K0);
+                if (r == EWS_ENOMEM && i > 0) {
+                    // the earlier shots' gradient state stays set up until
+                    // released: release it and try this shot again
+                    for (int j = 0; j < i && r == EWS_ENOMEM; ++j)
+                        if (shots[j].observed && ews_release_workspace(shots[j].sim) != EWS_OK)
+                            return EWS_ECUDA;
+                    r = ews_gradient(s, b.nt, b.dt, b.observed, 1, &b.misfit, b.g_lam, b.g_mu,
+                                     b.g_rho, 1, K0);
+                }
+                if (r == EWS_OK && b.seis && s->nrec > 0)
+                    BCK(cudaMemcpyAsync(b.seis, s->aux, (size_t)3 * s->nrec * b.nt * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, st));
+            } else {
+                r = ews_run(s, b.nt, b.dt, b.seis, 1, nullptr);
+            }
+            if (r != EWS_OK) return r;
+        }
+        BCK(cudaStreamSynchronize(st));
+        return EWS_OK;
+    }
+
+    if (!grad) return batch_persistent(nshots, shots, o, bnd, false, any_fs, st);
+    std::vector<int> all(nshots);
+    for (int i = 0; i < nshots; ++i) all[i] = i;
+    return batch_waves(shots, all, o, bnd, any_fs, st);
 }
 
 }  // extern "C"

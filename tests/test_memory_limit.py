@@ -123,3 +123,56 @@ def test_capped_batch_returns_enomem(ews):
     for p, d in zip(probs, shots):
         want = ews.simulation_for(p).run(p.nt, p.dt)
         assert rel(d["seis"].cpu().numpy(), want) <= 1e-6
+
+
+def test_gradient_batch_runs_in_waves_under_the_limit(ews):
+    """Three gradient shots whose gradient state fits the limit two at a time
+    but not three at once: ews_batch splits them into waves (the forward shot
+    rides with the first) and gives the results of the one-by-one path, which
+    itself releases earlier shots' gradient state when it needs the room."""
+    import torch
+    probs = [synth.small_problem(40, 36, 28, nt=60, boundary="sponge", width=5, seed=20 + i,
+                                 kind=("moment", "force")[i % 2]) for i in range(4)]
+    rng = np.random.default_rng(3)
+
+    def shots():
+        out = []
+        for i, p in enumerate(probs):
+            sim = ews.simulation_for(p)
+            sim.set_history_budget(0)                  # one segment of history per shot
+            d = {"sim": sim, "nt": p.nt, "dt": p.dt,
+                 "seis": torch.zeros((3, p.rec_pos.shape[0], p.nt), device="cuda")}
+            if i < 3:
+                obs = rng.standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32) * 1e-9
+                d["observed"] = torch.from_numpy(obs).cuda()
+                for k in ("g_lam", "g_mu", "g_rho"):
+                    d[k] = torch.zeros((p.nz, p.ny, p.nx), device="cuda")
+            out.append(d)
+        return out
+
+    rng = np.random.default_rng(3)
+    a = shots()
+    rng = np.random.default_rng(3)
+    b = shots()
+    torch.cuda.synchronize()
+    pitch = (probs[0].nx + 31) // 32 * 32
+    field = 4 * pitch * probs[0].ny * probs[0].nz
+    # per gradient shot: 17 FP32 + 8 FP64 adjoint fields, 2 checkpoints of 9
+    # fields, 21 history slots of 3 fields, seismogram buffers: ~120 fields
+    per_shot = (17 + 16 + 18 + 63 + 4) * field
+    try:
+        ews.ews_set_memory_limit(ews.ews_memory_in_use() + 2.5 * per_shot)
+        ma = ews.ews_batch(a, ckpt_every=20)
+        torch.cuda.synchronize()
+        for d in a:                                    # the last wave's state
+            d["sim"].release_workspace()
+        mb = ews.ews_batch(b, ckpt_every=20, mode=ews.EWS_BATCH_SEQUENTIAL)
+        torch.cuda.synchronize()
+    finally:
+        ews.ews_set_memory_limit(-1)
+    for i in range(4):
+        assert rel(a[i]["seis"].cpu().numpy(), b[i]["seis"].cpu().numpy()) <= 1e-6, i
+        if i < 3:
+            assert ma[i] == pytest.approx(mb[i], rel=1e-6)
+            for k in ("g_lam", "g_mu", "g_rho"):
+                assert rel(a[i][k].cpu().numpy(), b[i][k].cpu().numpy()) <= 1e-5, (i, k)
