@@ -629,8 +629,9 @@ def batch_report(args, local):
             job(ews.EWS_BATCH_PERSISTENT, gradient)
             job(ews.EWS_BATCH_SEQUENTIAL, gradient)
         tp = job(ews.EWS_BATCH_PERSISTENT, gradient)
-        for s in sims[:len(gprobs)]:
-            s.release_workspace()
+        if gradient:                             # the last wave's gradient state
+            for s in sims[:len(gprobs)]:
+                s.release_workspace()
         ts = job(ews.EWS_BATCH_SEQUENTIAL, gradient)
         c = cells_of(ps)
         out[name] = {"cell_steps": c, "persistent_s": round(tp, 3), "one_by_one_s": round(ts, 3),
