@@ -208,7 +208,8 @@ def algorithmic_bytes(prob, es: int = 4):
     W = prob.width if prob.boundary == "cpml" else 0
     slab = 2 * W * (prob.ny * prob.nz + prob.nx * prob.nz + prob.nx * prob.ny)
     return {"velocity": (12 * es + 4) * n + 24 * slab, "stress": (15 * es + 8) * n + 24 * slab,
-            "step_min": (18 * es + 12) * n + 48 * slab, "slab_cell_dirs": slab}
+            "step_min": (18 * es + 12) * n + 48 * slab, "step": (18 * es + 12) * n + 48 * slab,
+            "slab_cell_dirs": slab}
 
 
 def kernel_source_sha() -> str:
@@ -519,8 +520,8 @@ def storage_report(args, local, with_oracle: bool):
         kms, kl = sim.profile(reset=True)
         sim.set_profiling(False)
         alg = algorithmic_bytes(prob, es[st])
-        v_ms = kms[0] / max(kl[0], 1)
-        s_ms = kms[1] / max(kl[1], 1)
+        v_ms = kms[ews.EWS_KERNEL_VELOCITY] / max(kl[ews.EWS_KERNEL_VELOCITY], 1)
+        s_ms = kms[ews.EWS_KERNEL_STRESS] / max(kl[ews.EWS_KERNEL_STRESS], 1)
         step_ms = ms / nt
         # the tuned tile shape against the 32 x 8 tiles of the other passes
         tuned = sim.tile_shape
@@ -535,11 +536,37 @@ def storage_report(args, local, with_oracle: bool):
                    "tile_shape": tuned,
                    "gcells_32x8_tiles": round(prob.ncell * nt / (ms8 / 1e3) / 1e9, 3),
                    "ms_per_time_step": round(step_ms, 4),
-                   "velocity_frac": round(alg["velocity"] / (v_ms / 1e3) / 1e9 / peak, 4),
-                   "stress_frac": round(alg["stress"] / (s_ms / 1e3) / 1e9 / peak, 4),
+                   "velocity_frac": round(alg["velocity"] / (v_ms / 1e3) / 1e9 / peak, 4)
+                   if v_ms > 0 else None,
+                   "stress_frac": round(alg["stress"] / (s_ms / 1e3) / 1e9 / peak, 4)
+                   if s_ms > 0 else None,
                    "whole_step_frac": round(alg["step_min"] / (step_ms / 1e3) / 1e9 / peak, 4),
                    "algorithmic_bytes_per_cell": 18 * es[st] + 12,
                    "field_scales": [float(x) for x in sim.field_scales()]}
+        if st == "f32":
+            # the fused step (both passes in one launch, 84 B per cell) on the
+            # same loop, against the two-pass kernels above
+            sim.set_tile_shape("fused")
+            sim.run(nt, prob.dt, seis)               # warm-up (graph capture)
+            a.record(stream)
+            sim.run(nt, prob.dt, seis)
+            b.record(stream)
+            torch.cuda.synchronize()
+            msf = a.elapsed_time(b)
+            sim.set_profiling(True)
+            sim.run(nt, prob.dt, seis)
+            torch.cuda.synchronize()
+            kf, klf = sim.profile(reset=True)
+            sim.set_profiling(False)
+            f_ms = kf[ews.EWS_KERNEL_STEP] / max(klf[ews.EWS_KERNEL_STEP], 1)
+            out[st]["fused_step"] = {
+                "tile_shape": sim.tile_shape,
+                "gcells": round(prob.ncell * nt / (msf / 1e3) / 1e9, 3),
+                "step_launch_ms": round(f_ms, 4),
+                "frac": round(alg["step"] / (f_ms / 1e3) / 1e9 / peak, 4) if f_ms > 0 else None,
+                "note": "frac = 84 B per cell / launch time / peak; the launch is bound by "
+                        "instruction issue (the velocity of a 2-cell ring per tile is "
+                        "recomputed), not by DRAM"}
         sim.close()
         del seis
     del prob

@@ -279,17 +279,34 @@ ews_status ews_get_field_scales(ews_sim* sim, float* scale);
  * type (on a GB300 at 256^3: 32 x 8 with C-PML, 32 x 4 for FP32 with a
  * sponge, 32 x 16 for BF16 with a sponge).  Every shape runs the same
  * arithmetic per cell in the same order (separately compiled, so results
- * agree to FP32 rounding).  With EWS_TILE_AUTO (the default), ews_run picks the shape for its
- * grid size, boundary and storage type from a per-process table, filling a
- * missing entry by timing a few steps with each shape before the run (the
- * wavefields are reset afterwards); plain forward steps use it (runs with a
- * free surface or a coarse medium grid, the adjoint's forward part and
- * batched shots keep 32 x 8). */
-enum { EWS_TILE_AUTO = 0, EWS_TILE_32X8 = 1, EWS_TILE_32X4 = 2, EWS_TILE_32X16 = 3 };
+ * agree to FP32 rounding).  EWS_TILE_FUSED runs both passes of a step in one
+ * launch (32 x 8 tiles, the velocity of a 2-cell ring around each tile
+ * recomputed by its neighbours), reading one set of wavefields and writing a
+ * second one that the library allocates (9 more wavefields of device
+ * memory, released when the tuner picks another shape); it serves FP32
+ * storage at unit field scales with a sponge or no absorbing boundary, and
+ * other runs fall back to 32 x 8.  It moves 84 bytes per cell instead of
+ * 120 but recomputes the ring, so on a GB300 it is bound by instruction
+ * issue and runs slower than the two passes (0.78x at 256^3, 0.89x at
+ * 1024 x 1024 x 512); the tuner times it where the second set takes at
+ * most a quarter of the free device memory.  With EWS_TILE_AUTO (the default),
+ * ews_run picks the shape for its grid size, boundary and storage type from
+ * a per-process table, filling a missing entry by timing a few steps with
+ * each shape before the run (the wavefields are reset afterwards); plain
+ * forward steps use it (runs with a free surface or a coarse medium grid,
+ * the adjoint's forward part and batched shots keep 32 x 8). */
+enum {
+    EWS_TILE_AUTO = 0,
+    EWS_TILE_32X8 = 1,
+    EWS_TILE_32X4 = 2,
+    EWS_TILE_32X16 = 3,
+    EWS_TILE_FUSED = 4
+};
 
 /* Use this shape for later runs (EWS_TILE_AUTO: the tuned one). */
 ews_status ews_set_tile_shape(ews_sim* sim, int shape);
-/* The shape the forward passes of the last run used (EWS_TILE_32X8 ..). */
+/* The shape the forward passes of the last run used (EWS_TILE_32X8 ..
+ * EWS_TILE_FUSED). */
 int ews_get_tile_shape(ews_sim* sim);
 
 /* Tile-shape table, one entry per grid size, boundary and storage type;
@@ -299,7 +316,7 @@ typedef struct {
     int nx, ny, nz;           /* wavefield grid                                      */
     int boundary;             /* EWS_BOUNDARY_*                                      */
     int storage;              /* EWS_STORAGE_*                                       */
-    int shape;                /* EWS_TILE_32X8 .. EWS_TILE_32X16                     */
+    int shape;                /* EWS_TILE_32X8 .. EWS_TILE_FUSED                     */
 } ews_tuned_tile;
 
 /* Shape of the table entry for a grid (0 if not tuned yet). */
@@ -319,6 +336,7 @@ enum {
     EWS_KERNEL_INJECT = 2,     /* point-source injection                       */
     EWS_KERNEL_RECORD = 3,     /* receiver sampling, Sec. 2.4                  */
     EWS_KERNEL_POINTS = 4,     /* moment injection + receivers in one launch   */
+    EWS_KERNEL_STEP = 5,       /* velocity + stress passes in one launch       */
     EWS_NKERNEL = 8
 };
 

@@ -70,14 +70,56 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // capture) may run the passes of another tile shape; the others use 32 x 8.
 bool tile_eligible(const ews_sim* s) { return s->g.fs == kNoSurface && !s->g.cm[0]; }
 
+// The fused step serves FP32 storage at unit scales, sponge or no boundary.
+bool fused_eligible(const ews_sim* s) {
+    if (!tile_eligible(s) || !fused::fused_supported(s->g, s->B, s->opt.storage)) return false;
+    for (int q = 0; q < NFIELD; ++q)
+        if (s->scale[q] != 1.0f) return false;
+    return true;
+}
+
+// Shape of the forward passes of a plain (vcap null) or capturing step.
+int fwd_shape(const ews_sim* s, bool capture) {
+    if (capture || !tile_eligible(s)) return EWS_TILE_32X8;
+    if (s->tile_used == EWS_TILE_FUSED && !fused_eligible(s)) return EWS_TILE_32X8;
+    return s->tile_used;
+}
+
+void drop_fused(ews_sim* s) {
+    fused::fused_plan_destroy(static_cast<fused::FusedPlan*>(s->tplan[EWS_TILE_FUSED]));
+    s->tplan[EWS_TILE_FUSED] = nullptr;
+    dev_free(s->fields2);
+    s->fields2 = nullptr;
+}
+
 void drop_tile_plans(ews_sim* s) {
     t32x4::stencil_plan_destroy(static_cast<t32x4::StencilPlan*>(s->tplan[EWS_TILE_32X4]));
     t32x16::stencil_plan_destroy(static_cast<t32x16::StencilPlan*>(s->tplan[EWS_TILE_32X16]));
     s->tplan[EWS_TILE_32X4] = s->tplan[EWS_TILE_32X16] = nullptr;
+    drop_fused(s);
 }
 
 ews_status tile_plan(ews_sim* s, int shape) {
     if (shape == EWS_TILE_32X8 || s->tplan[shape]) return EWS_OK;
+    if (shape == EWS_TILE_FUSED) {
+        const size_t bytes = (size_t)NFIELD * s->fstride * sizeof(float);
+        cudaError_t e = dev_malloc((void**)&s->fields2, bytes);
+        if (e != cudaSuccess) {
+            s->fields2 = nullptr;
+            return fail(EWS_ENOMEM, "second wavefield set of the fused step (%zu bytes): %s", bytes,
+                        cudaGetErrorString(e));
+        }
+        fused::FusedPlan* p = nullptr;
+        e = cudaMemsetAsync(s->fields2, 0, bytes, s->stream);
+        if (e == cudaSuccess) e = fused::fused_plan_create(s->g, s->F(), s->F2(), s->M(), s->B, &p);
+        if (e != cudaSuccess) {
+            dev_free(s->fields2);
+            s->fields2 = nullptr;
+            return fail(EWS_ECUDA, "fused step plan: %s", cudaGetErrorString(e));
+        }
+        s->tplan[shape] = p;
+        return EWS_OK;
+    }
     if (shape == EWS_TILE_32X4) {
         t32x4::StencilPlan* p = nullptr;
         CK(t32x4::stencil_plan_create(s->g, s->F(), s->M(), s->B, s->opt.storage, &p));
@@ -435,11 +477,57 @@ cudaError_t str_launch(ews_sim* s, int shape, const DevFields& F, const float dt
     }
 }
 
+// Steps n0 .. n0 + nsteps - 1 with the fused step: step n0 + m reads the
+// wavefield set it wrote in step n0 + m - 1 (the simulation's own set at
+// m = 0) and writes the other; receivers and a moment source run on the set
+// just written, as after the two passes.  An odd step count ends with the
+// state copied back into the simulation's own set.
+ews_status steps_fused(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
+                       float* dseis, int ld) {
+    const fused::FusedPlan* fp = static_cast<const fused::FusedPlan*>(s->tplan[EWS_TILE_FUSED]);
+    DevMedium M = s->M();
+    const DevSource S = source_taps(s, src, dt);
+    const DevFields set[2] = {s->F(), s->F2()};
+    const float inv[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    const int stor = s->opt.storage;
+    s->fresh = false;
+    ews_status st;
+    if ((st = mark(s, -1)) != EWS_OK) return st;
+    for (int n = n0; n < n0 + nsteps; ++n) {
+        const int dir = (n - n0) & 1;
+        const DevFields& out = set[dir ^ 1];
+        CK(fused::launch_fused(fp, dir, s->g, M, s->B, (float)dt, S, s->wavelet, n, s->err,
+                               s->stream));
+        if ((st = mark(s, EWS_KERNEL_STEP)) != EWS_OK) return st;
+        const bool rec = s->nrec > 0 && dseis;
+        if (S.kind == EWS_SOURCE_MOMENT && rec) {
+            CK(launch_post_stress(s->g, out, M, s->B, S, s->wavelet, s->rtaps, s->nrec, dseis, ld, n,
+                                  stor, inv, s->err, s->stream));
+            if ((st = mark(s, EWS_KERNEL_POINTS)) != EWS_OK) return st;
+        } else {
+            if (rec) {
+                CK(launch_record(s->g, out, s->rtaps, s->nrec, dseis, ld, n, stor, inv, s->err,
+                                 s->stream));
+                if ((st = mark(s, EWS_KERNEL_RECORD)) != EWS_OK) return st;
+            }
+            if (S.kind == EWS_SOURCE_MOMENT) {
+                CK(launch_inject(s->g, out, M, s->B, S, s->wavelet, n, stor, s->err, s->stream));
+                if ((st = mark(s, EWS_KERNEL_INJECT)) != EWS_OK) return st;
+            }
+        }
+    }
+    if (nsteps & 1)
+        CK(cudaMemcpyAsync(s->fields, s->fields2, (size_t)NFIELD * s->fstride * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s->stream));
+    return EWS_OK;
+}
+
 ews_status steps_direct(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double dt,
                         float* dseis, int ld, float* vcap) {
-    const int shape = (!vcap && tile_eligible(s)) ? s->tile_used : EWS_TILE_32X8;
+    const int shape = fwd_shape(s, vcap != nullptr);
     ews_status st0 = tile_plan(s, shape);
     if (st0 != EWS_OK) return st0;
+    if (shape == EWS_TILE_FUSED) return steps_fused(s, src, n0, nsteps, dt, dseis, ld);
     DevFields F = s->F();
     DevMedium M = s->M();
     const DevSource S = source_taps(s, src, dt);
@@ -511,7 +599,7 @@ ews_status steps(ews_sim* s, const SourceSpec& src, int n0, int nsteps, double d
     if (!hit) {
         if (!s->cap_stream) CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
         // the tile shape's plan exists before the capture starts
-        ews_status sp = tile_plan(s, (!vcap && tile_eligible(s)) ? s->tile_used : EWS_TILE_32X8);
+        ews_status sp = tile_plan(s, fwd_shape(s, vcap != nullptr));
         if (sp != EWS_OK) return sp;
         long long before[EWS_NKERNEL];
         std::memcpy(before, s->launches, sizeof(before));
@@ -580,7 +668,8 @@ ews_status choose_tile(ews_sim* s, int nt, double dt) {
         return EWS_OK;
     }
     if (s->tile_req != EWS_TILE_AUTO) {
-        set_tile_used(s, s->tile_req);
+        set_tile_used(s, s->tile_req == EWS_TILE_FUSED && !fused_eligible(s) ? EWS_TILE_32X8
+                                                                              : s->tile_req);
         return EWS_OK;
     }
     const auto key = tile_key(s);
@@ -588,7 +677,8 @@ ews_status choose_tile(ews_sim* s, int nt, double dt) {
         std::lock_guard<std::mutex> lk(g_tile_mu);
         auto it = g_tile.find(key);
         if (it != g_tile.end()) {
-            set_tile_used(s, it->second);
+            set_tile_used(s, it->second == EWS_TILE_FUSED && !fused_eligible(s) ? EWS_TILE_32X8
+                                                                                : it->second);
             return EWS_OK;
         }
     }
@@ -607,7 +697,18 @@ ews_status choose_tile(ews_sim* s, int nt, double dt) {
     int best = EWS_TILE_32X8;
     float best_ms = 1e30f;
     ews_status st = EWS_OK;
-    for (int shape : {EWS_TILE_32X8, EWS_TILE_32X4, EWS_TILE_32X16}) {
+    std::vector<int> cand = {EWS_TILE_32X8, EWS_TILE_32X4, EWS_TILE_32X16};
+    // the fused step, if it applies and its second wavefield set takes at
+    // most a quarter of the device memory still free
+    if (fused_eligible(s)) {
+        size_t fr = 0, tot = 0;
+        const double set = (double)NFIELD * s->fstride * sizeof(float);
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess &&
+            set <= 0.25 * std::min((double)fr, dev_headroom()) &&
+            tile_plan(s, EWS_TILE_FUSED) == EWS_OK)
+            cand.push_back(EWS_TILE_FUSED);
+    }
+    for (int shape : cand) {
         s->tile_used = shape;
         float ms = 1e30f;
         for (int rep = 0; rep < 3 && st == EWS_OK; ++rep) {   // the first is a warm-up
@@ -630,6 +731,11 @@ ews_status choose_tile(ews_sim* s, int nt, double dt) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->tile_used = EWS_TILE_32X8;
+    if (best != EWS_TILE_FUSED || st != EWS_OK || ce != cudaSuccess) {
+        // the second wavefield set is only kept for the shape that uses it
+        const cudaError_t se = cudaStreamSynchronize(s->stream);
+        if (se == cudaSuccess) drop_fused(s);
+    }
     if (st != EWS_OK) return st;
     if (ce != cudaSuccess) return fail(EWS_ECUDA, "tile tuner: %s", cudaGetErrorString(ce));
     // the trial steps leave no trace: the error flag (an FP16 trial from
@@ -955,7 +1061,7 @@ int ews_version(void) { return 100; }
 
 ews_status ews_set_tile_shape(ews_sim* s, int shape) {
     if (!s) return fail(EWS_EINVAL, "null simulation");
-    if (shape < EWS_TILE_AUTO || shape > EWS_TILE_32X16)
+    if (shape < EWS_TILE_AUTO || shape > EWS_TILE_FUSED)
         return fail(EWS_EINVAL, "unknown tile shape %d", shape);
     s->tile_req = shape;
     if (shape != EWS_TILE_AUTO) set_tile_used(s, tile_eligible(s) ? shape : EWS_TILE_32X8);
@@ -995,7 +1101,9 @@ ews_status ews_tile_tuning_import(const ews_tuned_tile* in, int n) {
         const ews_tuned_tile& e = in[k];
         if (e.nx < 4 || e.ny < 4 || e.nz < 4 || e.boundary < EWS_BOUNDARY_NONE ||
             e.boundary > EWS_BOUNDARY_CPML || e.storage < EWS_STORAGE_F32 ||
-            e.storage > EWS_STORAGE_F16 || e.shape < EWS_TILE_32X8 || e.shape > EWS_TILE_32X16)
+            e.storage > EWS_STORAGE_F16 || e.shape < EWS_TILE_32X8 || e.shape > EWS_TILE_FUSED ||
+            (e.shape == EWS_TILE_FUSED &&
+             (e.boundary == EWS_BOUNDARY_CPML || e.storage != EWS_STORAGE_F32)))
             return fail(EWS_EINVAL,
                         "ews_tile_tuning_import: entry %d (%d x %d x %d, boundary %d, storage %d, "
                         "shape %d) is invalid; nothing imported",

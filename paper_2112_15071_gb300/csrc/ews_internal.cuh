@@ -430,6 +430,23 @@ cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const 
 EWS_SHAPE_DECLS(t32x4)
 EWS_SHAPE_DECLS(t32x16)
 
+// One launch per time step (ews_fused.cu): the velocity and stress passes of
+// step n fused, reading sigma^n, v^{n-1/2} from one set of wavefields and
+// writing v^{n+1/2}, sigma^{n+1} to a second set (dir 0: A -> B, dir 1:
+// B -> A), with a point force of step n (S.kind 1) added inside.  FP32
+// storage with unit scales, sponge or no absorbing boundary, no free surface
+// or coarse medium grid.
+namespace fused {
+struct FusedPlan;
+bool fused_supported(const DevGrid& g, const DevBoundary& B, int storage);
+cudaError_t fused_plan_create(const DevGrid& g, const DevFields& A, const DevFields& Bf,
+                              const DevMedium& M, const DevBoundary& B, FusedPlan** out);
+void fused_plan_destroy(FusedPlan* p);
+cudaError_t launch_fused(const FusedPlan* p, int dir, const DevGrid& g, const DevMedium& M,
+                         const DevBoundary& B, float dt, const DevSource& S, const float* wavelet,
+                         int n, int* err, cudaStream_t st);
+}  // namespace fused
+
 // History buffer of the reverse pass: nslot slots of 3 fields, slot s field c
 // at hist + (3 s + c) * fstride, pitched like the wavefields; and its 8 FP32
 // gradient accumulators, accumulator q at acc + q * fstride.

@@ -80,7 +80,10 @@ struct ews_sim {
     // and in use; plans of the other shapes, created on first use
     int tile_req = EWS_TILE_AUTO;
     int tile_used = EWS_TILE_32X8;
-    void* tplan[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* tplan[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // second set of wavefields of the fused step (9 * fstride floats, laid
+    // out like `fields`), held with its plan
+    float* fields2 = nullptr;
     cudaStream_t stream = nullptr;
     // launch accounting and optional per-launch event timing
     long long launches[EWS_NKERNEL] = {};
@@ -118,6 +121,11 @@ struct ews_sim {
     DevFields F() const {
         DevFields f;
         for (int q = 0; q < NFIELD; ++q) f.f[q] = (float*)field(q);
+        return f;
+    }
+    DevFields F2() const {
+        DevFields f;
+        for (int q = 0; q < NFIELD; ++q) f.f[q] = fields2 + (size_t)fslot(q) * fstride;
         return f;
     }
     bool wide() const { return opt.storage == EWS_STORAGE_F32; }

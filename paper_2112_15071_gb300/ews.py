@@ -28,9 +28,9 @@ EWS_STORAGE_F32, EWS_STORAGE_BF16, EWS_STORAGE_F16 = 0, 1, 2
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 EWS_SOURCE_MOMENT, EWS_SOURCE_FORCE = 0, 1
 EWS_KERNEL_VELOCITY, EWS_KERNEL_STRESS, EWS_KERNEL_INJECT, EWS_KERNEL_RECORD = 0, 1, 2, 3
-EWS_KERNEL_POINTS = 4
+EWS_KERNEL_POINTS, EWS_KERNEL_STEP = 4, 5
 EWS_NKERNEL = 8
-KERNEL_NAMES = ("velocity", "stress", "inject", "record", "points")
+KERNEL_NAMES = ("velocity", "stress", "inject", "record", "points", "step")
 BOUNDARY = {"none": 0, "sponge": 1, "cpml": 2}
 SOURCE = {"moment": 0, "force": 1}
 FIELDS = ("vx", "vy", "vz", "sxx", "syy", "szz", "sxy", "sxz", "syz")
@@ -77,9 +77,9 @@ class ews_tuned_tile(C.Structure):
 
 
 EWS_BATCH_PERSISTENT, EWS_BATCH_SEQUENTIAL = 0, 1
-EWS_TILE_AUTO, EWS_TILE_32X8, EWS_TILE_32X4, EWS_TILE_32X16 = 0, 1, 2, 3
+EWS_TILE_AUTO, EWS_TILE_32X8, EWS_TILE_32X4, EWS_TILE_32X16, EWS_TILE_FUSED = 0, 1, 2, 3, 4
 TILE = {"auto": EWS_TILE_AUTO, "32x8": EWS_TILE_32X8, "32x4": EWS_TILE_32X4,
-        "32x16": EWS_TILE_32X16}
+        "32x16": EWS_TILE_32X16, "fused": EWS_TILE_FUSED}
 
 _lock = threading.Lock()
 _lib = None

@@ -56,11 +56,13 @@ def oracle_centres(orc, p, st, cells):
     return out
 
 
-def gpu_step(ews, p, st, storage):
+def gpu_step(ews, p, st, storage, shape=None):
     """One step of the scheme (no source, no receivers) on the full grid."""
     import torch
     sim = ews.Simulation(p.nx, p.ny, p.nz, p.spacing, boundary=p.boundary, width=p.width,
                          storage=storage)
+    if shape:
+        sim.set_tile_shape(shape)
     sim.set_model_vel(p.vp, p.vs, p.rho)
     sim.set_state(st)
     sim.advance(0, 1, p.dt, None, 1)
@@ -79,6 +81,23 @@ def test_fp32_step_at_full_size(big, orc):
     g = got[:, cells[:, 0], cells[:, 1], cells[:, 2]].double().cpu().numpy().T
     err = np.abs(g - want) / scale
     assert err.max() <= 1e-5, err.max(axis=0)
+
+
+def test_fused_step_at_full_size(big, orc):
+    """The fused step (both passes in one launch, one z-chunk per tile at
+    this size, the state copied back after the odd step): the sampled cells
+    against the oracle, and every element against the two-pass step."""
+    ews, p, st, cells = big
+    got = gpu_step(ews, p, st, "f32", shape="fused")
+    want = oracle_centres(orc, p, st, cells)
+    scale = st.abs().amax(dim=(1, 2, 3)).double().cpu().numpy()
+    g = got[:, cells[:, 0], cells[:, 1], cells[:, 2]].double().cpu().numpy().T
+    err = np.abs(g - want) / scale
+    assert err.max() <= 1e-5, err.max(axis=0)
+    ref = gpu_step(ews, p, st, "f32", shape="32x8")
+    d = ((got - ref).abs().amax(dim=(1, 2, 3)) / ref.abs().amax(dim=(1, 2, 3))).cpu().numpy()
+    del got, ref
+    assert d.max() <= 1e-6, d
 
 
 def test_bf16_step_at_full_size(big, orc):

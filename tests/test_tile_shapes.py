@@ -80,7 +80,8 @@ def test_tuner_fills_the_table_without_changing_results(ews):
     sim = ews.simulation_for(p)                          # automatic shape
     got = sim.run(p.nt, p.dt)
     tuned = ews.ews_tile_tuned(g, "sponge", "f32")
-    assert tuned in (ews.EWS_TILE_32X8, ews.EWS_TILE_32X4, ews.EWS_TILE_32X16)
+    assert tuned in (ews.EWS_TILE_32X8, ews.EWS_TILE_32X4, ews.EWS_TILE_32X16,
+                     ews.EWS_TILE_FUSED)
     assert ews.ews_get_tile_shape(sim.handle) == tuned
     want, _ = run(ews, p, "32x8")
     assert rel(got, want) <= 1e-6

@@ -50,7 +50,21 @@ def test_import_export_and_lookup(table):
     assert len(ews.ews_tile_tuning_export()) == 3
 
 
+def test_fused_entries(table):
+    """The fused step is a valid entry for FP32 storage without C-PML only."""
+    ok = {"nx": 96, "ny": 96, "nz": 64, "boundary": "sponge", "storage": "f32", "shape": "fused"}
+    ews.ews_tile_tuning_import([ok])
+    g = ews.ews_grid(96, 96, 64, 20.0, 20.0, 20.0)
+    assert ews.ews_tile_tuned(g, "sponge", "f32") == ews.EWS_TILE_FUSED
+    assert ews.ews_tile_tuning_export() == [ok]
+    for bad in (dict(ok, boundary="cpml"), dict(ok, storage="bf16"), dict(ok, storage="f16")):
+        with pytest.raises(ews.EwsError):
+            ews.ews_tile_tuning_import([bad])
+    assert ews.ews_tile_tuning_export() == [ok]
+
+
 @pytest.mark.parametrize("bad", [dict(ENTRIES[0], shape=0), dict(ENTRIES[0], shape=4),
+                                 dict(ENTRIES[0], shape=5),
                                  dict(ENTRIES[0], nx=3), dict(ENTRIES[0], boundary=3),
                                  dict(ENTRIES[0], storage=5)])
 def test_an_invalid_entry_imports_nothing(table, bad):
