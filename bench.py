@@ -566,6 +566,7 @@ def storage_report(args, local, with_oracle: bool):
             b.record(stream)
             torch.cuda.synchronize()
             msf = a.elapsed_time(b)
+            sim.profile(reset=True)
             sim.set_profiling(True)
             sim.run(nt, prob.dt, seis)
             torch.cuda.synchronize()
