@@ -491,12 +491,9 @@ cudaError_t fused_plan_create(const DevGrid& g, const DevFields& A, const DevFie
     p->ntx = (g.nx + TX - 1) / TX;
     p->nty = (g.ny + TY - 1) / TY;
     const long long ntile = (long long)p->ntx * p->nty;
-    long long nchunk = ((long long)sms * occ * EWS_WAVES) / ntile;
-    if (nchunk > g.nz / 16) nchunk = g.nz / 16;   // the 4 halo planes of a chunk stay a small share
-    if (nchunk < 1) nchunk = 1;
-    p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
-    nchunk = (g.nz + p->zchunk - 1) / p->zchunk;
-    p->grid = (int)(ntile * nchunk);
+    // a chunk loads 4 planes beyond its own on each side
+    p->zchunk = chunk_planes(ntile, (long long)sms * occ, g.nz, 16, 4);
+    p->grid = (int)(ntile * ((g.nz + p->zchunk - 1) / p->zchunk));
     *out = p;
     return cudaSuccess;
 }

@@ -40,6 +40,7 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <new>
 #include <type_traits>
 
@@ -73,9 +74,6 @@ namespace {
 #endif
 #ifndef EWS_ROWS
 #define EWS_ROWS 1
-#endif
-#ifndef EWS_WAVES
-#define EWS_WAVES 4            // waves of (tile, z-chunk) CTAs per pass
 #endif
 constexpr int TX = 32, TY = EWS_TILE_Y;
 constexpr int HY = TY + 4;                        // halo rows: y0-2 .. y0+TY+1
@@ -1426,6 +1424,23 @@ cudaError_t occupancy(int* occ) {
     return e;
 }
 
+// CTAs per SM of the reverse velocity pass (0 where it does not exist).
+template <typename T>
+cudaError_t occupancy_grad(int kind, int* occ) {
+    *occ = 0;
+#if EWS_FULL
+    if constexpr (std::is_same<T, float>::value) {
+        if (kind == BND_SPONGE)
+            return prepare(k_velocity<BND_SPONGE, T, M_GRAD>, smem_v<BND_SPONGE, T, M_GRAD>(), occ);
+        if (kind == BND_NONE)
+            return prepare(k_velocity<BND_NONE, T, M_GRAD>, smem_v<BND_NONE, T, M_GRAD>(), occ);
+    }
+#else
+    (void)kind;
+#endif
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t occupancy_for(int kind, int* occ) {
     switch (kind) {
@@ -1490,9 +1505,35 @@ struct StencilPlan {
     int grid = 0;
     int ntx = 0, nty = 0;
     int zchunk = 0;
+    // the reverse velocity pass with the gradient products (fewer CTAs per
+    // SM) has its own z-chunks
+    int grid_grad = 0, zchunk_grad = 0;
 };
 
 namespace {
+
+// Planes per z-chunk of a pass over ntile tile columns with `slots` CTAs
+// resident at once: the chunk count n (chunks of at least min_planes
+// planes) that minimises the modelled pass time, the waves of (tile, chunk)
+// CTAs times the planes each CTA marches through, ceil(ntile n / slots) x
+// (nz / n + halo) with `halo` the planes a chunk loads beyond its own on
+// each side; ties go to more chunks.  Measured against the earlier rule of
+// about four waves (GB300, Gcell/s): 192^3 sponge 48.4 vs 44.5, 192^3 C-PML
+// 35.4 vs 33.8, 128^3 sponge 50.5 vs 39.4, 1024 x 1024 x 512 BF16 (32 x 16
+// tiles) 78.9 vs 75.9, 256^3 C-PML unchanged (7 chunks either way).
+int chunk_planes(long long ntile, long long slots, int nz, int min_planes, int halo) {
+    long long best_n = 1, best_cost = -1;
+    for (long long n = 1; n <= std::max(1, nz / min_planes); ++n) {
+        const long long zc = (nz + n - 1) / n;
+        const long long nn = (nz + zc - 1) / zc;               // chunks of zc planes
+        const long long cost = ((ntile * nn + slots - 1) / slots) * (zc + halo);
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best_n = n;
+        }
+    }
+    return (int)((nz + best_n - 1) / best_n);
+}
 
 cudaError_t plan_build(StencilPlan* p, const DevGrid& g, const DevFields& F, const DevMedium& M,
                        const DevBoundary& B, int storage) {
@@ -1521,21 +1562,18 @@ cudaError_t plan_build(StencilPlan* p, const DevGrid& g, const DevFields& F, con
     // Launch geometry: every tile column is cut into the same z-chunks and
     // chunk c of all tiles is resident at once, so neighbouring tiles march
     // through z together and the halo planes one CTA loads are still in L2
-    // when its neighbours load them.  Use as many chunks as a few waves of
-    // the resident slots allow (at least 8 planes each).  4 waves: on
-    // 256^3 C-PML, 3 / 4 / 6 / 8 / 12 waves gave 38.1 / 39.6 / 38.6 / 38.6 /
-    // 37.7 Gcell/s; without C-PML 4 waves were 4 % faster than 8; 16-bit
-    // storage (4 CTAs per SM) 8 waves 7 % slower than 4.
+    // when its neighbours load them.
     p->ntx = (g.nx + TX - 1) / TX;
     p->nty = (g.ny + TY - 1) / TY;
     const long long ntile = (long long)p->ntx * p->nty;
-    const long long slots = (long long)sms * occ;
-    long long nchunk = (slots * EWS_WAVES) / ntile;
-    if (nchunk > g.nz / 8) nchunk = g.nz / 8;
-    if (nchunk < 1) nchunk = 1;
-    p->zchunk = (int)((g.nz + nchunk - 1) / nchunk);
-    nchunk = (g.nz + p->zchunk - 1) / p->zchunk;
-    p->grid = (int)(ntile * nchunk);
+    p->zchunk = chunk_planes(ntile, (long long)sms * occ, g.nz, 8, 2);
+    p->grid = (int)(ntile * ((g.nz + p->zchunk - 1) / p->zchunk));
+    int occ_grad = 0;
+    if (storage == EWS_STORAGE_F32 && (e = occupancy_grad<float>(B.kind, &occ_grad)) != cudaSuccess)
+        return e;
+    p->zchunk_grad = occ_grad > 0 ? chunk_planes(ntile, (long long)sms * occ_grad, g.nz, 8, 2)
+                                  : p->zchunk;
+    p->grid_grad = (int)(ntile * ((g.nz + p->zchunk_grad - 1) / p->zchunk_grad));
     return cudaSuccess;
 }
 
@@ -1684,9 +1722,12 @@ cudaError_t launch_velocity_grad(const StencilPlan* sp, const DevGrid& g, const 
     if (sp->storage != EWS_STORAGE_F32 || sp->kind == BND_CPML || !sp->has_hist)
         return cudaErrorInvalidValue;
     const float one[NFIELD] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
-    PassParams P = pass_params(sp, g, F, B, dto, one, err);
+    StencilPlan q = *sp;                 // the reverse pass's own z-chunks
+    q.zchunk = sp->zchunk_grad;
+    q.grid = sp->grid_grad;
+    PassParams P = pass_params(&q, g, F, B, dto, one, err);
     P.X = X;
-    launch_v<float, M_GRAD>(sp, P, st);
+    launch_v<float, M_GRAD>(&q, P, st);
     return cudaGetLastError();
 }
 
