@@ -721,7 +721,8 @@ def paper_sweep(args, local):
         ms = a.elapsed_time(b)
         g = p.ncell * p.nt / (ms / 1e3) / 1e9
         rows.append({"level": lv, "grid": [p.nx, p.ny, p.nz], "ms_per_step": round(ms / p.nt, 4),
-                     "gcells": round(g, 3), "paper_gl_mcells": PAPER_GPU_MCELLS[lv],
+                     "gcells": round(g, 3), "tile_shape": sim.tile_shape,
+                     "paper_gl_mcells": PAPER_GPU_MCELLS[lv],
                      "x_paper": round(g * 1e3 / PAPER_GPU_MCELLS[lv], 1)})
         sim.close()
     return {"workload": "paper level table (Sec. 3.2.1): grids, spacings and dt as printed, 1D "
