@@ -788,6 +788,9 @@ constexpr int var_blocks() {
     return MODE == M_GRAD ? 2
            : (FS & VAR_COARSE) && blocks_for<T>(smem_v<BND, T, MODE>()) > 3
                ? 3
+           : (BND != BND_CPML && sizeof(T) == 4 && FS == ZS_NONE &&
+              (227 * 1024) / (int)(smem_v<BND, T, MODE>() + 1024) >= 4)
+               ? 4
                : blocks_for<T>(smem_v<BND, T, MODE>());
 }
 template <int BND, typename T, int FS>
