@@ -466,10 +466,10 @@ ews_status ews_fwi_iteration(int nshots, ews_batch_shot* shots, float* lam, floa
  * choice serves forward and gradient shots of that grid) and keeps it for
  * the life of the process, one entry per grid size, boundary kind and
  * surface form (shots with a free surface run other kernel forms).  A
- * batch of several forward shots then also times its first steps with
+ * batch of several shots then also times the first forward steps with
  * longer z-chunks (64 and 128 planes, whole tile columns) against the
- * table's values and keeps the fastest, cached per batch composition (not
- * part of the table; cleared with it).  The table can be exported and imported, so
+ * table's values and keeps the fastest for all its launches, cached per
+ * batch composition (not part of the table; cleared with it).  The table can be exported and imported, so
  * that a tuning persists across processes (the Python binding stores it
  * as JSON); entries are specific to the GPU they were timed on.  All four
  * calls touch host memory only. */

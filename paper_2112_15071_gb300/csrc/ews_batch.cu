@@ -400,7 +400,9 @@ ews_status tune_zchunk(ews_sim* s, const ews_batch_shot& in, int bnd, int exec, 
 // with the table, 42.4 with 64-plane chunks, 43.2 with 128-plane chunks.
 // So such a batch times its first steps with each candidate (the table;
 // 64 and 128 planes; whole tile columns) and keeps the fastest; the choice
-// is cached per batch composition.
+// is cached per batch composition.  Gradient batches take the choice of
+// their forward steps for every launch (48 gradient shots: 24.4 s with the
+// table, 23.2 s with the choice).
 constexpr int kBatchChunks[] = {0, 64, 128, 1 << 30};            // 0: the table
 std::map<std::vector<std::tuple<int, int, int, int, int>>, int> g_choice;   // under g_tune_mu
 
@@ -496,7 +498,7 @@ ews_status batch_persistent(int nshots, ews_batch_shot* shots, const ews_batch_o
     }
     const int lean = any_fs ? BX_LEAN_FS : BX_LEAN, rev = any_fs ? BX_GRAD_FS : BX_GRAD;
     int choice = 0;                            // the per-size table
-    if (o.zchunk == 0 && !grad && nshots > 1) {
+    if (o.zchunk == 0 && nshots > 1) {
         ews_status r = choose_batch_chunks(shots, nshots, zcs, bnd, lean, o.ctas_per_sm, d_err, st,
                                            &choice);
         if (r != EWS_OK) return r;
