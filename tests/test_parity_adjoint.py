@@ -53,6 +53,25 @@ def test_adjoint_matches_oracle(ews, orc, boundary, kind, dims):
             assert rel(got[q], want[q]) <= TOL_ORACLE, (budget, q, rel(got[q], want[q]))
 
 
+def test_adjoint_with_the_reverse_pass_own_chunks(ews, orc):
+    """A grid on which the reverse velocity pass (2 CTAs per SM, its own
+    z-chunk count) and the forward passes (3 per SM) are cut into different
+    z-chunks, both with a ragged last chunk: the gradient still matches the
+    FP64 adjoint, with the history resident and recomputed per segment."""
+    p = synth.small_problem(96, 88, 96, nt=60, boundary="sponge", width=6, kind="moment", nrec=6,
+                            seed=31)
+    A = np.random.default_rng(5).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
+    want = orc.gradient(p, A.astype(np.float64), ckpt_every=20,
+                        medium=[a.astype(np.float64) for a in p.lame()])
+    sim = ews.simulation_for(p)
+    sim.set_model_lame(*p.lame())
+    for budget in (-1, 0):
+        sim.set_history_budget(budget)
+        got = sim.adjoint(p.nt, p.dt, A, ckpt_every=20)
+        for q in range(3):
+            assert rel(got[q], want[q]) <= TOL_ORACLE, (budget, q, rel(got[q], want[q]))
+
+
 def test_checkpoint_interval_invariance(ews):
     p = problem((40, 36, 28), "sponge", "moment")
     A = np.random.default_rng(4).standard_normal((3, p.rec_pos.shape[0], p.nt)).astype(np.float32)
